@@ -1,0 +1,345 @@
+"""FP64 CPU oracle of the LLOID hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports this module:
+only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may use it.  It shares no code with
+the CUDA path; the only common dependency is the seeded input generator
+``workloads`` (templates, slice plans, noise, injections).
+
+What it computes (every array is float64, every step written out plainly):
+
+(A) ``brute_force_snr``  -- the matched filter of Eq. 1 in discrete form,
+    z_i[k] = sum_j hbar_i[j] d[k - j], hbar_i = h_c + i h_s, d[k < 0] = 0.
+(B) ``lloid_snr``        -- the LLOID approximation of (A), step by step in the
+    paper's order (Section II.C):
+      1. downsample the strain to each slice rate with the sinc-windowed-sinc
+         kernel of Eq. 4 (c = f N_down);
+      2. filter each slice with its SVD basis (Eq. 5), reading the segment
+         picked by pre-synchronisation (Eq. 9);
+      3. reconstruct each slice's SNR through sigma * v (Eq. 6);
+      4. from the lowest rate up, upsample with the polyphase form of
+         Eq. 7-8 (c = f N_up) and add the next rate's slices (Eq. 9 recursion).
+(C) ``triggers``         -- per window and template, the max of |z| above the
+    threshold, its time and phase, and the per-bank maximum (Section II.D.1).
+(D) ``svd_bank``         -- per-slice SVD of the real/imaginary-stacked
+    templates keeping 99.99 % of the slice energy (Eq. 3).
+
+Readings of points the paper leaves open (each is also listed in the design doc):
+* discrete unit-variance form of Eq. 1 (no factor 2): E|z|^2 = 2 in white
+  noise and an injection at amplitude A gives |z| = A;
+* downsampling is zero-phase (centred) with unit DC gain, w = g / sum(g), and
+  the decimated stream is scaled by sqrt(D) so it keeps unit variance; the
+  slice matrix carries the other sqrt(D): A^s[row][m] = sqrt(D) h[J_s + D m];
+* Eq. 5 is written in before-merger indexing:
+  Y^s_l[q] = sum_m u^s_l[m] d_s[q - J_s / D_s - m];
+* Eq. 8 is read as centred for every phase, Up[p] = sum_t z_phi[t]
+  x[floor(p / F) + N_up - t] (the printed causal form differs by the N_up
+  delay that pre-synchronisation absorbs); the upsampling kernel is not
+  renormalised (g[c] = 1 makes it interpolating);
+* the ladder is the bank's distinct slice rates plus f0;
+* triggers: windows [max(0, wW - overlap), (w + 1) W), "exceeds" is strict,
+  ties go to the earliest sample, the bank maximum to the lowest template.
+
+Parity status: (A), Eq. 4, Eq. 7-8, the reconstruction and the trigger rules
+are pinned by closed forms, special cases and brute force in
+``tests/test_oracle_pins.py``.  (B) as an approximation of (A) has no exact
+pin in the paper: it is held to 1 % relative SNR at injections (parity
+unpinned beyond that tolerance).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import List, Sequence
+
+import numpy as np
+
+N_DOWN = 32      # half-length of the downsampling kernel at the target rate (Section II.C.2)
+N_UP = 8         # half-length of the upsampling kernel (Section II.C.2)
+SNR_THRESHOLD = 4.0   # trigger threshold on |z| (Section II.D.1)
+
+
+# ----------------------------------------------------------------------------
+# Eq. 4: sinc-windowed sinc kernel
+# ----------------------------------------------------------------------------
+
+def sinc_kernel(f: int, c: int) -> np.ndarray:
+    """g[k], k = 0..2c: sinc of zero spacing f times a sinc window of half
+    length c, with g[c] = 1 (Eq. 4)."""
+    g = np.empty(2 * c + 1, dtype=np.float64)
+    for k in range(2 * c + 1):
+        if k == c:
+            g[k] = 1.0
+        else:
+            a = math.pi * (k - c) / f
+            b = math.pi * (k - c) / c
+            g[k] = (math.sin(a) / a) * (math.sin(b) / b)
+    return g
+
+
+# ----------------------------------------------------------------------------
+# A stream is an array plus the index of its first sample.
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Stream:
+    """Samples x[..., i] of index start + i (the last axis is time)."""
+    x: np.ndarray
+    start: int
+
+    @property
+    def stop(self) -> int:
+        return self.start + self.x.shape[-1]
+
+    def window(self, lo: int, hi: int) -> np.ndarray:
+        """Samples lo..hi-1, zero outside the stored range."""
+        out = np.zeros(self.x.shape[:-1] + (hi - lo,), dtype=np.float64)
+        a, b = max(lo, self.start), min(hi, self.stop)
+        if b > a:
+            out[..., a - lo:b - lo] = self.x[..., a - self.start:b - self.start]
+        return out
+
+
+# ----------------------------------------------------------------------------
+# (A) brute force, Eq. 1
+# ----------------------------------------------------------------------------
+
+def brute_force_snr(d: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """z_row[k] = sum_{j=0}^{N-1} rows[row][j] d[k - j] for k in [0, len(d)),
+    with d[k < 0] = 0.  ``rows`` is [2M, N] in before-merger order.  Returns the
+    real rows [2M, len(d)]; z_i = out[2i] + 1j out[2i+1]."""
+    d = np.asarray(d, dtype=np.float64)
+    T = d.size
+    out = np.empty((rows.shape[0], T))
+    for r in range(rows.shape[0]):
+        out[r] = np.convolve(d, rows[r])[:T]
+    return out
+
+
+def brute_force_snr_fft(d: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """Same as ``brute_force_snr`` through zero-padded FFTs (independent route)."""
+    d = np.asarray(d, dtype=np.float64)
+    T, N = d.size, rows.shape[1]
+    n = 1 << int(math.ceil(math.log2(T + N)))
+    D = np.fft.rfft(d, n)
+    H = np.fft.rfft(rows, n, axis=1)
+    return np.fft.irfft(H * D[None, :], n, axis=1)[:, :T]
+
+
+# ----------------------------------------------------------------------------
+# (D) SVD bank, Eq. 3
+# ----------------------------------------------------------------------------
+
+@dataclass
+class OracleSlice:
+    rate: int
+    j_start: int
+    bases: np.ndarray     # [L, N] orthonormal u_l
+    coeffs: np.ndarray    # [2M, L] = v_il sigma_l
+
+
+def slice_matrix(bank, rate: int, j_start: int, n_taps: int) -> np.ndarray:
+    """A^s[row][m] = sqrt(D) h_row[J_s + D m], m < N_s (the slice, decimated)."""
+    D = bank.f0 // rate
+    j = j_start + D * np.arange(n_taps)
+    return math.sqrt(D) * bank.rows(j)
+
+
+def svd_bank(bank, plan, energy: float = 0.9999, full_rank: bool = False) -> List[OracleSlice]:
+    """Per slice: A = U S V^T, keep the leading L bases holding ``energy`` of
+    sum S^2 (all of them with ``full_rank``); bases u_l = V^T[l], coefficients
+    v_il sigma_l = U[i, l] S[l] (Eq. 3)."""
+    out = []
+    for r, J, N in zip(plan.rate, plan.j_start, plan.n_taps):
+        A = slice_matrix(bank, r, J, N)
+        U, S, Vt = np.linalg.svd(A, full_matrices=False)
+        if full_rank:
+            L = S.size
+        else:
+            cum = np.cumsum(S ** 2)
+            L = int(np.searchsorted(cum, energy * cum[-1]) + 1)
+            L = min(L, S.size)
+        out.append(OracleSlice(r, J, Vt[:L].copy(), U[:, :L] * S[None, :L]))
+    return out
+
+
+def identity_bank(bank, plan) -> List[OracleSlice]:
+    """No compression: the bases are the slice rows themselves and the
+    coefficients the identity (the multirate path without SVD)."""
+    out = []
+    for r, J, N in zip(plan.rate, plan.j_start, plan.n_taps):
+        A = slice_matrix(bank, r, J, N)
+        out.append(OracleSlice(r, J, A.copy(), np.eye(A.shape[0])))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# (B) LLOID, Eq. 4-9
+# ----------------------------------------------------------------------------
+
+def downsample(d: Stream, D: int, q_lo: int, q_hi: int, n_down: int = N_DOWN) -> Stream:
+    """d_s[q] = sqrt(D) sum_{k=0}^{2c} w[k] d[D q + c - k], w = g / sum(g),
+    g from Eq. 4 with f = D and c = D N_down, for q in [q_lo, q_hi)."""
+    if D == 1:
+        return Stream(d.window(q_lo, q_hi), q_lo)
+    c = D * n_down
+    g = sinc_kernel(D, c)
+    w = g / g.sum()
+    lo = D * q_lo + c - 2 * c
+    hi = D * (q_hi - 1) + c + 1
+    seg = d.window(lo, hi)                  # seg[i] = d[lo + i]
+    conv = np.convolve(seg, w)              # conv[i] = sum_k w[k] seg[i - k]
+    q = np.arange(q_lo, q_hi)
+    return Stream(math.sqrt(D) * conv[D * q + c - lo], q_lo)
+
+
+def polyphase_upsample(x: Stream, F: int, n_up: int = N_UP) -> Stream:
+    """Eq. 7-8 (centred reading): the kernel g (Eq. 4, f = F, c = F N_up) is
+    split into F sub-kernels z_j[k] = g[k F + j], k = 0..2c/F, and output p
+    takes Up[p] = sum_k z_{p mod F}[k] x[floor(p / F) + N_up - k]."""
+    if F == 1:
+        return Stream(x.x.copy(), x.start)
+    c = F * n_up
+    g = sinc_kernel(F, c)
+    K = 2 * c // F
+    sub = np.zeros((F, K + 1))
+    for j in range(F):
+        for k in range(K + 1):
+            if k * F + j <= 2 * c:
+                sub[j, k] = g[k * F + j]
+    p = np.arange(F * x.start, F * x.stop)
+    out = np.zeros(x.x.shape[:-1] + (p.size,))
+    base = p // F + n_up
+    phase = p % F
+    b0 = int(base.min())
+    for k in range(K + 1):
+        xs = x.window(b0 - k, int(base.max()) - k + 1)     # xs[..., i] = x[b0 - k + i]
+        out += sub[phase, k] * xs[..., base - b0]
+    return Stream(out, F * x.start)
+
+
+def zero_stuff_upsample(x: Stream, F: int, n_up: int = N_UP) -> Stream:
+    """Textbook interpolation: insert F-1 zeros between samples and convolve
+    with g centred on c, Up[p] = sum_k x[k] g[p - F k + c] (used as a pin)."""
+    if F == 1:
+        return Stream(x.x.copy(), x.start)
+    c = F * n_up
+    g = sinc_kernel(F, c)
+    n = F * x.x.size
+    stuffed = np.zeros(n)
+    stuffed[::F] = x.x
+    full = np.convolve(stuffed, g)           # full[i] = sum_m stuffed[m] g[i - m]
+    return Stream(full[c:c + n], F * x.start)   # 1-D input only
+
+
+def ladder_rates(slices: Sequence[OracleSlice], f0: int) -> List[int]:
+    """Distinct slice rates plus f0, ascending."""
+    return sorted(set(s.rate for s in slices) | {f0})
+
+
+def presync_ok(slices: Sequence[OracleSlice], f0: int, n_down: int = N_DOWN, n_up: int = N_UP) -> bool:
+    """Pre-synchronisation without added latency (Section II.C.3, Eq. 9):
+    J_s / f0 >= N_down / f_s + sum over ladder rates f_s <= f < f0 of N_up / f."""
+    lad = ladder_rates(slices, f0)
+    for s in slices:
+        if s.rate == f0:
+            if s.j_start < 0:
+                return False
+            continue
+        need = n_down * (f0 // s.rate) + sum(n_up * (f0 // f) for f in lad if s.rate <= f < f0)
+        if s.j_start < need:
+            return False
+    return True
+
+
+def lloid_snr(d: np.ndarray, slices: Sequence[OracleSlice], f0: int, n_down: int = N_DOWN,
+              n_up: int = N_UP, pad: int = 8192) -> np.ndarray:
+    """LLOID SNR rows [2M, len(d)] for strain d starting at sample 0 with zero
+    history (d[k < 0] = 0).  Every stream is evaluated on a range padded by
+    ``pad`` full-rate samples on both sides so that truncation never reaches
+    the returned samples."""
+    d = np.asarray(d, dtype=np.float64)
+    T = d.size
+    lad = ladder_rates(slices, f0)
+    grid = f0 // lad[0]
+    Tg = -(-T // grid) * grid           # whole samples at every rate; the zeros
+    full = Stream(np.concatenate([d, np.zeros(Tg - T)]), 0)   # appended lie in the future
+    pad = -(-pad // grid) * grid
+    n_rows = slices[0].coeffs.shape[0]
+    # Per-rate sums S_r of the reconstructed slices (Eq. 5-6), on [lo_r, hi_r).
+    S = {}
+    for r in lad:
+        D = f0 // r
+        S[r] = Stream(np.zeros((n_rows, (Tg + 2 * pad) // D)), -pad // D)
+    for s in slices:
+        D = f0 // s.rate
+        off = s.j_start // D                      # pre-synchronisation offset (Eq. 9)
+        L, N = s.bases.shape
+        qa, qb = S[s.rate].start, S[s.rate].start + S[s.rate].x.shape[1]
+        ds = downsample(full, D, qa - off - N + 1, qb - off, n_down)
+        # Eq. 5: Y_l[q] = sum_m u_l[m] d_s[q - off - m]
+        Y = np.empty((L, qb - qa))
+        for l in range(L):
+            conv = np.convolve(ds.x, s.bases[l])   # conv[i] = sum_m u[m] ds.x[i - m]
+            # ds.x[i] is d_s[ds.start + i]; want index q - off  ->  i = q - off - ds.start
+            i = np.arange(qa, qb) - off - ds.start
+            Y[l] = conv[i]
+        # Eq. 6: reconstruction through sigma * v
+        S[s.rate].x += s.coeffs @ Y
+    # Eq. 9 recursion, lowest rate upward, with Eq. 7-8 upsampling.
+    acc = None
+    for r_lo, r_hi in zip([None] + lad[:-1], lad):
+        if acc is None:
+            acc = Stream(S[r_hi].x.copy(), S[r_hi].start)
+            continue
+        F = r_hi // r_lo
+        up = polyphase_upsample(acc, F, n_up)
+        tgt = S[r_hi]
+        acc = Stream(tgt.x + up.window(tgt.start, tgt.stop), tgt.start)
+    return acc.x[:, -acc.start:-acc.start + T]
+
+
+# ----------------------------------------------------------------------------
+# (C) triggers, Section II.D.1
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Trigger:
+    detector: int
+    bank: int
+    tmpl: int
+    window: int
+    sample: int
+    snr: float
+    phase: float
+    re: float
+    im: float
+    is_bank_max: bool
+
+
+def triggers(z_rows: np.ndarray, window: int, overlap: int = 0, threshold: float = SNR_THRESHOLD,
+             detector: int = 0, bank: int = 0, n_windows=None, t_offset: int = 0) -> List[Trigger]:
+    """For every complete window w, [max(0, wW - overlap), (w + 1) W), and
+    template i: k* = the first argmax of |z_i|^2; a trigger if |z_i[k*]| >
+    threshold.  The trigger of the template with the largest |z|^2 in the
+    bank (lowest template index on ties) is flagged ``is_bank_max``."""
+    re, im = z_rows[0::2], z_rows[1::2]
+    p = re * re + im * im
+    T = z_rows.shape[1]
+    nw = T // window if n_windows is None else n_windows
+    out = []
+    for w in range(nw):
+        a = max(0, w * window - overlap) - t_offset
+        b = (w + 1) * window - t_offset
+        if a < 0 or b > T:
+            continue
+        seg = p[:, a:b]
+        k = np.argmax(seg, axis=1)
+        best = seg[np.arange(seg.shape[0]), k]
+        top = int(np.argmax(best))
+        for i in range(seg.shape[0]):
+            if math.sqrt(best[i]) > threshold:
+                kk = a + int(k[i])
+                out.append(Trigger(detector, bank, i, w, kk + t_offset, math.sqrt(best[i]),
+                                   math.atan2(im[i, kk], re[i, kk]), re[i, kk], im[i, kk], i == top))
+    return out

@@ -1,0 +1,304 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms of Eq. 4, the textbook definition behind Eq. 7-8, a brute-force loop
+that is the definition of Eq. 1, two independent routes (direct sum and FFT),
+special cases where LLOID must reduce to the matched filter exactly, and
+invariants (linearity, shift equivariance on the multirate grid, causality
+under pre-synchronisation).  They are chosen so that a dropped term, a wrong
+sign or offset, a transposed operand or a missing sqrt(D) fails one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lloid_oracle as O
+
+F0 = 2048
+
+
+# --------------------------------------------------------------------------
+# constants the paper prints
+# --------------------------------------------------------------------------
+
+def test_paper_constants(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "paper_constants.json")))
+    assert O.N_DOWN == g["n_down"]["value"]
+    assert O.N_UP == g["n_up"]["value"]
+    assert O.SNR_THRESHOLD == g["snr_threshold"]["value"]
+    # Eq. 7: each polyphase sub-kernel has 2c/f + 1 = 2 N_up + 1 taps
+    assert 2 * O.N_UP + 1 == g["upsample_subkernel_len"]["value"]
+
+
+# --------------------------------------------------------------------------
+# Eq. 4 closed form
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("f,n_half", [(2, 32), (4, 32), (8, 32), (16, 32), (2, 8), (8, 8), (64, 8)])
+def test_sinc_kernel_closed_form(f, n_half):
+    c = f * n_half
+    g = O.sinc_kernel(f, c)
+    assert g.size == 2 * c + 1
+    assert g[c] == 1.0
+    # zeros of the sinc at every multiple of f away from the centre
+    for n in range(1, c // f + 1):
+        assert abs(g[c + n * f]) < 1e-15 and abs(g[c - n * f]) < 1e-15
+    # zero-phase (symmetric) and the sinc window vanishes at both ends
+    assert np.allclose(g, g[::-1], atol=0, rtol=0)
+    assert abs(g[0]) < 1e-15 and abs(g[-1]) < 1e-15
+    # one sample off a zero the kernel is the product of two sincs
+    k = c + 1
+    a, b = math.pi / f, math.pi / c
+    assert g[k] == pytest.approx(math.sin(a) / a * math.sin(b) / b, rel=1e-14)
+    # DC gain of a sinc with zero spacing f is f
+    assert g.sum() == pytest.approx(f, rel=2e-2)
+
+
+# --------------------------------------------------------------------------
+# Eq. 7-8 against zero-stuffing + convolution (textbook interpolation)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("F", [2, 4, 8, 16])
+def test_polyphase_equals_zero_stuff(F):
+    rng = np.random.default_rng(F)
+    x = O.Stream(rng.standard_normal(300), 0)
+    a = O.polyphase_upsample(x, F)
+    b = O.zero_stuff_upsample(x, F)
+    assert a.start == b.start == 0
+    assert np.max(np.abs(a.x - b.x)) < 1e-13
+    # interpolating: every F-th output is the input sample itself
+    assert np.max(np.abs(a.x[::F] - x.x)) < 1e-14
+
+
+def test_polyphase_2d_rows_match_1d():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((3, 50))
+    a = O.polyphase_upsample(O.Stream(X, -5), 4)
+    for r in range(3):
+        b = O.polyphase_upsample(O.Stream(X[r], -5), 4)
+        assert a.start == b.start == -20
+        assert np.max(np.abs(a.x[r] - b.x)) == 0.0
+
+
+# --------------------------------------------------------------------------
+# (A) brute force: the definition written as loops, and the FFT route
+# --------------------------------------------------------------------------
+
+def test_brute_force_is_the_definition():
+    rng = np.random.default_rng(11)
+    T, N = 40, 7
+    d = rng.standard_normal(T)
+    rows = rng.standard_normal((4, N))
+    z = O.brute_force_snr(d, rows)
+    for r in range(4):
+        for k in range(T):
+            s = 0.0
+            for j in range(N):
+                if k - j >= 0:
+                    s += rows[r, j] * d[k - j]
+            assert abs(z[r, k] - s) < 1e-12
+
+
+def test_brute_force_direct_equals_fft():
+    w = W.make_workload("tiny", n_seconds=6)
+    rows = w.banks[0].full()
+    d = w.strain(0).astype(np.float64)
+    a = O.brute_force_snr(d, rows)
+    b = O.brute_force_snr_fft(d, rows)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Injections and noise statistics (Eq. 1 normalisation)
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def bank64():
+    w = W.make_workload("bank64", n_seconds=16)
+    return w.banks[0], w.plans[0]
+
+
+@pytest.mark.parametrize("phase", [0.0, 1.1])
+def test_injection_recovers_amplitude(bank64, phase):
+    bank, plan = bank64
+    T = 16 * F0
+    A, i, k0 = 12.0, 5, 12 * F0 + 3
+    d = np.zeros(T)
+    rows = bank.full()
+    for j in range(rows.shape[1]):
+        d[k0 - j] += A * (math.cos(phase) * rows[2 * i, j] + math.sin(phase) * rows[2 * i + 1, j])
+    za = O.brute_force_snr_fft(d, rows)
+    cs = float(rows[2 * i] @ rows[2 * i + 1])          # <h_c, h_s>
+    assert za[2 * i, k0] == pytest.approx(A * (math.cos(phase) + math.sin(phase) * cs), abs=1e-10)
+    assert za[2 * i + 1, k0] == pytest.approx(A * (math.cos(phase) * cs + math.sin(phase)), abs=1e-10)
+    # LLOID recovers the same SNR to 1 % (the paper's <1 % agreement level)
+    zb = O.lloid_snr(d, O.svd_bank(bank, plan), F0)
+    snr_b = abs(zb[2 * i, k0] + 1j * zb[2 * i + 1, k0])
+    assert abs(snr_b - A) < 0.01 * A
+    assert abs(math.atan2(zb[2 * i + 1, k0], zb[2 * i, k0]) - phase) < 0.01
+
+
+def test_noise_expectation_two():
+    """E|z|^2 = ||h_c||^2 + ||h_s||^2 = 2 for unit white noise (Eq. 1)."""
+    w = W.make_workload("tiny", n_seconds=40)
+    rows = w.banks[0].full()
+    d = W.white_noise(40 * F0, 12345).astype(np.float64)
+    za = O.brute_force_snr_fft(d, rows)[:, 4 * F0:]
+    p = za[0::2] ** 2 + za[1::2] ** 2
+    # batch means over 2 s batches (longer than any template) for the error bar
+    nb = p.shape[1] // (2 * F0)
+    means = p[:, :nb * 2 * F0].reshape(p.shape[0], nb, 2 * F0).mean(axis=(0, 2))
+    m, se = means.mean(), means.std(ddof=1) / math.sqrt(nb)
+    assert abs(m - 2.0) < 5 * se
+    zb = O.lloid_snr(d, O.svd_bank(w.banks[0], w.plans[0]), F0)[:, 4 * F0:]
+    pb = zb[0::2] ** 2 + zb[1::2] ** 2
+    assert abs(pb.mean() / p.mean() - 1.0) < 0.02
+
+
+def test_downsampled_noise_has_unit_variance():
+    d = O.Stream(W.white_noise(64 * F0, 4).astype(np.float64), 0)
+    for D in (2, 8, 16):
+        ds = O.downsample(d, D, 64, 64 * F0 // D - 64)
+        assert abs(ds.x.var() - 1.0) < 0.03
+
+
+def test_sinusoid_down_then_up():
+    """An in-band sinusoid survives downsampling + upsampling with no delay."""
+    f0 = F0
+    t = np.arange(16 * f0)
+    for D in (2, 8, 16):
+        r = f0 // D
+        x = np.cos(2 * math.pi * 0.3 * r * t / f0 + 0.4)
+        ds = O.downsample(O.Stream(x, 0), D, 0, x.size // D)
+        up = O.polyphase_upsample(O.Stream(ds.x / math.sqrt(D), 0), D)
+        mid = slice(4 * f0, 12 * f0)
+        err = np.max(np.abs(up.x[mid] - x[mid]))
+        assert err < 2e-3, (D, err)
+
+
+# --------------------------------------------------------------------------
+# Special cases where LLOID must equal the matched filter
+# --------------------------------------------------------------------------
+
+def test_full_rank_single_rate_equals_brute_force():
+    """One slice at f0, D = 1, full-rank SVD: (B) == (A)."""
+    w = W.make_workload("tiny", n_seconds=8)
+    bank = w.banks[0]
+    plan = W.SlicePlan((F0,), (0,), (bank.n_samples,))
+    sl = O.svd_bank(bank, plan, full_rank=True)
+    d = w.strain(0).astype(np.float64)
+    zb = O.lloid_snr(d, sl, F0)
+    za = O.brute_force_snr_fft(d, bank.full())
+    assert np.max(np.abs(za - zb)) < 1e-10
+
+
+def test_full_rank_multirate_equals_no_svd(bank64):
+    """Full-rank SVD reproduces the per-template multirate path (no SVD)."""
+    bank, plan = bank64
+    d = W.white_noise(8 * F0, 77).astype(np.float64)
+    zs = O.lloid_snr(d, O.svd_bank(bank, plan, full_rank=True), F0)
+    zi = O.lloid_snr(d, O.identity_bank(bank, plan), F0)
+    assert np.max(np.abs(zs - zi)) < 1e-10
+
+
+def test_svd_bank_energy_and_orthonormality(bank64):
+    bank, plan = bank64
+    for s, (r, J, N) in zip(O.svd_bank(bank, plan), zip(plan.rate, plan.j_start, plan.n_taps)):
+        A = O.slice_matrix(bank, r, J, N)
+        L = s.bases.shape[0]
+        assert np.max(np.abs(s.bases @ s.bases.T - np.eye(L))) < 1e-12
+        Sv = np.linalg.svd(A, compute_uv=False)
+        tot = np.sum(Sv ** 2)
+        assert np.sum(Sv[:L] ** 2) >= 0.9999 * tot
+        assert np.sum(Sv[:L - 1] ** 2) < 0.9999 * tot
+        resid = A - s.coeffs @ s.bases
+        assert np.sum(resid ** 2) == pytest.approx(np.sum(Sv[L:] ** 2), rel=1e-6, abs=1e-20)
+
+
+# --------------------------------------------------------------------------
+# Invariants of (B)
+# --------------------------------------------------------------------------
+
+def test_linearity(bank64):
+    bank, plan = bank64
+    sl = O.svd_bank(bank, plan)
+    d1 = W.white_noise(6 * F0, 1).astype(np.float64)
+    d2 = W.white_noise(6 * F0, 2).astype(np.float64)
+    z = O.lloid_snr(2.5 * d1 - 0.75 * d2, sl, F0)
+    z12 = 2.5 * O.lloid_snr(d1, sl, F0) - 0.75 * O.lloid_snr(d2, sl, F0)
+    assert np.max(np.abs(z - z12)) < 1e-11
+
+
+def test_shift_equivariance_on_grid(bank64):
+    bank, plan = bank64
+    sl = O.svd_bank(bank, plan)
+    d = W.white_noise(6 * F0, 9).astype(np.float64)
+    Dmax = F0 // min(plan.rate)
+    for delta in (Dmax, 5 * Dmax):
+        z = O.lloid_snr(d, sl, F0)
+        zs = O.lloid_snr(np.concatenate([np.zeros(delta), d]), sl, F0)
+        assert np.max(np.abs(zs[:, delta:] - z)) < 1e-11
+    # off the multirate grid the output is only approximately shifted
+    zs = O.lloid_snr(np.concatenate([np.zeros(3), d]), sl, F0)
+    assert np.max(np.abs(zs[:, 3:] - z)) > 1e-6
+
+
+def test_presync_makes_output_causal(bank64):
+    """With pre-synchronisation (Eq. 9) z[k] depends on d[<= k] only."""
+    bank, plan = bank64
+    sl = O.svd_bank(bank, plan)
+    assert O.presync_ok(sl, F0)
+    d = W.white_noise(6 * F0, 21).astype(np.float64)
+    cut = 4 * F0 + 37
+    d2 = d.copy()
+    d2[cut:] = W.white_noise(d.size - cut, 22)
+    z1 = O.lloid_snr(d, sl, F0)
+    z2 = O.lloid_snr(d2, sl, F0)
+    assert np.max(np.abs(z1[:, :cut] - z2[:, :cut])) < 1e-12
+    assert np.max(np.abs(z1[:, cut:] - z2[:, cut:])) > 1e-3
+
+
+def test_presync_condition_values(bank64):
+    bank, plan = bank64
+    sl = O.svd_bank(bank, plan)
+    # 256 Hz slice: N_down / 256 + N_up / 256 seconds = 320 samples <= J = 2048
+    moved = [sl[0], O.OracleSlice(256, 320, sl[1].bases, sl[1].coeffs)]
+    assert O.presync_ok(moved, F0)
+    moved = [sl[0], O.OracleSlice(256, 312, sl[1].bases, sl[1].coeffs)]
+    assert not O.presync_ok(moved, F0)
+
+
+# --------------------------------------------------------------------------
+# (C) trigger rules on hand-built SNR series
+# --------------------------------------------------------------------------
+
+def test_triggers_hand_built():
+    W_ = 8
+    T = 3 * W_
+    z = np.zeros((6, T))                       # 3 templates
+    # template 0: |z| = 5 at k=2 and a tie at k=6 -> earliest (k=2); window 0
+    z[0, 2] = 5.0
+    z[1, 6] = 5.0
+    # template 1: |z| = 4 exactly at k=3 (not > 4), 4.5 in window 1 at k=12
+    z[2, 3] = 4.0
+    z[3, 12] = 4.5
+    # template 2: |z| = 6 in window 0 at k=7 (phase 90 deg), 4.5 in window 1 at k=9
+    z[5, 7] = 6.0
+    z[4, 9] = -4.5
+    tr = O.triggers(z, W_, threshold=4.0)
+    got = [(t.window, t.tmpl, t.sample, round(t.snr, 12), round(t.phase, 12), t.is_bank_max) for t in tr]
+    want = [
+        (0, 0, 2, 5.0, 0.0, False),
+        (0, 2, 7, 6.0, round(math.pi / 2, 12), True),
+        (1, 1, 12, 4.5, round(math.pi / 2, 12), True),     # ties with template 2: lowest index
+        (1, 2, 9, 4.5, round(math.pi, 12), False),
+    ]
+    assert got == want
+    # overlap: window 1 = [W - 2, 2W) also sees k = 6, 7
+    tr = O.triggers(z, W_, overlap=2, threshold=4.0)
+    w1 = [(t.tmpl, t.sample) for t in tr if t.window == 1]
+    assert w1 == [(0, 6), (1, 12), (2, 7)]
