@@ -1,0 +1,214 @@
+/*
+ * lloid.h -- C ABI of the B300 LLOID hot path.
+ *
+ * LLOID (the time-domain matched filter of SGNL, Section II.C of the paper)
+ * correlates whitened detector strain with a template bank that has been cut
+ * into time slices, each sampled at its own rate and compressed by an SVD
+ * (Eq. 3).  For every block of strain this library runs, on one GPU:
+ *
+ *   a0  ingest      block -> device ring (host or device source)
+ *   a1  downsample  to every power-of-two rate, sinc-windowed sinc kernel of
+ *                   Eq. 4 with c = D N_down, unit DC gain, scaled by sqrt(D)
+ *   a2  basis FIR   Y^s_l[q] = sum_m u^s_l[m] d_s[q - J_s/D_s - m]  (Eq. 5,
+ *                   read at the pre-synchronised offset of Eq. 9)
+ *   a3  recon       z_row = sum_s sum_l (sigma v)^s[row][l] Y^s_l  (Eq. 6)
+ *   a4  up + sum    polyphase upsampling ladder of Eq. 7-8 and the recursive
+ *                   sum of Eq. 9, to the full rate f0
+ *   a5  triggers    per window and template, max |z| above the threshold,
+ *                   its sample and phase; per bank the loudest template
+ *                   (Section II.D.1)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * * Time is the full-rate sample index since the stream started (sample 0);
+ *   the data before sample 0 are zero.  A template row is indexed by samples
+ *   before merger, so z[k] is the SNR of a merger at sample k.
+ * * Template i has two real rows: 2i (cosine / real part) and 2i+1 (sine /
+ *   imaginary part); z_i = z[2i] + i z[2i+1] (Section II.C, Eq. 1).
+ * * The downsampled stream at rate f0/D has unit variance for unit-variance
+ *   input: d_D[q] = sqrt(D) sum_k w[k] d[D q + c - k], w = g / sum(g) (g of
+ *   Eq. 4, zero phase).  A bank's bases are therefore built from
+ *   sqrt(D) h[J + D m] (the sqrt(D) pair restores the full-rate inner product).
+ * * Every call returns an lloid_status; no C++ exception crosses the ABI.
+ *   lloid_last_error() gives a one-line reason for the last failure.
+ * * The library copies everything it is given; the caller keeps ownership of
+ *   its buffers.  One context is used by one host thread at a time.
+ * * All GPU work of a context is ordered on one CUDA stream (the caller's, or
+ *   one the library creates).  Calls return once the work is enqueued, except
+ *   pull_triggers, snr_block and synchronize, which wait for it.
+ */
+#ifndef LLOID_H
+#define LLOID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LLOID_API __attribute__((visibility("default")))
+#else
+#define LLOID_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lloid_ctx lloid_ctx;
+
+typedef enum {
+    LLOID_OK = 0,
+    LLOID_EINVAL = -1,     /* bad argument, shape or bank (message says which) */
+    LLOID_ENOMEM = -2,     /* a device or host allocation failed */
+    LLOID_EBUDGET = -3,    /* loading the bank would exceed hbm_budget_bytes */
+    LLOID_EGAP = -4,       /* push t0 is not where the detector's stream ends */
+    LLOID_ENOTREADY = -5,  /* window not yet covered by pushed data */
+    LLOID_ETIMEOUT = -6,   /* GPU work not finished within timeout_ms */
+    LLOID_ECUDA = -7,      /* a CUDA call failed (message has the CUDA error) */
+    LLOID_ERANGE = -8,     /* output capacity too small (n_out has the need) */
+    LLOID_EEXPIRED = -9    /* the window's triggers were overwritten (pull sooner) */
+} lloid_status;
+
+typedef enum {
+    LLOID_FP32 = 0,        /* FP32 operands, FP32 accumulate (SIMT FMA) */
+    LLOID_FP16_SPLIT = 1,  /* tensor cores: FP16 operands with the data split
+                              into hi + lo halves, FP32 accumulate */
+    LLOID_BF16_SPLIT = 2   /* tensor cores: BF16 hi + lo on both operands
+                              (three products), FP32 accumulate */
+} lloid_precision;
+
+/* Context configuration.  lloid_config_default() fills the paper's values:
+ * f0 = 2048 Hz, N_down = 32 (Section II.C.2), N_up = 8 (Section II.C.2),
+ * 1 s windows with no overlap, threshold |z| > 4 (Section II.D.1). */
+typedef struct {
+    int32_t f0;                /* full sample rate (Hz); power of two */
+    int32_t n_detectors;       /* independent strain streams (>= 1) */
+    int32_t n_down;            /* downsampling half length at the target rate */
+    int32_t n_up;              /* upsampling half length at the lower rate */
+    int64_t window_samples;    /* trigger window W (multiple of 128) */
+    int64_t window_overlap;    /* window w covers [max(0, wW - overlap), (w+1)W);
+                                  only 0 is implemented (EINVAL otherwise) */
+    float snr_threshold;       /* a trigger needs |z| > snr_threshold */
+    int32_t precision;         /* lloid_precision */
+    int64_t max_block;         /* largest push, full-rate samples (multiple of 128) */
+    int64_t max_history;       /* longest template J_s + N_s D_s any bank may use */
+    int32_t min_rate;          /* lowest slice rate (power of two, f0/64 at least) */
+    int32_t device;            /* CUDA device ordinal */
+    size_t hbm_budget_bytes;   /* 0 = no budget; else cap on bank + state bytes */
+    void* cuda_stream;         /* cudaStream_t to order work on, or NULL */
+    uint32_t flags;            /* reserved, 0 */
+} lloid_config;
+
+/* One time slice of a bank (Eq. 3): the leading L bases and their
+ * reconstruction coefficients.  Rate = f0 / D with D a power of two; the
+ * slice covers before-merger full-rate samples [j_start, j_start + n_taps D);
+ * j_start must be a multiple of D and satisfy pre-synchronisation without
+ * latency (Eq. 9): j_start >= D N_down + sum over the bank's ladder rates
+ * f (rate <= f < f0) of N_up f0 / f, for D > 1. */
+typedef struct {
+    int32_t rate;
+    int32_t n_taps;            /* N_s, samples at this rate */
+    int64_t j_start;           /* J_s, full-rate samples before merger */
+    int32_t n_basis;           /* L_s >= 1 */
+    int32_t pad0;
+    const double* bases;       /* host, [n_basis][n_taps], u_l[m], m = samples
+                                  before merger at this rate (row-major) */
+    const double* coeffs;      /* host, [2M][n_basis], v_il sigma_l; row 2i is
+                                  the real part of template i, 2i+1 imaginary */
+} lloid_slice;
+
+typedef struct {
+    int32_t n_templates;       /* M (>= 1) */
+    int32_t n_slices;          /* S (>= 1) */
+    const lloid_slice* slices; /* host, [n_slices], any order, non-overlapping */
+} lloid_bank_desc;
+
+/* A trigger (Section II.D.1): template `tmpl` of bank `bank` in detector
+ * `detector` reached its window maximum |z| = snr > threshold at `sample`,
+ * with phase = atan2(im, re).  is_bank_max = 1 marks the bank's loudest
+ * template in that window (lowest template index on ties). */
+typedef struct {
+    int32_t detector;
+    int32_t bank;
+    int32_t tmpl;
+    int32_t is_bank_max;
+    int64_t window;
+    int64_t sample;
+    float snr;
+    float phase;
+    float re;
+    float im;
+} lloid_trigger;
+
+/* Fill *cfg with the defaults above (n_detectors = 1, max_block = 16384,
+ * max_history = 128 s, min_rate = 32, precision FP32). */
+LLOID_API void lloid_config_default(lloid_config* cfg);
+
+/* Create a context on cfg->device.  Allocates the per-detector strain rings
+ * and window buffers.  EINVAL on a bad configuration, ECUDA/ENOMEM on device
+ * failure.  *out is NULL on failure. */
+LLOID_API lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out);
+
+/* Free every device and host resource of the context (NULL is a no-op). */
+LLOID_API void lloid_destroy(lloid_ctx* ctx);
+
+/* Static text for a status code. */
+LLOID_API const char* lloid_strerror(lloid_status st);
+
+/* One-line reason for the last failing call on ctx (never NULL). */
+LLOID_API const char* lloid_last_error(const lloid_ctx* ctx);
+
+/* Load an SVD bank (Eq. 3, grouped as in Section II.C.1): validates shapes,
+ * rates, slice overlap and the pre-synchronisation condition of Eq. 9,
+ * converts to the context's precision and copies to the device.  Banks may be
+ * loaded while streaming; a bank's SNR is exact once its longest slice
+ * (j_start + n_taps D) has been streamed after loading.  *bank_id receives a
+ * small integer used in triggers.  EBUDGET when hbm_budget_bytes would be
+ * exceeded (nothing is kept), EINVAL with a reason otherwise. */
+LLOID_API lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bank, int32_t* bank_id);
+
+/* Release a bank's device memory.  Enqueued work that uses it completes first. */
+LLOID_API lloid_status lloid_unload_bank(lloid_ctx* ctx, int32_t bank_id);
+
+/* Push n samples of whitened strain of detector `det` starting at full-rate
+ * sample t0 (steps a0-a5 for every loaded bank).  `block` is a host pointer
+ * (is_device_ptr = 0; pinned memory avoids a staging copy) or a device
+ * pointer on the context's device (is_device_ptr = 1).  t0 must equal the
+ * end of the detector's previous push (0 at first): EGAP otherwise.  n must
+ * be a positive multiple of 128 and <= max_block: EINVAL otherwise.  Windows
+ * that the block completes are finalised on the device. */
+LLOID_API lloid_status lloid_push_strain(lloid_ctx* ctx, int32_t det, int64_t t0, const float* block,
+                               int64_t n, int is_device_ptr);
+
+/* The same for every detector at once: `blocks` is [n_detectors][n],
+ * row-major, and every detector's stream must end at t0. */
+LLOID_API lloid_status lloid_push_strain_all(lloid_ctx* ctx, int64_t t0, const float* blocks, int64_t n,
+                                   int is_device_ptr);
+
+/* Copy the triggers of window `window` (all detectors, all banks) into the
+ * host array out[cap], ordered by detector, bank, template.  ENOTREADY if a
+ * detector has not pushed data through the end of the window; waits up to
+ * timeout_ms (< 0: forever) for the GPU, then ETIMEOUT; ERANGE if cap is too
+ * small (*n_out = the number needed, nothing copied); EEXPIRED if the window
+ * is older than the retained ring (the 16 most recent windows). */
+LLOID_API lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid_trigger* out, int64_t cap,
+                                 int64_t* n_out, int32_t timeout_ms);
+
+/* Debug and parity aid: recompute the full-rate SNR rows of the most recent
+ * push of detector `det` for bank `bank` into the DEVICE array out
+ * [2M][n_last] (row 2i = real part of template i) with the same kernels and
+ * precision as the trigger path; *n_samples receives n_last and *t0 its first
+ * sample.  cap is out's length in floats (ERANGE when too small).  Waits. */
+LLOID_API lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* out, int64_t cap,
+                             int64_t* t0, int64_t* n_samples);
+
+/* Wait for all enqueued work of the context (ECUDA on a device error). */
+LLOID_API lloid_status lloid_synchronize(lloid_ctx* ctx);
+
+/* Number of kernel launches the context has issued so far. */
+LLOID_API int64_t lloid_launch_count(const lloid_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LLOID_H */

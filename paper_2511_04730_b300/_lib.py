@@ -1,0 +1,91 @@
+"""ctypes declarations of the C ABI in include/lloid.h.
+
+Loading fails loudly when the shared library is missing: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblloid_b300.so")
+
+LLOID_OK = 0
+STATUS_NAMES = {
+    0: "LLOID_OK", -1: "LLOID_EINVAL", -2: "LLOID_ENOMEM", -3: "LLOID_EBUDGET", -4: "LLOID_EGAP",
+    -5: "LLOID_ENOTREADY", -6: "LLOID_ETIMEOUT", -7: "LLOID_ECUDA", -8: "LLOID_ERANGE", -9: "LLOID_EEXPIRED",
+}
+PRECISIONS = {"fp32": 0, "fp16_split": 1, "bf16_split": 2}
+
+
+class LloidConfig(ctypes.Structure):
+    _fields_ = [
+        ("f0", ctypes.c_int32), ("n_detectors", ctypes.c_int32), ("n_down", ctypes.c_int32),
+        ("n_up", ctypes.c_int32), ("window_samples", ctypes.c_int64), ("window_overlap", ctypes.c_int64),
+        ("snr_threshold", ctypes.c_float), ("precision", ctypes.c_int32), ("max_block", ctypes.c_int64),
+        ("max_history", ctypes.c_int64), ("min_rate", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+    ]
+
+
+class LloidSlice(ctypes.Structure):
+    _fields_ = [
+        ("rate", ctypes.c_int32), ("n_taps", ctypes.c_int32), ("j_start", ctypes.c_int64),
+        ("n_basis", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("bases", ctypes.POINTER(ctypes.c_double)), ("coeffs", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class LloidBankDesc(ctypes.Structure):
+    _fields_ = [("n_templates", ctypes.c_int32), ("n_slices", ctypes.c_int32),
+                ("slices", ctypes.POINTER(LloidSlice))]
+
+
+class LloidTrigger(ctypes.Structure):
+    _fields_ = [
+        ("detector", ctypes.c_int32), ("bank", ctypes.c_int32), ("tmpl", ctypes.c_int32),
+        ("is_bank_max", ctypes.c_int32), ("window", ctypes.c_int64), ("sample", ctypes.c_int64),
+        ("snr", ctypes.c_float), ("phase", ctypes.c_float), ("re", ctypes.c_float), ("im", ctypes.c_float),
+    ]
+
+
+# (name, restype, argtypes) for every entry point of include/lloid.h
+SIGNATURES = [
+    ("lloid_config_default", None, [ctypes.POINTER(LloidConfig)]),
+    ("lloid_create", ctypes.c_int, [ctypes.POINTER(LloidConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    ("lloid_destroy", None, [ctypes.c_void_p]),
+    ("lloid_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("lloid_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("lloid_load_bank", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LloidBankDesc), ctypes.POINTER(ctypes.c_int32)]),
+    ("lloid_unload_bank", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("lloid_push_strain", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_int]),
+    ("lloid_push_strain_all", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_int]),
+    ("lloid_pull_triggers", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(LloidTrigger),
+                                           ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("lloid_snr_block", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("lloid_synchronize", ctypes.c_int, [ctypes.c_void_p]),
+    ("lloid_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (once) and declare every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"LLOID CUDA library not built: {path} is missing "
+                           "(run paper_2511_04730_b300/build.py or __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,426 @@
+// FP32 SIMT kernels of the LLOID hot path (the plain FP32 GPU path) and the
+// stages every precision shares: ingest, downsampling, slice upsampling,
+// window finalisation and trigger compaction.
+#pragma once
+#include "lloid_common.cuh"
+
+namespace lloid {
+
+__device__ __forceinline__ long long floordiv(long long a, long long b) {
+    long long q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+// Job that owns flat tile t: the largest j with tile_base[j] <= t.
+__device__ __forceinline__ int find_job(const int* __restrict__ tile_base, int n_jobs, int t) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_base + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// a0: block -> full-rate ring
+// ---------------------------------------------------------------------------
+__global__ void k_ingest(const float* __restrict__ src, long long src_det_stride, float* __restrict__ ring,
+                         long long ring_det_stride, int mask, long long k_a, int n, int det0) {
+    const int det = blockIdx.y;
+    const float* s = src + det * src_det_stride;
+    float* r = ring + (det0 + det) * ring_det_stride;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        r[(k_a + i) & mask] = s[i];
+}
+
+// ---------------------------------------------------------------------------
+// a1: d_D[q] = sum_k w'[k] d[D q + c - k], w' = sqrt(D) g / sum(g) (Eq. 4),
+// for the n/D new samples q in [k_a/D - N_down, k_b/D - N_down) of every rate.
+// One warp per output sample; lanes stride the 2c+1 taps.
+// ---------------------------------------------------------------------------
+struct DownParams {
+    const float* w[kMaxRates];
+    float* dst[kMaxRates];
+    long long dst_det_stride[kMaxRates];
+    int dst_mask[kMaxRates];
+    int D[kMaxRates];
+    int n_rates;
+};
+
+__global__ void k_downsample(DownParams p, const float* __restrict__ ring0, long long ring0_det_stride,
+                             int mask0, long long k_a, int n, int n_down, int det0) {
+    const int r = blockIdx.z;
+    if (r >= p.n_rates) return;
+    const int D = p.D[r];
+    const int nq = n / D;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (qi >= nq) return;
+    const int det = det0 + blockIdx.y;
+    const long long q = k_a / D - n_down + qi;
+    const int c = D * n_down;
+    const int taps = 2 * c + 1;
+    const float* src = ring0 + det * ring0_det_stride;
+    const float* w = p.w[r];
+    const long long base = (long long)D * q + c;
+    float acc = 0.f;
+    for (int k = lane; k < taps; k += 32) acc = fmaf(__ldg(w + k), src[(base - k) & mask0], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) p.dst[r][det * p.dst_det_stride[r] + (q & p.dst_mask[r])] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// a2 (FP32): Toeplitz GEMM, tile 64 bases x 128 outputs, 256 threads, each
+// thread 4 bases x 8 consecutive outputs with a sliding register window on x.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fir_f32(const FirJob* __restrict__ jobs, const int* __restrict__ tile_base,
+                                                 int n_jobs, long long k_a, int det0) {
+    const int t = blockIdx.x;
+    const int j = find_job(tile_base, n_jobs, t);
+    const FirJob& jb = jobs[j];
+    const int local = t - tile_base[j];
+    if (local >= jb.tiles_l * jb.tiles_q) return;
+    const int tl = local / jb.tiles_q, tq = local % jb.tiles_q;
+    const int det = det0 + blockIdx.y;
+    const long long q_start = (jb.D == 1) ? k_a : floordiv(k_a - 1 + jb.c_hi, jb.D) + 1;
+    const int l0 = tl * 64, qi0 = tq * 128;
+    const long long q0 = q_start + qi0;
+
+    __shared__ float us[64][33];
+    __shared__ float xs[128 + 32];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[i][q] = 0.f;
+
+    const float* src = jb.src + det * jb.src_det_stride;
+    for (int m0 = 0; m0 < jb.N; m0 += 32) {
+        for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+            int l = e >> 5, mm = e & 31;
+            int gl = l0 + l, gm = m0 + mm;
+            us[l][mm] = (gl < jb.L && gm < jb.N) ? __ldg(jb.bases + (long long)gl * jb.N + gm) : 0.f;
+        }
+        // xs[s] = x[q0 - m0 - 31 + s], x[i] = stream[i - src_off]
+        for (int s = threadIdx.x; s < 159; s += 256) {
+            long long i = q0 - m0 - 31 + s - jb.src_off;
+            xs[s] = src[i & jb.src_mask];
+        }
+        __syncthreads();
+        float xr[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xr[q] = xs[tx * 8 + 31 + q];
+#pragma unroll 8
+        for (int mm = 0; mm < 32; ++mm) {
+            float u0 = us[ty * 4 + 0][mm], u1 = us[ty * 4 + 1][mm];
+            float u2 = us[ty * 4 + 2][mm], u3 = us[ty * 4 + 3][mm];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                acc[0][q] = fmaf(u0, xr[q], acc[0][q]);
+                acc[1][q] = fmaf(u1, xr[q], acc[1][q]);
+                acc[2][q] = fmaf(u2, xr[q], acc[2][q]);
+                acc[3][q] = fmaf(u3, xr[q], acc[3][q]);
+            }
+#pragma unroll
+            for (int q = 7; q > 0; --q) xr[q] = xr[q - 1];
+            xr[0] = xs[(tx * 8 + 30 - mm) >= 0 ? (tx * 8 + 30 - mm) : 0];
+        }
+        __syncthreads();
+    }
+    float* dst = jb.dst + det * jb.dst_det_stride;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int l = l0 + ty * 4 + i;
+        if (l >= jb.L) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int qi = qi0 + tx * 8 + q;
+            if (qi >= jb.q_count) continue;
+            const long long qq = q_start + qi;
+            dst[(long long)l * jb.dst_ld + (qq & jb.dst_mask)] = acc[i][q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a4 (slice part): composed polyphase upsampler of each D > 1 slice into the
+// full-rate Yhat rows of the block.  OutT = float (FP32 path) or a split pair.
+// ---------------------------------------------------------------------------
+template <typename Store>
+__global__ void __launch_bounds__(256) k_upsample(const UpJob* __restrict__ jobs, const int* __restrict__ tile_base,
+                                                  int n_jobs, long long k_a, int n, int det0, Store store) {
+    extern __shared__ float Rs[];
+    const int t = blockIdx.x;
+    const int j = find_job(tile_base, n_jobs, t);
+    const UpJob& jb = jobs[j];
+    const int local = t - tile_base[j];
+    const int l = local / jb.tiles_k, kt = local % jb.tiles_k;
+    if (l >= jb.L) return;
+    for (int e = threadIdx.x; e < jb.rlen; e += blockDim.x) Rs[e] = __ldg(jb.R + e);
+    __syncthreads();
+    const int det = det0 + blockIdx.y;
+    const int kk = kt * 256 + threadIdx.x;
+    if (kk >= n) return;
+    const long long K = k_a + kk;
+    const float* y = jb.yring + det * jb.y_det_stride + (long long)l * jb.y_ld;
+    // q with 0 <= K - D q - e_min < rlen
+    const long long e_max = (long long)jb.e_min + jb.rlen - 1;
+    long long q_lo = -floordiv(-(K - e_max), jb.D);   // ceil((K - e_max) / D)
+    long long q_hi = floordiv(K - jb.e_min, jb.D);
+    float acc = 0.f;
+    for (long long q = q_lo; q <= q_hi; ++q)
+        acc = fmaf(y[q & jb.y_mask], Rs[K - (long long)jb.D * q - jb.e_min], acc);
+    store(jb, det, l, kk, acc);
+}
+
+struct StoreF32 {
+    __device__ __forceinline__ void operator()(const UpJob& jb, int det, int l, int kk, float v) const {
+        static_cast<float*>(jb.yhat)[det * jb.yhat_det_stride + (long long)l * jb.ldy + kk] = v;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// a3 + a5 (FP32): z = C Yhat for 64 templates x 128 samples per CTA, fused
+// |z|^2 and per-tile argmax (earliest sample on ties).  STORE_Z also writes
+// the SNR rows (debug / parity).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool better(float a, int ka, float b, int kb) {
+    return a > b || (a == b && ka < kb);
+}
+
+template <bool STORE_Z>
+__global__ void __launch_bounds__(256) k_recon_f32(const ReconJob* __restrict__ jobs, const int* __restrict__ tile_base,
+                                                   int n_jobs, long long k_a, int n, int det0, long long window,
+                                                   Partial* __restrict__ part, long long part_tmpl_stride,
+                                                   int n_slots, float* __restrict__ zout) {
+    const int t = blockIdx.x;
+    const int j = find_job(tile_base, n_jobs, t);
+    const ReconJob& jb = jobs[j];
+    const int local = t - tile_base[j];
+    const int tm = local / jb.tiles_t, tt = local % jb.tiles_t;
+    const int det = det0 + blockIdx.y;
+    const int m0 = tm * 64, t0 = tt * 128;
+    if (t0 >= n) return;
+    const float* cre = (const float*)jb.c_re;
+    const float* cim = (const float*)jb.c_im;
+    const float* yh = (const float*)jb.yhat + det * jb.yhat_det_stride;
+
+    __shared__ __align__(16) float sre[16][64];
+    __shared__ __align__(16) float sim[16][64];
+    __shared__ __align__(16) float sy[16][128];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float are[8][4], aim[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { are[i][q] = 0.f; aim[i][q] = 0.f; }
+
+    for (int k0 = 0; k0 < jb.Kpad; k0 += 16) {
+        for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+            int m = e >> 4, kk = e & 15;
+            long long off = (long long)(m0 + m) * jb.Kpad + k0 + kk;
+            sre[kk][m] = __ldg(cre + off);
+            sim[kk][m] = __ldg(cim + off);
+        }
+        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+            int kk = e >> 5, c4 = e & 31;
+            float4 v = __ldg(reinterpret_cast<const float4*>(yh + (long long)(k0 + kk) * jb.ldy + t0) + c4);
+            reinterpret_cast<float4*>(&sy[kk][0])[c4] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+            float4 r0 = reinterpret_cast<const float4*>(&sre[kk][w * 8])[0];
+            float4 r1 = reinterpret_cast<const float4*>(&sre[kk][w * 8])[1];
+            float4 i0 = reinterpret_cast<const float4*>(&sim[kk][w * 8])[0];
+            float4 i1 = reinterpret_cast<const float4*>(&sim[kk][w * 8])[1];
+            float4 y4 = reinterpret_cast<const float4*>(&sy[kk][lane * 4])[0];
+            float cr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            float ci[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+            float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    are[i][q] = fmaf(cr[i], yv[q], are[i][q]);
+                    aim[i][q] = fmaf(ci[i], yv[q], aim[i][q]);
+                }
+        }
+        __syncthreads();
+    }
+
+    // Epilogue: window maxima.  Tile [t0, t0+128) lies inside one window.
+    const long long tile_abs = (k_a + t0) / kTileT;
+    const long long kwin0 = ((k_a + t0) / window) * window;
+    const int slot = (int)(tile_abs & (n_slots - 1));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + w * 8 + i;
+        float best = -1.f, bre = 0.f, bim = 0.f;
+        int bk = 0x7fffffff;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float p = are[i][q] * are[i][q] + aim[i][q] * aim[i][q];
+            int k = (int)(k_a + t0 + lane * 4 + q - kwin0);
+            if (better(p, k, best, bk)) { best = p; bk = k; bre = are[i][q]; bim = aim[i][q]; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            float ore = __shfl_xor_sync(0xffffffffu, bre, o);
+            float oim = __shfl_xor_sync(0xffffffffu, bim, o);
+            if (better(ob, ok, best, bk)) { best = ob; bk = ok; bre = ore; bim = oim; }
+        }
+        if (m < jb.M) {
+            if (lane == 0 && part != nullptr)
+                part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots + slot] =
+                    make_float4(best, __int_as_float(bk), bre, bim);
+            if (STORE_Z) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    zout[(long long)(2 * m) * n + t0 + lane * 4 + q] = are[i][q];
+                    zout[(long long)(2 * m + 1) * n + t0 + lane * 4 + q] = aim[i][q];
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5: finalise window w for one (bank, detector): reduce the tile partials of
+// every template, threshold, and flag the bank's loudest template.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ jobs, const Partial* __restrict__ part,
+                                                  long long part_tmpl_stride, int n_slots, int tiles_per_window,
+                                                  long long w, float threshold, SlabEntry* __restrict__ slab,
+                                                  long long slab_det_stride, int det0) {
+    const FinJob jb = jobs[blockIdx.x];
+    const int det = det0 + blockIdx.y;
+    const int s0 = (int)((w * tiles_per_window) & (n_slots - 1));
+    SlabEntry* out = slab + det * slab_det_stride;
+    float tbest = -1.f;
+    int tidx = 0x7fffffff;
+    for (int m = threadIdx.x; m < jb.M; m += blockDim.x) {
+        const Partial* p = part + (long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots;
+        float best = -1.f, bre = 0.f, bim = 0.f;
+        int bk = 0x7fffffff;
+        for (int s = 0; s < tiles_per_window; ++s) {
+            float4 v = p[(s0 + s) & (n_slots - 1)];
+            int k = __float_as_int(v.y);
+            if (better(v.x, k, best, bk)) { best = v.x; bk = k; bre = v.z; bim = v.w; }
+        }
+        SlabEntry e;
+        e.snr = sqrtf(best);
+        e.phase = atan2f(bim, bre);
+        e.re = bre;
+        e.im = bim;
+        e.k_off = bk;
+        e.flags = (e.snr > threshold) ? 1 : 0;
+        out[jb.tmpl0 + m] = e;
+        if (best > tbest || (best == tbest && m < tidx)) { tbest = best; tidx = m; }
+    }
+    __shared__ float sb[32];
+    __shared__ int si[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ob = __shfl_xor_sync(0xffffffffu, tbest, o);
+        int oi = __shfl_xor_sync(0xffffffffu, tidx, o);
+        if (ob > tbest || (ob == tbest && oi < tidx)) { tbest = ob; tidx = oi; }
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sb[wid] = tbest; si[wid] = tidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 1; i < nw; ++i)
+            if (sb[i] > tbest || (sb[i] == tbest && si[i] < tidx)) { tbest = sb[i]; tidx = si[i]; }
+        if (tidx < jb.M && (out[jb.tmpl0 + tidx].flags & 1)) out[jb.tmpl0 + tidx].flags |= 2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Trigger compaction of one window slab: entries e = det * cap + tmpl, in
+// order; chunk counts, then each chunk scatters at its exclusive prefix.
+// ---------------------------------------------------------------------------
+struct TriggerOut {       // identical layout to lloid_trigger
+    int32_t detector, bank, tmpl, is_bank_max;
+    long long window, sample;
+    float snr, phase, re, im;
+};
+
+__global__ void k_gather_count(const SlabEntry* __restrict__ slab, long long cap, int M_used, int n_det,
+                               int* __restrict__ counts) {
+    const long long total = (long long)n_det * M_used;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int v = 0;
+    if (e < total) {
+        const long long det = e / M_used, m = e % M_used;
+        v = slab[det * cap + m].flags & 1;
+    }
+    v = __syncthreads_count(v);
+    if (threadIdx.x == 0) counts[blockIdx.x] = v;
+}
+
+__global__ void k_gather_scatter(const SlabEntry* __restrict__ slab, long long cap, int M_used, int n_det,
+                                 const int* __restrict__ counts, int n_chunks, const int* __restrict__ bank_of,
+                                 const int* __restrict__ tmpl0_of, long long window, long long W,
+                                 TriggerOut* __restrict__ out, long long out_cap, long long* __restrict__ total_out) {
+    __shared__ int red[1024 / 32];
+    __shared__ int base_s;
+    // exclusive prefix of the chunk counts
+    int s = 0;
+    for (int i = threadIdx.x; i < blockIdx.x; i += blockDim.x) s += counts[i];
+    int tot = 0;
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n_chunks; i += blockDim.x) tot += counts[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) { s += __shfl_xor_sync(0xffffffffu, s, o); tot += __shfl_xor_sync(0xffffffffu, tot, o); }
+    __shared__ int red2[1024 / 32];
+    if (lane == 0) { red[wid] = s; red2[wid] = tot; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0, b = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += red[i]; b += red2[i]; }
+        base_s = a;
+        if (blockIdx.x == 0) *total_out = b;
+    }
+    __syncthreads();
+    const long long total = (long long)n_det * M_used;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    SlabEntry en;
+    int v = 0;
+    long long det = 0, m = 0;
+    if (e < total) {
+        det = e / M_used; m = e % M_used;
+        en = slab[det * cap + m];
+        v = en.flags & 1;
+    }
+    // block-wide exclusive scan of v
+    unsigned ball = __ballot_sync(0xffffffffu, v);
+    int pre = __popc(ball & ((1u << lane) - 1));
+    __syncthreads();
+    if (lane == 0) red[wid] = __popc(ball);
+    __syncthreads();
+    int wpre = 0;
+    for (int i = 0; i < wid; ++i) wpre += red[i];
+    if (v) {
+        long long pos = (long long)base_s + wpre + pre;
+        if (pos < out_cap) {
+            TriggerOut o;
+            o.detector = (int)det;
+            o.bank = bank_of[m];
+            o.tmpl = (int)(m - tmpl0_of[o.bank]);
+            o.is_bank_max = (en.flags >> 1) & 1;
+            o.window = window;
+            o.sample = window * W + en.k_off;
+            o.snr = en.snr; o.phase = en.phase; o.re = en.re; o.im = en.im;
+            out[pos] = o;
+        }
+    }
+}
+
+}  // namespace lloid

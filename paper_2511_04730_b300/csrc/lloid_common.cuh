@@ -1,0 +1,79 @@
+// Device-side job descriptors shared by the LLOID kernels and the host code.
+//
+// Every launch covers many independent pieces of work (detectors, banks,
+// slices, tiles) through a flat grid: blockIdx.x enumerates tiles of all jobs,
+// a job's tiles start at tile_base[job], and blockIdx.y is the detector.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lloid {
+
+constexpr int kTileT = 128;      // time tile of the reconstruction = window granule
+constexpr int kMaxRates = 8;     // downsampled streams f0/2 ... f0/256
+
+// a2: one (bank, slice) basis-filter job.  Y^s_l[q] = sum_m u_l[m] x[q - src_off - m]
+// where x is the slice-rate stream (Eq. 5 with the pre-synchronised offset, Eq. 9).
+struct FirJob {
+    const float* bases;          // [L][N] FP32
+    const float* src;            // stream ring of this rate, detector 0
+    long long src_det_stride;
+    long long src_off;           // J_s / D_s
+    float* dst;                  // Y ring [L][y_len], detector 0
+    long long dst_det_stride;
+    int src_mask;
+    int dst_mask;                // ring mask
+    int dst_ld;                  // row stride of dst
+    int L, N, D;
+    int c_hi;                    // look-ahead of the slice's upsampler (full-rate samples)
+    int q_count;                 // new outputs per push (n / D)
+    int tiles_l, tiles_q;
+};
+
+// a4 (slice part): Yhat_l[K] = sum_q Y_l[q] R[K - D q - e_min], the slice's
+// ladder of Eq. 7-8 upsamplers composed into one polyphase filter R (R = [1]
+// for slices already at f0, which this step only converts).
+struct UpJob {
+    const float* yring;          // [L][y_len], detector 0
+    long long y_det_stride;
+    void* yhat;                  // first Yhat row of this slice, detector 0
+    void* yhat_lo;               // split formats: the low halves
+    long long yhat_det_stride;
+    const float* R;              // [rlen]
+    int y_mask;
+    int y_ld;
+    int ldy;                     // Yhat row stride (max_block)
+    int e_min, rlen;
+    int D, L;
+    int tiles_k;                 // K tiles of 256 per basis row
+};
+
+// a3 + a4 (sum) + a5: z = C Yhat for one bank, |z|^2 window maxima per tile.
+struct ReconJob {
+    const void* c_re;            // [Mpad][Kpad] real-part coefficient rows
+    const void* c_im;            // [Mpad][Kpad] imaginary-part rows
+    const void* yhat;            // [Kpad][ldy] (detector 0); split formats add yhat_lo
+    const void* yhat_lo;
+    long long yhat_det_stride;   // elements
+    int ldy;
+    int Kpad, Mpad, M;
+    int tmpl0;                   // first global template id of the bank
+    int tiles_m, tiles_t;
+};
+
+// Per (template, detector, time tile) partial maximum of |z|^2.
+// x = |z|^2, y = sample offset inside its window (int bits), z = Re, w = Im.
+using Partial = float4;
+
+// Dense per-window trigger slot for one (detector, template).
+struct SlabEntry {
+    float snr, phase, re, im;
+    int32_t k_off;               // sample - window start
+    int32_t flags;               // bit 0 valid (|z| > threshold), bit 1 bank max
+};
+
+struct FinJob {
+    int tmpl0, M;
+};
+
+}  // namespace lloid

@@ -1,0 +1,965 @@
+// Host side of the LLOID C ABI: context, bank registry, streaming state and
+// the per-push launch sequence.  Every arithmetic step of the hot path runs in
+// the kernels; the host validates, lays out, and enqueues.
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lloid.h"
+#include "kernels_simt.cuh"
+#include "kernels_tc.cuh"
+
+using namespace lloid;
+
+namespace {
+
+constexpr int kWindowRing = 16;      // retained trigger windows (slab ring)
+
+long long next_pow2(long long x) {
+    long long p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Eq. 4: sinc of zero spacing f windowed by a sinc of half length c, g[c] = 1.
+std::vector<double> sinc_windowed(int f, int c) {
+    std::vector<double> g(2 * c + 1);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k <= 2 * c; ++k) {
+        int x = k - c;
+        if (x == 0) { g[k] = 1.0; continue; }
+        double a = pi * x / f, b = pi * x / c;
+        g[k] = std::sin(a) / a * std::sin(b) / b;
+    }
+    return g;
+}
+
+struct SliceRT {
+    int rate = 0, D = 1, N = 0, L = 0;
+    long long J = 0;
+    int row0 = 0;                // first Yhat row of the slice within the bank
+    int e_min = 0, e_max = 0;    // support of the composed upsampler (full-rate offsets)
+    float* d_bases = nullptr;
+    float* d_R = nullptr;
+    float* d_yring = nullptr;    // [n_det][L][y_len]
+    int y_len = 0;
+};
+
+struct BankRT {
+    int id = 0, M = 0, Mpad = 0, K = 0, Kpad = 0, tmpl0 = 0;
+    std::vector<SliceRT> sl;
+    void* d_cre = nullptr;       // [Mpad][Kpad] (FP32 or half)
+    void* d_cim = nullptr;
+    void* d_cre_lo = nullptr;    // BF16 split: low parts of the coefficients
+    void* d_cim_lo = nullptr;
+    void* d_yhat = nullptr;      // [n_det][Kpad][max_block]
+    void* d_yhat_lo = nullptr;
+    long long yhat_det_stride = 0;
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+};
+
+}  // namespace
+
+struct lloid_ctx {
+    lloid_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    long long launches = 0;
+    size_t state_bytes = 0, bank_bytes = 0;
+
+    // strain rings
+    float* ring0 = nullptr;
+    long long ring0_len = 0;
+    int n_rates = 0;
+    int rate_D[kMaxRates] = {};
+    float* rate_ring[kMaxRates] = {};
+    long long rate_len[kMaxRates] = {};
+    float* w_down[kMaxRates] = {};
+    std::vector<long long> pos;        // end of each detector's stream
+    std::vector<long long> fin;        // last finalised window per detector
+
+    // staging
+    float* d_stage = nullptr;          // [n_det][max_block]
+    float* h_stage[2] = {nullptr, nullptr};
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    int stage_i = 0;
+    long long last_n[64];              // last push length per detector (parity aid)
+
+    // banks
+    std::map<int, BankRT*> banks;
+    int next_bank_id = 0;
+    int M_used = 0;                    // global template ids handed out
+    long long M_cap = 0;
+    int* d_bank_of = nullptr;          // [M_cap]
+    int* d_tmpl0_of = nullptr;         // [bank_cap]
+    int bank_cap = 0;
+    std::vector<int> h_bank_of, h_tmpl0_of;
+
+    // window state
+    int tiles_per_window = 0;
+    int n_slots = 0;                   // partial ring slots per (template, detector)
+    Partial* d_part = nullptr;         // [M_cap][n_det][n_slots]
+    SlabEntry* d_slab = nullptr;       // [kWindowRing][n_det][M_cap]
+    int* d_counts = nullptr;
+    int counts_cap = 0;
+    TriggerOut* d_trig = nullptr;
+    long long trig_cap = 0;
+    long long* d_total = nullptr;
+    long long* h_total = nullptr;
+
+    // job tables for the current push length
+    bool jobs_dirty = true;
+    long long jobs_n = -1;
+    FirJob* d_fir = nullptr; int* d_fir_base = nullptr; int n_fir = 0, fir_tiles = 0;
+    UpJob* d_up = nullptr; int* d_up_base = nullptr; int n_up = 0, up_tiles = 0, up_smem = 0;
+    ReconJob* d_rec = nullptr; int* d_rec_base = nullptr; int n_rec = 0, rec_tiles = 0;
+    FinJob* d_finj = nullptr; int n_fin = 0;
+    TcMaps* d_maps = nullptr;
+    std::vector<void*> job_allocs;
+    cudaEvent_t done_ev = nullptr;
+    int* d_err = nullptr;              // device-side wait-expiry code (0 = none)
+    int n_sm = 0;
+};
+
+namespace {
+
+lloid_status fail(lloid_ctx* c, lloid_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? LLOID_ENOMEM : LLOID_ECUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CKL()                                                                           \
+    do {                                                                                \
+        ++ctx->launches;                                                                \
+        cudaError_t e_ = cudaGetLastError();                                            \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, LLOID_ECUDA, "launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+template <typename T>
+lloid_status dalloc(lloid_ctx* ctx, T** p, size_t bytes, std::vector<void*>* owner, size_t* acct) {
+    void* q = nullptr;
+    CK(cudaMalloc(&q, bytes));
+    CK(cudaMemsetAsync(q, 0, bytes, ctx->stream));
+    *p = (T*)q;
+    if (owner) owner->push_back(q);
+    if (acct) *acct += bytes;
+    return LLOID_OK;
+}
+
+__global__ void k_fill_partials(Partial* p, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = make_float4(-1.f, __int_as_float(0x7fffffff), 0.f, 0.f);
+}
+
+// Composed response of the ladder upsamplers (Eq. 7-8, c = F N_up at each
+// stage) from `rate` up to f0, applied to a unit impulse at low-rate sample 0.
+// out[e - e_min] is the full-rate response at offset e.
+void compose_upsampler(const std::vector<int>& ladder_up, int n_up, std::vector<double>* out, int* e_min,
+                       int* e_max) {
+    // ladder_up: rates from the slice's rate (first) to f0 (last), ascending
+    std::vector<double> x(1, 1.0);
+    long long lo = 0;   // index of x[0] at the current rate
+    for (size_t s = 0; s + 1 < ladder_up.size(); ++s) {
+        int F = ladder_up[s + 1] / ladder_up[s];
+        int c = F * n_up;
+        std::vector<double> g = sinc_windowed(F, c);
+        long long y_lo = F * lo - c;
+        long long y_hi = F * (lo + (long long)x.size() - 1) + c;
+        std::vector<double> y(y_hi - y_lo + 1, 0.0);
+        for (size_t k = 0; k < x.size(); ++k)
+            for (int i = 0; i <= 2 * c; ++i)   // y[p] += x[k] g[p - F k + c]
+                y[F * (lo + (long long)k) - c + i - y_lo] += x[k] * g[i];
+        x.swap(y);
+        lo = y_lo;
+    }
+    *e_min = (int)lo;
+    *e_max = (int)(lo + (long long)x.size() - 1);
+    *out = x;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2-D K-major map: rows of `cols` 16-bit elements, box 64 x box_rows, 128-byte swizzle.
+bool encode_map(CUtensorMap* m, bool bf16, const void* base, long long cols, long long rows, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+lloid_status ensure_template_capacity(lloid_ctx* ctx, long long need) {
+    if (need <= ctx->M_cap) return LLOID_OK;
+    const int nd = ctx->cfg.n_detectors;
+    long long cap = std::max<long long>(need, 2 * ctx->M_cap);
+    cap = std::max<long long>(cap, 1024);
+    // partials: [M][det][slot] -> prefix copy
+    Partial* np = nullptr;
+    size_t pbytes = (size_t)cap * nd * ctx->n_slots * sizeof(Partial);
+    CK(cudaMalloc(&np, pbytes));
+    long long nfill = cap * nd * ctx->n_slots;
+    k_fill_partials<<<(unsigned)((nfill + 255) / 256), 256, 0, ctx->stream>>>(np, nfill);
+    CKL();
+    if (ctx->d_part) {
+        CK(cudaMemcpyAsync(np, ctx->d_part, (size_t)ctx->M_cap * nd * ctx->n_slots * sizeof(Partial),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    // slab: [ring][det][M] -> pitched copy
+    SlabEntry* ns = nullptr;
+    size_t sbytes = (size_t)kWindowRing * nd * cap * sizeof(SlabEntry);
+    CK(cudaMalloc(&ns, sbytes));
+    CK(cudaMemsetAsync(ns, 0, sbytes, ctx->stream));
+    if (ctx->d_slab) {
+        CK(cudaMemcpy2DAsync(ns, cap * sizeof(SlabEntry), ctx->d_slab, ctx->M_cap * sizeof(SlabEntry),
+                             ctx->M_cap * sizeof(SlabEntry), (size_t)kWindowRing * nd, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    }
+    int* nb = nullptr;
+    CK(cudaMalloc(&nb, cap * sizeof(int)));
+    if (ctx->d_bank_of) CK(cudaMemcpyAsync(nb, ctx->d_bank_of, ctx->M_cap * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+    int nchunks = (int)((nd * cap + 1023) / 1024);
+    int* nc = nullptr;
+    CK(cudaMalloc(&nc, nchunks * sizeof(int)));
+    TriggerOut* nt = nullptr;
+    CK(cudaMalloc(&nt, (size_t)nd * cap * sizeof(TriggerOut)));
+    CK(cudaStreamSynchronize(ctx->stream));
+    size_t old = ctx->M_cap ? ((size_t)ctx->M_cap * nd * ctx->n_slots * sizeof(Partial) +
+                               (size_t)kWindowRing * nd * ctx->M_cap * sizeof(SlabEntry) +
+                               ctx->M_cap * sizeof(int) + (size_t)nd * ctx->M_cap * sizeof(TriggerOut))
+                            : 0;
+    cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_counts); cudaFree(ctx->d_trig);
+    ctx->d_part = np; ctx->d_slab = ns; ctx->d_bank_of = nb; ctx->d_counts = nc; ctx->d_trig = nt;
+    ctx->counts_cap = nchunks;
+    ctx->trig_cap = (long long)nd * cap;
+    ctx->state_bytes += pbytes + sbytes + cap * sizeof(int) + (size_t)nd * cap * sizeof(TriggerOut) - old;
+    ctx->M_cap = cap;
+    ctx->h_bank_of.resize(cap, -1);
+    return LLOID_OK;
+}
+
+void free_jobs(lloid_ctx* ctx) {
+    for (void* p : ctx->job_allocs) cudaFree(p);
+    ctx->job_allocs.clear();
+    ctx->d_fir = nullptr; ctx->d_up = nullptr; ctx->d_rec = nullptr; ctx->d_finj = nullptr;
+}
+
+template <typename T>
+lloid_status upload_vec(lloid_ctx* ctx, T** dst, const std::vector<T>& v) {
+    size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
+    CK(cudaMalloc((void**)dst, bytes));
+    ctx->job_allocs.push_back(*dst);
+    if (!v.empty()) CK(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return LLOID_OK;
+}
+
+bool split_precision(const lloid_ctx* ctx) { return ctx->cfg.precision != LLOID_FP32; }
+
+// (Re)build the job tables for pushes of n samples.
+lloid_status build_jobs(lloid_ctx* ctx, long long n) {
+    if (!ctx->jobs_dirty && ctx->jobs_n == n) return LLOID_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_jobs(ctx);
+    std::vector<FirJob> fj;
+    std::vector<int> fb;
+    std::vector<UpJob> uj;
+    std::vector<int> ub;
+    std::vector<ReconJob> rj;
+    std::vector<int> rb;
+    std::vector<FinJob> fin;
+    std::vector<TcMaps> maps;
+    int ft = 0, ut = 0, rt = 0, max_rlen = 1;
+    for (auto& kv : ctx->banks) {
+        BankRT* b = kv.second;
+        for (auto& s : b->sl) {
+            FirJob f{};
+            f.bases = s.d_bases;
+            if (s.D == 1) {
+                f.src = ctx->ring0; f.src_det_stride = ctx->ring0_len; f.src_mask = (int)(ctx->ring0_len - 1);
+            } else {
+                int ri = 0;
+                while (ctx->rate_D[ri] != s.D) ++ri;
+                f.src = ctx->rate_ring[ri]; f.src_det_stride = ctx->rate_len[ri]; f.src_mask = (int)(ctx->rate_len[ri] - 1);
+            }
+            f.src_off = s.J / s.D;
+            f.dst = s.d_yring; f.dst_det_stride = (long long)s.L * s.y_len; f.dst_mask = s.y_len - 1; f.dst_ld = s.y_len;
+            f.L = s.L; f.N = s.N; f.D = s.D; f.c_hi = -s.e_min;
+            f.q_count = (int)(n / s.D);
+            f.tiles_l = (s.L + 63) / 64; f.tiles_q = (f.q_count + 127) / 128;
+            fj.push_back(f); fb.push_back(ft); ft += f.tiles_l * f.tiles_q;
+
+            UpJob u{};
+            u.yring = s.d_yring; u.y_det_stride = (long long)s.L * s.y_len; u.y_mask = s.y_len - 1; u.y_ld = s.y_len;
+            u.yhat = nullptr;  // set below per precision
+            u.yhat_det_stride = b->yhat_det_stride; u.ldy = (int)ctx->cfg.max_block;
+            u.R = s.d_R; u.e_min = s.e_min; u.rlen = s.e_max - s.e_min + 1; u.D = s.D; u.L = s.L;
+            if (!split_precision(ctx)) {
+                // FP32: Yhat[K][t], one thread per (row, sample), 256 samples per CTA
+                u.tiles_k = (int)((n + 255) / 256);
+                u.yhat = (char*)b->d_yhat + (size_t)s.row0 * u.ldy * 4;
+                u.yhat_lo = nullptr;
+                uj.push_back(u); ub.push_back(ut); ut += u.L * u.tiles_k;
+            } else {
+                // split: Yhat^T[t][Kpad], 64 rows x 64 samples per CTA
+                u.tiles_k = (int)((n + 63) / 64);
+                u.ldy = b->Kpad;
+                u.yhat = (char*)b->d_yhat + (size_t)s.row0 * 2;
+                u.yhat_lo = (char*)b->d_yhat_lo + (size_t)s.row0 * 2;
+                uj.push_back(u); ub.push_back(ut); ut += ((u.L + 63) / 64) * u.tiles_k;
+            }
+            max_rlen = std::max(max_rlen, u.rlen);
+        }
+        ReconJob r{};
+        r.c_re = b->d_cre; r.c_im = b->d_cim; r.yhat = b->d_yhat; r.yhat_lo = b->d_yhat_lo;
+        r.yhat_det_stride = b->yhat_det_stride; r.ldy = (int)ctx->cfg.max_block;
+        r.Kpad = b->Kpad; r.Mpad = b->Mpad; r.M = b->M; r.tmpl0 = b->tmpl0;
+        r.tiles_m = b->Mpad / (split_precision(ctx) ? 128 : 64);
+        r.tiles_t = (int)(n / (split_precision(ctx) ? kTcTileN : 128));
+        rj.push_back(r); rb.push_back(rt); rt += r.tiles_m * r.tiles_t;
+        fin.push_back(FinJob{b->tmpl0, b->M});
+        if (split_precision(ctx)) {
+            const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
+            TcMaps mp;
+            std::memset(&mp, 0, sizeof mp);
+            const long long yrows = (long long)ctx->cfg.n_detectors * ctx->cfg.max_block;
+            bool ok = encode_map(&mp.cre, bf, b->d_cre, b->Kpad, b->Mpad, kTcTileM) &&
+                      encode_map(&mp.cim, bf, b->d_cim, b->Kpad, b->Mpad, kTcTileM) &&
+                      encode_map(&mp.yhi, bf, b->d_yhat, b->Kpad, yrows, kTcTileN) &&
+                      encode_map(&mp.ylo, bf, b->d_yhat_lo, b->Kpad, yrows, kTcTileN);
+            if (ok && bf)
+                ok = encode_map(&mp.cre_lo, bf, b->d_cre_lo, b->Kpad, b->Mpad, kTcTileM) &&
+                     encode_map(&mp.cim_lo, bf, b->d_cim_lo, b->Kpad, b->Mpad, kTcTileM);
+            if (!ok) return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed for bank %d", b->id);
+            maps.push_back(mp);
+        }
+    }
+    lloid_status st;
+    if ((st = upload_vec(ctx, &ctx->d_fir, fj)) || (st = upload_vec(ctx, &ctx->d_fir_base, fb)) ||
+        (st = upload_vec(ctx, &ctx->d_up, uj)) || (st = upload_vec(ctx, &ctx->d_up_base, ub)) ||
+        (st = upload_vec(ctx, &ctx->d_rec, rj)) || (st = upload_vec(ctx, &ctx->d_rec_base, rb)) ||
+        (st = upload_vec(ctx, &ctx->d_finj, fin)) || (st = upload_vec(ctx, &ctx->d_maps, maps)))
+        return st;
+    ctx->n_fir = (int)fj.size(); ctx->fir_tiles = ft;
+    ctx->n_up = (int)uj.size(); ctx->up_tiles = ut; ctx->up_smem = max_rlen * 4;
+    ctx->n_rec = (int)rj.size(); ctx->rec_tiles = rt;
+    ctx->n_fin = (int)fin.size();
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->jobs_dirty = false;
+    ctx->jobs_n = n;
+    if (ctx->up_smem > 40 * 1024) {
+        CK(cudaFuncSetAttribute(k_upsample<StoreF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->up_smem));
+        CK(cudaFuncSetAttribute(k_upsample_t<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->up_smem));
+        CK(cudaFuncSetAttribute(k_upsample_t<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->up_smem));
+    }
+    return LLOID_OK;
+}
+
+lloid_status launch_recon(lloid_ctx* ctx, long long k_a, long long n, int det0, int n_det_push, bool store_z,
+                          const ReconJob* jobs, const TcMaps* maps, const int* base, int n_jobs, int tiles,
+                          float* zout) {
+    const long long part_stride = (long long)ctx->cfg.n_detectors * ctx->n_slots;
+    if (tiles == 0) return LLOID_OK;
+    dim3 grid(tiles, n_det_push);
+    if (!split_precision(ctx)) {
+        if (store_z)
+            k_recon_f32<true><<<grid, 256, 0, ctx->stream>>>(jobs, base, n_jobs, k_a, (int)n, det0,
+                                                            ctx->cfg.window_samples, nullptr, part_stride,
+                                                            ctx->n_slots, zout);
+        else
+            k_recon_f32<false><<<grid, 256, 0, ctx->stream>>>(jobs, base, n_jobs, k_a, (int)n, det0,
+                                                             ctx->cfg.window_samples, ctx->d_part, part_stride,
+                                                             ctx->n_slots, nullptr);
+        CKL();
+        return LLOID_OK;
+    }
+    const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
+    const int total = tiles * n_det_push;
+    dim3 g(std::min(total, ctx->n_sm));
+    const int smem = bf ? TcCfg<true>::SMEM : TcCfg<false>::SMEM;
+    Partial* part = store_z ? nullptr : ctx->d_part;
+#define LAUNCH_TC(BFV, SZ)                                                                                  \
+    do {                                                                                                    \
+        CK(cudaFuncSetAttribute(k_recon_tc<BFV, SZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
+        k_recon_tc<BFV, SZ><<<g, 192, smem, ctx->stream>>>(jobs, maps, base, n_jobs, tiles, k_a, (int)n, det0, \
+                                                           n_det_push, ctx->cfg.window_samples, part,       \
+                                                           part_stride, ctx->n_slots, zout, ctx->d_err);    \
+    } while (0)
+    if (bf) { if (store_z) LAUNCH_TC(true, true); else LAUNCH_TC(true, false); }
+    else { if (store_z) LAUNCH_TC(false, true); else LAUNCH_TC(false, false); }
+#undef LAUNCH_TC
+    CKL();
+    return LLOID_OK;
+}
+
+// Steps a1-a5 for detectors [det0, det0+nd) whose block [k_a, k_a+n) sits in d_stage (or src).
+lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long n, const float* src,
+                     long long src_det_stride) {
+    lloid_status st = build_jobs(ctx, n);
+    if (st) return st;
+    const int n_i = (int)n;
+    // a0 ingest
+    {
+        dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 1024), nd);
+        k_ingest<<<grid, 256, 0, ctx->stream>>>(src, src_det_stride, ctx->ring0, ctx->ring0_len,
+                                                (int)(ctx->ring0_len - 1), k_a, n_i, det0);
+        CKL();
+    }
+    // a1 downsample to every rate
+    {
+        DownParams p{};
+        p.n_rates = ctx->n_rates;
+        for (int r = 0; r < ctx->n_rates; ++r) {
+            p.w[r] = ctx->w_down[r]; p.dst[r] = ctx->rate_ring[r]; p.dst_det_stride[r] = ctx->rate_len[r];
+            p.dst_mask[r] = (int)(ctx->rate_len[r] - 1); p.D[r] = ctx->rate_D[r];
+        }
+        dim3 grid((unsigned)((n / 2 + 7) / 8), nd, ctx->n_rates);
+        k_downsample<<<grid, 256, 0, ctx->stream>>>(p, ctx->ring0, ctx->ring0_len, (int)(ctx->ring0_len - 1), k_a,
+                                                    n_i, ctx->cfg.n_down, det0);
+        CKL();
+    }
+    if (ctx->banks.empty()) return LLOID_OK;
+    // a2 basis FIR
+    if (ctx->fir_tiles) {
+        dim3 grid(ctx->fir_tiles, nd);
+        k_fir_f32<<<grid, 256, 0, ctx->stream>>>(ctx->d_fir, ctx->d_fir_base, ctx->n_fir, k_a, det0);
+        CKL();
+    }
+    // a4 (slice part) upsample each slice to Yhat
+    if (ctx->up_tiles) {
+        dim3 grid(ctx->up_tiles, nd);
+        if (!split_precision(ctx))
+            k_upsample<StoreF32><<<grid, 256, ctx->up_smem, ctx->stream>>>(ctx->d_up, ctx->d_up_base, ctx->n_up, k_a,
+                                                                         n_i, det0, StoreF32{});
+        else if (ctx->cfg.precision == LLOID_FP16_SPLIT)
+            k_upsample_t<__half><<<grid, 256, ctx->up_smem, ctx->stream>>>(ctx->d_up, ctx->d_up_base, ctx->n_up, k_a,
+                                                                          n_i, det0);
+        else
+            k_upsample_t<__nv_bfloat16><<<grid, 256, ctx->up_smem, ctx->stream>>>(ctx->d_up, ctx->d_up_base, ctx->n_up,
+                                                                                 k_a, n_i, det0);
+        CKL();
+    }
+    // a3 + a5 reconstruction with fused window maxima
+    st = launch_recon(ctx, k_a, n, det0, nd, false, ctx->d_rec, ctx->d_maps, ctx->d_rec_base, ctx->n_rec,
+                      ctx->rec_tiles, nullptr);
+    if (st) return st;
+    // a5 finalise completed windows
+    const long long W = ctx->cfg.window_samples;
+    for (long long w = k_a / W; (w + 1) * W <= k_a + n; ++w) {
+        SlabEntry* slab = ctx->d_slab + (size_t)(w % kWindowRing) * ctx->cfg.n_detectors * ctx->M_cap;
+        dim3 grid(ctx->n_fin, nd);
+        k_finalize<<<grid, 256, 0, ctx->stream>>>(ctx->d_finj, ctx->d_part,
+                                                  (long long)ctx->cfg.n_detectors * ctx->n_slots, ctx->n_slots,
+                                                  ctx->tiles_per_window, w, ctx->cfg.snr_threshold, slab,
+                                                  ctx->M_cap, det0);
+        CKL();
+    }
+    return LLOID_OK;
+}
+
+lloid_status push_common(lloid_ctx* ctx, int det0, int nd, long long t0, const float* block, long long n,
+                         int is_device_ptr) {
+    if (!block) return fail(ctx, LLOID_EINVAL, "block is NULL");
+    if (n <= 0 || n % kTileT || n > ctx->cfg.max_block)
+        return fail(ctx, LLOID_EINVAL, "block length %lld must be a positive multiple of %d and <= max_block %lld",
+                    n, kTileT, (long long)ctx->cfg.max_block);
+    for (int d = det0; d < det0 + nd; ++d)
+        if (ctx->pos[d] != t0)
+            return fail(ctx, LLOID_EGAP, "detector %d stream ends at %lld, push starts at %lld", d, ctx->pos[d], t0);
+    const float* src = block;
+    long long src_stride = n;
+    if (!is_device_ptr) {
+        const int i = ctx->stage_i;
+        CK(cudaEventSynchronize(ctx->stage_ev[i]));
+        std::memcpy(ctx->h_stage[i], block, (size_t)nd * n * sizeof(float));
+        CK(cudaMemcpyAsync(ctx->d_stage, ctx->h_stage[i], (size_t)nd * n * sizeof(float), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaEventRecord(ctx->stage_ev[i], ctx->stream));
+        ctx->stage_i ^= 1;
+        src = ctx->d_stage;
+    }
+    lloid_status st = process(ctx, det0, nd, t0, n, src, src_stride);
+    if (st) return st;
+    const long long W = ctx->cfg.window_samples;
+    for (int d = det0; d < det0 + nd; ++d) {
+        ctx->pos[d] = t0 + n;
+        ctx->fin[d] = (t0 + n) / W - 1;
+        ctx->last_n[d] = n;
+    }
+    CK(cudaEventRecord(ctx->done_ev, ctx->stream));
+    return LLOID_OK;
+}
+
+lloid_status wait_done(lloid_ctx* ctx, int timeout_ms) {
+    auto t_start = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ctx->done_ev);
+        if (e == cudaSuccess) return LLOID_OK;
+        if (e != cudaErrorNotReady) return fail(ctx, LLOID_ECUDA, "device error: %s", cudaGetErrorString(e));
+        if (timeout_ms >= 0) {
+            auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t_start);
+            if (el.count() >= timeout_ms) return fail(ctx, LLOID_ETIMEOUT, "GPU work not done after %d ms", timeout_ms);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+// A kernel whose bounded wait expired leaves a code in d_err (see kernels_tc.cuh).
+lloid_status check_kernel_err(lloid_ctx* ctx) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (e) return fail(ctx, LLOID_ETIMEOUT, "a kernel wait expired (code %d); results of the last pushes are invalid", e);
+    return LLOID_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void lloid_config_default(lloid_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->f0 = 2048;
+    c->n_detectors = 1;
+    c->n_down = 32;
+    c->n_up = 8;
+    c->window_samples = 2048;
+    c->window_overlap = 0;
+    c->snr_threshold = 4.0f;
+    c->precision = LLOID_FP32;
+    c->max_block = 16384;
+    c->max_history = 128LL * 2048;
+    c->min_rate = 32;
+    c->device = 0;
+    c->hbm_budget_bytes = 0;
+    c->cuda_stream = nullptr;
+    c->flags = 0;
+}
+
+const char* lloid_strerror(lloid_status st) {
+    switch (st) {
+        case LLOID_OK: return "ok";
+        case LLOID_EINVAL: return "invalid argument";
+        case LLOID_ENOMEM: return "out of memory";
+        case LLOID_EBUDGET: return "HBM budget exceeded";
+        case LLOID_EGAP: return "discontinuous push (t0 is not the stream end)";
+        case LLOID_ENOTREADY: return "window not yet covered by pushed data";
+        case LLOID_ETIMEOUT: return "timed out waiting for the GPU";
+        case LLOID_ECUDA: return "CUDA error";
+        case LLOID_ERANGE: return "output capacity too small";
+        case LLOID_EEXPIRED: return "window no longer retained";
+    }
+    return "unknown status";
+}
+
+const char* lloid_last_error(const lloid_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t lloid_launch_count(const lloid_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
+    if (!out) return LLOID_EINVAL;
+    *out = nullptr;
+    if (!cfg) return LLOID_EINVAL;
+    std::unique_ptr<lloid_ctx> h(new lloid_ctx());
+    lloid_ctx* ctx = h.get();
+    ctx->cfg = *cfg;
+    const lloid_config& c = ctx->cfg;
+    if (!is_pow2(c.f0) || c.n_detectors < 1 || c.n_detectors > 64 || c.n_down < 1 || c.n_up < 1 ||
+        c.window_samples <= 0 || c.window_samples % kTileT || c.max_block <= 0 || c.max_block % kTileT ||
+        c.max_history < 0 || !is_pow2(c.min_rate) || c.min_rate > c.f0 || c.f0 / c.min_rate > 256 ||
+        c.precision < 0 || c.precision > 2 || !(c.snr_threshold >= 0.f))
+        return fail(nullptr, LLOID_EINVAL, "bad configuration");
+    if (c.window_overlap != 0) return LLOID_EINVAL;
+    if (c.precision != LLOID_FP32 && c.max_block % kTcTileN) return LLOID_EINVAL;
+    CK(cudaSetDevice(c.device));
+    CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, c.device));
+    if (c.cuda_stream) {
+        ctx->stream = (cudaStream_t)c.cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    const int nd = c.n_detectors;
+    lloid_status st;
+    // full-rate ring: history for the D = 1 filters and the widest downsampler
+    const long long c_max = (long long)(c.f0 / c.min_rate) * c.n_down;
+    ctx->ring0_len = next_pow2(c.max_block + std::max<long long>(c.max_history, 2 * c_max) + 4 * kTileT);
+    if ((st = dalloc(ctx, &ctx->ring0, (size_t)nd * ctx->ring0_len * 4, nullptr, &ctx->state_bytes))) return st;
+    for (int D = 2; D <= c.f0 / c.min_rate; D *= 2) {
+        int r = ctx->n_rates++;
+        ctx->rate_D[r] = D;
+        ctx->rate_len[r] = next_pow2((c.max_block + c.max_history) / D + 2 * c.n_down + 4 * kTileT);
+        if ((st = dalloc(ctx, &ctx->rate_ring[r], (size_t)nd * ctx->rate_len[r] * 4, nullptr, &ctx->state_bytes)))
+            return st;
+        // w' = sqrt(D) g / sum(g), g from Eq. 4 with f = D, c = D N_down
+        std::vector<double> g = sinc_windowed(D, D * c.n_down);
+        double sum = 0;
+        for (double v : g) sum += v;
+        std::vector<float> w(g.size());
+        for (size_t k = 0; k < g.size(); ++k) w[k] = (float)(std::sqrt((double)D) * g[k] / sum);
+        if ((st = dalloc(ctx, &ctx->w_down[r], w.size() * 4, nullptr, &ctx->state_bytes))) return st;
+        CK(cudaMemcpyAsync(ctx->w_down[r], w.data(), w.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    ctx->pos.assign(nd, 0);
+    ctx->fin.assign(nd, -1);
+    for (int i = 0; i < 64; ++i) ctx->last_n[i] = 0;
+    if ((st = dalloc(ctx, &ctx->d_stage, (size_t)nd * c.max_block * 4, nullptr, &ctx->state_bytes))) return st;
+    for (int i = 0; i < 2; ++i) {
+        CK(cudaHostAlloc((void**)&ctx->h_stage[i], (size_t)nd * c.max_block * 4, cudaHostAllocDefault));
+        CK(cudaEventCreateWithFlags(&ctx->stage_ev[i], cudaEventDisableTiming));
+        CK(cudaEventRecord(ctx->stage_ev[i], ctx->stream));
+    }
+    CK(cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ctx->done_ev, ctx->stream));
+    ctx->tiles_per_window = (int)(c.window_samples / kTileT);
+    ctx->n_slots = (int)next_pow2(((c.max_block + c.window_samples - 1) / c.window_samples + 2) * ctx->tiles_per_window);
+    CK(cudaHostAlloc((void**)&ctx->h_total, sizeof(long long), cudaHostAllocDefault));
+    if ((st = dalloc(ctx, &ctx->d_err, sizeof(int), nullptr, &ctx->state_bytes))) return st;
+    if ((st = dalloc(ctx, &ctx->d_total, sizeof(long long), nullptr, &ctx->state_bytes))) return st;
+    if ((st = ensure_template_capacity(ctx, 1024))) return st;
+    CK(cudaStreamSynchronize(ctx->stream));
+    *out = h.release();
+    return LLOID_OK;
+}
+
+void lloid_destroy(lloid_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->cfg.device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->banks) {
+        for (void* p : kv.second->allocs) cudaFree(p);
+        delete kv.second;
+    }
+    free_jobs(ctx);
+    cudaFree(ctx->ring0);
+    for (int r = 0; r < ctx->n_rates; ++r) { cudaFree(ctx->rate_ring[r]); cudaFree(ctx->w_down[r]); }
+    cudaFree(ctx->d_stage);
+    for (int i = 0; i < 2; ++i) { cudaFreeHost(ctx->h_stage[i]); if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]); }
+    cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_tmpl0_of);
+    cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
+    cudaFree(ctx->d_err);
+    if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t* bank_id) {
+    if (!ctx) return LLOID_EINVAL;
+    if (!bd || !bank_id || bd->n_templates < 1 || bd->n_slices < 1 || !bd->slices)
+        return fail(ctx, LLOID_EINVAL, "bank descriptor is empty or NULL");
+    CK(cudaSetDevice(ctx->cfg.device));
+    const lloid_config& c = ctx->cfg;
+    const int M = bd->n_templates;
+    // ---- validate slices
+    std::vector<int> rates;
+    for (int s = 0; s < bd->n_slices; ++s) {
+        const lloid_slice& sl = bd->slices[s];
+        if (!is_pow2(sl.rate) || sl.rate > c.f0 || sl.rate < c.min_rate)
+            return fail(ctx, LLOID_EINVAL, "slice %d: rate %d is not a power of two in [min_rate, f0]", s, sl.rate);
+        const int D = c.f0 / sl.rate;
+        if (sl.n_taps < 1 || sl.n_basis < 1 || !sl.bases || !sl.coeffs)
+            return fail(ctx, LLOID_EINVAL, "slice %d: empty bases or coefficients", s);
+        if (sl.j_start < 0 || sl.j_start % D)
+            return fail(ctx, LLOID_EINVAL, "slice %d: j_start %lld is not a non-negative multiple of D = %d", s,
+                        (long long)sl.j_start, D);
+        if (sl.j_start + (long long)sl.n_taps * D > c.max_history)
+            return fail(ctx, LLOID_EINVAL, "slice %d ends at %lld samples, beyond max_history", s,
+                        (long long)(sl.j_start + (long long)sl.n_taps * D));
+        rates.push_back(sl.rate);
+    }
+    for (int a = 0; a < bd->n_slices; ++a)
+        for (int b = a + 1; b < bd->n_slices; ++b) {
+            const lloid_slice &x = bd->slices[a], &y = bd->slices[b];
+            long long xa = x.j_start, xb = x.j_start + (long long)x.n_taps * (c.f0 / x.rate);
+            long long ya = y.j_start, yb = y.j_start + (long long)y.n_taps * (c.f0 / y.rate);
+            if (xa < yb && ya < xb) return fail(ctx, LLOID_EINVAL, "slices %d and %d overlap", a, b);
+        }
+    // ---- ladder: distinct rates plus f0, ascending
+    std::vector<int> ladder = rates;
+    ladder.push_back(c.f0);
+    std::sort(ladder.begin(), ladder.end());
+    ladder.erase(std::unique(ladder.begin(), ladder.end()), ladder.end());
+
+    std::unique_ptr<BankRT> b(new BankRT());
+    b->M = M;
+    int row = 0;
+    for (int s = 0; s < bd->n_slices; ++s) {
+        const lloid_slice& sl = bd->slices[s];
+        SliceRT r;
+        r.rate = sl.rate; r.D = c.f0 / sl.rate; r.N = sl.n_taps; r.L = sl.n_basis; r.J = sl.j_start;
+        r.row0 = row;
+        row += r.L;
+        std::vector<int> up(ladder.begin() + (std::find(ladder.begin(), ladder.end(), sl.rate) - ladder.begin()),
+                            ladder.end());
+        std::vector<double> R;
+        compose_upsampler(up, c.n_up, &R, &r.e_min, &r.e_max);
+        // Pre-synchronisation without latency (Eq. 9): the newest Y sample the
+        // upsampler reads must already be computable from the pushed data.
+        if (r.D > 1 && r.J < -(long long)r.e_min + (long long)r.D * c.n_down)
+            return fail(ctx, LLOID_EINVAL,
+                        "slice %d (rate %d) starts %lld samples before merger; pre-synchronisation needs >= %lld",
+                        s, r.rate, r.J, -(long long)r.e_min + (long long)r.D * c.n_down);
+        b->sl.push_back(r);
+        // keep R for upload
+        b->sl.back().d_R = nullptr;
+        b->sl.back().y_len = (int)next_pow2(c.max_block / r.D + (r.e_max - r.e_min) / r.D + 4);
+        // stash R in a temporary via allocation below
+        std::vector<float> Rf(R.size());
+        for (size_t i = 0; i < R.size(); ++i) Rf[i] = (float)R[i];
+        lloid_status st;
+        if ((st = dalloc(ctx, &b->sl.back().d_R, Rf.size() * 4, &b->allocs, &b->bytes))) return st;
+        CK(cudaMemcpyAsync(b->sl.back().d_R, Rf.data(), Rf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    const bool split = split_precision(ctx);
+    b->K = row;
+    b->Kpad = (row + 63) / 64 * 64;
+    b->Mpad = (M + 127) / 128 * 128;
+    const int nd = c.n_detectors;
+    // ---- budget check before any large allocation
+    size_t esz = split ? 2 : 4;
+    size_t need = 0;
+    for (auto& r : b->sl)
+        need += (size_t)r.L * r.N * 4 + (size_t)nd * r.L * r.y_len * 4;
+    need += (size_t)b->Mpad * b->Kpad * esz * (c.precision == LLOID_BF16_SPLIT ? 4 : 2);
+    need += (size_t)nd * b->Kpad * c.max_block * esz * (split ? 2 : 1);
+    if (c.hbm_budget_bytes && ctx->state_bytes + ctx->bank_bytes + need > c.hbm_budget_bytes)
+        return fail(ctx, LLOID_EBUDGET, "bank needs %zu bytes; %zu of %zu in use", need,
+                    ctx->state_bytes + ctx->bank_bytes, (size_t)c.hbm_budget_bytes);
+    lloid_status st;
+    auto cleanup = [&]() { for (void* p : b->allocs) cudaFree(p); };
+    // ---- bases (FP32) and Y rings
+    for (int s = 0; s < bd->n_slices; ++s) {
+        const lloid_slice& sl = bd->slices[s];
+        SliceRT& r = b->sl[s];
+        std::vector<float> u((size_t)r.L * r.N);
+        for (size_t i = 0; i < u.size(); ++i) u[i] = (float)sl.bases[i];
+        if ((st = dalloc(ctx, &r.d_bases, u.size() * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
+        CK(cudaMemcpyAsync(r.d_bases, u.data(), u.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        if ((st = dalloc(ctx, &r.d_yring, (size_t)nd * r.L * r.y_len * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    // ---- coefficients: C[row][K] with the real rows and imaginary rows apart
+    {
+        std::vector<double> cre((size_t)b->Mpad * b->Kpad, 0.0), cim((size_t)b->Mpad * b->Kpad, 0.0);
+        for (int s = 0; s < bd->n_slices; ++s) {
+            const lloid_slice& sl = bd->slices[s];
+            const SliceRT& r = b->sl[s];
+            for (int i = 0; i < M; ++i)
+                for (int l = 0; l < r.L; ++l) {
+                    cre[(size_t)i * b->Kpad + r.row0 + l] = sl.coeffs[(size_t)(2 * i) * r.L + l];
+                    cim[(size_t)i * b->Kpad + r.row0 + l] = sl.coeffs[(size_t)(2 * i + 1) * r.L + l];
+                }
+        }
+        size_t n_el = (size_t)b->Mpad * b->Kpad;
+        if (!split) {
+            std::vector<float> a(n_el), bb(n_el);
+            for (size_t i = 0; i < n_el; ++i) { a[i] = (float)cre[i]; bb[i] = (float)cim[i]; }
+            if ((st = dalloc(ctx, (float**)&b->d_cre, n_el * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
+            if ((st = dalloc(ctx, (float**)&b->d_cim, n_el * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
+            CK(cudaMemcpyAsync(b->d_cre, a.data(), n_el * 4, cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(b->d_cim, bb.data(), n_el * 4, cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        } else {
+            std::vector<uint16_t> hre, him, lre, lim;
+            pack_coeffs_tc(c.precision == LLOID_BF16_SPLIT, cre, cim, b->Mpad, b->Kpad, &hre, &him, &lre, &lim);
+            void** dst[4] = {&b->d_cre, &b->d_cim, &b->d_cre_lo, &b->d_cim_lo};
+            std::vector<uint16_t>* srcv[4] = {&hre, &him, &lre, &lim};
+            for (int q = 0; q < 4; ++q) {
+                if (srcv[q]->empty()) continue;
+                if ((st = dalloc(ctx, (uint16_t**)dst[q], srcv[q]->size() * 2, &b->allocs, &b->bytes))) { cleanup(); return st; }
+                CK(cudaMemcpyAsync(*dst[q], srcv[q]->data(), srcv[q]->size() * 2, cudaMemcpyHostToDevice, ctx->stream));
+            }
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    }
+    // ---- Yhat block buffers (rows K..Kpad stay zero)
+    b->yhat_det_stride = (long long)b->Kpad * c.max_block;
+    if ((st = dalloc(ctx, (char**)&b->d_yhat, (size_t)nd * b->yhat_det_stride * esz, &b->allocs, &b->bytes))) { cleanup(); return st; }
+    if (split) {
+        if ((st = dalloc(ctx, (char**)&b->d_yhat_lo, (size_t)nd * b->yhat_det_stride * esz, &b->allocs, &b->bytes))) { cleanup(); return st; }
+    }
+    // ---- template ids, window state
+    b->tmpl0 = ctx->M_used;
+    if ((st = ensure_template_capacity(ctx, (long long)ctx->M_used + M))) { cleanup(); return st; }
+    b->id = ctx->next_bank_id++;
+    if (b->id >= ctx->bank_cap) {
+        int ncap = std::max(64, 2 * ctx->bank_cap);
+        int* nt = nullptr;
+        CK(cudaMalloc(&nt, ncap * sizeof(int)));
+        cudaFree(ctx->d_tmpl0_of);
+        ctx->d_tmpl0_of = nt;
+        ctx->bank_cap = ncap;
+        ctx->h_tmpl0_of.resize(ncap, 0);
+    }
+    ctx->h_tmpl0_of[b->id] = b->tmpl0;
+    for (int i = 0; i < M; ++i) ctx->h_bank_of[b->tmpl0 + i] = b->id;
+    CK(cudaMemcpyAsync(ctx->d_tmpl0_of, ctx->h_tmpl0_of.data(), ctx->bank_cap * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_bank_of + b->tmpl0, ctx->h_bank_of.data() + b->tmpl0, M * sizeof(int),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->M_used += M;
+    ctx->bank_bytes += b->bytes;
+    *bank_id = b->id;
+    ctx->banks[b->id] = b.release();
+    ctx->jobs_dirty = true;
+    return LLOID_OK;
+}
+
+lloid_status lloid_unload_bank(lloid_ctx* ctx, int32_t bank_id) {
+    if (!ctx) return LLOID_EINVAL;
+    auto it = ctx->banks.find(bank_id);
+    if (it == ctx->banks.end()) return fail(ctx, LLOID_EINVAL, "no bank %d", bank_id);
+    CK(cudaStreamSynchronize(ctx->stream));
+    // forget the bank's retained triggers so later pulls do not report them
+    CK(cudaMemset2DAsync(ctx->d_slab + it->second->tmpl0, ctx->M_cap * sizeof(SlabEntry), 0,
+                         (size_t)it->second->M * sizeof(SlabEntry), (size_t)kWindowRing * ctx->cfg.n_detectors,
+                         ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (void* p : it->second->allocs) cudaFree(p);
+    ctx->bank_bytes -= it->second->bytes;
+    delete it->second;
+    ctx->banks.erase(it);
+    ctx->jobs_dirty = true;
+    return LLOID_OK;
+}
+
+lloid_status lloid_push_strain(lloid_ctx* ctx, int32_t det, int64_t t0, const float* block, int64_t n,
+                               int is_device_ptr) {
+    if (!ctx) return LLOID_EINVAL;
+    if (det < 0 || det >= ctx->cfg.n_detectors) return fail(ctx, LLOID_EINVAL, "detector %d out of range", det);
+    return push_common(ctx, det, 1, t0, block, n, is_device_ptr);
+}
+
+lloid_status lloid_push_strain_all(lloid_ctx* ctx, int64_t t0, const float* blocks, int64_t n, int is_device_ptr) {
+    if (!ctx) return LLOID_EINVAL;
+    return push_common(ctx, 0, ctx->cfg.n_detectors, t0, blocks, n, is_device_ptr);
+}
+
+lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid_trigger* out, int64_t cap, int64_t* n_out,
+                                 int32_t timeout_ms) {
+    if (!ctx) return LLOID_EINVAL;
+    if (!n_out || (cap > 0 && !out) || window < 0) return fail(ctx, LLOID_EINVAL, "bad output arguments");
+    *n_out = 0;
+    const long long W = ctx->cfg.window_samples;
+    long long fin_min = ctx->fin[0], fin_max = ctx->fin[0];
+    for (long long f : ctx->fin) { fin_min = std::min(fin_min, f); fin_max = std::max(fin_max, f); }
+    if (window > fin_min) return fail(ctx, LLOID_ENOTREADY, "window %lld needs data through sample %lld", (long long)window, (window + 1) * W);
+    if (window + kWindowRing <= fin_max) return fail(ctx, LLOID_EEXPIRED, "window %lld is no longer retained", (long long)window);
+    lloid_status st = wait_done(ctx, timeout_ms);
+    if (st) return st;
+    if ((st = check_kernel_err(ctx))) return st;
+    const int nd = ctx->cfg.n_detectors;
+    const int M_used = ctx->M_used;
+    if (M_used == 0) return LLOID_OK;
+    const SlabEntry* slab = ctx->d_slab + (size_t)(window % kWindowRing) * nd * ctx->M_cap;
+    const long long total = (long long)nd * M_used;
+    const int chunks = (int)((total + 1023) / 1024);
+    k_gather_count<<<chunks, 1024, 0, ctx->stream>>>(slab, ctx->M_cap, M_used, nd, ctx->d_counts);
+    CKL();
+    k_gather_scatter<<<chunks, 1024, 0, ctx->stream>>>(slab, ctx->M_cap, M_used, nd, ctx->d_counts, chunks,
+                                                       ctx->d_bank_of, ctx->d_tmpl0_of, window, W, ctx->d_trig,
+                                                       ctx->trig_cap, ctx->d_total);
+    CKL();
+    CK(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const long long cnt = *ctx->h_total;
+    *n_out = cnt;
+    if (cnt > cap) return fail(ctx, LLOID_ERANGE, "window %lld has %lld triggers, capacity %lld", (long long)window, cnt, (long long)cap);
+    static_assert(sizeof(TriggerOut) == sizeof(lloid_trigger), "trigger layout");
+    if (cnt > 0) {
+        CK(cudaMemcpyAsync(out, ctx->d_trig, cnt * sizeof(lloid_trigger), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return LLOID_OK;
+}
+
+lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* out, int64_t cap, int64_t* t0,
+                             int64_t* n_samples) {
+    if (!ctx) return LLOID_EINVAL;
+    if (det < 0 || det >= ctx->cfg.n_detectors) return fail(ctx, LLOID_EINVAL, "detector %d out of range", det);
+    auto it = ctx->banks.find(bank);
+    if (it == ctx->banks.end()) return fail(ctx, LLOID_EINVAL, "no bank %d", bank);
+    const long long n = ctx->last_n[det];
+    if (n <= 0) return fail(ctx, LLOID_ENOTREADY, "detector %d has not pushed data", det);
+    BankRT* b = it->second;
+    if (cap < 2LL * b->M * n) { if (n_samples) *n_samples = n; return fail(ctx, LLOID_ERANGE, "need %lld floats", 2LL * b->M * n); }
+    lloid_status st0 = build_jobs(ctx, n);
+    if (st0) return st0;
+    int idx = 0;
+    for (auto& kv : ctx->banks) { if (kv.first == bank) break; ++idx; }
+    const bool split = split_precision(ctx);
+    const int tiles = (b->Mpad / (split ? 128 : 64)) * (int)(n / (split ? kTcTileN : 128));
+    int* db = nullptr;
+    CK(cudaMalloc(&db, sizeof(int)));
+    CK(cudaMemsetAsync(db, 0, sizeof(int), ctx->stream));
+    const long long k_a = ctx->pos[det] - n;
+    lloid_status st = launch_recon(ctx, k_a, n, det, 1, true, ctx->d_rec + idx, split ? ctx->d_maps + idx : nullptr,
+                                   db, 1, tiles, out);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(db);
+    if (st) return st;
+    if (e != cudaSuccess) return fail(ctx, LLOID_ECUDA, "snr_block: %s", cudaGetErrorString(e));
+    if ((st = check_kernel_err(ctx))) return st;
+    if (t0) *t0 = k_a;
+    if (n_samples) *n_samples = n;
+    return LLOID_OK;
+}
+
+lloid_status lloid_synchronize(lloid_ctx* ctx) {
+    if (!ctx) return LLOID_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return check_kernel_err(ctx);
+}
+
+}  // extern "C"

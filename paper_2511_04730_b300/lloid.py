@@ -1,0 +1,173 @@
+"""Python binding of the LLOID C ABI (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library; this module converts
+arguments (numpy arrays, torch tensors, streams) to the plain pointers and
+sizes of ``include/lloid.h`` and raises ``LloidError`` on a non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Iterable, Optional
+
+import numpy as np
+
+from . import _lib
+
+TRIGGER_DTYPE = np.dtype([
+    ("detector", np.int32), ("bank", np.int32), ("tmpl", np.int32), ("is_bank_max", np.int32),
+    ("window", np.int64), ("sample", np.int64), ("snr", np.float32), ("phase", np.float32),
+    ("re", np.float32), ("im", np.float32),
+])
+assert TRIGGER_DTYPE.itemsize == ctypes.sizeof(_lib.LloidTrigger)
+
+
+class LloidError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+        self.name = _lib.STATUS_NAMES.get(status, str(status))
+
+
+def default_config() -> _lib.LloidConfig:
+    lib = _lib.load()
+    cfg = _lib.LloidConfig()
+    lib.lloid_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+class Context:
+    """One LLOID streaming context on one GPU (``lloid_create``)."""
+
+    def __init__(self, n_detectors: int = 1, precision: str = "fp32", max_block: int = 16384,
+                 max_history: Optional[int] = None, window: int = 2048, threshold: float = 4.0,
+                 device: int = 0, stream=None, hbm_budget: int = 0, f0: int = 2048, min_rate: int = 32,
+                 n_down: int = 32, n_up: int = 8):
+        self._lib = _lib.load()
+        cfg = default_config()
+        cfg.f0, cfg.n_detectors, cfg.n_down, cfg.n_up = f0, n_detectors, n_down, n_up
+        cfg.window_samples, cfg.snr_threshold = window, threshold
+        cfg.precision = _lib.PRECISIONS[precision]
+        cfg.max_block = max_block
+        if max_history is not None:
+            cfg.max_history = max_history
+        cfg.min_rate, cfg.device, cfg.hbm_budget_bytes = min_rate, device, hbm_budget
+        cfg.cuda_stream = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        self.cfg = cfg
+        self.precision = precision
+        self.n_detectors = n_detectors
+        self.window = window
+        h = ctypes.c_void_p()
+        st = self._lib.lloid_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise LloidError(st, "lloid_create failed (bad configuration or device error)")
+        self._h = h
+        self.banks = {}
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, st: int):
+        if st != 0:
+            msg = self._lib.lloid_last_error(self._h).decode()
+            raise LloidError(st, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lloid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- banks ----------------------------------------------------------------
+    def load_bank(self, slices: Iterable) -> int:
+        """Load an SVD bank given as objects with rate, j_start, bases [L, N]
+        and coeffs [2M, L] (float64).  Returns the bank id."""
+        slices = list(slices)
+        keep = []
+        arr = (_lib.LloidSlice * len(slices))()
+        n_rows = None
+        for i, s in enumerate(slices):
+            b = np.ascontiguousarray(s.bases, dtype=np.float64)
+            c = np.ascontiguousarray(s.coeffs, dtype=np.float64)
+            keep += [b, c]
+            if n_rows is None:
+                n_rows = c.shape[0]
+            arr[i].rate, arr[i].n_taps, arr[i].j_start = int(s.rate), int(b.shape[1]), int(s.j_start)
+            arr[i].n_basis = int(b.shape[0])
+            arr[i].bases = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[i].coeffs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            if c.shape != (n_rows, b.shape[0]):
+                raise ValueError("coeffs must be [2M, L] with one 2M for the bank")
+        desc = _lib.LloidBankDesc(n_rows // 2, len(slices), arr)
+        bid = ctypes.c_int32()
+        self._check(self._lib.lloid_load_bank(self._h, ctypes.byref(desc), ctypes.byref(bid)))
+        self.banks[bid.value] = n_rows // 2
+        return bid.value
+
+    def unload_bank(self, bank_id: int):
+        self._check(self._lib.lloid_unload_bank(self._h, bank_id))
+        self.banks.pop(bank_id, None)
+
+    # -- streaming ------------------------------------------------------------
+    @staticmethod
+    def _ptr(block):
+        """(pointer, n, is_device) for a float32 numpy array or torch tensor."""
+        if isinstance(block, np.ndarray):
+            if block.dtype != np.float32 or not block.flags.c_contiguous:
+                raise ValueError("host blocks must be C-contiguous float32")
+            return block.ctypes.data, block.shape[-1], 0
+        import torch
+        if not isinstance(block, torch.Tensor) or block.dtype != torch.float32 or not block.is_contiguous():
+            raise ValueError("blocks must be contiguous float32 numpy arrays or torch tensors")
+        return block.data_ptr(), block.shape[-1], 1 if block.is_cuda else 0
+
+    def push(self, det: int, t0: int, block):
+        p, n, dev = self._ptr(block)
+        self._check(self._lib.lloid_push_strain(self._h, det, t0, ctypes.c_void_p(p), n, dev))
+
+    def push_all(self, t0: int, blocks):
+        p, n, dev = self._ptr(blocks)
+        self._check(self._lib.lloid_push_strain_all(self._h, t0, ctypes.c_void_p(p), n, dev))
+
+    def pull(self, window: int, timeout_ms: int = -1, cap: int = 1 << 16) -> np.ndarray:
+        """Triggers of one window as a numpy structured array (TRIGGER_DTYPE)."""
+        n_out = ctypes.c_int64()
+        while True:
+            out = np.zeros(cap, dtype=TRIGGER_DTYPE)
+            st = self._lib.lloid_pull_triggers(self._h, window, out.ctypes.data_as(ctypes.POINTER(_lib.LloidTrigger)),
+                                               cap, ctypes.byref(n_out), timeout_ms)
+            if st == -8:   # ERANGE: grow and retry
+                cap = int(n_out.value)
+                continue
+            self._check(st)
+            return out[: n_out.value].copy()
+
+    def snr_block(self, det: int, bank: int):
+        """SNR rows [2M, n] of the last push of ``det`` for ``bank`` (torch, on device)."""
+        import torch
+        M = self.banks[bank]
+        n = ctypes.c_int64()
+        t0 = ctypes.c_int64()
+        cap = ctypes.c_int64(0)
+        # ask for the size first
+        st = self._lib.lloid_snr_block(self._h, det, bank, None, 0, ctypes.byref(t0), ctypes.byref(n))
+        if st not in (0, -8):
+            self._check(st)
+        out = torch.empty((2 * M, int(n.value)), dtype=torch.float32, device=f"cuda:{self.cfg.device}")
+        self._check(self._lib.lloid_snr_block(self._h, det, bank, ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                              ctypes.byref(t0), ctypes.byref(n)))
+        return out, int(t0.value)
+
+    def synchronize(self):
+        self._check(self._lib.lloid_synchronize(self._h))
+
+    def launch_count(self) -> int:
+        return int(self._lib.lloid_launch_count(self._h))

@@ -1,0 +1,105 @@
+"""The C-ABI library loads and exports every entry point include/lloid.h
+declares, and the ctypes structures match the C layout (checked against gcc).
+No compute call is made: these run without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lloid.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_04730_b300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"LLOID_API\s+[\w\s\*]+?\b(lloid_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lloid_create", "lloid_load_bank", "lloid_push_strain", "lloid_pull_triggers", "lloid_destroy"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2511_04730_b300 import _lib
+    bound = {n for n, _, _ in _lib.SIGNATURES}
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in bound, f"{name} has no ctypes signature"
+
+
+def test_struct_layout_matches_c(lib):
+    from paper_2511_04730_b300 import _lib
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "lloid.h"
+#define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
+int main(void) {
+  printf("lloid_config %zu\nlloid_slice %zu\nlloid_bank_desc %zu\nlloid_trigger %zu\n",
+         sizeof(lloid_config), sizeof(lloid_slice), sizeof(lloid_bank_desc), sizeof(lloid_trigger));
+  P(lloid_config, max_block) P(lloid_config, hbm_budget_bytes) P(lloid_config, cuda_stream) P(lloid_config, flags)
+  P(lloid_slice, j_start) P(lloid_slice, bases) P(lloid_slice, coeffs)
+  P(lloid_trigger, window) P(lloid_trigger, sample) P(lloid_trigger, snr) P(lloid_trigger, im)
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    m = {"lloid_config": _lib.LloidConfig, "lloid_slice": _lib.LloidSlice,
+         "lloid_bank_desc": _lib.LloidBankDesc, "lloid_trigger": _lib.LloidTrigger}
+    for k, v in got.items():
+        if "." in k:
+            t, f = k.split(".")
+            assert getattr(m[t], f).offset == int(v), k
+        else:
+            assert ctypes.sizeof(m[k]) == int(v), k
+
+
+def test_host_only_calls(lib):
+    from paper_2511_04730_b300 import _lib
+    cfg = _lib.LloidConfig()
+    lib.lloid_config_default(ctypes.byref(cfg))
+    # the paper's constants (Section II.C.2, II.D.1)
+    assert (cfg.f0, cfg.n_down, cfg.n_up, cfg.window_samples) == (2048, 32, 8, 2048)
+    assert cfg.snr_threshold == 4.0 and cfg.window_overlap == 0
+    assert lib.lloid_strerror(-4) == b"discontinuous push (t0 is not the stream end)"
+    assert lib.lloid_strerror(0) == b"ok"
+    assert lib.lloid_last_error(None) == b"null context"
+
+
+def test_product_path_has_no_oracle_import():
+    """The product package never imports the oracle (test infrastructure)."""
+    pkg = os.path.join(ROOT, "paper_2511_04730_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2511_04730_b300 import _lib
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="not built"):
+            _lib.load(str(tmp_path / "nope.so"))
+    finally:
+        _lib._lib = saved
