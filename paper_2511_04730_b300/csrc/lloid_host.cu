@@ -850,8 +850,9 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->M_used += M;
     ctx->bank_bytes += b->bytes;
-    *bank_id = b->id;
-    ctx->banks[b->id] = b.release();
+    const int id = b->id;
+    *bank_id = id;
+    ctx->banks[id] = b.release();
     ctx->jobs_dirty = true;
     return LLOID_OK;
 }
