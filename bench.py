@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Throughput of the LLOID hot path on B300: template-seconds filtered per second.
+
+Workload (the 1000-template configuration): 1000 Newtonian chirp templates,
+chirp mass log-uniform in [1, 20] Msun, 64 s long, cut into 9 time slices at
+2048/1024/512/256/128 Hz and SVD-compressed to 99.99 % of each slice's
+energy; 2 detectors x 1024 s of seeded unit white noise at 2048 Hz with 20
+injections per detector at SNR U[6, 20] (synthetic stand-in for the paper's
+mock-data-challenge strain).
+
+A step pushes one block (--block-seconds, default 8 s) of strain for every
+detector through every stage (ingest, downsample, basis FIR, upsample,
+reconstruction + window maxima, finalisation) and pulls the triggers of the
+windows the block completes.  The stream continues across steps, cycling
+through the 1024 s record.  L2 is flushed (256 MB write) between steps,
+outside the timed intervals, which are CUDA-event pairs on the library's
+stream around each step.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (bounded samples of the same workload).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+F0 = 2048
+REF_M = 8          # templates per reference-arm step (a bounded oracle sample)
+METRIC = "template-seconds filtered/s at max |dSNR|<=5e-3 vs FP32 path; p50/p99 block latency"
+UNIT = "template-s/s"
+WORKLOAD = ("1000 Newtonian chirp templates (Mc log-U[1,20] Msun, 64 s, 9 slices 2048/1024/512/256/128 Hz, "
+            "SVD 99.99%), 2 detectors x 1024 s white noise + 20 injections/detector, 1 s trigger windows")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--warmup", type=int, default=4)
+    p.add_argument("--impl", default="lloid", choices=["lloid", "reference"])
+    p.add_argument("--precision", default="fp16_split", choices=["fp32", "fp16_split", "bf16_split"])
+    p.add_argument("--block-seconds", type=int, default=8)
+    p.add_argument("--templates", type=int, default=1000)
+    p.add_argument("--seconds", type=int, default=1024)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp32-compare", action="store_true")
+    p.add_argument("--latency-steps", type=int, default=32)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (weak scaling: every rank filters its own replica)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "lloid" else "gloo"
+        dist.init_process_group(backend=backend)
+        return dist.get_rank(), dist.get_world_size(), dist
+    return 0, 1, None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_inputs(args, rank):
+    import numpy as np
+    import workloads as W
+    w = W.make_workload("bank1000", n_templates=args.templates, n_seconds=args.seconds)
+    w.seed_base = 100 + 10 * rank
+    strain = np.stack([w.strain(d) for d in range(w.n_det)]).astype(np.float32)
+    return w, strain
+
+
+def algorithmic_work(slices, M, f0=F0, n_up=8):
+    """Per detector-second per bank (the hot-path accounting of Eq. 5-8):
+    FIR 2 L N r, reconstruction 2 (2M) L r, ladder 2 (2M) 2 N_up r (F-1)/F,
+    window maxima 2M f0 compares."""
+    fir = sum(2.0 * s.n_basis * s.n_taps * s.rate for s in slices)
+    rec = sum(2.0 * (2 * M) * s.n_basis * s.rate for s in slices)
+    lad = sorted(set(s.rate for s in slices) | {f0})
+    up = sum(2.0 * (2 * M) * 2 * n_up * hi * (hi // lo - 1) / (hi // lo) for lo, hi in zip(lad[:-1], lad[1:]))
+    cmp_ = 2.0 * M * f0
+    return {"fir": fir, "recon": rec, "ladder": up, "max": cmp_}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(M=64, seconds=68, seed_det=0):
+    """Time the FP64 oracle's LLOID on a bounded sample: the first M templates'
+    worth of the 1000-template family (same Mc range, same slicing rule), one
+    detector, `seconds` of data (64 s of template history + 4 s)."""
+    import numpy as np
+    from threadpoolctl import threadpool_limits
+    import workloads as W
+    from oracle import lloid_oracle as O
+    w = W.make_workload("bank1000", n_templates=M, n_seconds=seconds, n_det=1, n_inj=1)
+    sl = O.svd_bank(w.banks[0], w.plans[0])
+    d = w.strain(seed_det).astype(np.float64)
+    with threadpool_limits(limits=1):
+        t = time.perf_counter()
+        z = O.lloid_snr(d, sl, F0)
+        O.triggers(z, F0)
+        dt = time.perf_counter() - t
+    return M * seconds / dt, dt, f"{M} templates of the 1000-template family x 1 detector x {seconds} s " \
+                                 f"(oracle FP64 numpy LLOID + triggers, one thread)"
+
+
+def run_reference(args, rank, world, dist):
+    """The base contract's reference arm: the oracle, timed on host cores."""
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(M=REF_M, seconds=68)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, dt, sample = oracle_sample(M=REF_M, seconds=68)
+        vals.append(dt)
+    wall = time.perf_counter() - t0
+    value = REF_M * 68 * args.steps / sum(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: " + sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_lloid(args, rank, world, dist):
+    import numpy as np
+    import torch
+    import paper_2511_04730_b300 as P
+    from paper_2511_04730_b300 import build
+
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w, strain = make_inputs(args, rank)
+    bank, plan = w.banks[0], w.plans[0]
+    sb = P.build_svd_bank(bank, plan)
+    M = bank.n_templates
+    n_det = w.n_det
+    B = args.block_seconds * F0
+    T = strain.shape[1]
+    assert T % B == 0
+    n_blk = T // B
+    # blocks laid out [block][detector][sample] so that every step's input is contiguous
+    blocks = np.ascontiguousarray(strain.reshape(n_det, n_blk, B).transpose(1, 0, 2))
+    d_blocks = torch.from_numpy(blocks).to(f"cuda:{dev}")
+    h_blocks = torch.from_numpy(blocks).pin_memory()
+
+    def make_ctx(precision, timing):
+        return P.Context(n_detectors=n_det, precision=precision, max_block=B, max_history=64 * F0,
+                         device=dev, stage_timing=timing)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def run_steps(ctx, k_steps, pos, host=False, lat=None):
+        """k_steps timed steps; returns (ms per step list, pos, launches, h2d, d2h)."""
+        ext = torch.cuda.ExternalStream(ctx.stream_ptr, device=f"cuda:{dev}")
+        ms, h2d, d2h = [], 0, 0
+        l0 = ctx.launch_count()
+        with torch.cuda.stream(ext):
+            for _ in range(k_steps):
+                flush.fill_(pos & 0xFF)                       # L2 flush, outside the events
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                k = (pos // B) % n_blk
+                a.record(ext)
+                t_host = time.perf_counter()
+                if host:
+                    blk = h_blocks[k].numpy()                 # pinned host memory
+                    ctx.push_all(pos, blk)
+                    h2d += blk.nbytes
+                else:
+                    ctx.push_all(pos, d_blocks[k])
+                for win in range(pos // F0, (pos + B) // F0):
+                    tr = ctx.pull(win)
+                    d2h += 8 + tr.nbytes
+                b.record(ext)
+                b.synchronize()
+                if lat is not None:
+                    lat.append(1000 * (time.perf_counter() - t_host))
+                ms.append(a.elapsed_time(b))
+                pos += B
+        return ms, pos, ctx.launch_count() - l0, h2d, d2h
+
+    result = {}
+    per_ctx = {}
+    precisions = [args.precision] + ([] if args.no_fp32_compare or args.precision == "fp32" else ["fp32"])
+    clocks = None
+    for prec in precisions:
+        ctx = make_ctx(prec, timing=True)
+        bid = ctx.load_bank(sb)
+        pos = 0
+        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
+        ctx.stage_times(reset=True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev) if prec == args.precision else None
+        if sampler:
+            sampler.start()
+        ms, pos, launches, _, _ = run_steps(ctx, args.steps, pos)
+        torch.cuda.synchronize()
+        if sampler:
+            clocks = sampler.stop()
+        st = ctx.stage_times(reset=True)
+        per_ctx[prec] = {"ms": ms, "launches": launches, "stages": st}
+        ctx.close()
+
+    # accuracy of the measured path against the FP32 path (same stream, same blocks)
+    max_dsnr = None
+    if args.precision != "fp32" and not args.no_fp32_compare:
+        a, b = make_ctx(args.precision, False), make_ctx("fp32", False)
+        ia, ib = a.load_bank(sb), b.load_bank(sb)
+        max_dsnr = 0.0
+        for k in range((72 * F0) // B):
+            blk = d_blocks[k % n_blk]
+            a.push_all(k * B, blk)
+            b.push_all(k * B, blk)
+            if (k + 1) * B >= 64 * F0:
+                for det in range(n_det):
+                    za, _ = a.snr_block(det, ia)
+                    zb, _ = b.snr_block(det, ib)
+                    dz = torch.sqrt(((za - zb) ** 2).view(M, 2, -1).sum(1)).max().item()
+                    max_dsnr = max(max_dsnr, dz)
+        a.close()
+        b.close()
+
+    # end to end: host blocks in, triggers out, through the public API
+    e2e = None
+    if not args.no_e2e:
+        ctx = make_ctx(args.precision, False)
+        ctx.load_bank(sb)
+        pos = 0
+        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, host=True)
+        ms_e, pos, _, h2d, d2h = run_steps(ctx, args.steps, pos, host=True)
+        ctx.close()
+        e2e = {"value": M * args.block_seconds * n_det * args.steps / (sum(ms_e) / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    # per-block latency at 1 s blocks (block arrival on the host -> its window's triggers on the host)
+    lat = []
+    if args.latency_steps:
+        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=F0, max_history=64 * F0, device=dev)
+        ctx.load_bank(sb)
+        pos = 0
+        ext = torch.cuda.ExternalStream(ctx.stream_ptr, device=f"cuda:{dev}")
+        h_sec = torch.from_numpy(np.ascontiguousarray(
+            strain.reshape(n_det, T // F0, F0).transpose(1, 0, 2))).pin_memory()
+        for k in range(72 + args.latency_steps):
+            blk = h_sec[(pos // F0) % (T // F0)].numpy()
+            t0 = time.perf_counter()
+            ctx.push_all(pos, blk)
+            ctx.pull(pos // F0)
+            if k >= 72:
+                lat.append(1000 * (time.perf_counter() - t0))
+            pos += F0
+        ctx.close()
+
+    main = per_ctx[args.precision]
+    ms = main["ms"]
+    units = M * args.block_seconds * n_det
+    my_time = sum(ms) / 1000.0
+    if dist is not None:
+        t = torch.tensor([my_time], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        my_time = float(t.item())
+    value = units * args.steps * world / my_time
+
+    # roofline of the dominant kernel (stage with the largest device time)
+    stages = main["stages"]
+    dom = max(("fir", "upsample", "recon"), key=lambda k: stages[k][0])
+    dur_ms = stages[dom][0] / max(1, stages[dom][1])
+    work = algorithmic_work(sb, M)
+    det_s = args.block_seconds * n_det
+    pk, pk_kind = peaks()
+    if args.precision == "fp32":
+        bound, unit_p = "alu", "TFLOP/s"
+        peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        peak_note = "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock"
+    else:
+        bound, unit_p = "tensor", "TFLOP/s"
+        peak = pk["bf16_tflops_sustained"]
+        peak_note = f"{pk_kind} dense bf16 sustained (fp16 nominal rate equal)"
+    alg = {"fir": work["fir"], "upsample": work["ladder"], "recon": work["recon"] + work["max"]}[dom] * det_s
+    achieved = alg / (dur_ms / 1000.0) / 1e12
+    Kpad = -(-sum(s.n_basis for s in sb) // 64) * 64
+    Mpad = -(-M // 128) * 128
+    n_mma = {"fp32": 1, "fp16_split": 2, "bf16_split": 3}[args.precision]
+    executed = {"recon": 2.0 * 2 * Mpad * Kpad * F0 * det_s * n_mma}.get(dom)
+    roofline = {"kernel": {"recon": "k_recon_tc" if args.precision != "fp32" else "k_recon_f32",
+                           "fir": "k_fir_f32", "upsample": "k_upsample"}[dom],
+                "bound": bound, "achieved": achieved, "peak": peak, "unit": unit_p, "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_note,
+                "algorithmic_flop_per_launch": alg, "launch_ms": dur_ms}
+    if executed:
+        roofline["executed_tflops"] = executed / (dur_ms / 1000.0) / 1e12
+    stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items()}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, sample = oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp16_split": "f16", "bf16_split": "bf16"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_templates": M, "n_detectors": n_det,
+                       "block_seconds": args.block_seconds, "precision": args.precision,
+                       "l2": "flushed between steps (256 MB write, outside the timed events)",
+                       "bases_total": sum(s.n_basis for s in sb), "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": main["launches"], "clocks": clocks,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "max_dsnr_vs_fp32": max_dsnr,
+            "latency_ms_1s_blocks": ({"p50": statistics.median(lat),
+                                      "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
+                                      "n": len(lat)} if lat else None),
+            "stage_ms_per_step": stage_ms,
+            "paths": {p: units * args.steps / (sum(v["ms"]) / 1000.0) for p, v in per_ctx.items()},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, dist = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world, dist)
+    else:
+        run_lloid(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

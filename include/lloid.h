@@ -207,6 +207,20 @@ LLOID_API lloid_status lloid_synchronize(lloid_ctx* ctx);
 /* Number of kernel launches the context has issued so far. */
 LLOID_API int64_t lloid_launch_count(const lloid_ctx* ctx);
 
+/* The cudaStream_t every kernel of the context runs on (as void*), so that a
+ * caller can order its own work (e.g. the producer of a device block) with it. */
+LLOID_API void* lloid_stream(const lloid_ctx* ctx);
+
+/* Per-stage device time, measured with CUDA events recorded on the context's
+ * stream around every stage of every push and pull when cfg.flags has
+ * LLOID_FLAG_STAGE_TIMING.  Fills ms[i] (milliseconds) and launches[i] for the
+ * LLOID_N_STAGES stages (ingest, downsample, fir, upsample, recon, finalize,
+ * gather) accumulated since the last reset; reset != 0 clears them.  Waits
+ * for the context's stream.  Either output may be NULL. */
+#define LLOID_FLAG_STAGE_TIMING 1u
+#define LLOID_N_STAGES 7
+LLOID_API lloid_status lloid_stage_times(lloid_ctx* ctx, double* ms, int64_t* launches, int reset);
+
 #ifdef __cplusplus
 }
 #endif

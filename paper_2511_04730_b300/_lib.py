@@ -69,7 +69,14 @@ SIGNATURES = [
                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("lloid_synchronize", ctypes.c_int, [ctypes.c_void_p]),
     ("lloid_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("lloid_stream", ctypes.c_void_p, [ctypes.c_void_p]),
+    ("lloid_stage_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
 ]
+
+FLAG_STAGE_TIMING = 1
+N_STAGES = 7
+STAGE_NAMES = ("ingest", "downsample", "fir", "upsample", "recon", "finalize", "gather")
 
 _lib = None
 

@@ -134,6 +134,13 @@ struct lloid_ctx {
     cudaEvent_t done_ev = nullptr;
     int* d_err = nullptr;              // device-side wait-expiry code (0 = none)
     int n_sm = 0;
+
+    // stage timing (LLOID_FLAG_STAGE_TIMING)
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    double stage_ms[LLOID_N_STAGES] = {};
+    long long stage_launches[LLOID_N_STAGES] = {};
 };
 
 namespace {
@@ -302,6 +309,46 @@ lloid_status upload_vec(lloid_ctx* ctx, T** dst, const std::vector<T>& v) {
 
 bool split_precision(const lloid_ctx* ctx) { return ctx->cfg.precision != LLOID_FP32; }
 
+bool timing(const lloid_ctx* ctx) { return (ctx->cfg.flags & LLOID_FLAG_STAGE_TIMING) != 0; }
+
+lloid_status resolve_timers(lloid_ctx* ctx) {
+    if (ctx->pending.empty()) return LLOID_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.a, p.b));
+        ctx->stage_ms[p.stage] += ms;
+        ctx->ev_pool.push_back(p.a);
+        ctx->ev_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    return LLOID_OK;
+}
+
+// RAII pair of events around one stage's launches on the context stream.
+struct StageTimer {
+    lloid_ctx* ctx;
+    int stage;
+    cudaEvent_t a = nullptr, b = nullptr;
+    long long l0;
+    StageTimer(lloid_ctx* c, int s) : ctx(c), stage(s), l0(c->launches) {
+        if (!timing(ctx)) return;
+        if (ctx->pending.size() > 4096) resolve_timers(ctx);
+        for (cudaEvent_t* e : {&a, &b}) {
+            if (!ctx->ev_pool.empty()) { *e = ctx->ev_pool.back(); ctx->ev_pool.pop_back(); }
+            else cudaEventCreate(e);
+        }
+        cudaEventRecord(a, ctx->stream);
+    }
+    ~StageTimer() {
+        ctx->stage_launches[stage] += ctx->launches - l0;
+        if (!a) return;
+        cudaEventRecord(b, ctx->stream);
+        ctx->pending.push_back({stage, a, b});
+    }
+};
+
+
 // (Re)build the job tables for pushes of n samples.
 lloid_status build_jobs(lloid_ctx* ctx, long long n) {
     if (!ctx->jobs_dirty && ctx->jobs_n == n) return LLOID_OK;
@@ -446,6 +493,7 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     const int n_i = (int)n;
     // a0 ingest
     {
+        StageTimer tm(ctx, 0);
         dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 1024), nd);
         k_ingest<<<grid, 256, 0, ctx->stream>>>(src, src_det_stride, ctx->ring0, ctx->ring0_len,
                                                 (int)(ctx->ring0_len - 1), k_a, n_i, det0);
@@ -453,6 +501,7 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     }
     // a1 downsample to every rate
     {
+        StageTimer tm(ctx, 1);
         DownParams p{};
         p.n_rates = ctx->n_rates;
         for (int r = 0; r < ctx->n_rates; ++r) {
@@ -467,12 +516,14 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     if (ctx->banks.empty()) return LLOID_OK;
     // a2 basis FIR
     if (ctx->fir_tiles) {
+        StageTimer tm(ctx, 2);
         dim3 grid(ctx->fir_tiles, nd);
         k_fir_f32<<<grid, 256, 0, ctx->stream>>>(ctx->d_fir, ctx->d_fir_base, ctx->n_fir, k_a, det0);
         CKL();
     }
     // a4 (slice part) upsample each slice to Yhat
     if (ctx->up_tiles) {
+        StageTimer tm(ctx, 3);
         dim3 grid(ctx->up_tiles, nd);
         if (!split_precision(ctx))
             k_upsample<StoreF32><<<grid, 256, ctx->up_smem, ctx->stream>>>(ctx->d_up, ctx->d_up_base, ctx->n_up, k_a,
@@ -486,11 +537,15 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
         CKL();
     }
     // a3 + a5 reconstruction with fused window maxima
-    st = launch_recon(ctx, k_a, n, det0, nd, false, ctx->d_rec, ctx->d_maps, ctx->d_rec_base, ctx->n_rec,
+    {
+        StageTimer tm(ctx, 4);
+        st = launch_recon(ctx, k_a, n, det0, nd, false, ctx->d_rec, ctx->d_maps, ctx->d_rec_base, ctx->n_rec,
                       ctx->rec_tiles, nullptr);
+    }
     if (st) return st;
     // a5 finalise completed windows
     const long long W = ctx->cfg.window_samples;
+    StageTimer tmf(ctx, 5);
     for (long long w = k_a / W; (w + 1) * W <= k_a + n; ++w) {
         SlabEntry* slab = ctx->d_slab + (size_t)(w % kWindowRing) * ctx->cfg.n_detectors * ctx->M_cap;
         dim3 grid(ctx->n_fin, nd);
@@ -606,6 +661,20 @@ const char* lloid_last_error(const lloid_ctx* ctx) { return ctx ? ctx->err.c_str
 
 int64_t lloid_launch_count(const lloid_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+void* lloid_stream(const lloid_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+lloid_status lloid_stage_times(lloid_ctx* ctx, double* ms, int64_t* launches, int reset) {
+    if (!ctx) return LLOID_EINVAL;
+    lloid_status st = resolve_timers(ctx);
+    if (st) return st;
+    for (int i = 0; i < LLOID_N_STAGES; ++i) {
+        if (ms) ms[i] = ctx->stage_ms[i];
+        if (launches) launches[i] = ctx->stage_launches[i];
+        if (reset) { ctx->stage_ms[i] = 0; ctx->stage_launches[i] = 0; }
+    }
+    return LLOID_OK;
+}
+
 lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
     if (!out) return LLOID_EINVAL;
     *out = nullptr;
@@ -689,6 +758,8 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
     cudaFree(ctx->d_err);
     if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
+    for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -906,6 +977,7 @@ lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid_trigger* 
     const SlabEntry* slab = ctx->d_slab + (size_t)(window % kWindowRing) * nd * ctx->M_cap;
     const long long total = (long long)nd * M_used;
     const int chunks = (int)((total + 1023) / 1024);
+    StageTimer tmg(ctx, 6);
     k_gather_count<<<chunks, 1024, 0, ctx->stream>>>(slab, ctx->M_cap, M_used, nd, ctx->d_counts);
     CKL();
     k_gather_scatter<<<chunks, 1024, 0, ctx->stream>>>(slab, ctx->M_cap, M_used, nd, ctx->d_counts, chunks,

@@ -41,7 +41,7 @@ class Context:
     def __init__(self, n_detectors: int = 1, precision: str = "fp32", max_block: int = 16384,
                  max_history: Optional[int] = None, window: int = 2048, threshold: float = 4.0,
                  device: int = 0, stream=None, hbm_budget: int = 0, f0: int = 2048, min_rate: int = 32,
-                 n_down: int = 32, n_up: int = 8):
+                 n_down: int = 32, n_up: int = 8, stage_timing: bool = False):
         self._lib = _lib.load()
         cfg = default_config()
         cfg.f0, cfg.n_detectors, cfg.n_down, cfg.n_up = f0, n_detectors, n_down, n_up
@@ -52,6 +52,7 @@ class Context:
             cfg.max_history = max_history
         cfg.min_rate, cfg.device, cfg.hbm_budget_bytes = min_rate, device, hbm_budget
         cfg.cuda_stream = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        cfg.flags = _lib.FLAG_STAGE_TIMING if stage_timing else 0
         self.cfg = cfg
         self.precision = precision
         self.n_detectors = n_detectors
@@ -62,6 +63,8 @@ class Context:
             raise LloidError(st, "lloid_create failed (bad configuration or device error)")
         self._h = h
         self.banks = {}
+        self.stream_ptr = int(self._lib.lloid_stream(h) or 0)
+        self._ext_stream = None
 
     # -- helpers --------------------------------------------------------------
     def _check(self, st: int):
@@ -129,12 +132,25 @@ class Context:
             raise ValueError("blocks must be contiguous float32 numpy arrays or torch tensors")
         return block.data_ptr(), block.shape[-1], 1 if block.is_cuda else 0
 
+    def _after_torch(self):
+        """Order the library stream after torch's current stream (device inputs/outputs)."""
+        import torch
+        if self._ext_stream is None:
+            self._ext_stream = torch.cuda.ExternalStream(self.stream_ptr, device=f"cuda:{self.cfg.device}")
+        cur = torch.cuda.current_stream(self.cfg.device)
+        if cur.cuda_stream != self.stream_ptr:
+            self._ext_stream.wait_stream(cur)
+
     def push(self, det: int, t0: int, block):
         p, n, dev = self._ptr(block)
+        if dev:
+            self._after_torch()
         self._check(self._lib.lloid_push_strain(self._h, det, t0, ctypes.c_void_p(p), n, dev))
 
     def push_all(self, t0: int, blocks):
         p, n, dev = self._ptr(blocks)
+        if dev:
+            self._after_torch()
         self._check(self._lib.lloid_push_strain_all(self._h, t0, ctypes.c_void_p(p), n, dev))
 
     def pull(self, window: int, timeout_ms: int = -1, cap: int = 1 << 16) -> np.ndarray:
@@ -162,6 +178,7 @@ class Context:
         if st not in (0, -8):
             self._check(st)
         out = torch.empty((2 * M, int(n.value)), dtype=torch.float32, device=f"cuda:{self.cfg.device}")
+        self._after_torch()
         self._check(self._lib.lloid_snr_block(self._h, det, bank, ctypes.c_void_p(out.data_ptr()), out.numel(),
                                               ctypes.byref(t0), ctypes.byref(n)))
         return out, int(t0.value)
@@ -171,3 +188,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._lib.lloid_launch_count(self._h))
+
+    def stage_times(self, reset: bool = False) -> dict:
+        """{stage: (milliseconds, launches)} since the last reset (needs stage_timing=True)."""
+        ms = (ctypes.c_double * _lib.N_STAGES)()
+        ln = (ctypes.c_int64 * _lib.N_STAGES)()
+        self._check(self._lib.lloid_stage_times(self._h, ms, ln, 1 if reset else 0))
+        return {name: (ms[i], int(ln[i])) for i, name in enumerate(_lib.STAGE_NAMES)}

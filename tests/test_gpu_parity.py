@@ -64,9 +64,11 @@ def test_trigger_parity_bank64(lloid, bank64_case, precision):
     sb = lloid.build_svd_bank(bank, plan)
     with _ctx(lloid, precision) as ctx:
         bid = ctx.load_bank(sb)
+        got = []
         for t in range(0, d.size, 4096):
             ctx.push(0, t, d[t:t + 4096].copy())
-        trig = np.concatenate([ctx.pull(win) for win in range(d.size // F0)])
+            got += [ctx.pull(win) for win in range(t // F0, (t + 4096) // F0)]
+        trig = np.concatenate(got)
     otr = O.triggers(z_or, F0)
     assert len(trig) > 0
     problems = compare_triggers(trig, otr, z_or, TOL[precision], F0)
@@ -168,8 +170,10 @@ def test_error_codes(lloid, bank64_case):
             ctx.pull(1)                                 # window 1 not pushed yet
         assert e.value.name == "LLOID_ENOTREADY"
         ctx.pull(0)
-        # pre-synchronisation violated: 256 Hz slice starting 1 ms before merger
-        bad = [sb[0], lloid.SliceArrays(256, 8, sb[1].bases, sb[1].coeffs, 1.0)]
+        # pre-synchronisation violated: a 256 Hz slice needs J >= 8 (N_down + N_up) = 320
+        bad = [lloid.SliceArrays(256, 312, sb[1].bases, sb[1].coeffs, 1.0)]
+        ok = [lloid.SliceArrays(256, 320, sb[1].bases, sb[1].coeffs, 1.0)]
+        ctx.load_bank(ok)
         with pytest.raises(lloid.LloidError) as e:
             ctx.load_bank(bad)
         assert e.value.name == "LLOID_EINVAL" and "pre-synchronisation" in str(e.value)

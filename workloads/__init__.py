@@ -144,12 +144,13 @@ class ChirpBank:
     def n_rows(self) -> int:
         return 2 * self.n_templates
 
-    def _raw(self, j):
+    def _raw(self, j, which=None):
         j = np.asarray(j, dtype=np.int64)
-        M = self.mchirp.size
-        out = np.zeros((2 * M, j.size), dtype=np.float64)
+        idx = range(self.mchirp.size) if which is None else list(which)
+        out = np.zeros((2 * len(idx), j.size), dtype=np.float64)
         tau = j / float(self.f0)
-        for i, mc in enumerate(self.mchirp):
+        for o, i in enumerate(idx):
+            mc = self.mchirp[i]
             sel = (j >= self.j_lo[i]) & (j < self.j_hi[i])
             if not np.any(sel):
                 continue
@@ -157,15 +158,17 @@ class ChirpBank:
             amp = t ** -0.25
             ph = phase_of_tau(t, mc)
             win = _tukey(int(self.j_hi[i] - self.j_lo[i]), j[sel] - self.j_lo[i])
-            out[2 * i, sel] = amp * np.cos(ph) * win
-            out[2 * i + 1, sel] = amp * np.sin(ph) * win
+            out[2 * o, sel] = amp * np.cos(ph) * win
+            out[2 * o + 1, sel] = amp * np.sin(ph) * win
         return out
 
-    def rows(self, j) -> np.ndarray:
-        """FP64 samples [2M, len(j)] of the unit-norm rows at before-merger indices j."""
-        r = self._raw(j)
-        r[0::2] /= self.norm_c[:, None]
-        r[1::2] /= self.norm_s[:, None]
+    def rows(self, j, which=None) -> np.ndarray:
+        """FP64 samples [2M, len(j)] of the unit-norm rows at before-merger
+        indices j (only templates ``which``, in that order, if given)."""
+        r = self._raw(j, which)
+        idx = np.arange(self.mchirp.size) if which is None else np.asarray(list(which))
+        r[0::2] /= self.norm_c[idx, None]
+        r[1::2] /= self.norm_s[idx, None]
         return r
 
     def full(self) -> np.ndarray:
@@ -278,8 +281,8 @@ def add_injection(strain: np.ndarray, bank: ChirpBank, inj: Injection) -> None:
     j = np.arange(int(bank.j_lo[i]), int(bank.j_hi[i]))
     j = j[inj.end_sample - j >= 0]
     j = j[inj.end_sample - j < strain.size]
-    bank_rows = bank.rows(j)
-    sig = inj.snr * (math.cos(inj.phase) * bank_rows[2 * i] + math.sin(inj.phase) * bank_rows[2 * i + 1])
+    r = bank.rows(j, [i])
+    sig = inj.snr * (math.cos(inj.phase) * r[0] + math.sin(inj.phase) * r[1])
     np.add.at(strain, inj.end_sample - j, sig.astype(strain.dtype))
 
 
