@@ -161,19 +161,18 @@ def oracle_sample(M=64, seconds=68, seed_det=0):
     worth of the 1000-template family (same Mc range, same slicing rule), one
     detector, `seconds` of data (64 s of template history + 4 s)."""
     import numpy as np
-    from threadpoolctl import threadpool_limits
     import workloads as W
     from oracle import lloid_oracle as O
     w = W.make_workload("bank1000", n_templates=M, n_seconds=seconds, n_det=1, n_inj=1)
     sl = O.svd_bank(w.banks[0], w.plans[0])
     d = w.strain(seed_det).astype(np.float64)
-    with threadpool_limits(limits=1):
-        t = time.perf_counter()
-        z = O.lloid_snr(d, sl, F0)
-        O.triggers(z, F0)
-        dt = time.perf_counter() - t
+    t, c = time.perf_counter(), time.process_time()
+    z = O.lloid_snr(d, sl, F0)
+    O.triggers(z, F0)
+    dt, dc = time.perf_counter() - t, time.process_time() - c
+    cores = max(1, round(dc / dt, 1))          # threads actually busy (CPU time / wall time)
     return M * seconds / dt, dt, f"{M} templates of the 1000-template family x 1 detector x {seconds} s " \
-                                 f"(oracle FP64 numpy LLOID + triggers, one thread)"
+                                 f"(oracle FP64 numpy LLOID + triggers)", cores
 
 
 def run_reference(args, rank, world, dist):
@@ -181,19 +180,21 @@ def run_reference(args, rank, world, dist):
     if rank != 0:
         return
     vals = []
+    cores = []
     for _ in range(args.warmup):
         oracle_sample(M=REF_M, seconds=68)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, dt, sample = oracle_sample(M=REF_M, seconds=68)
+        v, dt, sample, c = oracle_sample(M=REF_M, seconds=68)
         vals.append(dt)
+        cores.append(c)
     wall = time.perf_counter() - t0
     value = REF_M * 68 * args.steps / sum(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(cores), "kind": "oracle",
                              "sample": "each step: " + sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -377,8 +378,8 @@ def run_lloid(args, rank, world, dist):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, dt, sample = oracle_sample()
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": dt}
+        v, dt, sample, cores = oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample, "seconds": dt}
 
     if rank == 0:
         line = {

@@ -146,12 +146,16 @@ class Context:
         if dev:
             self._after_torch()
         self._check(self._lib.lloid_push_strain(self._h, det, t0, ctypes.c_void_p(p), n, dev))
+        if dev:
+            block.record_stream(self._ext_stream)     # keep the memory until the library read it
 
     def push_all(self, t0: int, blocks):
         p, n, dev = self._ptr(blocks)
         if dev:
             self._after_torch()
         self._check(self._lib.lloid_push_strain_all(self._h, t0, ctypes.c_void_p(p), n, dev))
+        if dev:
+            blocks.record_stream(self._ext_stream)
 
     def pull(self, window: int, timeout_ms: int = -1, cap: int = 1 << 16) -> np.ndarray:
         """Triggers of one window as a numpy structured array (TRIGGER_DTYPE)."""
