@@ -353,27 +353,30 @@ def run_lloid(args, rank, world, dist):
     work = algorithmic_work(sb, M)
     det_s = args.block_seconds * n_det
     pk, pk_kind = peaks()
-    if args.precision == "fp32":
-        bound, unit_p = "alu", "TFLOP/s"
-        peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        peak_note = "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock"
-    else:
-        bound, unit_p = "tensor", "TFLOP/s"
-        peak = pk["bf16_tflops_sustained"]
-        peak_note = f"{pk_kind} dense bf16 sustained (fp16 nominal rate equal)"
-    alg = {"fir": work["fir"], "upsample": work["ladder"], "recon": work["recon"] + work["max"]}[dom] * det_s
+    alu_peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    tc = args.precision != "fp32"
+    kinds = {   # stage -> (kernel, bound, peak, peak note, algorithmic flop per detector-second)
+        "fir": ("k_fir_f32", "alu", alu_peak, "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock", work["fir"]),
+        "upsample": ("k_upsample_t" if tc else "k_upsample", "alu", alu_peak,
+                     "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock", work["ladder"]),
+        "recon": (("k_recon_tc", "tensor", pk["bf16_tflops_sustained"],
+                   f"{pk_kind} dense bf16 sustained x 1 (fp16 nominal rate equal)") if tc else
+                  ("k_recon_f32", "alu", alu_peak, "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock"))
+                 + (work["recon"] + work["max"],),
+    }
+    kname, bound, peak, peak_note, per_dets = kinds[dom]
+    alg = per_dets * det_s
     achieved = alg / (dur_ms / 1000.0) / 1e12
     Kpad = -(-sum(s.n_basis for s in sb) // 64) * 64
     Mpad = -(-M // 128) * 128
     n_mma = {"fp32": 1, "fp16_split": 2, "bf16_split": 3}[args.precision]
-    executed = {"recon": 2.0 * 2 * Mpad * Kpad * F0 * det_s * n_mma}.get(dom)
-    roofline = {"kernel": {"recon": "k_recon_tc" if args.precision != "fp32" else "k_recon_f32",
-                           "fir": "k_fir_f32", "upsample": "k_upsample"}[dom],
-                "bound": bound, "achieved": achieved, "peak": peak, "unit": unit_p, "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_note,
+    roofline = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
                 "algorithmic_flop_per_launch": alg, "launch_ms": dur_ms}
-    if executed:
-        roofline["executed_tflops"] = executed / (dur_ms / 1000.0) / 1e12
+    rec_ms = stages["recon"][0] / max(1, stages["recon"][1])
+    executed_recon = 2.0 * 2 * Mpad * Kpad * F0 * det_s * n_mma
+    recon_info = {"launch_ms": rec_ms, "executed_tflops": executed_recon / (rec_ms / 1000.0) / 1e12,
+                  "algorithmic_tflops": (work["recon"] + work["max"]) * det_s / (rec_ms / 1000.0) / 1e12}
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items()}
 
     cpu = None
@@ -399,6 +402,7 @@ def run_lloid(args, rank, world, dist):
                                       "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
                                       "n": len(lat)} if lat else None),
             "stage_ms_per_step": stage_ms,
+            "recon_kernel": recon_info,
             "paths": {p: units * args.steps / (sum(v["ms"]) / 1000.0) for p, v in per_ctx.items()},
         }
         print(json.dumps(line), flush=True)

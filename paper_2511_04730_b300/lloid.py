@@ -141,13 +141,22 @@ class Context:
         if cur.cuda_stream != self.stream_ptr:
             self._ext_stream.wait_stream(cur)
 
+    def _torch_after(self):
+        """Order torch's current stream after the library's reads of a device
+        block, so the caching allocator cannot hand the block's memory to new
+        work before the library has consumed it."""
+        import torch
+        cur = torch.cuda.current_stream(self.cfg.device)
+        if cur.cuda_stream != self.stream_ptr:
+            cur.wait_stream(self._ext_stream)
+
     def push(self, det: int, t0: int, block):
         p, n, dev = self._ptr(block)
         if dev:
             self._after_torch()
         self._check(self._lib.lloid_push_strain(self._h, det, t0, ctypes.c_void_p(p), n, dev))
         if dev:
-            block.record_stream(self._ext_stream)     # keep the memory until the library read it
+            self._torch_after()
 
     def push_all(self, t0: int, blocks):
         p, n, dev = self._ptr(blocks)
@@ -155,7 +164,7 @@ class Context:
             self._after_torch()
         self._check(self._lib.lloid_push_strain_all(self._h, t0, ctypes.c_void_p(p), n, dev))
         if dev:
-            blocks.record_stream(self._ext_stream)
+            self._torch_after()
 
     def pull(self, window: int, timeout_ms: int = -1, cap: int = 1 << 16) -> np.ndarray:
         """Triggers of one window as a numpy structured array (TRIGGER_DTYPE)."""
