@@ -24,13 +24,27 @@ __device__ __forceinline__ int find_job(const int* __restrict__ tile_base, int n
 // ---------------------------------------------------------------------------
 // a0: block -> full-rate ring
 // ---------------------------------------------------------------------------
+// Split paths (mode 1 FP16, 2 BF16) also write hi/lo halves to a double-mapped
+// ring: sample k at k mod s_len and k mod s_len + s_len.
 __global__ void k_ingest(const float* __restrict__ src, long long src_det_stride, float* __restrict__ ring,
-                         long long ring_det_stride, int mask, long long k_a, int n, int det0) {
+                         long long ring_det_stride, int mask, long long k_a, int n, int det0,
+                         uint16_t* __restrict__ s_hi, uint16_t* __restrict__ s_lo, long long s_det_stride,
+                         int s_len, int mode) {
     const int det = blockIdx.y;
     const float* s = src + det * src_det_stride;
     float* r = ring + (det0 + det) * ring_det_stride;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        r[(k_a + i) & mask] = s[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float v = s[i];
+        r[(k_a + i) & mask] = v;
+        if (mode) {
+            uint16_t h, l;
+            split_hilo_rt(v, mode, h, l);
+            const long long p = (k_a + i) & (s_len - 1);
+            const long long o = (det0 + det) * s_det_stride;
+            s_hi[o + p] = h; s_hi[o + p + s_len] = h;
+            s_lo[o + p] = l; s_lo[o + p + s_len] = l;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -44,7 +58,12 @@ struct DownParams {
     long long dst_det_stride[kMaxRates];
     int dst_mask[kMaxRates];
     int D[kMaxRates];
+    uint16_t* s_hi[kMaxRates];          // split paths: hi/lo double-mapped rings
+    uint16_t* s_lo[kMaxRates];
+    long long s_det_stride[kMaxRates];
+    int s_len[kMaxRates];
     int n_rates;
+    int mode;                           // 0 FP32 only, 1 FP16, 2 BF16
 };
 
 __global__ void k_downsample(DownParams p, const float* __restrict__ ring0, long long ring0_det_stride,
@@ -67,7 +86,17 @@ __global__ void k_downsample(DownParams p, const float* __restrict__ ring0, long
     for (int k = lane; k < taps; k += 32) acc = fmaf(__ldg(w + k), src[(base - k) & mask0], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) p.dst[r][det * p.dst_det_stride[r] + (q & p.dst_mask[r])] = acc;
+    if (lane == 0) {
+        p.dst[r][det * p.dst_det_stride[r] + (q & p.dst_mask[r])] = acc;
+        if (p.mode) {
+            uint16_t h, l;
+            split_hilo_rt(acc, p.mode, h, l);
+            const long long ps = q & (p.s_len[r] - 1);
+            const long long o = det * p.s_det_stride[r];
+            p.s_hi[r][o + ps] = h; p.s_hi[r][o + ps + p.s_len[r]] = h;
+            p.s_lo[r][o + ps] = l; p.s_lo[r][o + ps + p.s_len[r]] = l;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

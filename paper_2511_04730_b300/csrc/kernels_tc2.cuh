@@ -1,0 +1,589 @@
+// Tensor-core (tcgen05) basis filter and per-rate reconstruction for the
+// split-precision paths, in the paper's order (Eq. 5, Eq. 6, Eq. 7-9).
+//
+// k_fir_tc  (a2): Y^s_l[q] = sum_m u_l[m] x[q - m] as a GEMM over 8 output
+//   phases: q = 8c + t, A'[(l,t)][j] = u_l[t + N' - 1 - j] (bases expanded
+//   over the 8 phases, zero outside the filter), B'[c][j] = x[8c - N' + 1 + j].
+//   B' rows are 16 bytes apart in a contiguous strip of the stream, so the
+//   strip itself is the operand: a no-swizzle K-major descriptor whose
+//   K-adjacent core matrices are 16 B apart (LBO) and N-adjacent 128 B apart
+//   (SBO).  Nothing is materialised; the strip (hi and lo halves) is one bulk
+//   copy per tile, the expanded bases stream through a TMA pipeline.  The
+//   epilogue writes Y (hi/lo) into the level's operand ring through a
+//   shared-memory transpose (rows = time, columns = bases).
+//
+// k_level_tc (a3 + a4 + a5): for ladder level j (rate r_j, lowest first)
+//   Acc_j[q] = C_j Y_j[q] + Up_F(Acc_{j-1})[q], Up of Eq. 8 in its centred
+//   reading; Acc is kept transposed ([q][template], templates contiguous) so
+//   that the epilogue's reads and writes coalesce.  The top level (f0) forms
+//   |z|^2 and the per-tile argmax instead of storing Acc.
+#pragma once
+#include "kernels_tc.cuh"
+
+namespace lloid {
+
+constexpr int kFirNC = 128;       // max c-groups per FIR tile (1024 outputs)
+constexpr int kEpiThreads = 128;  // epilogue warps 2..5
+
+// ---------------------------------------------------------------------------
+struct FirTcJob {
+    const uint16_t* s_hi;          // stream ring (double-mapped) of this rate, detector 0
+    const uint16_t* s_lo;
+    long long s_det_stride;        // elements
+    uint16_t* y_hi;                // level ring, first column of this slice, detector 0
+    uint16_t* y_lo;
+    long long y_det_stride;        // elements
+    long long J_over_D;
+    int s_len;                     // stream ring length (power of two); 2*s_len stored
+    int y_rows;                    // level ring rows (power of two); 2*y_rows stored
+    int y_ld;                      // level ring row length (Kpad of the level)
+    int Mtiles;                    // M'pad / 128 (16 bases per tile)
+    int Kp;                        // K'pad (multiple of 64)
+    int Np;                        // N' (padded filter length)
+    int NC;                        // c-groups per tile (multiple of 16, <= kFirNC)
+    int ctiles;                    // c tiles per push
+    int D, Lambda, q_count, map;   // map = index into the FIR tensor-map array
+};
+
+struct LevelJob {
+    const float* acc_in;           // level below, transposed [2][rows][Mpad], detector 0
+    float* acc_out;                // this level (non-top), transposed, detector 0
+    long long acc_in_det_stride, acc_out_det_stride;   // elements
+    const float* upz;              // [F][2 N_up + 1] polyphase sub-kernels (Eq. 7)
+    int acc_in_rows, acc_out_rows; // rows per re/im plane
+    int Kp;                        // Kpad of the level (0: no slice at this rate)
+    int M, Mpad, tmpl0;
+    int tiles_m, tiles_t;
+    int D, Lambda;                 // this level
+    int F, D_lo, Lambda_lo;        // factor to the level below (0: lowest level)
+    int y_rows;                    // level ring rows
+    int map;                       // index into the level tensor-map array
+};
+
+struct FirMaps { CUtensorMap a, a_lo; };
+struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo; };
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t desc_nosw(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;
+    return d;   // layout type 0: no swizzle
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+
+__device__ __forceinline__ int job_of(const int* __restrict__ base, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(base + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ long long fdiv(long long a, long long b) {
+    long long q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+template <typename T>
+__device__ __forceinline__ uint16_t h_bits(T v) { return *reinterpret_cast<uint16_t*>(&v); }
+
+template <bool BF16>
+__device__ __forceinline__ void split_hilo(float v, uint16_t& hi, uint16_t& lo) {
+    if (BF16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi = h_bits(h);
+        lo = h_bits(__float2bfloat16_rn(v - __bfloat162float(h)));
+    } else {
+        __half h = __float2half_rn(v);
+        hi = h_bits(h);
+        lo = h_bits(__float2half_rn(v - __half2float(h)));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a2 on the tensor cores
+// ---------------------------------------------------------------------------
+template <bool BF16>
+struct FirCfg {
+    static constexpr int STAGES = 4;
+    static constexpr int TILE_A = 128 * kTcK * 2;              // 16 KB
+    static constexpr int STAGE_BYTES = (BF16 ? 2 : 1) * TILE_A;
+    static constexpr int STAGE_AREA = STAGES * STAGE_BYTES;
+    static constexpr int EPI_BYTES = 2 * 256 * 16 * 2;         // staging [256 q][16 bases] hi + lo
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(192, 1)
+    k_fir_tc(const FirTcJob* __restrict__ jobs, const FirMaps* __restrict__ maps, const int* __restrict__ tile_base,
+             int n_jobs, int tiles_per_det, long long k_a, int det0, int n_det_push, int strip_bytes,
+             int* __restrict__ err) {
+    using C = FirCfg<BF16>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* stage_area = smem;
+    uint8_t* strip_area = smem + C::STAGE_AREA;                // 2 buffers x (hi, lo) x strip_bytes
+    uint16_t* epi = reinterpret_cast<uint16_t*>(strip_area + 4 * strip_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(epi) + C::EPI_BYTES);
+    uint64_t* a_full = bars;
+    uint64_t* a_empty = a_full + C::STAGES;
+    uint64_t* s_full = a_empty + C::STAGES;
+    uint64_t* s_empty = s_full + 2;
+    uint64_t* t_full = s_empty + 2;
+    uint64_t* t_empty = t_full + 2;
+    uint64_t* drain = t_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) { mbar_init(a_full + s, 1); mbar_init(a_empty + s, 1); }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(s_full + b, 1); mbar_init(s_empty + b, 1);
+            mbar_init(t_full + b, 1); mbar_init(t_empty + b, kEpiThreads);
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int total = tiles_per_det * n_det_push;
+
+    if (warp == 0) {
+        if (lane == 0) {   // ------------------------------------------------ producer
+            int stage = 0, sb = 0;
+            uint32_t phase = 0, sphase = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < total && ok; it += gridDim.x) {
+                const int det = det0 + it / tiles_per_det;
+                const int t = it % tiles_per_det;
+                const int jx = job_of(tile_base, n_jobs, t);
+                const FirTcJob& jb = jobs[jx];
+                const int local = t - tile_base[jx];
+                const int mt = local % jb.Mtiles, ct = local / jb.Mtiles;
+                const long long qa = fdiv(k_a - 1 + jb.Lambda, jb.D) + 1;
+                const long long c0 = fdiv(qa, 8) + (long long)ct * jb.NC;
+                const long long i0 = 8 * c0 - jb.Np + 1 - jb.J_over_D;       // multiple of 8
+                const long long p0 = i0 & (jb.s_len - 1);
+                const uint32_t bytes = (uint32_t)(2 * (8 * jb.NC + jb.Kp));
+                if (!mbar_wait(s_empty + sb, sphase ^ 1, err, 21)) { ok = false; break; }
+                mbar_expect_tx(s_full + sb, 2 * bytes);
+                bulk_g2s(strip_area + (2 * sb) * strip_bytes, jb.s_hi + det * jb.s_det_stride + p0, bytes, s_full + sb);
+                bulk_g2s(strip_area + (2 * sb + 1) * strip_bytes, jb.s_lo + det * jb.s_det_stride + p0, bytes,
+                         s_full + sb);
+                if (++sb == 2) { sb = 0; sphase ^= 1; }
+                const FirMaps* mp = maps + jb.map;
+                for (int kc = 0; kc < jb.Kp; kc += kTcK) {
+                    if (!mbar_wait(a_empty + stage, phase ^ 1, err, 22)) { ok = false; break; }
+                    uint8_t* st = stage_area + stage * C::STAGE_BYTES;
+                    mbar_expect_tx(a_full + stage, C::STAGE_BYTES);
+                    tma_load_2d(st, &mp->a, a_full + stage, kc, mt * 128);
+                    if (BF16) tma_load_2d(st + C::TILE_A, &mp->a_lo, a_full + stage, kc, mt * 128);
+                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                }
+            }
+            for (int s = 0; s < C::STAGES; ++s) {                 // drain the A stages
+                if (!mbar_wait(a_empty + stage, phase ^ 1, err, 23)) break;
+                if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+            }
+            for (int s = 0; s < 2; ++s) {                         // and the strips
+                if (!mbar_wait(s_empty + sb, sphase ^ 1, err, 24)) break;
+                if (++sb == 2) { sb = 0; sphase ^= 1; }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ------------------------------------------------ MMA issuer
+            int stage = 0, sb = 0, i = 0;
+            uint32_t phase = 0, sphase = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < total && ok; it += gridDim.x, ++i) {
+                const int t = it % tiles_per_det;
+                const int jx = job_of(tile_base, n_jobs, t);
+                const int Kp = jobs[jx].Kp, NC = jobs[jx].NC;
+                const uint32_t idesc = idesc_f16(BF16, 128, NC);
+                const int buf = i & 1;
+                if (!mbar_wait(t_empty + buf, ((i >> 1) & 1) ^ 1, err, 25)) { ok = false; break; }
+                if (!mbar_wait(s_full + sb, sphase, err, 26)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + buf * 128;
+                const uint32_t s_hi = smem_u32(strip_area + (2 * sb) * strip_bytes);
+                const uint32_t s_lo = smem_u32(strip_area + (2 * sb + 1) * strip_bytes);
+                for (int kc = 0; kc < Kp; kc += kTcK) {
+                    if (!mbar_wait(a_full + stage, phase, err, 27)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(stage_area + stage * C::STAGE_BYTES);
+#pragma unroll
+                    for (int k = 0; k < kTcK / 16; ++k) {
+                        const uint32_t boff = 2 * (kc + 16 * k);
+                        const uint64_t da = desc_sw128(a + 32 * k);
+                        const uint64_t bh = desc_nosw(s_hi + boff, 16, 128);
+                        const uint64_t bl = desc_nosw(s_lo + boff, 16, 128);
+                        umma_f16(d, da, bh, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                        umma_f16(d, da, bl, idesc, 1u);
+                        if (BF16) umma_f16(d, desc_sw128(a + C::TILE_A + 32 * k), bh, idesc, 1u);
+                    }
+                    umma_commit(a_empty + stage);
+                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                umma_commit(s_empty + sb);
+                umma_commit(t_full + buf);
+                if (++sb == 2) { sb = 0; sphase ^= 1; }
+            }
+            umma_commit(drain);
+            mbar_wait(drain, 0, err, 28);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int et = threadIdx.x - 64;                // 0..127
+        const int qd = warp & 3;                        // TMEM lane quarter
+        const int row = qd * 32 + lane;                 // A' row in the tile = 8 l + t
+        const int l_loc = row >> 3, tph = row & 7;
+        int i = 0;
+        for (int it = blockIdx.x; it < total; it += gridDim.x, ++i) {
+            const int det = det0 + it / tiles_per_det;
+            const int t = it % tiles_per_det;
+            const int jx = job_of(tile_base, n_jobs, t);
+            const FirTcJob& jb = jobs[jx];
+            const int local = t - tile_base[jx];
+            const int mt = local % jb.Mtiles, ct = local / jb.Mtiles;
+            const long long qa = fdiv(k_a - 1 + jb.Lambda, jb.D) + 1;
+            const long long c0 = fdiv(qa, 8) + (long long)ct * jb.NC;
+            const int buf = i & 1;
+            const bool got = mbar_wait(t_full + buf, (i >> 1) & 1, err, 29);
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc_fence_after();
+            uint16_t* yh = jb.y_hi + det * jb.y_det_stride + mt * 16;
+            uint16_t* yl = jb.y_lo + det * jb.y_det_stride + mt * 16;
+            for (int cc = 0; cc < jb.NC; cc += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + buf * 128 + cc, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    uint16_t h, l;
+                    split_hilo<BF16>(v[j], h, l);
+                    epi[(8 * j + tph) * 16 + l_loc] = h;
+                    epi[256 * 16 + (8 * j + tph) * 16 + l_loc] = l;
+                }
+                epi_sync();
+                // 256 rows x 32 B (hi) + 256 x 32 B (lo) as 16-byte stores, both ring mappings
+                for (int e = et; e < 2 * 256 * 2; e += kEpiThreads) {
+                    const int part = e >> 9;             // 0 hi, 1 lo
+                    const int r = (e >> 1) & 255, h16 = e & 1;
+                    const long long q = 8 * (c0 + cc) + r;
+                    if (cc + (r >> 3) >= jb.NC || q < qa || q >= qa + jb.q_count) continue;
+                    const uint4 val = *reinterpret_cast<const uint4*>(epi + part * 256 * 16 + r * 16 + h16 * 8);
+                    uint16_t* dst = part ? yl : yh;
+                    const long long rr = q & (jb.y_rows - 1);
+                    *reinterpret_cast<uint4*>(dst + rr * jb.y_ld + h16 * 8) = val;
+                    *reinterpret_cast<uint4*>(dst + (rr + jb.y_rows) * jb.y_ld + h16 * 8) = val;
+                }
+                epi_sync();
+            }
+            tc_fence_before();
+            mbar_arrive(t_empty + buf);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3 + a4 + a5 per ladder level
+// ---------------------------------------------------------------------------
+template <bool BF16>
+struct LevCfg {
+    static constexpr int NA = BF16 ? 4 : 2;
+    static constexpr int STAGES = BF16 ? 2 : 3;
+    static constexpr int TILE_A = kTcTileM * kTcK * 2;
+    static constexpr int TILE_B = kTcTileN * kTcK * 2;
+    static constexpr int STAGE_BYTES = NA * TILE_A + 2 * TILE_B;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+// Up_F of the level below for 32 consecutive outputs q0..q0+31 of one
+// template (column m of the transposed plane), added into v[].
+// Eq. 8 centred: Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
+// Level tiles start at multiples of 128, so q0 mod F is PH0 = 0 for F <= 32
+// and 0 or 32 for F = 64: every register index below is a compile-time constant.
+template <int F, int NUP, int PH0>
+__device__ __forceinline__ void add_up32(float (&v)[32], const float* __restrict__ plane, int Mpad, int m,
+                                         long long q0, long long lo_in, int rows_in, const float* __restrict__ z) {
+    constexpr int NW = (PH0 + 31) / F + 2 * NUP + 1;
+    const long long a0 = fdiv(q0, F) - NUP;          // x index of window slot 0
+    float x[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const long long idx = a0 + w - lo_in;
+        x[w] = (idx >= 0 && idx < rows_in) ? __ldg(plane + idx * Mpad + m) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int ph = (PH0 + j) % F;
+        const int b = (PH0 + j) / F + NUP;           // floor(q/F) + N_up - a0
+        float s = 0.f;
+#pragma unroll
+        for (int t = 0; t <= 2 * NUP; ++t) s = fmaf(__ldg(z + ph * (2 * NUP + 1) + t), x[b - t], s);
+        v[j] += s;
+    }
+}
+
+template <int NUP>
+__device__ __forceinline__ void add_up_dispatch(int F, float (&v)[32], const float* plane, int Mpad, int m,
+                                                long long q0, long long lo_in, int rows_in, const float* z) {
+    switch (F) {
+        case 2: add_up32<2, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
+        case 4: add_up32<4, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
+        case 8: add_up32<8, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
+        case 16: add_up32<16, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
+        case 32: add_up32<32, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
+        case 64:
+            if ((q0 & 63) == 0) add_up32<64, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z);
+            else add_up32<64, NUP, 32>(v, plane, Mpad, m, q0, lo_in, rows_in, z);
+            break;
+        default: break;
+    }
+}
+
+template <bool BF16, bool TOP, bool STORE_Z>
+__global__ void __launch_bounds__(192, 1)
+    k_level_tc(const LevelJob* __restrict__ jobs, const LevelMaps* __restrict__ maps,
+               const int* __restrict__ tile_base, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
+               int det0, int n_det_push, long long window, Partial* __restrict__ part, long long part_tmpl_stride,
+               int n_slots, float* __restrict__ zout, int* __restrict__ err) {
+    constexpr int NUP = 8;
+    using C = LevCfg<BF16>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* tfull = empty + C::STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(tfull + b, 1); mbar_init(tempty + b, kEpiThreads); }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int total = tiles_per_det * n_det_push;
+
+    if (warp == 0) {
+        if (lane == 0) {   // ------------------------------------------------ producer
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < total && ok; it += gridDim.x) {
+                const int det = det0 + it / tiles_per_det;
+                const int t = it % tiles_per_det;
+                const int jx = job_of(tile_base, n_jobs, t);
+                const LevelJob& jb = jobs[jx];
+                const LevelMaps* mp = maps + jb.map;
+                const int local = t - tile_base[jx];
+                const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
+                const long long Q0 = fdiv(fdiv(k_a - jb.Lambda, jb.D), 128) * 128;
+                const int yrow = det * 2 * jb.y_rows + (int)((Q0 + 128LL * tt) & (jb.y_rows - 1));
+                for (int kc = 0; kc < jb.Kp; kc += kTcK) {
+                    if (!mbar_wait(empty + stage, phase ^ 1, err, 31)) { ok = false; break; }
+                    uint8_t* sb = smem + stage * C::STAGE_BYTES;
+                    mbar_expect_tx(full + stage, C::STAGE_BYTES);
+                    tma_load_2d(sb, &mp->cre, full + stage, kc, tm * 128);
+                    tma_load_2d(sb + C::TILE_A, &mp->cim, full + stage, kc, tm * 128);
+                    if (BF16) {
+                        tma_load_2d(sb + 2 * C::TILE_A, &mp->cre_lo, full + stage, kc, tm * 128);
+                        tma_load_2d(sb + 3 * C::TILE_A, &mp->cim_lo, full + stage, kc, tm * 128);
+                    }
+                    tma_load_2d(sb + C::NA * C::TILE_A, &mp->yhi, full + stage, kc, yrow);
+                    tma_load_2d(sb + C::NA * C::TILE_A + C::TILE_B, &mp->ylo, full + stage, kc, yrow);
+                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                }
+            }
+            for (int s = 0; s < C::STAGES; ++s) {
+                if (!mbar_wait(empty + stage, phase ^ 1, err, 32)) break;
+                if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ------------------------------------------------ MMA issuer
+            constexpr uint32_t idesc = idesc_f16(BF16, kTcTileM, kTcTileN);
+            int stage = 0, i = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < total && ok; it += gridDim.x, ++i) {
+                const int t = it % tiles_per_det;
+                const int jx = job_of(tile_base, n_jobs, t);
+                const int Kp = jobs[jx].Kp;
+                const int buf = i & 1;
+                if (!mbar_wait(tempty + buf, ((i >> 1) & 1) ^ 1, err, 33)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_re = tmem + buf * 256, d_im = d_re + 128;
+                for (int kc = 0; kc < Kp; kc += kTcK) {
+                    if (!mbar_wait(full + stage, phase, err, 34)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sb = smem_u32(smem + stage * C::STAGE_BYTES);
+                    const uint32_t a_re = sb, a_im = sb + C::TILE_A;
+                    const uint32_t a_re_lo = sb + 2 * C::TILE_A, a_im_lo = sb + 3 * C::TILE_A;
+                    const uint32_t b_hi = sb + C::NA * C::TILE_A, b_lo = b_hi + C::TILE_B;
+#pragma unroll
+                    for (int k = 0; k < kTcK / 16; ++k) {
+                        const uint32_t off = k * 32;
+                        const uint32_t acc0 = (kc > 0 || k > 0) ? 1u : 0u;
+                        umma_f16(d_re, desc_sw128(a_re + off), desc_sw128(b_hi + off), idesc, acc0);
+                        umma_f16(d_re, desc_sw128(a_re + off), desc_sw128(b_lo + off), idesc, 1u);
+                        umma_f16(d_im, desc_sw128(a_im + off), desc_sw128(b_hi + off), idesc, acc0);
+                        umma_f16(d_im, desc_sw128(a_im + off), desc_sw128(b_lo + off), idesc, 1u);
+                        if (BF16) {
+                            umma_f16(d_re, desc_sw128(a_re_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+                            umma_f16(d_im, desc_sw128(a_im_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+                        }
+                    }
+                    umma_commit(empty + stage);
+                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                umma_commit(tfull + buf);     // with Kp == 0 this only signals the epilogue
+            }
+            umma_commit(drain);
+            mbar_wait(drain, 0, err, 35);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int qd = warp & 3;
+        const int rowm = qd * 32 + lane;
+        int i = 0;
+        for (int it = blockIdx.x; it < total; it += gridDim.x, ++i) {
+            const int det = det0 + it / tiles_per_det;
+            const int t = it % tiles_per_det;
+            const int jx = job_of(tile_base, n_jobs, t);
+            const LevelJob& jb = jobs[jx];
+            const int local = t - tile_base[jx];
+            const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
+            const int buf = i & 1;
+            const bool got = mbar_wait(tfull + buf, (i >> 1) & 1, err, 36);
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc_fence_after();
+            const long long lo = fdiv(k_a - jb.Lambda, jb.D);
+            const long long hi = fdiv(k_b - 1 + jb.Lambda, jb.D);
+            const long long Q0 = fdiv(lo, 128) * 128;
+            const long long lo_in = jb.F ? fdiv(k_a - jb.Lambda_lo, jb.D_lo) : 0;
+            const int m = tm * kTcTileM + rowm;
+            const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + buf * 256;
+            float best = -1.f, bre = 0.f, bim = 0.f;
+            int bk = 0x7fffffff;
+            const float* in_re = jb.F ? jb.acc_in + det * jb.acc_in_det_stride : nullptr;
+            const float* in_im = jb.F ? in_re + (long long)jb.acc_in_rows * jb.Mpad : nullptr;
+#pragma unroll 1
+            for (int c = 0; c < kTcTileN; c += 32) {
+                float re[32], im[32];
+                if (jb.Kp > 0) {
+                    tmem_ld32(base + c, re);
+                    tmem_ld32(base + 128 + c, im);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) { re[j] = 0.f; im[j] = 0.f; }
+                }
+                const long long q0 = Q0 + 128LL * tt + c;
+                if (jb.F) {
+                    add_up_dispatch<NUP>(jb.F, re, in_re, jb.Mpad, m, q0, lo_in, jb.acc_in_rows, jb.upz);
+                    add_up_dispatch<NUP>(jb.F, im, in_im, jb.Mpad, m, q0, lo_in, jb.acc_in_rows, jb.upz);
+                }
+                if (TOP) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float p = re[j] * re[j] + im[j] * im[j];
+                        if (p > best) { best = p; bk = c + j; bre = re[j]; bim = im[j]; }
+                    }
+                    if (STORE_Z && m < jb.M) {
+                        const int n = (int)(k_b - k_a);
+                        float* zr = zout + (long long)(2 * m) * n + tt * kTcTileN + c;
+                        float* zi = zr + n;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) { zr[j] = re[j]; zi[j] = im[j]; }
+                    }
+                } else {
+                    float* o_re = jb.acc_out + det * jb.acc_out_det_stride;
+                    float* o_im = o_re + (long long)jb.acc_out_rows * jb.Mpad;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const long long q = q0 + j;
+                        if (q >= lo && q <= hi) {
+                            o_re[(q - lo) * jb.Mpad + m] = re[j];
+                            o_im[(q - lo) * jb.Mpad + m] = im[j];
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty + buf);
+            if (TOP && !STORE_Z && m < jb.M) {
+                const long long k0 = Q0 + 128LL * tt;         // Q0 == lo == k_a at the top level
+                const long long kwin0 = (k0 / window) * window;
+                const int slot = (int)((k0 / kTcTileN) & (n_slots - 1));
+                part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots + slot] =
+                    make_float4(best, __int_as_float((int)(k0 - kwin0) + bk), bre, bim);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stream rings for the tensor-core FIR: FP32 stream -> hi/lo halves, written
+// at i mod R and i mod R + R (double-mapped so any strip <= R is contiguous)
+// ---------------------------------------------------------------------------
+template <bool BF16>
+__global__ void k_split_stream(const float* __restrict__ src, long long src_det_stride, int src_mask,
+                               uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, long long dst_det_stride,
+                               int dst_len, long long i0, int count, int det0) {
+    const int det = det0 + blockIdx.y;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        const long long i = i0 + e;
+        const float v = src[det * src_det_stride + (i & src_mask)];
+        uint16_t h, l;
+        split_hilo<BF16>(v, h, l);
+        const long long p = i & (dst_len - 1);
+        hi[det * dst_det_stride + p] = h;
+        hi[det * dst_det_stride + p + dst_len] = h;
+        lo[det * dst_det_stride + p] = l;
+        lo[det * dst_det_stride + p + dst_len] = l;
+    }
+}
+
+}  // namespace lloid

@@ -5,9 +5,27 @@
 // a job's tiles start at tile_base[job], and blockIdx.y is the detector.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lloid {
+
+// Split v into a 16-bit hi part and the 16-bit rounding of the remainder:
+// mode 1 = FP16, mode 2 = BF16 (the data operand of the split-precision paths).
+__device__ __forceinline__ void split_hilo_rt(float v, int mode, uint16_t& hi, uint16_t& lo) {
+    if (mode == 2) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        hi = *reinterpret_cast<uint16_t*>(&h);
+        lo = *reinterpret_cast<uint16_t*>(&l);
+    } else {
+        __half h = __float2half_rn(v);
+        __half l = __float2half_rn(v - __half2float(h));
+        hi = *reinterpret_cast<uint16_t*>(&h);
+        lo = *reinterpret_cast<uint16_t*>(&l);
+    }
+}
 
 constexpr int kTileT = 128;      // time tile of the reconstruction = window granule
 constexpr int kMaxRates = 8;     // downsampled streams f0/2 ... f0/256

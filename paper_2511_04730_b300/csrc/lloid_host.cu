@@ -20,6 +20,7 @@
 #include "../../include/lloid.h"
 #include "kernels_simt.cuh"
 #include "kernels_tc.cuh"
+#include "kernels_tc2.cuh"
 
 using namespace lloid;
 
@@ -58,9 +59,27 @@ struct SliceRT {
     int y_len = 0;
 };
 
+// Split-precision (tensor-core) path: one ladder level per distinct rate of
+// the bank plus f0, lowest first.
+struct LevelRT {
+    int rate = 0, D = 1, Lambda = 0;   // Lambda: look-ahead of this level (full-rate samples)
+    int K = 0, Kp = 0;                 // bases at this rate (16-aligned per slice), padded to 64
+    void *d_cre = nullptr, *d_cim = nullptr, *d_cre_lo = nullptr, *d_cim_lo = nullptr;  // [Mpad][Kp]
+    uint16_t *d_yhi = nullptr, *d_ylo = nullptr;   // operand ring [n_det][2R][Kp]
+    int R = 0;
+    float* d_acc = nullptr;            // transposed [n_det][2][acc_rows][Mpad] (below the top)
+    int acc_rows = 0;
+};
+struct FirSliceRT {
+    int level = 0, col = 0, Np = 0, Kp = 0, Mtiles = 0;
+    void *d_a = nullptr, *d_a_lo = nullptr;   // 8-phase expanded bases [Mtiles*128][Kp]
+};
+
 struct BankRT {
     int id = 0, M = 0, Mpad = 0, K = 0, Kpad = 0, tmpl0 = 0;
     std::vector<SliceRT> sl;
+    std::vector<LevelRT> lev;          // split path
+    std::vector<FirSliceRT> fs;        // split path, parallel to sl
     void* d_cre = nullptr;       // [Mpad][Kpad] (FP32 or half)
     void* d_cim = nullptr;
     void* d_cre_lo = nullptr;    // BF16 split: low parts of the coefficients
@@ -129,7 +148,19 @@ struct lloid_ctx {
     UpJob* d_up = nullptr; int* d_up_base = nullptr; int n_up = 0, up_tiles = 0, up_smem = 0;
     ReconJob* d_rec = nullptr; int* d_rec_base = nullptr; int n_rec = 0, rec_tiles = 0;
     FinJob* d_finj = nullptr; int n_fin = 0;
-    TcMaps* d_maps = nullptr;
+    // split path job tables: FIR over all slices, levels per depth below the top
+    FirTcJob* d_firtc = nullptr; FirMaps* d_firmaps = nullptr; int* d_firtc_base = nullptr;
+    int n_firtc = 0, firtc_tiles = 0, firtc_smem = 0, firtc_strip = 0;
+    static constexpr int kMaxDepth = 8;
+    LevelJob* d_lev[kMaxDepth] = {}; LevelMaps* d_levmaps[kMaxDepth] = {}; int* d_lev_base[kMaxDepth] = {};
+    int n_lev[kMaxDepth] = {}, lev_tiles[kMaxDepth] = {};
+    int max_depth = 0;
+    std::vector<int> top_job_of_bank;  // bank id -> index in the depth-0 table
+    // split path streams: index 0 = f0, index r + 1 = rate_D[r]; hi/lo halves, double-mapped
+    uint16_t* s_hi[kMaxRates + 1] = {};
+    uint16_t* s_lo[kMaxRates + 1] = {};
+    long long s_len[kMaxRates + 1] = {};
+    float* d_upz[7] = {};              // Eq. 7 sub-kernels for F = 2, 4, ..., 128
     std::vector<void*> job_allocs;
     cudaEvent_t done_ev = nullptr;
     int* d_err = nullptr;              // device-side wait-expiry code (0 = none)
@@ -296,6 +327,12 @@ void free_jobs(lloid_ctx* ctx) {
     for (void* p : ctx->job_allocs) cudaFree(p);
     ctx->job_allocs.clear();
     ctx->d_fir = nullptr; ctx->d_up = nullptr; ctx->d_rec = nullptr; ctx->d_finj = nullptr;
+    ctx->d_firtc = nullptr; ctx->d_firmaps = nullptr; ctx->d_firtc_base = nullptr;
+    for (int d = 0; d < lloid_ctx::kMaxDepth; ++d) {
+        ctx->d_lev[d] = nullptr; ctx->d_levmaps[d] = nullptr; ctx->d_lev_base[d] = nullptr;
+        ctx->n_lev[d] = 0; ctx->lev_tiles[d] = 0;
+    }
+    ctx->n_firtc = ctx->firtc_tiles = 0;
 }
 
 template <typename T>
@@ -349,20 +386,145 @@ struct StageTimer {
 };
 
 
+// Job tables of the split (tensor-core) path for pushes of n samples.
+lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
+    const lloid_config& c = ctx->cfg;
+    const bool bf = c.precision == LLOID_BF16_SPLIT;
+    const int nd = c.n_detectors;
+    std::vector<FirTcJob> fj;
+    std::vector<FirMaps> fm;
+    std::vector<int> fb;
+    std::vector<LevelJob> lj[lloid_ctx::kMaxDepth];
+    std::vector<LevelMaps> lm[lloid_ctx::kMaxDepth];
+    std::vector<int> lb[lloid_ctx::kMaxDepth];
+    int lt[lloid_ctx::kMaxDepth] = {};
+    int ft = 0, strip = 128, max_depth = 0;
+    ctx->top_job_of_bank.assign(ctx->next_bank_id, -1);
+    for (auto& kv : ctx->banks) {
+        BankRT* b = kv.second;
+        const int nl = (int)b->lev.size();
+        if (nl > lloid_ctx::kMaxDepth) return fail(ctx, LLOID_EINVAL, "bank %d has more than 8 ladder levels", b->id);
+        max_depth = std::max(max_depth, nl);
+        for (size_t si = 0; si < b->sl.size(); ++si) {
+            const SliceRT& sl = b->sl[si];
+            const FirSliceRT& fsr = b->fs[si];
+            const LevelRT& L = b->lev[fsr.level];
+            int ri = 0;
+            if (sl.D > 1) { ri = 1; while (ctx->rate_D[ri - 1] != sl.D) ++ri; }
+            FirTcJob f{};
+            f.s_hi = ctx->s_hi[ri]; f.s_lo = ctx->s_lo[ri];
+            f.s_det_stride = 2 * ctx->s_len[ri]; f.s_len = (int)ctx->s_len[ri];
+            f.y_hi = L.d_yhi + fsr.col; f.y_lo = L.d_ylo + fsr.col;
+            f.y_det_stride = 2LL * L.R * L.Kp; f.y_rows = L.R; f.y_ld = L.Kp;
+            f.J_over_D = sl.J / sl.D;
+            f.Mtiles = fsr.Mtiles; f.Kp = fsr.Kp; f.Np = fsr.Np;
+            const long long ncg = n / (8LL * sl.D) + 2;
+            if (ncg <= kFirNC) { f.NC = (int)((ncg + 15) / 16 * 16); f.ctiles = 1; }
+            else { f.NC = kFirNC; f.ctiles = (int)((ncg + kFirNC - 1) / kFirNC); }
+            f.D = sl.D; f.Lambda = L.Lambda; f.q_count = (int)(n / sl.D); f.map = (int)fj.size();
+            FirMaps mp;
+            std::memset(&mp, 0, sizeof mp);
+            bool ok = encode_map(&mp.a, bf, fsr.d_a, fsr.Kp, (long long)fsr.Mtiles * 128, 128);
+            if (ok && bf) ok = encode_map(&mp.a_lo, bf, fsr.d_a_lo, fsr.Kp, (long long)fsr.Mtiles * 128, 128);
+            if (!ok) return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (FIR bank %d)", b->id);
+            strip = std::max(strip, (2 * (8 * f.NC + f.Kp) + 127) / 128 * 128);
+            fj.push_back(f); fm.push_back(mp); fb.push_back(ft); ft += f.Mtiles * f.ctiles;
+        }
+        for (int j = 0; j < nl; ++j) {
+            const LevelRT& L = b->lev[j];
+            const int depth = nl - 1 - j;
+            LevelJob q{};
+            if (j > 0) {
+                const LevelRT& P = b->lev[j - 1];
+                q.acc_in = P.d_acc; q.acc_in_det_stride = 2LL * P.acc_rows * b->Mpad; q.acc_in_rows = P.acc_rows;
+                q.F = P.D / L.D; q.D_lo = P.D; q.Lambda_lo = P.Lambda;
+                int li = 0;
+                while ((2 << li) != q.F) ++li;
+                q.upz = ctx->d_upz[li];
+            }
+            if (j < nl - 1) { q.acc_out = L.d_acc; q.acc_out_det_stride = 2LL * L.acc_rows * b->Mpad; q.acc_out_rows = L.acc_rows; }
+            q.Kp = L.Kp; q.M = b->M; q.Mpad = b->Mpad; q.tmpl0 = b->tmpl0;
+            q.tiles_m = b->Mpad / kTcTileM;
+            if (depth == 0) q.tiles_t = (int)(n / kTcTileN);
+            else q.tiles_t = (int)((((n - 1 + 2LL * L.Lambda) / L.D + 2) + 127 + 127) / 128);
+            q.D = L.D; q.Lambda = L.Lambda; q.y_rows = L.R; q.map = (int)lj[depth].size();
+            LevelMaps mp;
+            std::memset(&mp, 0, sizeof mp);
+            if (L.Kp > 0) {
+                bool ok = encode_map(&mp.cre, bf, L.d_cre, L.Kp, b->Mpad, kTcTileM) &&
+                          encode_map(&mp.cim, bf, L.d_cim, L.Kp, b->Mpad, kTcTileM) &&
+                          encode_map(&mp.yhi, bf, L.d_yhi, L.Kp, (long long)nd * 2 * L.R, kTcTileN) &&
+                          encode_map(&mp.ylo, bf, L.d_ylo, L.Kp, (long long)nd * 2 * L.R, kTcTileN);
+                if (ok && bf)
+                    ok = encode_map(&mp.cre_lo, bf, L.d_cre_lo, L.Kp, b->Mpad, kTcTileM) &&
+                         encode_map(&mp.cim_lo, bf, L.d_cim_lo, L.Kp, b->Mpad, kTcTileM);
+                if (!ok) return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (level, bank %d)", b->id);
+            }
+            if (depth == 0) ctx->top_job_of_bank[b->id] = (int)lj[0].size();
+            lj[depth].push_back(q); lm[depth].push_back(mp); lb[depth].push_back(lt[depth]);
+            lt[depth] += q.tiles_m * q.tiles_t;
+        }
+    }
+    lloid_status st;
+    if ((st = upload_vec(ctx, &ctx->d_firtc, fj)) || (st = upload_vec(ctx, &ctx->d_firmaps, fm)) ||
+        (st = upload_vec(ctx, &ctx->d_firtc_base, fb)))
+        return st;
+    for (int d = 0; d < lloid_ctx::kMaxDepth; ++d) {
+        ctx->d_lev[d] = nullptr; ctx->d_levmaps[d] = nullptr; ctx->d_lev_base[d] = nullptr;
+        ctx->n_lev[d] = (int)lj[d].size(); ctx->lev_tiles[d] = lt[d];
+        if (lj[d].empty()) continue;
+        if ((st = upload_vec(ctx, &ctx->d_lev[d], lj[d])) || (st = upload_vec(ctx, &ctx->d_levmaps[d], lm[d])) ||
+            (st = upload_vec(ctx, &ctx->d_lev_base[d], lb[d])))
+            return st;
+    }
+    ctx->n_firtc = (int)fj.size();
+    ctx->firtc_tiles = ft;
+    ctx->firtc_strip = strip;
+    ctx->max_depth = max_depth;
+    const int fsmem = (bf ? FirCfg<true>::STAGE_AREA : FirCfg<false>::STAGE_AREA) + 4 * strip +
+                      FirCfg<false>::EPI_BYTES + 256 + 1024;
+    ctx->firtc_smem = fsmem;
+    if (fsmem > 227 * 1024) return fail(ctx, LLOID_EINVAL, "FIR shared memory %d exceeds the limit", fsmem);
+    if (bf) CK(cudaFuncSetAttribute(k_fir_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
+    else CK(cudaFuncSetAttribute(k_fir_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
+    const int lsmem = bf ? LevCfg<true>::SMEM : LevCfg<false>::SMEM;
+    if (bf) {
+        CK(cudaFuncSetAttribute(k_level_tc<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
+        CK(cudaFuncSetAttribute(k_level_tc<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
+        CK(cudaFuncSetAttribute(k_level_tc<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
+    } else {
+        CK(cudaFuncSetAttribute(k_level_tc<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
+        CK(cudaFuncSetAttribute(k_level_tc<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
+        CK(cudaFuncSetAttribute(k_level_tc<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
+    }
+    return LLOID_OK;
+}
+
 // (Re)build the job tables for pushes of n samples.
 lloid_status build_jobs(lloid_ctx* ctx, long long n) {
     if (!ctx->jobs_dirty && ctx->jobs_n == n) return LLOID_OK;
     CK(cudaStreamSynchronize(ctx->stream));
     free_jobs(ctx);
+    std::vector<FinJob> fin;
+    for (auto& kv : ctx->banks) fin.push_back(FinJob{kv.second->tmpl0, kv.second->M});
+    lloid_status st;
+    if ((st = upload_vec(ctx, &ctx->d_finj, fin))) return st;
+    ctx->n_fin = (int)fin.size();
+    if (split_precision(ctx)) {
+        if ((st = build_jobs_split(ctx, n))) return st;
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->jobs_dirty = false;
+        ctx->jobs_n = n;
+        return LLOID_OK;
+    }
     std::vector<FirJob> fj;
     std::vector<int> fb;
     std::vector<UpJob> uj;
     std::vector<int> ub;
     std::vector<ReconJob> rj;
     std::vector<int> rb;
-    std::vector<FinJob> fin;
-    std::vector<TcMaps> maps;
     int ft = 0, ut = 0, rt = 0, max_rlen = 1;
+    ctx->top_job_of_bank.assign(ctx->next_bank_id, -1);
     for (auto& kv : ctx->banks) {
         BankRT* b = kv.second;
         for (auto& s : b->sl) {
@@ -384,103 +546,73 @@ lloid_status build_jobs(lloid_ctx* ctx, long long n) {
 
             UpJob u{};
             u.yring = s.d_yring; u.y_det_stride = (long long)s.L * s.y_len; u.y_mask = s.y_len - 1; u.y_ld = s.y_len;
-            u.yhat = nullptr;  // set below per precision
             u.yhat_det_stride = b->yhat_det_stride; u.ldy = (int)ctx->cfg.max_block;
             u.R = s.d_R; u.e_min = s.e_min; u.rlen = s.e_max - s.e_min + 1; u.D = s.D; u.L = s.L;
-            if (!split_precision(ctx)) {
-                // FP32: Yhat[K][t], one thread per (row, sample), 256 samples per CTA
-                u.tiles_k = (int)((n + 255) / 256);
-                u.yhat = (char*)b->d_yhat + (size_t)s.row0 * u.ldy * 4;
-                u.yhat_lo = nullptr;
-                uj.push_back(u); ub.push_back(ut); ut += u.L * u.tiles_k;
-            } else {
-                // split: Yhat^T[t][Kpad], 64 rows x 64 samples per CTA
-                u.tiles_k = (int)((n + 63) / 64);
-                u.ldy = b->Kpad;
-                u.yhat = (char*)b->d_yhat + (size_t)s.row0 * 2;
-                u.yhat_lo = (char*)b->d_yhat_lo + (size_t)s.row0 * 2;
-                uj.push_back(u); ub.push_back(ut); ut += ((u.L + 63) / 64) * u.tiles_k;
-            }
+            u.tiles_k = (int)((n + 255) / 256);
+            u.yhat = (char*)b->d_yhat + (size_t)s.row0 * u.ldy * 4;
+            u.yhat_lo = nullptr;
+            uj.push_back(u); ub.push_back(ut); ut += u.L * u.tiles_k;
             max_rlen = std::max(max_rlen, u.rlen);
         }
         ReconJob r{};
-        r.c_re = b->d_cre; r.c_im = b->d_cim; r.yhat = b->d_yhat; r.yhat_lo = b->d_yhat_lo;
+        r.c_re = b->d_cre; r.c_im = b->d_cim; r.yhat = b->d_yhat; r.yhat_lo = nullptr;
         r.yhat_det_stride = b->yhat_det_stride; r.ldy = (int)ctx->cfg.max_block;
         r.Kpad = b->Kpad; r.Mpad = b->Mpad; r.M = b->M; r.tmpl0 = b->tmpl0;
-        r.tiles_m = b->Mpad / (split_precision(ctx) ? 128 : 64);
-        r.tiles_t = (int)(n / (split_precision(ctx) ? kTcTileN : 128));
+        r.tiles_m = b->Mpad / 64;
+        r.tiles_t = (int)(n / 128);
+        ctx->top_job_of_bank[b->id] = (int)rj.size();
         rj.push_back(r); rb.push_back(rt); rt += r.tiles_m * r.tiles_t;
-        fin.push_back(FinJob{b->tmpl0, b->M});
-        if (split_precision(ctx)) {
-            const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
-            TcMaps mp;
-            std::memset(&mp, 0, sizeof mp);
-            const long long yrows = (long long)ctx->cfg.n_detectors * ctx->cfg.max_block;
-            bool ok = encode_map(&mp.cre, bf, b->d_cre, b->Kpad, b->Mpad, kTcTileM) &&
-                      encode_map(&mp.cim, bf, b->d_cim, b->Kpad, b->Mpad, kTcTileM) &&
-                      encode_map(&mp.yhi, bf, b->d_yhat, b->Kpad, yrows, kTcTileN) &&
-                      encode_map(&mp.ylo, bf, b->d_yhat_lo, b->Kpad, yrows, kTcTileN);
-            if (ok && bf)
-                ok = encode_map(&mp.cre_lo, bf, b->d_cre_lo, b->Kpad, b->Mpad, kTcTileM) &&
-                     encode_map(&mp.cim_lo, bf, b->d_cim_lo, b->Kpad, b->Mpad, kTcTileM);
-            if (!ok) return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed for bank %d", b->id);
-            maps.push_back(mp);
-        }
     }
-    lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_fir, fj)) || (st = upload_vec(ctx, &ctx->d_fir_base, fb)) ||
         (st = upload_vec(ctx, &ctx->d_up, uj)) || (st = upload_vec(ctx, &ctx->d_up_base, ub)) ||
-        (st = upload_vec(ctx, &ctx->d_rec, rj)) || (st = upload_vec(ctx, &ctx->d_rec_base, rb)) ||
-        (st = upload_vec(ctx, &ctx->d_finj, fin)) || (st = upload_vec(ctx, &ctx->d_maps, maps)))
+        (st = upload_vec(ctx, &ctx->d_rec, rj)) || (st = upload_vec(ctx, &ctx->d_rec_base, rb)))
         return st;
     ctx->n_fir = (int)fj.size(); ctx->fir_tiles = ft;
     ctx->n_up = (int)uj.size(); ctx->up_tiles = ut; ctx->up_smem = max_rlen * 4;
     ctx->n_rec = (int)rj.size(); ctx->rec_tiles = rt;
-    ctx->n_fin = (int)fin.size();
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->jobs_dirty = false;
     ctx->jobs_n = n;
-    if (ctx->up_smem > 40 * 1024) {
+    if (ctx->up_smem > 40 * 1024)
         CK(cudaFuncSetAttribute(k_upsample<StoreF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->up_smem));
-        CK(cudaFuncSetAttribute(k_upsample_t<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->up_smem));
-        CK(cudaFuncSetAttribute(k_upsample_t<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->up_smem));
-    }
     return LLOID_OK;
 }
 
-lloid_status launch_recon(lloid_ctx* ctx, long long k_a, long long n, int det0, int n_det_push, bool store_z,
-                          const ReconJob* jobs, const TcMaps* maps, const int* base, int n_jobs, int tiles,
-                          float* zout) {
+lloid_status launch_recon_f32(lloid_ctx* ctx, long long k_a, long long n, int det0, int n_det_push, bool store_z,
+                              const ReconJob* jobs, const int* base, int n_jobs, int tiles, float* zout) {
     const long long part_stride = (long long)ctx->cfg.n_detectors * ctx->n_slots;
     if (tiles == 0) return LLOID_OK;
     dim3 grid(tiles, n_det_push);
-    if (!split_precision(ctx)) {
-        if (store_z)
-            k_recon_f32<true><<<grid, 256, 0, ctx->stream>>>(jobs, base, n_jobs, k_a, (int)n, det0,
-                                                            ctx->cfg.window_samples, nullptr, part_stride,
-                                                            ctx->n_slots, zout);
-        else
-            k_recon_f32<false><<<grid, 256, 0, ctx->stream>>>(jobs, base, n_jobs, k_a, (int)n, det0,
-                                                             ctx->cfg.window_samples, ctx->d_part, part_stride,
-                                                             ctx->n_slots, nullptr);
-        CKL();
-        return LLOID_OK;
-    }
+    if (store_z)
+        k_recon_f32<true><<<grid, 256, 0, ctx->stream>>>(jobs, base, n_jobs, k_a, (int)n, det0, ctx->cfg.window_samples,
+                                                        nullptr, part_stride, ctx->n_slots, zout);
+    else
+        k_recon_f32<false><<<grid, 256, 0, ctx->stream>>>(jobs, base, n_jobs, k_a, (int)n, det0,
+                                                         ctx->cfg.window_samples, ctx->d_part, part_stride,
+                                                         ctx->n_slots, nullptr);
+    CKL();
+    return LLOID_OK;
+}
+
+// One ladder depth of the split path (depth 0 = f0: |z|^2 and window maxima).
+lloid_status launch_level(lloid_ctx* ctx, int depth, long long k_a, long long n, int det0, int n_det_push,
+                          bool store_z, const LevelJob* jobs, const LevelMaps* maps, const int* base, int n_jobs,
+                          int tiles, float* zout) {
+    if (tiles == 0 || n_jobs == 0) return LLOID_OK;
     const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
+    const long long part_stride = (long long)ctx->cfg.n_detectors * ctx->n_slots;
     const int total = tiles * n_det_push;
     dim3 g(std::min(total, ctx->n_sm));
-    const int smem = bf ? TcCfg<true>::SMEM : TcCfg<false>::SMEM;
+    const int smem = bf ? LevCfg<true>::SMEM : LevCfg<false>::SMEM;
     Partial* part = store_z ? nullptr : ctx->d_part;
-#define LAUNCH_TC(BFV, SZ)                                                                                  \
-    do {                                                                                                    \
-        CK(cudaFuncSetAttribute(k_recon_tc<BFV, SZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
-        k_recon_tc<BFV, SZ><<<g, 192, smem, ctx->stream>>>(jobs, maps, base, n_jobs, tiles, k_a, (int)n, det0, \
-                                                           n_det_push, ctx->cfg.window_samples, part,       \
-                                                           part_stride, ctx->n_slots, zout, ctx->d_err);    \
-    } while (0)
-    if (bf) { if (store_z) LAUNCH_TC(true, true); else LAUNCH_TC(true, false); }
-    else { if (store_z) LAUNCH_TC(false, true); else LAUNCH_TC(false, false); }
-#undef LAUNCH_TC
+#define LAUNCH_LV(BFV, TOPV, SZ)                                                                                   \
+    k_level_tc<BFV, TOPV, SZ><<<g, 192, smem, ctx->stream>>>(jobs, maps, base, n_jobs, tiles, k_a, k_a + n, det0,  \
+                                                              n_det_push, ctx->cfg.window_samples, part, part_stride, \
+                                                              ctx->n_slots, zout, ctx->d_err)
+    if (depth > 0) { if (bf) LAUNCH_LV(true, false, false); else LAUNCH_LV(false, false, false); }
+    else if (store_z) { if (bf) LAUNCH_LV(true, true, true); else LAUNCH_LV(false, true, true); }
+    else { if (bf) LAUNCH_LV(true, true, false); else LAUNCH_LV(false, true, false); }
+#undef LAUNCH_LV
     CKL();
     return LLOID_OK;
 }
@@ -496,7 +628,9 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
         StageTimer tm(ctx, 0);
         dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 1024), nd);
         k_ingest<<<grid, 256, 0, ctx->stream>>>(src, src_det_stride, ctx->ring0, ctx->ring0_len,
-                                                (int)(ctx->ring0_len - 1), k_a, n_i, det0);
+                                                (int)(ctx->ring0_len - 1), k_a, n_i, det0, ctx->s_hi[0],
+                                                ctx->s_lo[0], 2 * ctx->s_len[0], (int)ctx->s_len[0],
+                                                ctx->cfg.precision);
         CKL();
     }
     // a1 downsample to every rate
@@ -507,42 +641,73 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
         for (int r = 0; r < ctx->n_rates; ++r) {
             p.w[r] = ctx->w_down[r]; p.dst[r] = ctx->rate_ring[r]; p.dst_det_stride[r] = ctx->rate_len[r];
             p.dst_mask[r] = (int)(ctx->rate_len[r] - 1); p.D[r] = ctx->rate_D[r];
+            p.s_hi[r] = ctx->s_hi[r + 1]; p.s_lo[r] = ctx->s_lo[r + 1];
+            p.s_det_stride[r] = 2 * ctx->s_len[r + 1]; p.s_len[r] = (int)ctx->s_len[r + 1];
         }
+        p.mode = ctx->cfg.precision;
         dim3 grid((unsigned)((n / 2 + 7) / 8), nd, ctx->n_rates);
         k_downsample<<<grid, 256, 0, ctx->stream>>>(p, ctx->ring0, ctx->ring0_len, (int)(ctx->ring0_len - 1), k_a,
                                                     n_i, ctx->cfg.n_down, det0);
         CKL();
     }
     if (ctx->banks.empty()) return LLOID_OK;
-    // a2 basis FIR
-    if (ctx->fir_tiles) {
-        StageTimer tm(ctx, 2);
-        dim3 grid(ctx->fir_tiles, nd);
-        k_fir_f32<<<grid, 256, 0, ctx->stream>>>(ctx->d_fir, ctx->d_fir_base, ctx->n_fir, k_a, det0);
-        CKL();
-    }
-    // a4 (slice part) upsample each slice to Yhat
-    if (ctx->up_tiles) {
-        StageTimer tm(ctx, 3);
-        dim3 grid(ctx->up_tiles, nd);
-        if (!split_precision(ctx))
+    if (!split_precision(ctx)) {
+        // a2 basis FIR (FP32)
+        if (ctx->fir_tiles) {
+            StageTimer tm(ctx, 2);
+            dim3 grid(ctx->fir_tiles, nd);
+            k_fir_f32<<<grid, 256, 0, ctx->stream>>>(ctx->d_fir, ctx->d_fir_base, ctx->n_fir, k_a, det0);
+            CKL();
+        }
+        // a4 (slice part) composed upsampler of each slice into Yhat
+        if (ctx->up_tiles) {
+            StageTimer tm(ctx, 3);
+            dim3 grid(ctx->up_tiles, nd);
             k_upsample<StoreF32><<<grid, 256, ctx->up_smem, ctx->stream>>>(ctx->d_up, ctx->d_up_base, ctx->n_up, k_a,
                                                                          n_i, det0, StoreF32{});
-        else if (ctx->cfg.precision == LLOID_FP16_SPLIT)
-            k_upsample_t<__half><<<grid, 256, ctx->up_smem, ctx->stream>>>(ctx->d_up, ctx->d_up_base, ctx->n_up, k_a,
-                                                                          n_i, det0);
-        else
-            k_upsample_t<__nv_bfloat16><<<grid, 256, ctx->up_smem, ctx->stream>>>(ctx->d_up, ctx->d_up_base, ctx->n_up,
-                                                                                 k_a, n_i, det0);
-        CKL();
+            CKL();
+        }
+        // a3 + a5 reconstruction with fused window maxima
+        {
+            StageTimer tm(ctx, 4);
+            st = launch_recon_f32(ctx, k_a, n, det0, nd, false, ctx->d_rec, ctx->d_rec_base, ctx->n_rec,
+                                  ctx->rec_tiles, nullptr);
+        }
+        if (st) return st;
+    } else {
+        // a2 basis FIR on the tensor cores
+        if (ctx->firtc_tiles) {
+            StageTimer tm(ctx, 2);
+            const int total = ctx->firtc_tiles * nd;
+            dim3 g(std::min(total, ctx->n_sm));
+            if (ctx->cfg.precision == LLOID_BF16_SPLIT)
+                k_fir_tc<true><<<g, 192, ctx->firtc_smem, ctx->stream>>>(ctx->d_firtc, ctx->d_firmaps,
+                                                                         ctx->d_firtc_base, ctx->n_firtc,
+                                                                         ctx->firtc_tiles, k_a, det0, nd,
+                                                                         ctx->firtc_strip, ctx->d_err);
+            else
+                k_fir_tc<false><<<g, 192, ctx->firtc_smem, ctx->stream>>>(ctx->d_firtc, ctx->d_firmaps,
+                                                                          ctx->d_firtc_base, ctx->n_firtc,
+                                                                          ctx->firtc_tiles, k_a, det0, nd,
+                                                                          ctx->firtc_strip, ctx->d_err);
+            CKL();
+        }
+        // a3 + a4: reconstruction rate by rate with the Eq. 7-8 ladder, lowest rate first
+        {
+            StageTimer tm(ctx, 3);
+            for (int d = ctx->max_depth - 1; d >= 1; --d)
+                if ((st = launch_level(ctx, d, k_a, n, det0, nd, false, ctx->d_lev[d], ctx->d_levmaps[d],
+                                       ctx->d_lev_base[d], ctx->n_lev[d], ctx->lev_tiles[d], nullptr)))
+                    return st;
+        }
+        // top level (f0) + a5 window maxima
+        {
+            StageTimer tm(ctx, 4);
+            st = launch_level(ctx, 0, k_a, n, det0, nd, false, ctx->d_lev[0], ctx->d_levmaps[0], ctx->d_lev_base[0],
+                              ctx->n_lev[0], ctx->lev_tiles[0], nullptr);
+        }
+        if (st) return st;
     }
-    // a3 + a5 reconstruction with fused window maxima
-    {
-        StageTimer tm(ctx, 4);
-        st = launch_recon(ctx, k_a, n, det0, nd, false, ctx->d_rec, ctx->d_maps, ctx->d_rec_base, ctx->n_rec,
-                      ctx->rec_tiles, nullptr);
-    }
-    if (st) return st;
     // a5 finalise completed windows
     const long long W = ctx->cfg.window_samples;
     StageTimer tmf(ctx, 5);
@@ -603,6 +768,115 @@ lloid_status wait_done(lloid_ctx* ctx, int timeout_ms) {
         }
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
+}
+
+// Split path: ladder levels, 8-phase expanded bases for the tensor-core FIR,
+// per-level coefficient blocks, operand rings and Acc planes.  Uploads
+// everything and accounts the bytes in b.
+lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const std::vector<int>& ladder,
+                                BankRT* b, bool dry_run, size_t* need_out) {
+    const lloid_config& c = ctx->cfg;
+    const bool bf = c.precision == LLOID_BF16_SPLIT;
+    const int nd = c.n_detectors;
+    const int nl = (int)ladder.size();
+    const int M = bd->n_templates;
+    std::vector<LevelRT> lev(nl);
+    for (int j = 0; j < nl; ++j) { lev[j].rate = ladder[j]; lev[j].D = c.f0 / ladder[j]; }
+    lev[nl - 1].Lambda = 0;
+    for (int j = nl - 2; j >= 0; --j) lev[j].Lambda = lev[j + 1].Lambda + c.n_up * lev[j].D;
+    std::vector<FirSliceRT> fs(bd->n_slices);
+    for (int s = 0; s < bd->n_slices; ++s) {
+        const lloid_slice& sl = bd->slices[s];
+        const int j = (int)(std::find(ladder.begin(), ladder.end(), sl.rate) - ladder.begin());
+        const int D = c.f0 / sl.rate;
+        fs[s].level = j;
+        fs[s].col = lev[j].K;
+        lev[j].K += (sl.n_basis + 15) / 16 * 16;
+        const long long JD = sl.j_start / D;
+        int Np = sl.n_taps;
+        while (((Np - 1 + JD) % 8 + 8) % 8) ++Np;
+        fs[s].Np = Np;
+        fs[s].Kp = (Np + 7 + 63) / 64 * 64;
+        fs[s].Mtiles = (8 * sl.n_basis + 127) / 128;
+        if (2 * (8 * kFirNC + fs[s].Kp) > 40 * 1024)
+            return fail(ctx, LLOID_EINVAL, "slice %d: %d taps exceed the tensor-core FIR strip limit", s, sl.n_taps);
+    }
+    size_t need = 0;
+    const size_t es = 2;
+    for (int j = 0; j < nl; ++j) {
+        LevelRT& L = lev[j];
+        L.Kp = (L.K + 63) / 64 * 64;
+        const long long cnt = (c.max_block - 1 + 2LL * L.Lambda) / L.D + 2;
+        L.R = (int)next_pow2(cnt + 128 + 64);
+        if (j < nl - 1) L.acc_rows = (int)cnt + 2;
+        need += (size_t)b->Mpad * L.Kp * es * (bf ? 4 : 2);
+        need += (size_t)nd * 2 * L.R * L.Kp * es * 2;
+        need += (size_t)nd * 2 * L.acc_rows * b->Mpad * 4;
+    }
+    for (auto& f : fs) need += (size_t)f.Mtiles * 128 * f.Kp * es * (bf ? 2 : 1);
+    *need_out = need;
+    if (dry_run) return LLOID_OK;
+
+    lloid_status st;
+    // expanded bases: A'[(8l + t)][j] = u_l[t + N' - 1 - j] inside the filter, else 0
+    for (int s = 0; s < bd->n_slices; ++s) {
+        const lloid_slice& sl = bd->slices[s];
+        FirSliceRT& f = fs[s];
+        const size_t rows = (size_t)f.Mtiles * 128;
+        std::vector<double> A(rows * f.Kp, 0.0);
+        for (int l = 0; l < sl.n_basis; ++l)
+            for (int t = 0; t < 8; ++t)
+                for (int jj = 0; jj < f.Kp; ++jj) {
+                    const int m = t + f.Np - 1 - jj;
+                    if (m >= 0 && m < sl.n_taps) A[(size_t)(8 * l + t) * f.Kp + jj] = sl.bases[(size_t)l * sl.n_taps + m];
+                }
+        std::vector<uint16_t> hi, lo, dummy_h, dummy_l;
+        std::vector<double> zero;
+        pack_coeffs_tc(bf, A, A, (int)rows, f.Kp, &hi, &dummy_h, &lo, &dummy_l);
+        if ((st = dalloc(ctx, (uint16_t**)&f.d_a, hi.size() * 2, &b->allocs, &b->bytes))) return st;
+        CK(cudaMemcpyAsync(f.d_a, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, ctx->stream));
+        if (bf) {
+            if ((st = dalloc(ctx, (uint16_t**)&f.d_a_lo, lo.size() * 2, &b->allocs, &b->bytes))) return st;
+            CK(cudaMemcpyAsync(f.d_a_lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, ctx->stream));
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    // per-level coefficient blocks, rings, Acc planes
+    for (int j = 0; j < nl; ++j) {
+        LevelRT& L = lev[j];
+        if (L.Kp > 0) {
+            std::vector<double> cre((size_t)b->Mpad * L.Kp, 0.0), cim((size_t)b->Mpad * L.Kp, 0.0);
+            for (int s = 0; s < bd->n_slices; ++s) {
+                if (fs[s].level != j) continue;
+                const lloid_slice& sl = bd->slices[s];
+                for (int i = 0; i < M; ++i)
+                    for (int l = 0; l < sl.n_basis; ++l) {
+                        cre[(size_t)i * L.Kp + fs[s].col + l] = sl.coeffs[(size_t)(2 * i) * sl.n_basis + l];
+                        cim[(size_t)i * L.Kp + fs[s].col + l] = sl.coeffs[(size_t)(2 * i + 1) * sl.n_basis + l];
+                    }
+            }
+            std::vector<uint16_t> hre, him, lre, lim;
+            pack_coeffs_tc(bf, cre, cim, b->Mpad, L.Kp, &hre, &him, &lre, &lim);
+            void** dst[4] = {&L.d_cre, &L.d_cim, &L.d_cre_lo, &L.d_cim_lo};
+            std::vector<uint16_t>* srcv[4] = {&hre, &him, &lre, &lim};
+            for (int q = 0; q < 4; ++q) {
+                if (srcv[q]->empty()) continue;
+                if ((st = dalloc(ctx, (uint16_t**)dst[q], srcv[q]->size() * 2, &b->allocs, &b->bytes))) return st;
+                CK(cudaMemcpyAsync(*dst[q], srcv[q]->data(), srcv[q]->size() * 2, cudaMemcpyHostToDevice, ctx->stream));
+            }
+            const size_t rb = (size_t)nd * 2 * L.R * L.Kp * 2;
+            if ((st = dalloc(ctx, &L.d_yhi, rb, &b->allocs, &b->bytes))) return st;
+            if ((st = dalloc(ctx, &L.d_ylo, rb, &b->allocs, &b->bytes))) return st;
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+        if (L.acc_rows > 0) {
+            if ((st = dalloc(ctx, &L.d_acc, (size_t)nd * 2 * L.acc_rows * b->Mpad * 4, &b->allocs, &b->bytes)))
+                return st;
+        }
+    }
+    b->lev = lev;
+    b->fs = fs;
+    return LLOID_OK;
 }
 
 // A kernel whose bounded wait expired leaves a code in d_err (see kernels_tc.cuh).
@@ -689,7 +963,8 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         c.precision < 0 || c.precision > 2 || !(c.snr_threshold >= 0.f))
         return fail(nullptr, LLOID_EINVAL, "bad configuration");
     if (c.window_overlap != 0) return LLOID_EINVAL;
-    if (c.precision != LLOID_FP32 && c.max_block % kTcTileN) return LLOID_EINVAL;
+    if (c.precision != LLOID_FP32 && (c.max_block % kTcTileN || c.n_up != 8))
+        return fail(nullptr, LLOID_EINVAL, "tensor-core paths need max_block % 128 == 0 and n_up == 8");
     CK(cudaSetDevice(c.device));
     CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, c.device));
     if (c.cuda_stream) {
@@ -718,6 +993,29 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         for (size_t k = 0; k < g.size(); ++k) w[k] = (float)(std::sqrt((double)D) * g[k] / sum);
         if ((st = dalloc(ctx, &ctx->w_down[r], w.size() * 4, nullptr, &ctx->state_bytes))) return st;
         CK(cudaMemcpyAsync(ctx->w_down[r], w.data(), w.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (c.precision != LLOID_FP32) {
+        // hi/lo double-mapped streams for the tensor-core FIR (index 0 = f0)
+        for (int r = 0; r <= ctx->n_rates; ++r) {
+            const int D = r == 0 ? 1 : ctx->rate_D[r - 1];
+            ctx->s_len[r] = next_pow2((c.max_block + c.max_history) / D + 2 * c.n_down + 16 * kFirNC + 1024);
+            const size_t bytes = (size_t)nd * 2 * ctx->s_len[r] * sizeof(uint16_t);
+            if ((st = dalloc(ctx, &ctx->s_hi[r], bytes, nullptr, &ctx->state_bytes))) return st;
+            if ((st = dalloc(ctx, &ctx->s_lo[r], bytes, nullptr, &ctx->state_bytes))) return st;
+        }
+        // Eq. 7 sub-kernels z_phi[t] = g[t F + phi], t = 0..2 N_up, g of Eq. 4 with c = F N_up
+        for (int i = 0; i < 7; ++i) {
+            const int F = 2 << i;
+            std::vector<double> g = sinc_windowed(F, F * c.n_up);
+            std::vector<float> z((size_t)F * (2 * c.n_up + 1), 0.f);
+            for (int ph = 0; ph < F; ++ph)
+                for (int t = 0; t <= 2 * c.n_up; ++t) {
+                    const long long k = (long long)t * F + ph;
+                    if (k <= 2LL * F * c.n_up) z[(size_t)ph * (2 * c.n_up + 1) + t] = (float)g[k];
+                }
+            if ((st = dalloc(ctx, &ctx->d_upz[i], z.size() * 4, nullptr, &ctx->state_bytes))) return st;
+            CK(cudaMemcpyAsync(ctx->d_upz[i], z.data(), z.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        }
     }
     ctx->pos.assign(nd, 0);
     ctx->fin.assign(nd, -1);
@@ -757,6 +1055,8 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_tmpl0_of);
     cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
     cudaFree(ctx->d_err);
+    for (int r = 0; r <= kMaxRates; ++r) { cudaFree(ctx->s_hi[r]); cudaFree(ctx->s_lo[r]); }
+    for (int i = 0; i < 7; ++i) cudaFree(ctx->d_upz[i]);
     if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
     for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -821,47 +1121,53 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
                         "slice %d (rate %d) starts %lld samples before merger; pre-synchronisation needs >= %lld",
                         s, r.rate, r.J, -(long long)r.e_min + (long long)r.D * c.n_down);
         b->sl.push_back(r);
-        // keep R for upload
-        b->sl.back().d_R = nullptr;
         b->sl.back().y_len = (int)next_pow2(c.max_block / r.D + (r.e_max - r.e_min) / r.D + 4);
-        // stash R in a temporary via allocation below
-        std::vector<float> Rf(R.size());
-        for (size_t i = 0; i < R.size(); ++i) Rf[i] = (float)R[i];
-        lloid_status st;
-        if ((st = dalloc(ctx, &b->sl.back().d_R, Rf.size() * 4, &b->allocs, &b->bytes))) return st;
-        CK(cudaMemcpyAsync(b->sl.back().d_R, Rf.data(), Rf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+        if (!split_precision(ctx)) {   // the FP32 path upsamples each slice with the composed filter
+            std::vector<float> Rf(R.size());
+            for (size_t i = 0; i < R.size(); ++i) Rf[i] = (float)R[i];
+            lloid_status st;
+            if ((st = dalloc(ctx, &b->sl.back().d_R, Rf.size() * 4, &b->allocs, &b->bytes))) return st;
+            CK(cudaMemcpyAsync(b->sl.back().d_R, Rf.data(), Rf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
     }
     const bool split = split_precision(ctx);
     b->K = row;
     b->Kpad = (row + 63) / 64 * 64;
     b->Mpad = (M + 127) / 128 * 128;
     const int nd = c.n_detectors;
-    // ---- budget check before any large allocation
-    size_t esz = split ? 2 : 4;
-    size_t need = 0;
-    for (auto& r : b->sl)
-        need += (size_t)r.L * r.N * 4 + (size_t)nd * r.L * r.y_len * 4;
-    need += (size_t)b->Mpad * b->Kpad * esz * (c.precision == LLOID_BF16_SPLIT ? 4 : 2);
-    need += (size_t)nd * b->Kpad * c.max_block * esz * (split ? 2 : 1);
-    if (c.hbm_budget_bytes && ctx->state_bytes + ctx->bank_bytes + need > c.hbm_budget_bytes)
-        return fail(ctx, LLOID_EBUDGET, "bank needs %zu bytes; %zu of %zu in use", need,
-                    ctx->state_bytes + ctx->bank_bytes, (size_t)c.hbm_budget_bytes);
     lloid_status st;
     auto cleanup = [&]() { for (void* p : b->allocs) cudaFree(p); };
-    // ---- bases (FP32) and Y rings
-    for (int s = 0; s < bd->n_slices; ++s) {
-        const lloid_slice& sl = bd->slices[s];
-        SliceRT& r = b->sl[s];
-        std::vector<float> u((size_t)r.L * r.N);
-        for (size_t i = 0; i < u.size(); ++i) u[i] = (float)sl.bases[i];
-        if ((st = dalloc(ctx, &r.d_bases, u.size() * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
-        CK(cudaMemcpyAsync(r.d_bases, u.data(), u.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-        if ((st = dalloc(ctx, &r.d_yring, (size_t)nd * r.L * r.y_len * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
-        CK(cudaStreamSynchronize(ctx->stream));
+    // ---- budget check before any large allocation
+    size_t need = 0;
+    if (!split) {
+        for (auto& r : b->sl) need += (size_t)r.L * r.N * 4 + (size_t)nd * r.L * r.y_len * 4;
+        need += (size_t)b->Mpad * b->Kpad * 4 * 2;
+        need += (size_t)nd * b->Kpad * c.max_block * 4;
+    } else if ((st = prepare_split_bank(ctx, bd, ladder, b.get(), true, &need))) {
+        cleanup();
+        return st;
     }
-    // ---- coefficients: C[row][K] with the real rows and imaginary rows apart
-    {
+    if (c.hbm_budget_bytes && ctx->state_bytes + ctx->bank_bytes + need > c.hbm_budget_bytes) {
+        cleanup();
+        return fail(ctx, LLOID_EBUDGET, "bank needs %zu bytes; %zu of %zu in use", need,
+                    ctx->state_bytes + ctx->bank_bytes, (size_t)c.hbm_budget_bytes);
+    }
+    if (split) {
+        if ((st = prepare_split_bank(ctx, bd, ladder, b.get(), false, &need))) { cleanup(); return st; }
+    } else {
+        // ---- bases (FP32) and Y rings
+        for (int s = 0; s < bd->n_slices; ++s) {
+            const lloid_slice& sl = bd->slices[s];
+            SliceRT& r = b->sl[s];
+            std::vector<float> u((size_t)r.L * r.N);
+            for (size_t i = 0; i < u.size(); ++i) u[i] = (float)sl.bases[i];
+            if ((st = dalloc(ctx, &r.d_bases, u.size() * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
+            CK(cudaMemcpyAsync(r.d_bases, u.data(), u.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+            if ((st = dalloc(ctx, &r.d_yring, (size_t)nd * r.L * r.y_len * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+        // ---- coefficients: C[row][K] with the real rows and imaginary rows apart
         std::vector<double> cre((size_t)b->Mpad * b->Kpad, 0.0), cim((size_t)b->Mpad * b->Kpad, 0.0);
         for (int s = 0; s < bd->n_slices; ++s) {
             const lloid_slice& sl = bd->slices[s];
@@ -872,33 +1178,17 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
                     cim[(size_t)i * b->Kpad + r.row0 + l] = sl.coeffs[(size_t)(2 * i + 1) * r.L + l];
                 }
         }
-        size_t n_el = (size_t)b->Mpad * b->Kpad;
-        if (!split) {
-            std::vector<float> a(n_el), bb(n_el);
-            for (size_t i = 0; i < n_el; ++i) { a[i] = (float)cre[i]; bb[i] = (float)cim[i]; }
-            if ((st = dalloc(ctx, (float**)&b->d_cre, n_el * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
-            if ((st = dalloc(ctx, (float**)&b->d_cim, n_el * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
-            CK(cudaMemcpyAsync(b->d_cre, a.data(), n_el * 4, cudaMemcpyHostToDevice, ctx->stream));
-            CK(cudaMemcpyAsync(b->d_cim, bb.data(), n_el * 4, cudaMemcpyHostToDevice, ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-        } else {
-            std::vector<uint16_t> hre, him, lre, lim;
-            pack_coeffs_tc(c.precision == LLOID_BF16_SPLIT, cre, cim, b->Mpad, b->Kpad, &hre, &him, &lre, &lim);
-            void** dst[4] = {&b->d_cre, &b->d_cim, &b->d_cre_lo, &b->d_cim_lo};
-            std::vector<uint16_t>* srcv[4] = {&hre, &him, &lre, &lim};
-            for (int q = 0; q < 4; ++q) {
-                if (srcv[q]->empty()) continue;
-                if ((st = dalloc(ctx, (uint16_t**)dst[q], srcv[q]->size() * 2, &b->allocs, &b->bytes))) { cleanup(); return st; }
-                CK(cudaMemcpyAsync(*dst[q], srcv[q]->data(), srcv[q]->size() * 2, cudaMemcpyHostToDevice, ctx->stream));
-            }
-            CK(cudaStreamSynchronize(ctx->stream));
-        }
-    }
-    // ---- Yhat block buffers (rows K..Kpad stay zero)
-    b->yhat_det_stride = (long long)b->Kpad * c.max_block;
-    if ((st = dalloc(ctx, (char**)&b->d_yhat, (size_t)nd * b->yhat_det_stride * esz, &b->allocs, &b->bytes))) { cleanup(); return st; }
-    if (split) {
-        if ((st = dalloc(ctx, (char**)&b->d_yhat_lo, (size_t)nd * b->yhat_det_stride * esz, &b->allocs, &b->bytes))) { cleanup(); return st; }
+        const size_t n_el = (size_t)b->Mpad * b->Kpad;
+        std::vector<float> a(n_el), bb(n_el);
+        for (size_t i = 0; i < n_el; ++i) { a[i] = (float)cre[i]; bb[i] = (float)cim[i]; }
+        if ((st = dalloc(ctx, (float**)&b->d_cre, n_el * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
+        if ((st = dalloc(ctx, (float**)&b->d_cim, n_el * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
+        CK(cudaMemcpyAsync(b->d_cre, a.data(), n_el * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(b->d_cim, bb.data(), n_el * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        // ---- Yhat block buffers (rows K..Kpad stay zero)
+        b->yhat_det_stride = (long long)b->Kpad * c.max_block;
+        if ((st = dalloc(ctx, (char**)&b->d_yhat, (size_t)nd * b->yhat_det_stride * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
     }
     // ---- template ids, window state
     b->tmpl0 = ctx->M_used;
@@ -1009,16 +1299,19 @@ lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* o
     if (cap < 2LL * b->M * n) { if (n_samples) *n_samples = n; return fail(ctx, LLOID_ERANGE, "need %lld floats", 2LL * b->M * n); }
     lloid_status st0 = build_jobs(ctx, n);
     if (st0) return st0;
-    int idx = 0;
-    for (auto& kv : ctx->banks) { if (kv.first == bank) break; ++idx; }
-    const bool split = split_precision(ctx);
-    const int tiles = (b->Mpad / (split ? 128 : 64)) * (int)(n / (split ? kTcTileN : 128));
+    const int idx = ctx->top_job_of_bank[bank];
     int* db = nullptr;
     CK(cudaMalloc(&db, sizeof(int)));
     CK(cudaMemsetAsync(db, 0, sizeof(int), ctx->stream));
     const long long k_a = ctx->pos[det] - n;
-    lloid_status st = launch_recon(ctx, k_a, n, det, 1, true, ctx->d_rec + idx, split ? ctx->d_maps + idx : nullptr,
-                                   db, 1, tiles, out);
+    lloid_status st;
+    if (!split_precision(ctx)) {
+        const int tiles = (b->Mpad / 64) * (int)(n / 128);
+        st = launch_recon_f32(ctx, k_a, n, det, 1, true, ctx->d_rec + idx, db, 1, tiles, out);
+    } else {
+        const int tiles = (b->Mpad / kTcTileM) * (int)(n / kTcTileN);
+        st = launch_level(ctx, 0, k_a, n, det, 1, true, ctx->d_lev[0] + idx, ctx->d_levmaps[0], db, 1, tiles, out);
+    }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     cudaFree(db);
     if (st) return st;

@@ -84,14 +84,15 @@ def test_trigger_parity_bank64(lloid, bank64_case, precision):
     assert np.allclose(trig["phase"], np.arctan2(trig["im"], trig["re"]), atol=1e-5)
 
 
-def test_streaming_block_sizes_identical(lloid, bank64_case):
+@pytest.mark.parametrize("precision", ["fp32", "fp16_split"])
+def test_streaming_block_sizes_identical(lloid, bank64_case, precision):
     """The SNR does not depend on how the stream is cut into blocks."""
     w, bank, plan, d, _ = bank64_case
     sb = lloid.build_svd_bank(bank, plan)
     d = d[: 24 * F0]
     outs = []
     for block in (16384, 384, 1152, 2048):
-        with _ctx(lloid, "fp32") as ctx:
+        with _ctx(lloid, precision) as ctx:
             bid = ctx.load_bank(sb)
             outs.append(stream_snr(ctx, bid, d, block))
     for z in outs[1:]:
@@ -132,26 +133,33 @@ def test_device_pointer_push(lloid, bank64_case):
         assert torch.equal(za, zb)
 
 
-def test_multirate_ladder_bank1000_segments(lloid):
-    """Five-rate bank (2048/1024/512/256/128 Hz, 64 s templates): sampled
-    segments of the stream against the oracle run on the segment's history."""
+@pytest.fixture(scope="module")
+def ladder_case():
     w = W.make_workload("bank1000", n_templates=96, n_seconds=96, n_det=1, n_inj=2)
     bank, plan = w.banks[0], w.plans[0]
-    assert sorted(set(plan.rate)) == [128, 256, 512, 1024, 2048]
     d = w.strain(0)
-    sb = lloid.build_svd_bank(bank, plan)
-    with _ctx(lloid, "fp32", max_history=64 * F0) as ctx:
-        bid = ctx.load_bank(sb)
-        z = stream_snr(ctx, bid, d, 16384)
     # oracle on [a - H, a + S): H = one full template plus the ladder halos, a
     # multiple of the lowest rate's decimation so the grid is preserved
     sl = O.svd_bank(bank, plan)
     H, S = 66 * F0, 2 * F0
-    for a in (66 * F0, 90 * F0):
-        zo = O.lloid_snr(d[a - H:a + S].astype(np.float64), sl, F0)[:, H:]
+    segs = {a: O.lloid_snr(d[a - H:a + S].astype(np.float64), sl, F0)[:, H:] for a in (66 * F0, 90 * F0)}
+    return bank, plan, d, segs, S
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16_split", "bf16_split"])
+def test_multirate_ladder_bank1000_segments(lloid, ladder_case, precision):
+    """Five-rate bank (2048/1024/512/256/128 Hz, 64 s templates): sampled
+    segments of the stream against the oracle run on the segment's history."""
+    bank, plan, d, segs, S = ladder_case
+    assert sorted(set(plan.rate)) == [128, 256, 512, 1024, 2048]
+    sb = lloid.build_svd_bank(bank, plan)
+    with _ctx(lloid, precision, max_history=64 * F0) as ctx:
+        bid = ctx.load_bank(sb)
+        z = stream_snr(ctx, bid, d, 16384)
+    for a, zo in segs.items():
         err = max_abs_complex(z[:, a:a + S], zo)
-        print(f"segment {a}: max|dz| = {err:.3e}")
-        assert err <= TOL["fp32"]
+        print(f"{precision} segment {a}: max|dz| = {err:.3e}")
+        assert err <= TOL[precision]
 
 
 def test_error_codes(lloid, bank64_case):
