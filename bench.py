@@ -135,14 +135,18 @@ def make_inputs(args, rank):
 
 def algorithmic_work(slices, M, f0=F0, n_up=8):
     """Per detector-second per bank (the hot-path accounting of Eq. 5-8):
-    FIR 2 L N r, reconstruction 2 (2M) L r, ladder 2 (2M) 2 N_up r (F-1)/F,
-    window maxima 2M f0 compares."""
+    FIR 2 L N r, reconstruction 2 (2M) L r, ladder 2 (2M) 2 N_up r (F-1)/F
+    for each stage into rate r, window maxima 2M f0 compares."""
     fir = sum(2.0 * s.n_basis * s.n_taps * s.rate for s in slices)
-    rec = sum(2.0 * (2 * M) * s.n_basis * s.rate for s in slices)
+    rec_by = {}
+    for s in slices:
+        rec_by[s.rate] = rec_by.get(s.rate, 0.0) + 2.0 * (2 * M) * s.n_basis * s.rate
     lad = sorted(set(s.rate for s in slices) | {f0})
-    up = sum(2.0 * (2 * M) * 2 * n_up * hi * (hi // lo - 1) / (hi // lo) for lo, hi in zip(lad[:-1], lad[1:]))
+    up_by = {hi: 2.0 * (2 * M) * 2 * n_up * hi * (hi // lo - 1) / (hi // lo) for lo, hi in zip(lad[:-1], lad[1:])}
     cmp_ = 2.0 * M * f0
-    return {"fir": fir, "recon": rec, "ladder": up, "max": cmp_}
+    return {"fir": fir, "recon": sum(rec_by.values()), "ladder": sum(up_by.values()), "max": cmp_,
+            "below_f0": sum(v for r, v in rec_by.items() if r < f0) + sum(v for r, v in up_by.items() if r < f0),
+            "at_f0": rec_by.get(f0, 0.0) + up_by.get(f0, 0.0) + cmp_}
 
 
 def peaks():
@@ -251,9 +255,8 @@ def run_lloid(args, rank, world, dist):
                     h2d += blk.nbytes
                 else:
                     ctx.push_all(pos, d_blocks[k])
-                for win in range(pos // F0, (pos + B) // F0):
-                    tr = ctx.pull(win)
-                    d2h += 8 + tr.nbytes
+                tr = ctx.pull(pos // F0, n_windows=B // F0)      # the windows this block completes
+                d2h += 8 + tr.nbytes
                 b.record(ext)
                 b.synchronize()
                 if lat is not None:
@@ -355,15 +358,16 @@ def run_lloid(args, rank, world, dist):
     pk, pk_kind = peaks()
     alu_peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     tc = args.precision != "fp32"
-    kinds = {   # stage -> (kernel, bound, peak, peak note, algorithmic flop per detector-second)
-        "fir": ("k_fir_f32", "alu", alu_peak, "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock", work["fir"]),
-        "upsample": ("k_upsample_t" if tc else "k_upsample", "alu", alu_peak,
-                     "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock", work["ladder"]),
-        "recon": (("k_recon_tc", "tensor", pk["bf16_tflops_sustained"],
-                   f"{pk_kind} dense bf16 sustained x 1 (fp16 nominal rate equal)") if tc else
-                  ("k_recon_f32", "alu", alu_peak, "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock"))
-                 + (work["recon"] + work["max"],),
-    }
+    alu_note = "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock"
+    tc_peak, tc_note = pk["bf16_tflops_sustained"], f"{pk_kind} dense bf16 sustained (fp16 nominal rate equal)"
+    if tc:   # stage -> (kernel, bound, peak, peak note, algorithmic flop per detector-second)
+        kinds = {"fir": ("k_fir_tc", "tensor", tc_peak, tc_note, work["fir"]),
+                 "upsample": ("k_level_tc (levels below f0)", "tensor", tc_peak, tc_note, work["below_f0"]),
+                 "recon": ("k_level_tc (f0 level + window maxima)", "tensor", tc_peak, tc_note, work["at_f0"])}
+    else:
+        kinds = {"fir": ("k_fir_f32", "alu", alu_peak, alu_note, work["fir"]),
+                 "upsample": ("k_upsample", "alu", alu_peak, alu_note, work["ladder"]),
+                 "recon": ("k_recon_f32", "alu", alu_peak, alu_note, work["recon"] + work["max"])}
     kname, bound, peak, peak_note, per_dets = kinds[dom]
     alg = per_dets * det_s
     achieved = alg / (dur_ms / 1000.0) / 1e12
@@ -373,10 +377,13 @@ def run_lloid(args, rank, world, dist):
     roofline = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
                 "algorithmic_flop_per_launch": alg, "launch_ms": dur_ms}
-    rec_ms = stages["recon"][0] / max(1, stages["recon"][1])
-    executed_recon = 2.0 * 2 * Mpad * Kpad * F0 * det_s * n_mma
-    recon_info = {"launch_ms": rec_ms, "executed_tflops": executed_recon / (rec_ms / 1000.0) / 1e12,
-                  "algorithmic_tflops": (work["recon"] + work["max"]) * det_s / (rec_ms / 1000.0) / 1e12}
+    per_stage = {}
+    for st_name in ("fir", "upsample", "recon"):
+        ms_l = stages[st_name][0] / max(1, stages[st_name][1])
+        k = kinds[st_name]
+        per_stage[st_name] = {"kernel": k[0], "launch_ms": ms_l, "launches_per_step": stages[st_name][1] / args.steps,
+                              "algorithmic_tflops": k[4] * det_s / (ms_l / 1000.0) / 1e12 if ms_l > 0 else None}
+    recon_info = per_stage
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items()}
 
     cpu = None
@@ -402,7 +409,7 @@ def run_lloid(args, rank, world, dist):
                                       "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
                                       "n": len(lat)} if lat else None),
             "stage_ms_per_step": stage_ms,
-            "recon_kernel": recon_info,
+            "kernels": recon_info,
             "paths": {p: units * args.steps / (sum(v["ms"]) / 1000.0) for p, v in per_ctx.items()},
         }
         print(json.dumps(line), flush=True)

@@ -193,6 +193,12 @@ LLOID_API lloid_status lloid_push_strain_all(lloid_ctx* ctx, int64_t t0, const f
 LLOID_API lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid_trigger* out, int64_t cap,
                                  int64_t* n_out, int32_t timeout_ms);
 
+/* The same for the n_windows consecutive windows w0 .. w0 + n_windows - 1
+ * (1 <= n_windows <= 16), ordered by window, detector, bank, template, with
+ * one compaction pass and one wait for all of them. */
+LLOID_API lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_trigger* out,
+                                                 int64_t cap, int64_t* n_out, int32_t timeout_ms);
+
 /* Debug and parity aid: recompute the full-rate SNR rows of the most recent
  * push of detector `det` for bank `bank` into the DEVICE array out
  * [2M][n_last] (row 2i = real part of template i) with the same kernels and

@@ -322,12 +322,16 @@ __global__ void __launch_bounds__(256) k_recon_f32(const ReconJob* __restrict__ 
 // a5: finalise window w for one (bank, detector): reduce the tile partials of
 // every template, threshold, and flag the bank's loudest template.
 // ---------------------------------------------------------------------------
+// grid (bank, detector, window): windows w0 .. w0 + gridDim.z - 1; window w's
+// slab is slab_base + (w mod ring) * n_det_total * slab_det_stride.
 __global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ jobs, const Partial* __restrict__ part,
                                                   long long part_tmpl_stride, int n_slots, int tiles_per_window,
-                                                  long long w, float threshold, SlabEntry* __restrict__ slab,
-                                                  long long slab_det_stride, int det0) {
+                                                  long long w0, float threshold, SlabEntry* __restrict__ slab_base,
+                                                  int ring, int n_det_total, long long slab_det_stride, int det0) {
     const FinJob jb = jobs[blockIdx.x];
     const int det = det0 + blockIdx.y;
+    const long long w = w0 + blockIdx.z;
+    SlabEntry* slab = slab_base + (size_t)(w % ring) * n_det_total * slab_det_stride;
     const int s0 = (int)((w * tiles_per_window) & (n_slots - 1));
     SlabEntry* out = slab + det * slab_det_stride;
     float tbest = -1.f;
@@ -380,22 +384,32 @@ struct TriggerOut {       // identical layout to lloid_trigger
     float snr, phase, re, im;
 };
 
+// Entries e = (wl * n_det + det) * M_used + m for windows w0 .. w0 + n_win - 1.
+__device__ __forceinline__ const SlabEntry& slab_at(const SlabEntry* slab, long long cap, int M_used, int n_det,
+                                                    long long w0, int ring, long long e, long long* w_out,
+                                                    long long* det_out, long long* m_out) {
+    const long long m = e % M_used, r = e / M_used;
+    const long long det = r % n_det, wl = r / n_det;
+    *w_out = w0 + wl; *det_out = det; *m_out = m;
+    return slab[((w0 + wl) % ring) * n_det * cap + det * cap + m];
+}
+
 __global__ void k_gather_count(const SlabEntry* __restrict__ slab, long long cap, int M_used, int n_det,
-                               int* __restrict__ counts) {
-    const long long total = (long long)n_det * M_used;
+                               long long w0, int n_win, int ring, int* __restrict__ counts) {
+    const long long total = (long long)n_win * n_det * M_used;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int v = 0;
     if (e < total) {
-        const long long det = e / M_used, m = e % M_used;
-        v = slab[det * cap + m].flags & 1;
+        long long w, det, m;
+        v = slab_at(slab, cap, M_used, n_det, w0, ring, e, &w, &det, &m).flags & 1;
     }
     v = __syncthreads_count(v);
     if (threadIdx.x == 0) counts[blockIdx.x] = v;
 }
 
 __global__ void k_gather_scatter(const SlabEntry* __restrict__ slab, long long cap, int M_used, int n_det,
-                                 const int* __restrict__ counts, int n_chunks, const int* __restrict__ bank_of,
-                                 const int* __restrict__ tmpl0_of, long long window, long long W,
+                                 long long w0, int n_win, int ring, const int* __restrict__ counts, int n_chunks,
+                                 const int* __restrict__ bank_of, const int* __restrict__ tmpl0_of, long long W,
                                  TriggerOut* __restrict__ out, long long out_cap, long long* __restrict__ total_out) {
     __shared__ int red[1024 / 32];
     __shared__ int base_s;
@@ -418,14 +432,13 @@ __global__ void k_gather_scatter(const SlabEntry* __restrict__ slab, long long c
         if (blockIdx.x == 0) *total_out = b;
     }
     __syncthreads();
-    const long long total = (long long)n_det * M_used;
+    const long long total = (long long)n_win * n_det * M_used;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     SlabEntry en;
     int v = 0;
-    long long det = 0, m = 0;
+    long long det = 0, m = 0, window = 0;
     if (e < total) {
-        det = e / M_used; m = e % M_used;
-        en = slab[det * cap + m];
+        en = slab_at(slab, cap, M_used, n_det, w0, ring, e, &window, &det, &m);
         v = en.flags & 1;
     }
     // block-wide exclusive scan of v

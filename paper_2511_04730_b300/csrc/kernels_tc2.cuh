@@ -49,7 +49,7 @@ struct LevelJob {
     const float* acc_in;           // level below, transposed [2][rows][Mpad], detector 0
     float* acc_out;                // this level (non-top), transposed, detector 0
     long long acc_in_det_stride, acc_out_det_stride;   // elements
-    const float* upz;              // [F][2 N_up + 1] polyphase sub-kernels (Eq. 7)
+    const float* upz;              // unused (sub-kernels live in c_upz)
     int acc_in_rows, acc_out_rows; // rows per re/im plane
     int Kp;                        // Kpad of the level (0: no slice at this rate)
     int M, Mpad, tmpl0;
@@ -61,6 +61,14 @@ struct LevelJob {
 };
 
 struct FirMaps { CUtensorMap a, a_lo; };
+
+// Eq. 7 polyphase sub-kernels z_phi[t] = g[t F + phi] (t = 0..16, N_up = 8) for
+// F = 2, 4, ..., 64, packed F after F (offset 17 (F - 2)); filled once per
+// device.  Indexed with compile-time constants, so each tap is one FFMA with a
+// constant-bank operand.
+constexpr int kUpTaps = 17;
+constexpr int kUpTable = kUpTaps * (2 + 4 + 8 + 16 + 32 + 64);
+__constant__ float c_upz[kUpTable];
 struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo; };
 
 // ---------------------------------------------------------------------------
@@ -327,8 +335,10 @@ struct LevCfg {
 // and 0 or 32 for F = 64: every register index below is a compile-time constant.
 template <int F, int NUP, int PH0>
 __device__ __forceinline__ void add_up32(float (&v)[32], const float* __restrict__ plane, int Mpad, int m,
-                                         long long q0, long long lo_in, int rows_in, const float* __restrict__ z) {
+                                         long long q0, long long lo_in, int rows_in) {
+    static_assert(NUP == 8, "the constant tables hold N_up = 8");
     constexpr int NW = (PH0 + 31) / F + 2 * NUP + 1;
+    constexpr int OFF = kUpTaps * (F - 2);
     const long long a0 = fdiv(q0, F) - NUP;          // x index of window slot 0
     float x[NW];
 #pragma unroll
@@ -339,26 +349,30 @@ __device__ __forceinline__ void add_up32(float (&v)[32], const float* __restrict
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
         const int ph = (PH0 + j) % F;
-        const int b = (PH0 + j) / F + NUP;           // floor(q/F) + N_up - a0
+        const int b = (PH0 + j) / F + 2 * NUP;       // (floor(q/F) + N_up) - a0
+        if (ph == 0) {                               // z_0 = g[t F]: 1 at t = N_up, 0 elsewhere
+            v[j] += x[b - NUP];
+            continue;
+        }
         float s = 0.f;
 #pragma unroll
-        for (int t = 0; t <= 2 * NUP; ++t) s = fmaf(__ldg(z + ph * (2 * NUP + 1) + t), x[b - t], s);
+        for (int t = 0; t <= 2 * NUP; ++t) s = fmaf(c_upz[OFF + ph * kUpTaps + t], x[b - t], s);
         v[j] += s;
     }
 }
 
 template <int NUP>
 __device__ __forceinline__ void add_up_dispatch(int F, float (&v)[32], const float* plane, int Mpad, int m,
-                                                long long q0, long long lo_in, int rows_in, const float* z) {
+                                                long long q0, long long lo_in, int rows_in) {
     switch (F) {
-        case 2: add_up32<2, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
-        case 4: add_up32<4, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
-        case 8: add_up32<8, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
-        case 16: add_up32<16, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
-        case 32: add_up32<32, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z); break;
+        case 2: add_up32<2, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
+        case 4: add_up32<4, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
+        case 8: add_up32<8, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
+        case 16: add_up32<16, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
+        case 32: add_up32<32, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
         case 64:
-            if ((q0 & 63) == 0) add_up32<64, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in, z);
-            else add_up32<64, NUP, 32>(v, plane, Mpad, m, q0, lo_in, rows_in, z);
+            if ((q0 & 63) == 0) add_up32<64, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in);
+            else add_up32<64, NUP, 32>(v, plane, Mpad, m, q0, lo_in, rows_in);
             break;
         default: break;
     }
@@ -515,8 +529,8 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 const long long q0 = Q0 + 128LL * tt + c;
                 if (jb.F) {
-                    add_up_dispatch<NUP>(jb.F, re, in_re, jb.Mpad, m, q0, lo_in, jb.acc_in_rows, jb.upz);
-                    add_up_dispatch<NUP>(jb.F, im, in_im, jb.Mpad, m, q0, lo_in, jb.acc_in_rows, jb.upz);
+                    add_up_dispatch<NUP>(jb.F, re, in_re, jb.Mpad, m, q0, lo_in, jb.acc_in_rows);
+                    add_up_dispatch<NUP>(jb.F, im, in_im, jb.Mpad, m, q0, lo_in, jb.acc_in_rows);
                 }
                 if (TOP) {
 #pragma unroll

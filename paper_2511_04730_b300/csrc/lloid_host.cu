@@ -160,7 +160,6 @@ struct lloid_ctx {
     uint16_t* s_hi[kMaxRates + 1] = {};
     uint16_t* s_lo[kMaxRates + 1] = {};
     long long s_len[kMaxRates + 1] = {};
-    float* d_upz[7] = {};              // Eq. 7 sub-kernels for F = 2, 4, ..., 128
     std::vector<void*> job_allocs;
     cudaEvent_t done_ev = nullptr;
     int* d_err = nullptr;              // device-side wait-expiry code (0 = none)
@@ -438,9 +437,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                 const LevelRT& P = b->lev[j - 1];
                 q.acc_in = P.d_acc; q.acc_in_det_stride = 2LL * P.acc_rows * b->Mpad; q.acc_in_rows = P.acc_rows;
                 q.F = P.D / L.D; q.D_lo = P.D; q.Lambda_lo = P.Lambda;
-                int li = 0;
-                while ((2 << li) != q.F) ++li;
-                q.upz = ctx->d_upz[li];
+                q.upz = nullptr;   // the kernels read the constant tables
             }
             if (j < nl - 1) { q.acc_out = L.d_acc; q.acc_out_det_stride = 2LL * L.acc_rows * b->Mpad; q.acc_out_rows = L.acc_rows; }
             q.Kp = L.Kp; q.M = b->M; q.Mpad = b->Mpad; q.tmpl0 = b->tmpl0;
@@ -711,13 +708,13 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     // a5 finalise completed windows
     const long long W = ctx->cfg.window_samples;
     StageTimer tmf(ctx, 5);
-    for (long long w = k_a / W; (w + 1) * W <= k_a + n; ++w) {
-        SlabEntry* slab = ctx->d_slab + (size_t)(w % kWindowRing) * ctx->cfg.n_detectors * ctx->M_cap;
-        dim3 grid(ctx->n_fin, nd);
+    const long long w_first = k_a / W, w_end = (k_a + n) / W;   // windows completed by this push
+    if (w_end > w_first && ctx->n_fin > 0) {
+        dim3 grid(ctx->n_fin, nd, (unsigned)(w_end - w_first));
         k_finalize<<<grid, 256, 0, ctx->stream>>>(ctx->d_finj, ctx->d_part,
                                                   (long long)ctx->cfg.n_detectors * ctx->n_slots, ctx->n_slots,
-                                                  ctx->tiles_per_window, w, ctx->cfg.snr_threshold, slab,
-                                                  ctx->M_cap, det0);
+                                                  ctx->tiles_per_window, w_first, ctx->cfg.snr_threshold, ctx->d_slab,
+                                                  kWindowRing, ctx->cfg.n_detectors, ctx->M_cap, det0);
         CKL();
     }
     return LLOID_OK;
@@ -963,7 +960,7 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         c.precision < 0 || c.precision > 2 || !(c.snr_threshold >= 0.f))
         return fail(nullptr, LLOID_EINVAL, "bad configuration");
     if (c.window_overlap != 0) return LLOID_EINVAL;
-    if (c.precision != LLOID_FP32 && (c.max_block % kTcTileN || c.n_up != 8))
+    if (c.precision != LLOID_FP32 && (c.max_block % kTcTileN || c.n_up != 8 || c.f0 / c.min_rate > 64))
         return fail(nullptr, LLOID_EINVAL, "tensor-core paths need max_block % 128 == 0 and n_up == 8");
     CK(cudaSetDevice(c.device));
     CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, c.device));
@@ -1004,18 +1001,20 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
             if ((st = dalloc(ctx, &ctx->s_lo[r], bytes, nullptr, &ctx->state_bytes))) return st;
         }
         // Eq. 7 sub-kernels z_phi[t] = g[t F + phi], t = 0..2 N_up, g of Eq. 4 with c = F N_up
-        for (int i = 0; i < 7; ++i) {
-            const int F = 2 << i;
-            std::vector<double> g = sinc_windowed(F, F * c.n_up);
-            std::vector<float> z((size_t)F * (2 * c.n_up + 1), 0.f);
+        // (the sinc's zeros at multiples of F written as exact zeros)
+        std::vector<float> z(kUpTable, 0.f);
+        for (int F = 2; F <= 64; F *= 2) {
+            const int cF = F * c.n_up;
+            std::vector<double> g = sinc_windowed(F, cF);
             for (int ph = 0; ph < F; ++ph)
-                for (int t = 0; t <= 2 * c.n_up; ++t) {
+                for (int t = 0; t < kUpTaps; ++t) {
                     const long long k = (long long)t * F + ph;
-                    if (k <= 2LL * F * c.n_up) z[(size_t)ph * (2 * c.n_up + 1) + t] = (float)g[k];
+                    double v = (k <= 2LL * cF) ? g[k] : 0.0;
+                    if ((k - cF) % F == 0 && k != cF) v = 0.0;
+                    z[(size_t)kUpTaps * (F - 2) + (size_t)ph * kUpTaps + t] = (float)v;
                 }
-            if ((st = dalloc(ctx, &ctx->d_upz[i], z.size() * 4, nullptr, &ctx->state_bytes))) return st;
-            CK(cudaMemcpyAsync(ctx->d_upz[i], z.data(), z.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
         }
+        CK(cudaMemcpyToSymbol(c_upz, z.data(), z.size() * sizeof(float)));
     }
     ctx->pos.assign(nd, 0);
     ctx->fin.assign(nd, -1);
@@ -1056,7 +1055,7 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
     cudaFree(ctx->d_err);
     for (int r = 0; r <= kMaxRates; ++r) { cudaFree(ctx->s_hi[r]); cudaFree(ctx->s_lo[r]); }
-    for (int i = 0; i < 7; ++i) cudaFree(ctx->d_upz[i]);
+
     if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
     for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -1248,43 +1247,60 @@ lloid_status lloid_push_strain_all(lloid_ctx* ctx, int64_t t0, const float* bloc
     return push_common(ctx, 0, ctx->cfg.n_detectors, t0, blocks, n, is_device_ptr);
 }
 
-lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid_trigger* out, int64_t cap, int64_t* n_out,
-                                 int32_t timeout_ms) {
+lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_trigger* out,
+                                       int64_t cap, int64_t* n_out, int32_t timeout_ms) {
     if (!ctx) return LLOID_EINVAL;
-    if (!n_out || (cap > 0 && !out) || window < 0) return fail(ctx, LLOID_EINVAL, "bad output arguments");
+    if (!n_out || (cap > 0 && !out) || w0 < 0 || n_windows < 1 || n_windows > kWindowRing)
+        return fail(ctx, LLOID_EINVAL, "bad output arguments");
     *n_out = 0;
     const long long W = ctx->cfg.window_samples;
+    const long long w1 = w0 + n_windows - 1;
     long long fin_min = ctx->fin[0], fin_max = ctx->fin[0];
     for (long long f : ctx->fin) { fin_min = std::min(fin_min, f); fin_max = std::max(fin_max, f); }
-    if (window > fin_min) return fail(ctx, LLOID_ENOTREADY, "window %lld needs data through sample %lld", (long long)window, (window + 1) * W);
-    if (window + kWindowRing <= fin_max) return fail(ctx, LLOID_EEXPIRED, "window %lld is no longer retained", (long long)window);
+    if (w1 > fin_min) return fail(ctx, LLOID_ENOTREADY, "window %lld needs data through sample %lld", w1, (w1 + 1) * W);
+    if (w0 + kWindowRing <= fin_max) return fail(ctx, LLOID_EEXPIRED, "window %lld is no longer retained", (long long)w0);
     lloid_status st = wait_done(ctx, timeout_ms);
     if (st) return st;
     if ((st = check_kernel_err(ctx))) return st;
     const int nd = ctx->cfg.n_detectors;
     const int M_used = ctx->M_used;
     if (M_used == 0) return LLOID_OK;
-    const SlabEntry* slab = ctx->d_slab + (size_t)(window % kWindowRing) * nd * ctx->M_cap;
-    const long long total = (long long)nd * M_used;
+    const long long total = n_windows * nd * M_used;
     const int chunks = (int)((total + 1023) / 1024);
+    if (chunks > ctx->counts_cap) {
+        cudaFree(ctx->d_counts);
+        CK(cudaMalloc(&ctx->d_counts, chunks * sizeof(int)));
+        ctx->counts_cap = chunks;
+    }
+    if (total > ctx->trig_cap) {
+        cudaFree(ctx->d_trig);
+        CK(cudaMalloc(&ctx->d_trig, total * sizeof(TriggerOut)));
+        ctx->trig_cap = total;
+    }
     StageTimer tmg(ctx, 6);
-    k_gather_count<<<chunks, 1024, 0, ctx->stream>>>(slab, ctx->M_cap, M_used, nd, ctx->d_counts);
+    k_gather_count<<<chunks, 1024, 0, ctx->stream>>>(ctx->d_slab, ctx->M_cap, M_used, nd, w0, (int)n_windows,
+                                                     kWindowRing, ctx->d_counts);
     CKL();
-    k_gather_scatter<<<chunks, 1024, 0, ctx->stream>>>(slab, ctx->M_cap, M_used, nd, ctx->d_counts, chunks,
-                                                       ctx->d_bank_of, ctx->d_tmpl0_of, window, W, ctx->d_trig,
-                                                       ctx->trig_cap, ctx->d_total);
+    k_gather_scatter<<<chunks, 1024, 0, ctx->stream>>>(ctx->d_slab, ctx->M_cap, M_used, nd, w0, (int)n_windows,
+                                                       kWindowRing, ctx->d_counts, chunks, ctx->d_bank_of,
+                                                       ctx->d_tmpl0_of, W, ctx->d_trig, ctx->trig_cap, ctx->d_total);
     CKL();
     CK(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const long long cnt = *ctx->h_total;
     *n_out = cnt;
-    if (cnt > cap) return fail(ctx, LLOID_ERANGE, "window %lld has %lld triggers, capacity %lld", (long long)window, cnt, (long long)cap);
+    if (cnt > cap) return fail(ctx, LLOID_ERANGE, "%lld triggers, capacity %lld", cnt, (long long)cap);
     static_assert(sizeof(TriggerOut) == sizeof(lloid_trigger), "trigger layout");
     if (cnt > 0) {
         CK(cudaMemcpyAsync(out, ctx->d_trig, cnt * sizeof(lloid_trigger), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
     return LLOID_OK;
+}
+
+lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid_trigger* out, int64_t cap, int64_t* n_out,
+                                 int32_t timeout_ms) {
+    return lloid_pull_triggers_range(ctx, window, 1, out, cap, n_out, timeout_ms);
 }
 
 lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* out, int64_t cap, int64_t* t0,

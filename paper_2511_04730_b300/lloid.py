@@ -166,13 +166,15 @@ class Context:
         if dev:
             self._torch_after()
 
-    def pull(self, window: int, timeout_ms: int = -1, cap: int = 1 << 16) -> np.ndarray:
-        """Triggers of one window as a numpy structured array (TRIGGER_DTYPE)."""
+    def pull(self, window: int, timeout_ms: int = -1, cap: int = 1 << 16, n_windows: int = 1) -> np.ndarray:
+        """Triggers of windows window .. window + n_windows - 1 as a numpy
+        structured array (TRIGGER_DTYPE)."""
         n_out = ctypes.c_int64()
         while True:
             out = np.zeros(cap, dtype=TRIGGER_DTYPE)
-            st = self._lib.lloid_pull_triggers(self._h, window, out.ctypes.data_as(ctypes.POINTER(_lib.LloidTrigger)),
-                                               cap, ctypes.byref(n_out), timeout_ms)
+            st = self._lib.lloid_pull_triggers_range(self._h, window, n_windows,
+                                                     out.ctypes.data_as(ctypes.POINTER(_lib.LloidTrigger)),
+                                                     cap, ctypes.byref(n_out), timeout_ms)
             if st == -8:   # ERANGE: grow and retry
                 cap = int(n_out.value)
                 continue

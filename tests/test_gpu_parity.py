@@ -99,6 +99,24 @@ def test_streaming_block_sizes_identical(lloid, bank64_case, precision):
         assert np.array_equal(z, outs[0])
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16_split", "bf16_split"])
+@pytest.mark.parametrize("which", [0, 1])
+def test_single_slice_banks(lloid, bank64_case, precision, which):
+    """One slice at a time: slice 0 alone (f0, no ladder: FIR + top level) and
+    slice 1 alone (256 Hz: the SNR comes only through the Eq. 7-8 ladder)."""
+    w, bank, plan, d, _ = bank64_case
+    sb = lloid.build_svd_bank(bank, plan)
+    sl = O.svd_bank(bank, plan)
+    d = d[: 16 * F0]
+    z_or = O.lloid_snr(d.astype(np.float64), [sl[which]], F0)
+    with _ctx(lloid, precision) as ctx:
+        bid = ctx.load_bank([sb[which]])
+        z = stream_snr(ctx, bid, d, 4096)
+    err = max_abs_complex(z, z_or)
+    print(f"{precision} slice {which}: max|dz| = {err:.3e}")
+    assert err <= TOL[precision]
+
+
 def test_push_all_equals_single_detector_pushes(lloid, bank64_case):
     w, bank, plan, d, _ = bank64_case
     sb = lloid.build_svd_bank(bank, plan)
