@@ -325,7 +325,10 @@ struct LevCfg {
     static constexpr int TILE_A = kTcTileM * kTcK * 2;
     static constexpr int TILE_B = kTcTileN * kTcK * 2;
     static constexpr int STAGE_BYTES = NA * TILE_A + 2 * TILE_B;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr int XCHG = 2 * 128 * 16;          // tile-argmax exchange between the column halves
+    static constexpr int SMEM = STAGES * STAGE_BYTES + XCHG + 1024 + 256;
+    static constexpr int EPI_WARPS = 8;                 // two per TMEM lane quarter, 64 columns each
+    static constexpr int THREADS = 64 + 32 * EPI_WARPS;
 };
 
 // Up_F of the level below for 32 consecutive outputs q0..q0+31 of one
@@ -379,16 +382,18 @@ __device__ __forceinline__ void add_up_dispatch(int F, float (&v)[32], const flo
 }
 
 template <bool BF16, bool TOP, bool STORE_Z>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
     k_level_tc(const LevelJob* __restrict__ jobs, const LevelMaps* __restrict__ maps,
                const int* __restrict__ tile_base, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
                int det0, int n_det_push, long long window, Partial* __restrict__ part, long long part_tmpl_stride,
                int n_slots, float* __restrict__ zout, int* __restrict__ err) {
     constexpr int NUP = 8;
     using C = LevCfg<BF16>;
+    constexpr int EPI = 32 * C::EPI_WARPS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+    float4* xchg = reinterpret_cast<float4*>(smem + C::STAGES * C::STAGE_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES + C::XCHG);
     uint64_t* empty = full + C::STAGES;
     uint64_t* tfull = empty + C::STAGES;
     uint64_t* tempty = tfull + 2;
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(192, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(tfull + b, 1); mbar_init(tempty + b, kEpiThreads); }
+        for (int b = 0; b < 2; ++b) { mbar_init(tfull + b, 1); mbar_init(tempty + b, EPI); }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -493,7 +498,10 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         // ---------------------------------------------------------------- epilogue
+        // 8 warps: warp & 3 picks the TMEM lane quarter (rows), (warp - 2) / 4 the
+        // 64-column half of the 128-sample tile.
         const int qd = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int rowm = qd * 32 + lane;
         int i = 0;
         for (int it = blockIdx.x; it < total; it += gridDim.x, ++i) {
@@ -518,7 +526,7 @@ __global__ void __launch_bounds__(192, 1)
             const float* in_re = jb.F ? jb.acc_in + det * jb.acc_in_det_stride : nullptr;
             const float* in_im = jb.F ? in_re + (long long)jb.acc_in_rows * jb.Mpad : nullptr;
 #pragma unroll 1
-            for (int c = 0; c < kTcTileN; c += 32) {
+            for (int c = half * 64; c < half * 64 + 64; c += 32) {
                 float re[32], im[32];
                 if (jb.Kp > 0) {
                     tmem_ld32(base + c, re);
@@ -560,12 +568,20 @@ __global__ void __launch_bounds__(192, 1)
             }
             tc_fence_before();
             mbar_arrive(tempty + buf);
-            if (TOP && !STORE_Z && m < jb.M) {
-                const long long k0 = Q0 + 128LL * tt;         // Q0 == lo == k_a at the top level
-                const long long kwin0 = (k0 / window) * window;
-                const int slot = (int)((k0 / kTcTileN) & (n_slots - 1));
-                part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots + slot] =
-                    make_float4(best, __int_as_float((int)(k0 - kwin0) + bk), bre, bim);
+            if (TOP && !STORE_Z) {
+                // the later half hands its tile argmax to the earlier half (which wins ties)
+                float4* xb = xchg + buf * 128;
+                if (half == 1) xb[rowm] = make_float4(best, __int_as_float(bk), bre, bim);
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI) : "memory");
+                if (half == 0 && m < jb.M) {
+                    const float4 o = xb[rowm];
+                    if (o.x > best) { best = o.x; bk = __float_as_int(o.y); bre = o.z; bim = o.w; }
+                    const long long k0 = Q0 + 128LL * tt;         // Q0 == lo == k_a at the top level
+                    const long long kwin0 = (k0 / window) * window;
+                    const int slot = (int)((k0 / kTcTileN) & (n_slots - 1));
+                    part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots + slot] =
+                        make_float4(best, __int_as_float((int)(k0 - kwin0) + bk), bre, bim);
+                }
             }
         }
     }

@@ -603,7 +603,7 @@ lloid_status launch_level(lloid_ctx* ctx, int depth, long long k_a, long long n,
     const int smem = bf ? LevCfg<true>::SMEM : LevCfg<false>::SMEM;
     Partial* part = store_z ? nullptr : ctx->d_part;
 #define LAUNCH_LV(BFV, TOPV, SZ)                                                                                   \
-    k_level_tc<BFV, TOPV, SZ><<<g, 192, smem, ctx->stream>>>(jobs, maps, base, n_jobs, tiles, k_a, k_a + n, det0,  \
+    k_level_tc<BFV, TOPV, SZ><<<g, LevCfg<BFV>::THREADS, smem, ctx->stream>>>(jobs, maps, base, n_jobs, tiles, k_a, k_a + n, det0,  \
                                                               n_det_push, ctx->cfg.window_samples, part, part_stride, \
                                                               ctx->n_slots, zout, ctx->d_err)
     if (depth > 0) { if (bf) LAUNCH_LV(true, false, false); else LAUNCH_LV(false, false, false); }
