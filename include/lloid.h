@@ -227,6 +227,33 @@ LLOID_API void* lloid_stream(const lloid_ctx* ctx);
 #define LLOID_N_STAGES 7
 LLOID_API lloid_status lloid_stage_times(lloid_ctx* ctx, double* ms, int64_t* launches, int reset);
 
+/* Allocation-free trigger extraction (no counterpart in the paper; a service
+ * for callers that cannot allocate device memory while they run, such as a
+ * real-time strain callback that must not block in cudaMalloc, or a host
+ * framework that owns the device memory pool).  Finds the triggers of an SNR
+ * block the caller already holds: z is a DEVICE array [2 n_templates][n]
+ * (row 2i real, 2i+1 imaginary part of template i) covering full-rate samples
+ * [t0, t0 + n), with t0 and n multiples of `window`.  Per window and template
+ * the maximum |z| (earliest sample on ties) becomes a trigger if it exceeds
+ * `threshold`; the window's loudest template (lowest index on ties) is
+ * flagged is_bank_max -- the same rules as lloid_pull_triggers.  Triggers go
+ * to the DEVICE array out[cap] in (window, template) order with `detector`
+ * and `bank` copied into each record; the total count (even when above cap)
+ * goes to the DEVICE int64 *n_out.  Work is enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and the call returns at once.
+ * It calls no allocating routine: its scratch is one array compiled into the
+ * library (about 4.2 MB on every GPU that loads it, held until exit), whose
+ * device address the first call on each device looks up -- make that first
+ * call before any stream capture.  Every call shares that array and leaves
+ * its contents behind (each call rewrites all it reads), so calls whose GPU
+ * work overlaps race: serialise them.  LLOID_ERANGE when n_templates x
+ * (n / window) exceeds 262144 (split the block), LLOID_EINVAL on bad
+ * arguments, LLOID_ECUDA if a launch fails. */
+LLOID_API lloid_status lloid_triggers_from_snr_noalloc(const float* z, int32_t n_templates, int64_t n, int64_t t0,
+                                                       int64_t window, float threshold, int32_t detector,
+                                                       int32_t bank, lloid_trigger* out, int64_t cap,
+                                                       int64_t* n_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

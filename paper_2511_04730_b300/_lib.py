@@ -73,6 +73,9 @@ SIGNATURES = [
     ("lloid_synchronize", ctypes.c_int, [ctypes.c_void_p]),
     ("lloid_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
     ("lloid_stream", ctypes.c_void_p, [ctypes.c_void_p]),
+    ("lloid_triggers_from_snr_noalloc", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
+      ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     ("lloid_stage_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
 ]

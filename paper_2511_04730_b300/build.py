@@ -11,8 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblloid_b300.so")
-SOURCES = ["lloid_host.cu"]
-HEADERS = ["lloid_common.cuh", "kernels_simt.cuh", "kernels_tc.cuh"]
+SOURCES = ["lloid_host.cu", "lloid_noalloc.cu"]
+HEADERS = ["lloid_common.cuh", "kernels_simt.cuh", "kernels_tc.cuh", "kernels_tc2.cuh"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -210,3 +210,31 @@ class Context:
         ln = (ctypes.c_int64 * _lib.N_STAGES)()
         self._check(self._lib.lloid_stage_times(self._h, ms, ln, 1 if reset else 0))
         return {name: (ms[i], int(ln[i])) for i, name in enumerate(_lib.STAGE_NAMES)}
+
+
+def triggers_from_snr_noalloc(z, t0: int, window: int = 2048, threshold: float = 4.0, detector: int = 0,
+                              bank: int = 0, out=None, n_out=None, stream=None):
+    """Allocation-free trigger extraction for an SNR block already on the GPU.
+
+    For callers that must not allocate device memory while they run: the
+    library call itself uses only its compiled-in scratch.  ``z`` is a
+    contiguous float32 CUDA tensor [2M, n]; ``out`` (uint8 CUDA tensor of
+    cap * 48 bytes) and ``n_out`` (int64 CUDA tensor of one element) are
+    preallocated by the caller, or allocated here for convenience.  Returns
+    the triggers as a numpy structured array (this read-back synchronises)."""
+    import torch
+    lib = _lib.load()
+    n_rows, n = z.shape
+    if out is None:
+        out = torch.empty((n_rows // 2) * (n // window) * TRIGGER_DTYPE.itemsize, dtype=torch.uint8, device=z.device)
+    if n_out is None:
+        n_out = torch.zeros(1, dtype=torch.int64, device=z.device)
+    cap = out.numel() // TRIGGER_DTYPE.itemsize
+    s = torch.cuda.current_stream(z.device) if stream is None else stream
+    st = lib.lloid_triggers_from_snr_noalloc(ctypes.c_void_p(z.data_ptr()), n_rows // 2, n, t0, window, threshold,
+                                             detector, bank, ctypes.c_void_p(out.data_ptr()), cap,
+                                             ctypes.c_void_p(n_out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise LloidError(st, "lloid_triggers_from_snr_noalloc failed")
+    k = int(n_out.item())
+    return np.frombuffer(out[: min(k, cap) * TRIGGER_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=TRIGGER_DTYPE)
