@@ -369,7 +369,8 @@ def run_lloid(args, rank, world, dist):
                  "upsample": ("k_upsample", "alu", alu_peak, alu_note, work["ladder"]),
                  "recon": ("k_recon_f32", "alu", alu_peak, alu_note, work["recon"] + work["max"])}
     kname, bound, peak, peak_note, per_dets = kinds[dom]
-    alg = per_dets * det_s
+    launches_dom = max(1.0, stages[dom][1] / args.steps)
+    alg = per_dets * det_s / launches_dom          # one launch's share of the stage's work
     achieved = alg / (dur_ms / 1000.0) / 1e12
     Kpad = -(-sum(s.n_basis for s in sb) // 64) * 64
     Mpad = -(-M // 128) * 128
@@ -381,8 +382,10 @@ def run_lloid(args, rank, world, dist):
     for st_name in ("fir", "upsample", "recon"):
         ms_l = stages[st_name][0] / max(1, stages[st_name][1])
         k = kinds[st_name]
-        per_stage[st_name] = {"kernel": k[0], "launch_ms": ms_l, "launches_per_step": stages[st_name][1] / args.steps,
-                              "algorithmic_tflops": k[4] * det_s / (ms_l / 1000.0) / 1e12 if ms_l > 0 else None}
+        lps = stages[st_name][1] / args.steps
+        per_stage[st_name] = {"kernel": k[0], "launch_ms": ms_l, "launches_per_step": lps,
+                              "algorithmic_tflops": (k[4] * det_s / max(lps, 1.0)) / (ms_l / 1000.0) / 1e12
+                              if ms_l > 0 else None}
     recon_info = per_stage
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items()}
 

@@ -126,7 +126,8 @@ struct FirCfg {
     static constexpr int TILE_A = 128 * kTcK * 2;              // 16 KB
     static constexpr int STAGE_BYTES = (BF16 ? 2 : 1) * TILE_A;
     static constexpr int STAGE_AREA = STAGES * STAGE_BYTES;
-    static constexpr int EPI_BYTES = 2 * 256 * 16 * 2;         // staging [256 q][16 bases] hi + lo
+    static constexpr int EPI_LD = 24;                          // staging row pitch (halves): conflict-free, 16 B aligned
+    static constexpr int EPI_BYTES = 2 * 256 * EPI_LD * 2;     // staging [256 q][16 bases (+pad)] hi + lo
 };
 
 template <bool BF16>
@@ -284,8 +285,8 @@ __global__ void __launch_bounds__(192, 1)
                 for (int j = 0; j < 32; ++j) {
                     uint16_t h, l;
                     split_hilo<BF16>(v[j], h, l);
-                    epi[(8 * j + tph) * 16 + l_loc] = h;
-                    epi[256 * 16 + (8 * j + tph) * 16 + l_loc] = l;
+                    epi[(8 * j + tph) * C::EPI_LD + l_loc] = h;
+                    epi[256 * C::EPI_LD + (8 * j + tph) * C::EPI_LD + l_loc] = l;
                 }
                 epi_sync();
                 // 256 rows x 32 B (hi) + 256 x 32 B (lo) as 16-byte stores, both ring mappings
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(192, 1)
                     const int r = (e >> 1) & 255, h16 = e & 1;
                     const long long q = 8 * (c0 + cc) + r;
                     if (cc + (r >> 3) >= jb.NC || q < qa || q >= qa + jb.q_count) continue;
-                    const uint4 val = *reinterpret_cast<const uint4*>(epi + part * 256 * 16 + r * 16 + h16 * 8);
+                    const uint4 val = *reinterpret_cast<const uint4*>(epi + part * 256 * C::EPI_LD + r * C::EPI_LD + h16 * 8);
                     uint16_t* dst = part ? yl : yh;
                     const long long rr = q & (jb.y_rows - 1);
                     *reinterpret_cast<uint4*>(dst + rr * jb.y_ld + h16 * 8) = val;
@@ -336,46 +337,68 @@ struct LevCfg {
 // Eq. 8 centred: Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
 // Level tiles start at multiples of 128, so q0 mod F is PH0 = 0 for F <= 32
 // and 0 or 32 for F = 64: every register index below is a compile-time constant.
-template <int F, int NUP, int PH0>
-__device__ __forceinline__ void add_up32(float (&v)[32], const float* __restrict__ plane, int Mpad, int m,
-                                         long long q0, long long lo_in, int rows_in) {
+// Up_F of the level below for CH consecutive outputs q0..q0+CH-1 of one
+// template (column m of the transposed planes), added into vr/vi.  Eq. 8
+// centred: Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
+// Level tiles start at multiples of 128 and chunks at multiples of CH, so
+// q0 mod F is the compile-time PH0: every register index is a constant.
+template <int CH, int F, int NUP, int PH0>
+__device__ __forceinline__ void add_up(float (&vr)[CH], float (&vi)[CH], const float* __restrict__ pre,
+                                       const float* __restrict__ pim, int Mpad, int m, long long q0,
+                                       long long lo_in, int rows_in) {
     static_assert(NUP == 8, "the constant tables hold N_up = 8");
-    constexpr int NW = (PH0 + 31) / F + 2 * NUP + 1;
+    constexpr int NW = (PH0 + CH - 1) / F + 2 * NUP + 1;
     constexpr int OFF = kUpTaps * (F - 2);
     const long long a0 = fdiv(q0, F) - NUP;          // x index of window slot 0
-    float x[NW];
+    float xr[NW], xi[NW];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
+    for (int w = 0; w < NW; ++w) {                   // both windows in flight before any use
         const long long idx = a0 + w - lo_in;
-        x[w] = (idx >= 0 && idx < rows_in) ? __ldg(plane + idx * Mpad + m) : 0.f;
+        const bool in = idx >= 0 && idx < rows_in;
+        xr[w] = in ? __ldg(pre + idx * Mpad + m) : 0.f;
+        xi[w] = in ? __ldg(pim + idx * Mpad + m) : 0.f;
     }
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < CH; ++j) {
         const int ph = (PH0 + j) % F;
         const int b = (PH0 + j) / F + 2 * NUP;       // (floor(q/F) + N_up) - a0
         if (ph == 0) {                               // z_0 = g[t F]: 1 at t = N_up, 0 elsewhere
-            v[j] += x[b - NUP];
+            vr[j] += xr[b - NUP];
+            vi[j] += xi[b - NUP];
             continue;
         }
-        float s = 0.f;
+        float sr = 0.f, si = 0.f;
 #pragma unroll
-        for (int t = 0; t <= 2 * NUP; ++t) s = fmaf(c_upz[OFF + ph * kUpTaps + t], x[b - t], s);
-        v[j] += s;
+        for (int t = 0; t <= 2 * NUP; ++t) {
+            if (t * F + ph > 2 * F * NUP) continue;   // beyond the kernel: identically zero
+            const float zc = c_upz[OFF + ph * kUpTaps + t];
+            sr = fmaf(zc, xr[b - t], sr);
+            si = fmaf(zc, xi[b - t], si);
+        }
+        vr[j] += sr;
+        vi[j] += si;
     }
 }
 
 template <int NUP>
-__device__ __forceinline__ void add_up_dispatch(int F, float (&v)[32], const float* plane, int Mpad, int m,
-                                                long long q0, long long lo_in, int rows_in) {
+__device__ __forceinline__ void add_up_dispatch(int F, float (&vr)[16], float (&vi)[16], const float* pre,
+                                                const float* pim, int Mpad, int m, long long q0, long long lo_in,
+                                                int rows_in) {
+    const int ph0 = (int)(q0 & (F - 1));
     switch (F) {
-        case 2: add_up32<2, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
-        case 4: add_up32<4, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
-        case 8: add_up32<8, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
-        case 16: add_up32<16, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
-        case 32: add_up32<32, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in); break;
+        case 2: add_up<16, 2, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in); break;
+        case 4: add_up<16, 4, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in); break;
+        case 8: add_up<16, 8, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in); break;
+        case 16: add_up<16, 16, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in); break;
+        case 32:
+            if (ph0 == 0) add_up<16, 32, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
+            else add_up<16, 32, NUP, 16>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
+            break;
         case 64:
-            if ((q0 & 63) == 0) add_up32<64, NUP, 0>(v, plane, Mpad, m, q0, lo_in, rows_in);
-            else add_up32<64, NUP, 32>(v, plane, Mpad, m, q0, lo_in, rows_in);
+            if (ph0 == 0) add_up<16, 64, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
+            else if (ph0 == 16) add_up<16, 64, NUP, 16>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
+            else if (ph0 == 32) add_up<16, 64, NUP, 32>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
+            else add_up<16, 64, NUP, 48>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
             break;
         default: break;
     }
@@ -526,23 +549,20 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
             const float* in_re = jb.F ? jb.acc_in + det * jb.acc_in_det_stride : nullptr;
             const float* in_im = jb.F ? in_re + (long long)jb.acc_in_rows * jb.Mpad : nullptr;
 #pragma unroll 1
-            for (int c = half * 64; c < half * 64 + 64; c += 32) {
-                float re[32], im[32];
+            for (int c = half * 64; c < half * 64 + 64; c += 16) {
+                float re[16], im[16];
                 if (jb.Kp > 0) {
-                    tmem_ld32(base + c, re);
-                    tmem_ld32(base + 128 + c, im);
+                    tmem_ld16(base + c, re);
+                    tmem_ld16(base + 128 + c, im);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) { re[j] = 0.f; im[j] = 0.f; }
+                    for (int j = 0; j < 16; ++j) { re[j] = 0.f; im[j] = 0.f; }
                 }
                 const long long q0 = Q0 + 128LL * tt + c;
-                if (jb.F) {
-                    add_up_dispatch<NUP>(jb.F, re, in_re, jb.Mpad, m, q0, lo_in, jb.acc_in_rows);
-                    add_up_dispatch<NUP>(jb.F, im, in_im, jb.Mpad, m, q0, lo_in, jb.acc_in_rows);
-                }
+                if (jb.F) add_up_dispatch<NUP>(jb.F, re, im, in_re, in_im, jb.Mpad, m, q0, lo_in, jb.acc_in_rows);
                 if (TOP) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < 16; ++j) {
                         const float p = re[j] * re[j] + im[j] * im[j];
                         if (p > best) { best = p; bk = c + j; bre = re[j]; bim = im[j]; }
                     }
@@ -551,13 +571,13 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                         float* zr = zout + (long long)(2 * m) * n + tt * kTcTileN + c;
                         float* zi = zr + n;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) { zr[j] = re[j]; zi[j] = im[j]; }
+                        for (int j = 0; j < 16; ++j) { zr[j] = re[j]; zi[j] = im[j]; }
                     }
                 } else {
                     float* o_re = jb.acc_out + det * jb.acc_out_det_stride;
                     float* o_im = o_re + (long long)jb.acc_out_rows * jb.Mpad;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < 16; ++j) {
                         const long long q = q0 + j;
                         if (q >= lo && q <= hi) {
                             o_re[(q - lo) * jb.Mpad + m] = re[j];

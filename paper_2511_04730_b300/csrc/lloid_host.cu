@@ -479,7 +479,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     ctx->firtc_strip = strip;
     ctx->max_depth = max_depth;
     const int fsmem = (bf ? FirCfg<true>::STAGE_AREA : FirCfg<false>::STAGE_AREA) + 4 * strip +
-                      FirCfg<false>::EPI_BYTES + 256 + 1024;
+                      FirCfg<false>::EPI_BYTES + 256 + 1024;   // EPI_BYTES is the same for both
     ctx->firtc_smem = fsmem;
     if (fsmem > 227 * 1024) return fail(ctx, LLOID_EINVAL, "FIR shared memory %d exceeds the limit", fsmem);
     if (bf) CK(cudaFuncSetAttribute(k_fir_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
