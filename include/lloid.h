@@ -210,6 +210,11 @@ LLOID_API lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank
 /* Wait for all enqueued work of the context (ECUDA on a device error). */
 LLOID_API lloid_status lloid_synchronize(lloid_ctx* ctx);
 
+/* Device bytes held by the context: *state_bytes for streams, rings and
+ * window state, *bank_bytes for the loaded banks (either may be NULL).  These
+ * are the quantities hbm_budget_bytes is checked against. */
+LLOID_API lloid_status lloid_bytes_in_use(const lloid_ctx* ctx, size_t* state_bytes, size_t* bank_bytes);
+
 /* Number of kernel launches the context has issued so far. */
 LLOID_API int64_t lloid_launch_count(const lloid_ctx* ctx);
 

@@ -72,6 +72,8 @@ SIGNATURES = [
                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("lloid_synchronize", ctypes.c_int, [ctypes.c_void_p]),
     ("lloid_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("lloid_bytes_in_use", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
+                                          ctypes.POINTER(ctypes.c_size_t)]),
     ("lloid_stream", ctypes.c_void_p, [ctypes.c_void_p]),
     ("lloid_triggers_from_snr_noalloc", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,

@@ -932,6 +932,13 @@ const char* lloid_last_error(const lloid_ctx* ctx) { return ctx ? ctx->err.c_str
 
 int64_t lloid_launch_count(const lloid_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+lloid_status lloid_bytes_in_use(const lloid_ctx* ctx, size_t* state_bytes, size_t* bank_bytes) {
+    if (!ctx) return LLOID_EINVAL;
+    if (state_bytes) *state_bytes = ctx->state_bytes;
+    if (bank_bytes) *bank_bytes = ctx->bank_bytes;
+    return LLOID_OK;
+}
+
 void* lloid_stream(const lloid_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
 lloid_status lloid_stage_times(lloid_ctx* ctx, double* ms, int64_t* launches, int reset) {

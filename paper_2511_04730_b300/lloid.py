@@ -204,6 +204,12 @@ class Context:
     def launch_count(self) -> int:
         return int(self._lib.lloid_launch_count(self._h))
 
+    def bytes_in_use(self):
+        """(state bytes, bank bytes) held on the device."""
+        a, b = ctypes.c_size_t(), ctypes.c_size_t()
+        self._check(self._lib.lloid_bytes_in_use(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
+
     def stage_times(self, reset: bool = False) -> dict:
         """{stage: (milliseconds, launches)} since the last reset (needs stage_timing=True)."""
         ms = (ctypes.c_double * _lib.N_STAGES)()
