@@ -54,6 +54,13 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp32-compare", action="store_true")
     p.add_argument("--latency-steps", type=int, default=32)
+    p.add_argument("--workload", default="bank1000", choices=["bank1000", "banks20", "banks500"])
+    p.add_argument("--banks", type=int, default=None, help="use the first N banks of a multi-bank workload")
+    p.add_argument("--detectors", type=int, default=None)
+    p.add_argument("--serve", action="store_true", help="paced serving loop with latency percentiles")
+    p.add_argument("--serve-block", type=int, default=2048)
+    p.add_argument("--pace", type=float, default=1.0)
+    p.add_argument("--serve-seconds", type=int, default=60)
     return p.parse_args()
 
 
@@ -124,13 +131,53 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
+WORKLOADS = {
+    "bank1000": WORKLOAD,
+    "banks20": ("10,000 Newtonian chirp templates (Mc log-U[1,20] Msun) in 20 contiguous-Mc SVD banks of 200-800, "
+                "durations 8-64 s, 2 detectors x 4096 s white noise + 100 injections"),
+    "banks500": ("500 SVD banks of U{100..1000} templates (~280k, Mc log-U[1,50] Msun, durations 2-128 s, 1-10 slices, "
+                 "32-2048 Hz), 3 detectors x 1024 s white noise"),
+}
+
+
+def _svd_job(args):
+    from paper_2511_04730_b300 import build_svd_bank
+    bank, plan = args
+    return build_svd_bank(bank, plan)
+
+
 def make_inputs(args, rank):
     import numpy as np
     import workloads as W
-    w = W.make_workload("bank1000", n_templates=args.templates, n_seconds=args.seconds)
+    workers = max(1, min(16, os.cpu_count() or 1))
+    if args.workload == "bank1000":
+        w = W.make_workload("bank1000", n_templates=args.templates, n_seconds=args.seconds, n_det=args.detectors)
+    else:
+        secs = args.seconds if args.seconds != 1024 or args.workload == "banks500" else None
+        w = W.make_workload(args.workload, n_seconds=secs, n_banks=args.banks, n_det=args.detectors,
+                            workers=workers)
     w.seed_base = 100 + 10 * rank
     strain = np.stack([w.strain(d) for d in range(w.n_det)]).astype(np.float32)
     return w, strain
+
+
+def build_banks(w):
+    """SVD banks of every bank of the workload (a spawn pool for many banks)."""
+    from paper_2511_04730_b300 import build_svd_bank
+    if len(w.banks) < 4:
+        return [build_svd_bank(b, p) for b, p in zip(w.banks, w.plans)]
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+    os.environ.update(OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1")
+    try:
+        with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+            return pool.map(_svd_job, list(zip(w.banks, w.plans)), chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def algorithmic_work(slices, M, f0=F0, n_up=8):
@@ -217,10 +264,19 @@ def run_lloid(args, rank, world, dist):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     w, strain = make_inputs(args, rank)
-    bank, plan = w.banks[0], w.plans[0]
-    sb = P.build_svd_bank(bank, plan)
-    M = bank.n_templates
+    all_banks = build_banks(w)
+    if len(all_banks) > 1 and world > 1:            # shard the bank set: LPT on per-bank work
+        from paper_2511_04730_b300 import sharding
+        costs = [sharding.bank_cost(sb_, b.n_templates) for sb_, b in zip(all_banks, w.banks)]
+        mine = sharding.assign_banks(costs, world)[rank]
+    else:
+        mine = list(range(len(all_banks)))
+    banks_sb = [all_banks[i] for i in mine]
+    M_list = [w.banks[i].n_templates for i in mine]
+    sb = banks_sb[0]
+    M = sum(M_list)
     n_det = w.n_det
+    max_hist = max(b.n_samples for b in w.banks)
     B = args.block_seconds * F0
     T = strain.shape[1]
     assert T % B == 0
@@ -231,8 +287,40 @@ def run_lloid(args, rank, world, dist):
     h_blocks = torch.from_numpy(blocks).pin_memory()
 
     def make_ctx(precision, timing):
-        return P.Context(n_detectors=n_det, precision=precision, max_block=B, max_history=64 * F0,
+        return P.Context(n_detectors=n_det, precision=precision, max_block=B, max_history=max_hist,
                          device=dev, stage_timing=timing)
+
+    def load_all(ctx):
+        return [ctx.load_bank(x) for x in banks_sb]
+
+    if args.serve:
+        from paper_2511_04730_b300.serving import Server
+        SB = args.serve_block
+        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=SB, max_history=max_hist, device=dev)
+        srv = Server(ctx, SB)
+        for i, x in enumerate(banks_sb):
+            srv.submit(x, tag=i)
+        nb = T // SB
+        blocks_s = np.ascontiguousarray(strain.reshape(n_det, nb, SB).transpose(1, 0, 2))
+        src = lambda k: blocks_s[k % nb]
+        warm = max_hist // SB + 4
+        for k in range(warm):                          # admit every bank and fill the history
+            srv.step(src(k))
+        srv.latency_ms.clear()
+        n_serve = args.serve_seconds * F0 // SB
+        t0 = time.perf_counter()
+        srv.run_paced(lambda k: src(warm + k), n_serve, pace=args.pace)
+        wall = time.perf_counter() - t0
+        ctx.close()
+        if rank == 0:
+            lat = srv.latency_summary()
+            print(json.dumps({
+                "mode": "serve", "metric": "per-block latency (block arrival -> its windows' triggers on the host)",
+                "latency_ms": lat, "block_seconds": SB / F0, "pace": args.pace, "seconds_streamed": n_serve * SB / F0,
+                "wall_s": wall, "template_s_per_s": M * n_det * n_serve * SB / F0 / wall,
+                "n_templates": M, "n_banks": len(banks_sb), "n_detectors": n_det, "precision": args.precision,
+                "workload": WORKLOADS[args.workload]}), flush=True)
+        return
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
 
@@ -271,7 +359,7 @@ def run_lloid(args, rank, world, dist):
     clocks = None
     for prec in precisions:
         ctx = make_ctx(prec, timing=True)
-        bid = ctx.load_bank(sb)
+        load_all(ctx)
         pos = 0
         _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
         ctx.stage_times(reset=True)
@@ -293,18 +381,20 @@ def run_lloid(args, rank, world, dist):
     max_dsnr = None
     if args.precision != "fp32" and not args.no_fp32_compare:
         a, b = make_ctx(args.precision, False), make_ctx("fp32", False)
-        ia, ib = a.load_bank(sb), b.load_bank(sb)
+        ia, ib = load_all(a), load_all(b)
         max_dsnr = 0.0
-        for k in range((72 * F0) // B):
+        n_chk = min(8, len(ia))                       # compare the first banks (all of them for one bank)
+        for k in range((max_hist + 8 * F0) // B):
             blk = d_blocks[k % n_blk]
             a.push_all(k * B, blk)
             b.push_all(k * B, blk)
-            if (k + 1) * B >= 64 * F0:
+            if (k + 1) * B >= max_hist:
                 for det in range(n_det):
-                    za, _ = a.snr_block(det, ia)
-                    zb, _ = b.snr_block(det, ib)
-                    dz = torch.sqrt(((za - zb) ** 2).view(M, 2, -1).sum(1)).max().item()
-                    max_dsnr = max(max_dsnr, dz)
+                    for j in range(n_chk):
+                        za, _ = a.snr_block(det, ia[j])
+                        zb, _ = b.snr_block(det, ib[j])
+                        dz = torch.sqrt(((za - zb) ** 2).view(M_list[j], 2, -1).sum(1)).max().item()
+                        max_dsnr = max(max_dsnr, dz)
         a.close()
         b.close()
 
@@ -312,7 +402,7 @@ def run_lloid(args, rank, world, dist):
     e2e = None
     if not args.no_e2e:
         ctx = make_ctx(args.precision, False)
-        ctx.load_bank(sb)
+        load_all(ctx)
         pos = 0
         _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, host=True)
         ms_e, pos, _, h2d, d2h = run_steps(ctx, args.steps, pos, host=True)
@@ -323,18 +413,18 @@ def run_lloid(args, rank, world, dist):
     # per-block latency at 1 s blocks (block arrival on the host -> its window's triggers on the host)
     lat = []
     if args.latency_steps:
-        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=F0, max_history=64 * F0, device=dev)
-        ctx.load_bank(sb)
+        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=F0, max_history=max_hist, device=dev)
+        load_all(ctx)
         pos = 0
-        ext = torch.cuda.ExternalStream(ctx.stream_ptr, device=f"cuda:{dev}")
         h_sec = torch.from_numpy(np.ascontiguousarray(
             strain.reshape(n_det, T // F0, F0).transpose(1, 0, 2))).pin_memory()
-        for k in range(72 + args.latency_steps):
+        warm = max_hist // F0 + 8
+        for k in range(warm + args.latency_steps):
             blk = h_sec[(pos // F0) % (T // F0)].numpy()
             t0 = time.perf_counter()
             ctx.push_all(pos, blk)
             ctx.pull(pos // F0)
-            if k >= 72:
+            if k >= warm:
                 lat.append(1000 * (time.perf_counter() - t0))
             pos += F0
         ctx.close()
@@ -347,13 +437,17 @@ def run_lloid(args, rank, world, dist):
         t = torch.tensor([my_time], device=f"cuda:{dev}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         my_time = float(t.item())
-    value = units * args.steps * world / my_time
+    if len(all_banks) == 1:                        # replicas: every rank filters its own copy
+        value = units * args.steps * world / my_time
+    else:                                          # shards of one bank set
+        value = w.n_templates * args.block_seconds * n_det * args.steps / my_time
 
     # roofline of the dominant kernel (stage with the largest device time)
     stages = main["stages"]
     dom = max(("fir", "upsample", "recon"), key=lambda k: stages[k][0])
     dur_ms = stages[dom][0] / max(1, stages[dom][1])
-    work = algorithmic_work(sb, M)
+    works = [algorithmic_work(x, m) for x, m in zip(banks_sb, M_list)]
+    work = {k: sum(wk[k] for wk in works) for k in works[0]}
     det_s = args.block_seconds * n_det
     pk, pk_kind = peaks()
     alu_peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
@@ -372,9 +466,6 @@ def run_lloid(args, rank, world, dist):
     launches_dom = max(1.0, stages[dom][1] / args.steps)
     alg = per_dets * det_s / launches_dom          # one launch's share of the stage's work
     achieved = alg / (dur_ms / 1000.0) / 1e12
-    Kpad = -(-sum(s.n_basis for s in sb) // 64) * 64
-    Mpad = -(-M // 128) * 128
-    n_mma = {"fp32": 1, "fp16_split": 2, "bf16_split": 3}[args.precision]
     roofline = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
                 "algorithmic_flop_per_launch": alg, "launch_ms": dur_ms}
@@ -398,13 +489,14 @@ def run_lloid(args, rank, world, dist):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "weak" if len(all_banks) == 1 else "strong", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp16_split": "f16", "bf16_split": "bf16"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_templates": M, "n_detectors": n_det,
-                       "block_seconds": args.block_seconds, "precision": args.precision,
+            "config": {"workload": WORKLOADS[args.workload], "n_templates": M, "n_banks": len(banks_sb),
+                       "n_detectors": n_det, "block_seconds": args.block_seconds, "precision": args.precision,
                        "l2": "flushed between steps (256 MB write, outside the timed events)",
-                       "bases_total": sum(s.n_basis for s in sb), "parallelism": f"replicas x{world}"},
+                       "bases_total": sum(s.n_basis for x in banks_sb for s in x),
+                       "parallelism": (f"replicas x{world}" if len(all_banks) == 1 else f"bank shards x{world}")},
             "e2e": e2e, "gpu_launches": main["launches"], "clocks": clocks,
             "roofline": roofline, "cpu_baseline": cpu,
             "max_dsnr_vs_fp32": max_dsnr,

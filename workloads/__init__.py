@@ -122,19 +122,13 @@ class ChirpBank:
             self.j_hi[i] = min(int(math.floor(t_low * self.f0)) + 1, self.n_samples)
             if self.j_hi[i] <= self.j_lo[i] + 1:
                 raise ValueError(f"template {i} (Mc={mc}) has empty support")
-        self.norm_c = np.ones(M)
-        self.norm_s = np.ones(M)
-        # Unit-normalise h_c and h_s separately (FP64), in chunks.
-        ss_c = np.zeros(M)
-        ss_s = np.zeros(M)
-        chunk = 1 << 15
-        for a in range(0, self.n_samples, chunk):
-            j = np.arange(a, min(a + chunk, self.n_samples))
-            r = self._raw(j)
-            ss_c += np.einsum("ij,ij->i", r[0::2], r[0::2])
-            ss_s += np.einsum("ij,ij->i", r[1::2], r[1::2])
-        self.norm_c = np.sqrt(ss_c)
-        self.norm_s = np.sqrt(ss_s)
+        # Unit-normalise h_c and h_s separately (FP64) over each support.
+        self.norm_c = np.empty(M)
+        self.norm_s = np.empty(M)
+        for i in range(M):
+            hc, hs = self._one(i, np.arange(self.j_lo[i], self.j_hi[i]))
+            self.norm_c[i] = math.sqrt(float(np.einsum("i,i->", hc, hc)))
+            self.norm_s[i] = math.sqrt(float(np.einsum("i,i->", hs, hs)))
 
     @property
     def n_templates(self) -> int:
@@ -144,22 +138,41 @@ class ChirpBank:
     def n_rows(self) -> int:
         return 2 * self.n_templates
 
+    def _one(self, i: int, jj: np.ndarray) -> tuple:
+        """Unnormalised (h_c, h_s) of template i at samples jj, all inside its support."""
+        t = jj / float(self.f0)
+        amp = t ** -0.25
+        ph = phase_of_tau(t, self.mchirp[i])
+        win = _tukey(int(self.j_hi[i] - self.j_lo[i]), jj - self.j_lo[i])
+        g = amp * win
+        return g * np.cos(ph), g * np.sin(ph)
+
     def _raw(self, j, which=None):
+        """Unnormalised rows [2M', len(j)] at before-merger samples j.  When j
+        is an arithmetic progression (every use here) each template is only
+        evaluated on the part of j inside its support."""
         j = np.asarray(j, dtype=np.int64)
         idx = range(self.mchirp.size) if which is None else list(which)
         out = np.zeros((2 * len(idx), j.size), dtype=np.float64)
-        tau = j / float(self.f0)
+        step = int(j[1] - j[0]) if j.size > 1 else 1
+        regular = j.size > 1 and step > 0 and np.all(np.diff(j) == step)
         for o, i in enumerate(idx):
-            mc = self.mchirp[i]
-            sel = (j >= self.j_lo[i]) & (j < self.j_hi[i])
-            if not np.any(sel):
-                continue
-            t = tau[sel]
-            amp = t ** -0.25
-            ph = phase_of_tau(t, mc)
-            win = _tukey(int(self.j_hi[i] - self.j_lo[i]), j[sel] - self.j_lo[i])
-            out[2 * o, sel] = amp * np.cos(ph) * win
-            out[2 * o + 1, sel] = amp * np.sin(ph) * win
+            lo, hi = int(self.j_lo[i]), int(self.j_hi[i])
+            if regular:
+                m0 = max(0, -(-(lo - int(j[0])) // step))
+                m1 = min(j.size, -(-(hi - int(j[0])) // step))
+                if m1 <= m0:
+                    continue
+                hc, hs = self._one(i, j[m0:m1])
+                out[2 * o, m0:m1] = hc
+                out[2 * o + 1, m0:m1] = hs
+            else:
+                sel = (j >= lo) & (j < hi)
+                if not np.any(sel):
+                    continue
+                hc, hs = self._one(i, j[sel])
+                out[2 * o, sel] = hc
+                out[2 * o + 1, sel] = hs
         return out
 
     def rows(self, j, which=None) -> np.ndarray:
@@ -315,19 +328,38 @@ class Workload:
         return d if n is None else d[:n]
 
 
-def _contiguous_banks(mchirp_sorted, sizes, n_seconds_fn, f0):
-    banks = []
+def _make_bank(args):
+    mc, n_samples, f0 = args
+    return ChirpBank(mc, n_samples, f0)
+
+
+def _contiguous_banks(mchirp_sorted, sizes, n_seconds_fn, f0, workers: int = 1):
+    jobs = []
     a = 0
     for sz in sizes:
         mc = mchirp_sorted[a:a + sz]
         a += sz
-        banks.append(ChirpBank(mc, n_seconds_fn(mc) * f0, f0))
-    return banks
+        jobs.append((mc, n_seconds_fn(mc) * f0, f0))
+    if workers <= 1 or len(jobs) < 2:
+        return [_make_bank(j) for j in jobs]
+    import multiprocessing as mp
+    import os
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+    os.environ.update(OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1")   # one thread per worker
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:  # spawn: safe next to a CUDA context
+            return pool.map(_make_bank, jobs, chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def make_workload(name: str, n_det: Optional[int] = None, n_seconds: Optional[int] = None,
                   n_templates: Optional[int] = None, n_banks: Optional[int] = None,
-                  n_inj: Optional[int] = None) -> Workload:
+                  n_inj: Optional[int] = None, workers: int = 1) -> Workload:
     """Build one of the paper-shaped synthetic workloads by name.
 
     * ``tiny``   : 8 templates, Mc in [5, 15], 4 s, two slices; 16 s, 1 detector.
@@ -341,7 +373,8 @@ def make_workload(name: str, n_det: Optional[int] = None, n_seconds: Optional[in
       injections at SNR U[5, 25].
     * ``banks500``: 500 banks of U{100..1000} templates (Mc log-U[1, 50],
       durations clip(tau(30 Hz), 2, 128) s); 1024 s, 3 detectors.
-    Any size argument overrides the default (used for bounded samples).
+    Any size argument overrides the default (used for bounded samples);
+    ``workers`` > 1 builds multi-bank workloads in a process pool.
     """
     f0 = F0
     if name == "tiny":
@@ -405,7 +438,7 @@ def make_workload(name: str, n_det: Optional[int] = None, n_seconds: Optional[in
             d = int(np.clip(math.ceil(float(tau_of_f(F_LOW, m.min()))), dmin, dmax))
             return 1 << int(math.ceil(math.log2(d)))
 
-        banks = _contiguous_banks(mc, sizes, dur_fn, f0)
+        banks = _contiguous_banks(mc, sizes, dur_fn, f0, workers)
         plans = [plan_slices(b, DEFAULT_BOUNDARIES_S, r_min=rmin) for b in banks]
         nd, ns = n_det or nd_def, n_seconds or ns_def
         injs, ib = [], []
