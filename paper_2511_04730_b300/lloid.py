@@ -166,17 +166,19 @@ class Context:
         if dev:
             self._torch_after()
 
-    def pull(self, window: int, timeout_ms: int = -1, cap: int = 1 << 16, n_windows: int = 1) -> np.ndarray:
+    def pull(self, window: int, timeout_ms: int = -1, n_windows: int = 1) -> np.ndarray:
         """Triggers of windows window .. window + n_windows - 1 as a numpy
         structured array (TRIGGER_DTYPE)."""
         n_out = ctypes.c_int64()
+        if getattr(self, "_pull_buf", None) is None:
+            self._pull_buf = np.empty(1 << 14, dtype=TRIGGER_DTYPE)
         while True:
-            out = np.zeros(cap, dtype=TRIGGER_DTYPE)
+            out = self._pull_buf
             st = self._lib.lloid_pull_triggers_range(self._h, window, n_windows,
                                                      out.ctypes.data_as(ctypes.POINTER(_lib.LloidTrigger)),
-                                                     cap, ctypes.byref(n_out), timeout_ms)
-            if st == -8:   # ERANGE: grow and retry
-                cap = int(n_out.value)
+                                                     out.size, ctypes.byref(n_out), timeout_ms)
+            if st == -8:   # ERANGE: grow the reusable buffer and retry
+                self._pull_buf = np.empty(int(n_out.value) * 2, dtype=TRIGGER_DTYPE)
                 continue
             self._check(st)
             return out[: n_out.value].copy()

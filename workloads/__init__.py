@@ -47,6 +47,7 @@ F_LOW = 30.0                 # lower frequency of every template (Hz)
 ISCO_NUM = 4397.0            # f_ISCO ~ 4397 Hz / (M_total / M_sun)
 TUKEY_ALPHA = 0.1
 DEFAULT_BOUNDARIES_S = (0.0, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 32.0, 64.0, 128.0)
+N_DOWN_DESIGN, N_UP_DESIGN = 32, 8    # filter half-lengths the slice plan must leave room for
 
 
 # ----------------------------------------------------------------------------
@@ -245,6 +246,11 @@ def plan_slices(bank: ChirpBank, boundaries_s: Sequence[float] = DEFAULT_BOUNDAR
             fmax = bank.max_freq_in(a, b)
             r = r_min
             while r < f0 and 0.4 * r < fmax:
+                r *= 2
+            # pre-synchronisation (Eq. 9) needs the slice to start at least
+            # D (N_down + sum of the ladder's N_up terms) < D (N_down + 2 N_up)
+            # samples before merger: raise the rate until it does
+            while r < f0 and a < (f0 // r) * (N_DOWN_DESIGN + 2 * N_UP_DESIGN):
                 r *= 2
         D = f0 // r
         if a % D or (b - a) % D:
