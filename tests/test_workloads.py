@@ -18,7 +18,7 @@ def _check_plans(w):
 
 
 def test_plans_satisfy_presync():
-    _check_plans(W.make_workload("bank64", n_seconds=8))
+    _check_plans(W.make_workload("bank64", n_seconds=8, n_inj=0))
     _check_plans(W.make_workload("bank1000", n_templates=50, n_seconds=8, n_det=1, n_inj=0))
     _check_plans(W.make_workload("banks20", n_templates=400, n_banks=8, n_seconds=8, n_det=1, n_inj=0))
     _check_plans(W.make_workload("banks500", n_templates=3000, n_banks=40, n_seconds=8, n_det=1, n_inj=0))
