@@ -285,6 +285,8 @@ def draw_injections(n_inj: int, n_templates: int, n_data: int, tmpl_len: int,
     [tmpl_len + f0, n_data - f0), SNR uniform in snr_range, phase uniform."""
     rng = np.random.Generator(np.random.PCG64(seed))
     lo, hi = tmpl_len + f0, n_data - f0
+    if n_inj == 0:
+        return []
     if hi <= lo:
         raise ValueError("data too short for injections")
     out = []
