@@ -58,6 +58,7 @@ struct LevelJob {
     int F, D_lo, Lambda_lo;        // factor to the level below (0: lowest level)
     int y_rows;                    // level ring rows
     int map;                       // index into the level tensor-map array
+    int nwt;                       // up-window rows per 128-sample tile: 127/F + 2 N_up + 1
 };
 
 struct FirMaps { CUtensorMap a, a_lo; };
@@ -69,7 +70,10 @@ struct FirMaps { CUtensorMap a, a_lo; };
 constexpr int kUpTaps = 17;
 constexpr int kUpTable = kUpTaps * (2 + 4 + 8 + 16 + 32 + 64);
 __constant__ float c_upz[kUpTable];
-struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo; };
+// accin: the level below's transposed Acc planes as FP32 rows of Mpad
+// templates (plane rows stacked det-major: [det][re, im][rows]); box 128
+// templates x nwt rows, loaded once per tile into shared memory.
+struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo, accin; };
 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t desc_nosw(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -322,12 +326,14 @@ __global__ void __launch_bounds__(192, 1)
 template <bool BF16>
 struct LevCfg {
     static constexpr int NA = BF16 ? 4 : 2;
-    static constexpr int STAGES = BF16 ? 2 : 3;
+    static constexpr int STAGES = BF16 ? 1 : 2;
     static constexpr int TILE_A = kTcTileM * kTcK * 2;
     static constexpr int TILE_B = kTcTileN * kTcK * 2;
     static constexpr int STAGE_BYTES = NA * TILE_A + 2 * TILE_B;
     static constexpr int XCHG = 2 * 128 * 16;          // tile-argmax exchange between the column halves
-    static constexpr int SMEM = STAGES * STAGE_BYTES + XCHG + 1024 + 256;
+    static constexpr int NWT_MAX = 80;                 // up-window rows for F = 2
+    static constexpr int WIN = 2 * NWT_MAX * 128 * 4;  // re + im windows of the level below
+    static constexpr int SMEM = STAGES * STAGE_BYTES + WIN + XCHG + 1024 + 256;
     static constexpr int EPI_WARPS = 8;                 // two per TMEM lane quarter, 64 columns each
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
 };
@@ -338,30 +344,27 @@ struct LevCfg {
 // Level tiles start at multiples of 128, so q0 mod F is PH0 = 0 for F <= 32
 // and 0 or 32 for F = 64: every register index below is a compile-time constant.
 // Up_F of the level below for CH consecutive outputs q0..q0+CH-1 of one
-// template (column m of the transposed planes), added into vr/vi.  Eq. 8
-// centred: Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
-// Level tiles start at multiples of 128 and chunks at multiples of CH, so
-// q0 mod F is the compile-time PH0: every register index is a constant.
+// template, added into vr/vi.  Eq. 8 centred:
+//   Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
+// x comes from the shared-memory window of the tile (row w = x index
+// floor(Q_tile/F) - N_up + w, column = template within the tile); wb is the
+// window row of floor(q0/F) - N_up.  Tiles start at multiples of 128 and
+// chunks at multiples of CH, so q0 mod F is the compile-time PH0.
 template <int CH, int F, int NUP, int PH0>
-__device__ __forceinline__ void add_up(float (&vr)[CH], float (&vi)[CH], const float* __restrict__ pre,
-                                       const float* __restrict__ pim, int Mpad, int m, long long q0,
-                                       long long lo_in, int rows_in) {
+__device__ __forceinline__ void add_up_s(float (&vr)[CH], float (&vi)[CH], const float* __restrict__ wre,
+                                         const float* __restrict__ wim, int wb, int col) {
     static_assert(NUP == 8, "the constant tables hold N_up = 8");
     constexpr int NW = (PH0 + CH - 1) / F + 2 * NUP + 1;
     constexpr int OFF = kUpTaps * (F - 2);
-    const long long a0 = fdiv(q0, F) - NUP;          // x index of window slot 0
+    const float* pr = wre + wb * 128 + col;
+    const float* pi = wim + wb * 128 + col;
     float xr[NW], xi[NW];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {                   // both windows in flight before any use
-        const long long idx = a0 + w - lo_in;
-        const bool in = idx >= 0 && idx < rows_in;
-        xr[w] = in ? __ldg(pre + idx * Mpad + m) : 0.f;
-        xi[w] = in ? __ldg(pim + idx * Mpad + m) : 0.f;
-    }
+    for (int w = 0; w < NW; ++w) { xr[w] = pr[w * 128]; xi[w] = pi[w * 128]; }
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
         const int ph = (PH0 + j) % F;
-        const int b = (PH0 + j) / F + 2 * NUP;       // (floor(q/F) + N_up) - a0
+        const int b = (PH0 + j) / F + 2 * NUP;       // (floor(q/F) + N_up) - (floor(q0/F) - N_up)
         if (ph == 0) {                               // z_0 = g[t F]: 1 at t = N_up, 0 elsewhere
             vr[j] += xr[b - NUP];
             vi[j] += xi[b - NUP];
@@ -381,24 +384,24 @@ __device__ __forceinline__ void add_up(float (&vr)[CH], float (&vi)[CH], const f
 }
 
 template <int NUP>
-__device__ __forceinline__ void add_up_dispatch(int F, float (&vr)[16], float (&vi)[16], const float* pre,
-                                                const float* pim, int Mpad, int m, long long q0, long long lo_in,
-                                                int rows_in) {
-    const int ph0 = (int)(q0 & (F - 1));
+__device__ __forceinline__ void add_up_dispatch(int F, int c, float (&vr)[16], float (&vi)[16], const float* wre,
+                                                const float* wim, int col) {
+    const int wb = c / F;                            // floor(q0/F) - floor(Q_tile/F)
+    const int ph0 = c & (F - 1);
     switch (F) {
-        case 2: add_up<16, 2, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in); break;
-        case 4: add_up<16, 4, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in); break;
-        case 8: add_up<16, 8, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in); break;
-        case 16: add_up<16, 16, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in); break;
+        case 2: add_up_s<16, 2, NUP, 0>(vr, vi, wre, wim, wb, col); break;
+        case 4: add_up_s<16, 4, NUP, 0>(vr, vi, wre, wim, wb, col); break;
+        case 8: add_up_s<16, 8, NUP, 0>(vr, vi, wre, wim, wb, col); break;
+        case 16: add_up_s<16, 16, NUP, 0>(vr, vi, wre, wim, wb, col); break;
         case 32:
-            if (ph0 == 0) add_up<16, 32, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
-            else add_up<16, 32, NUP, 16>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
+            if (ph0 == 0) add_up_s<16, 32, NUP, 0>(vr, vi, wre, wim, wb, col);
+            else add_up_s<16, 32, NUP, 16>(vr, vi, wre, wim, wb, col);
             break;
         case 64:
-            if (ph0 == 0) add_up<16, 64, NUP, 0>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
-            else if (ph0 == 16) add_up<16, 64, NUP, 16>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
-            else if (ph0 == 32) add_up<16, 64, NUP, 32>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
-            else add_up<16, 64, NUP, 48>(vr, vi, pre, pim, Mpad, m, q0, lo_in, rows_in);
+            if (ph0 == 0) add_up_s<16, 64, NUP, 0>(vr, vi, wre, wim, wb, col);
+            else if (ph0 == 16) add_up_s<16, 64, NUP, 16>(vr, vi, wre, wim, wb, col);
+            else if (ph0 == 32) add_up_s<16, 64, NUP, 32>(vr, vi, wre, wim, wb, col);
+            else add_up_s<16, 64, NUP, 48>(vr, vi, wre, wim, wb, col);
             break;
         default: break;
     }
@@ -415,19 +418,25 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
     constexpr int EPI = 32 * C::EPI_WARPS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float4* xchg = reinterpret_cast<float4*>(smem + C::STAGES * C::STAGE_BYTES);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES + C::XCHG);
+    float* win_re = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES);
+    float* win_im = win_re + C::NWT_MAX * 128;
+    float4* xchg = reinterpret_cast<float4*>(smem + C::STAGES * C::STAGE_BYTES + C::WIN);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES + C::WIN + C::XCHG);
     uint64_t* empty = full + C::STAGES;
     uint64_t* tfull = empty + C::STAGES;
     uint64_t* tempty = tfull + 2;
     uint64_t* drain = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* wfull = drain + 1;
+    uint64_t* wempty = wfull + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wempty + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(tfull + b, 1); mbar_init(tempty + b, EPI); }
         mbar_init(drain, 1);
+        mbar_init(wfull, 1);
+        mbar_init(wempty, EPI);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -444,7 +453,7 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
             int stage = 0;
-            uint32_t phase = 0;
+            uint32_t phase = 0, wphase = 0;
             bool ok = true;
             for (int it = blockIdx.x; it < total && ok; it += gridDim.x) {
                 const int det = det0 + it / tiles_per_det;
@@ -456,6 +465,16 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                 const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
                 const long long Q0 = fdiv(fdiv(k_a - jb.Lambda, jb.D), 128) * 128;
                 const int yrow = det * 2 * jb.y_rows + (int)((Q0 + 128LL * tt) & (jb.y_rows - 1));
+                if (jb.F) {   // the level below's window for this tile (rows outside the planes read 0)
+                    if (!mbar_wait(wempty, wphase ^ 1, err, 37)) { ok = false; break; }
+                    const long long lo_in = fdiv(k_a - jb.Lambda_lo, jb.D_lo);
+                    const long long a_t = fdiv(Q0 + 128LL * tt, jb.F) - 8 - lo_in;
+                    const int base_row = det * 2 * jb.acc_in_rows;
+                    mbar_expect_tx(wfull, 2u * jb.nwt * 128 * 4);
+                    tma_load_2d(win_re, &mp->accin, wfull, tm * 128, (int)(base_row + a_t));
+                    tma_load_2d(win_im, &mp->accin, wfull, tm * 128, (int)(base_row + jb.acc_in_rows + a_t));
+                    wphase ^= 1;
+                }
                 for (int kc = 0; kc < jb.Kp; kc += kTcK) {
                     if (!mbar_wait(empty + stage, phase ^ 1, err, 31)) { ok = false; break; }
                     uint8_t* sb = smem + stage * C::STAGE_BYTES;
@@ -475,6 +494,7 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                 if (!mbar_wait(empty + stage, phase ^ 1, err, 32)) break;
                 if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
             }
+            mbar_wait(wempty, wphase ^ 1, err, 38);    // the last window was consumed
         }
     } else if (warp == 1) {
         if (lane == 0) {   // ------------------------------------------------ MMA issuer
@@ -526,6 +546,7 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
         const int qd = warp & 3;
         const int half = (warp - 2) >> 2;
         const int rowm = qd * 32 + lane;
+        uint32_t wph = 0;
         int i = 0;
         for (int it = blockIdx.x; it < total; it += gridDim.x, ++i) {
             const int det = det0 + it / tiles_per_det;
@@ -541,13 +562,15 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
             const long long lo = fdiv(k_a - jb.Lambda, jb.D);
             const long long hi = fdiv(k_b - 1 + jb.Lambda, jb.D);
             const long long Q0 = fdiv(lo, 128) * 128;
-            const long long lo_in = jb.F ? fdiv(k_a - jb.Lambda_lo, jb.D_lo) : 0;
             const int m = tm * kTcTileM + rowm;
             const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + buf * 256;
             float best = -1.f, bre = 0.f, bim = 0.f;
             int bk = 0x7fffffff;
-            const float* in_re = jb.F ? jb.acc_in + det * jb.acc_in_det_stride : nullptr;
-            const float* in_im = jb.F ? in_re + (long long)jb.acc_in_rows * jb.Mpad : nullptr;
+            if (jb.F) {
+                const bool wgot = mbar_wait(wfull, wph, err, 39);
+                if (!__all_sync(0xffffffffu, wgot)) break;
+                wph ^= 1;
+            }
 #pragma unroll 1
             for (int c = half * 64; c < half * 64 + 64; c += 16) {
                 float re[16], im[16];
@@ -559,7 +582,7 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                     for (int j = 0; j < 16; ++j) { re[j] = 0.f; im[j] = 0.f; }
                 }
                 const long long q0 = Q0 + 128LL * tt + c;
-                if (jb.F) add_up_dispatch<NUP>(jb.F, re, im, in_re, in_im, jb.Mpad, m, q0, lo_in, jb.acc_in_rows);
+                if (jb.F) add_up_dispatch<NUP>(jb.F, c, re, im, win_re, win_im, rowm);
                 if (TOP) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -588,6 +611,7 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
             }
             tc_fence_before();
             mbar_arrive(tempty + buf);
+            if (jb.F) mbar_arrive(wempty);          // the window may be refilled
             if (TOP && !STORE_Z) {
                 // the later half hands its tile argmax to the earlier half (which wins ties)
                 float4* xb = xchg + buf * 128;

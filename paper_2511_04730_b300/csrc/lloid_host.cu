@@ -273,6 +273,20 @@ bool encode_map(CUtensorMap* m, bool bf16, const void* base, long long cols, lon
     return r == CUDA_SUCCESS;
 }
 
+// 2-D FP32 map without swizzle: rows of `cols` floats, box box_cols x box_rows.
+bool encode_map_f32(CUtensorMap* m, const void* base, long long cols, long long rows, int box_cols, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 lloid_status ensure_template_capacity(lloid_ctx* ctx, long long need) {
     if (need <= ctx->M_cap) return LLOID_OK;
     const int nd = ctx->cfg.n_detectors;
@@ -447,6 +461,14 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             q.D = L.D; q.Lambda = L.Lambda; q.y_rows = L.R; q.map = (int)lj[depth].size();
             LevelMaps mp;
             std::memset(&mp, 0, sizeof mp);
+            if (j > 0) {
+                const LevelRT& P = b->lev[j - 1];
+                q.nwt = 127 / q.F + 2 * c.n_up + 1;
+                if (q.nwt > LevCfg<false>::NWT_MAX)
+                    return fail(ctx, LLOID_EINVAL, "upsampling window of %d rows exceeds %d", q.nwt, LevCfg<false>::NWT_MAX);
+                if (!encode_map_f32(&mp.accin, P.d_acc, b->Mpad, (long long)nd * 2 * P.acc_rows, 128, q.nwt))
+                    return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (window, bank %d)", b->id);
+            }
             if (L.Kp > 0) {
                 bool ok = encode_map(&mp.cre, bf, L.d_cre, L.Kp, b->Mpad, kTcTileM) &&
                           encode_map(&mp.cim, bf, L.d_cim, L.Kp, b->Mpad, kTcTileM) &&
