@@ -207,6 +207,20 @@ LLOID_API lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int
 LLOID_API lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* out, int64_t cap,
                              int64_t* t0, int64_t* n_samples);
 
+/* Checkpoint of the streaming state (SGNL snapshots its state periodically,
+ * Section II.D.4): every per-detector stream ring, every bank's history ring,
+ * the window partials and retained trigger windows, and the stream
+ * positions, written to the host buffer buf[*len] after waiting for the
+ * context's stream.  With buf == NULL, *len receives the size and the call
+ * returns LLOID_OK; with *len too small it returns LLOID_ERANGE and the size. */
+LLOID_API lloid_status lloid_save_state(lloid_ctx* ctx, void* buf, size_t* len);
+
+/* Resume from a checkpoint: ctx must have been created with the same
+ * configuration and have the same banks loaded in the same order as the
+ * saved context (LLOID_EINVAL otherwise).  Streaming then continues exactly
+ * as the saved context would have. */
+LLOID_API lloid_status lloid_restore_state(lloid_ctx* ctx, const void* buf, size_t len);
+
 /* Wait for all enqueued work of the context (ECUDA on a device error). */
 LLOID_API lloid_status lloid_synchronize(lloid_ctx* ctx);
 

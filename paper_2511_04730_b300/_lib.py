@@ -71,6 +71,8 @@ SIGNATURES = [
     ("lloid_snr_block", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("lloid_synchronize", ctypes.c_int, [ctypes.c_void_p]),
+    ("lloid_save_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("lloid_restore_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("lloid_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
     ("lloid_bytes_in_use", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
                                           ctypes.POINTER(ctypes.c_size_t)]),

@@ -898,6 +898,46 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
     return LLOID_OK;
 }
 
+// Checkpoint layout: header words describing the context, then every
+// stateful device segment in a fixed order.
+struct Segment { void* p; size_t bytes; };
+
+void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segment>* seg) {
+    const lloid_config& c = ctx->cfg;
+    const int nd = c.n_detectors;
+    hdr->clear();
+    seg->clear();
+    long long h[] = {0x4C4C4F4944535431LL, 1, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
+                     c.max_block, c.max_history, c.min_rate, (long long)ctx->banks.size(), ctx->M_used,
+                     ctx->M_cap, ctx->n_slots};
+    hdr->assign(h, h + sizeof h / sizeof h[0]);
+    for (int d = 0; d < nd; ++d) { hdr->push_back(ctx->pos[d]); hdr->push_back(ctx->fin[d]); hdr->push_back(ctx->last_n[d]); }
+    seg->push_back({ctx->ring0, (size_t)nd * ctx->ring0_len * 4});
+    for (int r = 0; r < ctx->n_rates; ++r) seg->push_back({ctx->rate_ring[r], (size_t)nd * ctx->rate_len[r] * 4});
+    for (int r = 0; r <= kMaxRates; ++r)
+        if (ctx->s_hi[r]) {
+            seg->push_back({ctx->s_hi[r], (size_t)nd * 2 * ctx->s_len[r] * 2});
+            seg->push_back({ctx->s_lo[r], (size_t)nd * 2 * ctx->s_len[r] * 2});
+        }
+    seg->push_back({ctx->d_part, (size_t)ctx->M_cap * nd * ctx->n_slots * sizeof(Partial)});
+    seg->push_back({ctx->d_slab, (size_t)kWindowRing * nd * ctx->M_cap * sizeof(SlabEntry)});
+    for (auto& kv : ctx->banks) {
+        const BankRT* b = kv.second;
+        hdr->push_back(kv.first); hdr->push_back(b->M); hdr->push_back(b->tmpl0); hdr->push_back((long long)b->sl.size());
+        for (const auto& sl : b->sl) {
+            hdr->push_back(sl.rate); hdr->push_back(sl.J); hdr->push_back(sl.N); hdr->push_back(sl.L);
+            if (sl.d_yring) seg->push_back({sl.d_yring, (size_t)nd * sl.L * sl.y_len * 4});
+        }
+        for (const auto& L : b->lev)
+            if (L.d_yhi) {
+                seg->push_back({L.d_yhi, (size_t)nd * 2 * L.R * L.Kp * 2});
+                seg->push_back({L.d_ylo, (size_t)nd * 2 * L.R * L.Kp * 2});
+            }
+    }
+    hdr->push_back((long long)seg->size());
+    for (auto& x : *seg) hdr->push_back((long long)x.bytes);
+}
+
 // A kernel whose bounded wait expired leaves a code in d_err (see kernels_tc.cuh).
 lloid_status check_kernel_err(lloid_ctx* ctx) {
     int e = 0;
@@ -1364,6 +1404,70 @@ lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* o
     if ((st = check_kernel_err(ctx))) return st;
     if (t0) *t0 = k_a;
     if (n_samples) *n_samples = n;
+    return LLOID_OK;
+}
+
+lloid_status lloid_save_state(lloid_ctx* ctx, void* buf, size_t* len) {
+    if (!ctx || !len) return LLOID_EINVAL;
+    std::vector<long long> hdr;
+    std::vector<Segment> seg;
+    state_layout(ctx, &hdr, &seg);
+    size_t need = sizeof(long long) * (1 + hdr.size());
+    for (auto& x : seg) need += x.bytes;
+    if (!buf || *len < need) {
+        *len = need;
+        return buf ? fail(ctx, LLOID_ERANGE, "checkpoint needs %zu bytes", need) : LLOID_OK;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    char* o = static_cast<char*>(buf);
+    long long nh = (long long)hdr.size();
+    std::memcpy(o, &nh, sizeof nh);
+    o += sizeof nh;
+    std::memcpy(o, hdr.data(), hdr.size() * sizeof(long long));
+    o += hdr.size() * sizeof(long long);
+    for (auto& x : seg) {
+        CK(cudaMemcpy(o, x.p, x.bytes, cudaMemcpyDeviceToHost));
+        o += x.bytes;
+    }
+    *len = need;
+    return LLOID_OK;
+}
+
+lloid_status lloid_restore_state(lloid_ctx* ctx, const void* buf, size_t len) {
+    if (!ctx || !buf) return LLOID_EINVAL;
+    std::vector<long long> hdr;
+    std::vector<Segment> seg;
+    CK(cudaStreamSynchronize(ctx->stream));
+    // positions are part of the header: compare everything else
+    state_layout(ctx, &hdr, &seg);
+    const char* in = static_cast<const char*>(buf);
+    long long nh = 0;
+    if (len < sizeof nh) return fail(ctx, LLOID_EINVAL, "checkpoint too short");
+    std::memcpy(&nh, in, sizeof nh);
+    if (nh != (long long)hdr.size() || len < sizeof(long long) * (1 + (size_t)nh))
+        return fail(ctx, LLOID_EINVAL, "checkpoint does not match this context (layout)");
+    std::vector<long long> saved((size_t)nh);
+    std::memcpy(saved.data(), in + sizeof nh, (size_t)nh * sizeof(long long));
+    const int nd = ctx->cfg.n_detectors;
+    const size_t pos_at = 15, pos_end = 15 + 3 * (size_t)nd;
+    for (size_t i = 0; i < hdr.size(); ++i) {
+        if (i >= pos_at && i < pos_end) continue;
+        if (saved[i] != hdr[i]) return fail(ctx, LLOID_EINVAL, "checkpoint does not match this context (word %zu)", i);
+    }
+    size_t need = sizeof(long long) * (1 + hdr.size());
+    for (auto& x : seg) need += x.bytes;
+    if (len < need) return fail(ctx, LLOID_EINVAL, "checkpoint truncated");
+    const char* o = in + sizeof(long long) * (1 + hdr.size());
+    for (auto& x : seg) {
+        CK(cudaMemcpy(x.p, o, x.bytes, cudaMemcpyHostToDevice));
+        o += x.bytes;
+    }
+    for (int d = 0; d < nd; ++d) {
+        ctx->pos[d] = saved[pos_at + 3 * d];
+        ctx->fin[d] = saved[pos_at + 3 * d + 1];
+        ctx->last_n[d] = saved[pos_at + 3 * d + 2];
+    }
+    CK(cudaEventRecord(ctx->done_ev, ctx->stream));
     return LLOID_OK;
 }
 

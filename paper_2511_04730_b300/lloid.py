@@ -200,6 +200,18 @@ class Context:
                                               ctypes.byref(t0), ctypes.byref(n)))
         return out, int(t0.value)
 
+    def save_state(self) -> bytes:
+        """Checkpoint of the streaming state (lloid_save_state)."""
+        n = ctypes.c_size_t(0)
+        self._check(self._lib.lloid_save_state(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self._lib.lloid_save_state(self._h, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def restore_state(self, blob: bytes):
+        """Resume from save_state() output (same configuration and banks)."""
+        self._check(self._lib.lloid_restore_state(self._h, blob, len(blob)))
+
     def synchronize(self):
         self._check(self._lib.lloid_synchronize(self._h))
 
