@@ -33,7 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 F0 = 2048
-REF_M = 8          # templates per reference-arm step (a bounded oracle sample)
+REF_M = 8                    # templates per reference-arm step (a bounded oracle sample)
+REF_SECONDS = 24             # seconds of strain per reference-arm step (~0.4 s of oracle work)
 METRIC = "template-seconds filtered/s at max |dSNR|<=5e-3 vs FP32 path; p50/p99 block latency"
 UNIT = "template-s/s"
 WORKLOAD = ("1000 Newtonian chirp templates (Mc log-U[1,20] Msun, 64 s, 9 slices 2048/1024/512/256/128 Hz, "
@@ -43,8 +44,8 @@ WORKLOAD = ("1000 Newtonian chirp templates (Mc log-U[1,20] Msun, 64 s, 9 slices
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=40)
-    p.add_argument("--warmup", type=int, default=4)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="lloid", choices=["lloid", "reference"])
     p.add_argument("--precision", default="fp16_split", choices=["fp32", "fp16_split", "bf16_split"])
     p.add_argument("--block-seconds", type=int, default=8)
@@ -79,53 +80,105 @@ def dist_init(args):
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
+_NVML_SAMPLER = r"""
+import ctypes, sys, time
+out = open(sys.argv[2], "w", buffering=1)
+try:
+    nv = ctypes.CDLL("libnvidia-ml.so.1")
+    if nv.nvmlInit_v2() != 0:
+        raise RuntimeError("nvmlInit failed")
+    want = sys.argv[3].replace("-", "").lower()
+    n = ctypes.c_uint(0)
+    nv.nvmlDeviceGetCount_v2(ctypes.byref(n))
+    h = None
+    for i in range(n.value):                       # the device whose UUID matches, else the index
+        c = ctypes.c_void_p()
+        nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(i), ctypes.byref(c))
+        buf = ctypes.create_string_buffer(96)
+        nv.nvmlDeviceGetUUID(c, buf, ctypes.c_uint(96))
+        if want and want in buf.value.decode().replace("-", "").lower():
+            h = c
+    if h is None:
+        h = ctypes.c_void_p()
+        nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(int(sys.argv[1])), ctypes.byref(h))
+    reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+        nv.nvmlDeviceGetCurrentClocksThrottleReasons
+    sm, mx, r = ctypes.c_uint(0), ctypes.c_uint(0), ctypes.c_ulonglong(0)
+    nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))          # 1 = SM clock domain
+    while True:
+        nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm))
+        reasons_fn(h, ctypes.byref(r))
+        out.write(f"{time.time():.6f} {sm.value} {mx.value} {r.value}\n")
+        time.sleep(0.002)
+except Exception as e:
+    out.write("# " + repr(e).replace("\n", " ") + "\n")
+"""
+
+
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons sampled every ~2 ms by a separate
+    process (NVML), started before the timed region and trimmed to it."""
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4}
 
     def __init__(self, device):
         self.device = device
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
+        self.error = None
+        try:
+            import torch
+            self.uuid = str(torch.cuda.get_device_properties(device).uuid)
+        except Exception:
+            self.uuid = ""
 
     def start(self):
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            fd, self.path = tempfile.mkstemp(suffix=".txt")
             os.close(fd)
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except Exception:
+            self.proc = subprocess.Popen([sys.executable, "-c", _NVML_SAMPLER, str(self.device), self.path,
+                                          self.uuid],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 20
+            while time.time() < deadline and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)
+        except Exception as e:
+            self.error = repr(e)
             self.proc = None
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
-            return None
+            return {"error": self.error or "sampler not started"}
         self.proc.terminate()
         try:
             self.proc.wait(5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
+            if line.startswith("#"):
+                self.error = line[1:].strip()
+            f = line.split()
+            if len(f) == 4 and not line.startswith("#"):
+                rows.append((float(f[0]), float(f[1]), float(f[2]), int(f[3])))
         os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        if not rows:
+            return {"error": self.error or "no samples"}
+        t0, t1 = self.t0 or rows[0][0], self.t1 or rows[-1][0]
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        if len(inside) < 3:      # a region shorter than a few samples: the samples nearest to it
+            inside = sorted(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + t1)))[:3]
+        reasons = sorted(n for n, bit in self.REASONS.items() if any(r[3] & bit for r in inside))
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "samples": len(inside), "region_ms": round(1000 * (t1 - t0), 2), "source": "nvml",
+                "reasons": reasons}
 
 
 # ---------------------------------------------------------------------------
@@ -210,11 +263,11 @@ def peaks():
 def oracle_sample(M=64, seconds=68, seed_det=0):
     """Time the FP64 oracle's LLOID on a bounded sample: the first M templates'
     worth of the 1000-template family (same Mc range, same slicing rule), one
-    detector, `seconds` of data (64 s of template history + 4 s)."""
+    detector, `seconds` of data from the start of the stream."""
     import numpy as np
     import workloads as W
     from oracle import lloid_oracle as O
-    w = W.make_workload("bank1000", n_templates=M, n_seconds=seconds, n_det=1, n_inj=1)
+    w = W.make_workload("bank1000", n_templates=M, n_seconds=seconds, n_det=1, n_inj=0)
     sl = O.svd_bank(w.banks[0], w.plans[0])
     d = w.strain(seed_det).astype(np.float64)
     t, c = time.perf_counter(), time.process_time()
@@ -232,15 +285,16 @@ def run_reference(args, rank, world, dist):
         return
     vals = []
     cores = []
+    secs = REF_SECONDS
     for _ in range(args.warmup):
-        oracle_sample(M=REF_M, seconds=68)
+        oracle_sample(M=REF_M, seconds=secs)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, dt, sample, c = oracle_sample(M=REF_M, seconds=68)
+        v, dt, sample, c = oracle_sample(M=REF_M, seconds=secs)
         vals.append(dt)
         cores.append(c)
     wall = time.perf_counter() - t0
-    value = REF_M * 68 * args.steps / sum(vals)
+    value = REF_M * secs * args.steps / sum(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -358,23 +412,38 @@ def run_lloid(args, rank, world, dist):
     precisions = [args.precision] + ([] if args.no_fp32_compare or args.precision == "fp32" else ["fp32"])
     clocks = None
     for prec in precisions:
-        ctx = make_ctx(prec, timing=True)
+        # throughput: K steps without per-stage events
+        ctx = make_ctx(prec, timing=False)
         load_all(ctx)
         pos = 0
         _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
-        ctx.stage_times(reset=True)
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
         sampler = ClockSampler(dev) if prec == args.precision else None
         if sampler:
             sampler.start()
+            sampler.begin()
         ms, pos, launches, _, _ = run_steps(ctx, args.steps, pos)
         torch.cuda.synchronize()
         if sampler:
+            sampler.end()
             clocks = sampler.stop()
-        st = ctx.stage_times(reset=True)
-        per_ctx[prec] = {"ms": ms, "launches": launches, "stages": st}
+        ctx.close()
+        per_ctx[prec] = {"ms": ms, "launches": launches}
+        if prec != args.precision:
+            continue
+        # stage breakdown and roofline: the same K steps again, with CUDA events around every stage
+        ctx = make_ctx(prec, timing=True)
+        load_all(ctx)
+        pos = 0
+        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
+        ctx.stage_times(reset=True)
+        torch.cuda.synchronize()
+        ms_t, pos, _, _, _ = run_steps(ctx, args.steps, pos)
+        torch.cuda.synchronize()
+        per_ctx[prec]["stages"] = ctx.stage_times(reset=True)
+        per_ctx[prec]["ms_timed_stages"] = ms_t
         ctx.close()
 
     # accuracy of the measured path against the FP32 path (same stream, same blocks)
@@ -504,6 +573,7 @@ def run_lloid(args, rank, world, dist):
                                       "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
                                       "n": len(lat)} if lat else None),
             "stage_ms_per_step": stage_ms,
+            "ms_per_step_with_stage_events": statistics.mean(main["ms_timed_stages"]),
             "kernels": recon_info,
             "paths": {p: units * args.steps / (sum(v["ms"]) / 1000.0) for p, v in per_ctx.items()},
         }

@@ -338,82 +338,202 @@ struct LevCfg {
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
 };
 
-// Up_F of the level below for 32 consecutive outputs q0..q0+31 of one
-// template (column m of the transposed plane), added into v[].
-// Eq. 8 centred: Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
-// Level tiles start at multiples of 128, so q0 mod F is PH0 = 0 for F <= 32
-// and 0 or 32 for F = 64: every register index below is a compile-time constant.
-// Up_F of the level below for CH consecutive outputs q0..q0+CH-1 of one
-// template, added into vr/vi.  Eq. 8 centred:
-//   Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
-// x comes from the shared-memory window of the tile (row w = x index
-// floor(Q_tile/F) - N_up + w, column = template within the tile); wb is the
-// window row of floor(q0/F) - N_up.  Tiles start at multiples of 128 and
-// chunks at multiples of CH, so q0 mod F is the compile-time PH0.
-template <int CH, int F, int NUP, int PH0>
-__device__ __forceinline__ void add_up_s(float (&vr)[CH], float (&vi)[CH], const float* __restrict__ wre,
-                                         const float* __restrict__ wim, int wb, int col) {
-    static_assert(NUP == 8, "the constant tables hold N_up = 8");
-    constexpr int NW = (PH0 + CH - 1) / F + 2 * NUP + 1;
-    constexpr int OFF = kUpTaps * (F - 2);
-    const float* pr = wre + wb * 128 + col;
-    const float* pi = wim + wb * 128 + col;
-    float xr[NW], xi[NW];
+// One epilogue thread: template m (TMEM lane), columns 64 h .. 64 h + 63 of
+// the tile.  Acc[q] = (C Y)[q] + Up_F(Acc_below)[q] with Eq. 8 in its centred
+// reading, Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
+// The shared-memory window holds x from floor(Q_tile/F) - N_up on (row w);
+// output column c of the tile reads rows floor(c/F) + 2 N_up - t.  The rows
+// this half needs are copied to registers first and the window is released
+// at once, so that the next tile's window streams in while this one
+// finishes.  Tiles start at multiples of 128 and F divides 64, so every
+// register index is a compile-time constant.
+template <int F, bool TOP, bool STORE_Z>
+__device__ __forceinline__ float4 epi_half(uint32_t tb, bool has_acc, const float* __restrict__ wre,
+                                        const float* __restrict__ wim, int col, int half, uint64_t* wempty,
+                                        float* o_re, float* o_im, long long q0, long long lo, long long hi, int Mpad,
+                                        int m, float* zr, float* zi, bool zvalid) {
+    float best = -1.f, bre = 0.f, bim = 0.f;
+    int bk = 0x7fffffff;
+    constexpr int NUP = 8;
+    constexpr int FF = F ? F : 1;
+    constexpr int NWH = F ? 63 / FF + 2 * NUP + 1 : 1;
+    constexpr int OFF = F ? kUpTaps * (F - 2) : 0;
+    if constexpr (F >= 8 && F <= 32) {
+        // One F-block of outputs per iteration, rolled, with its 2 N_up + 1 window rows read
+        // from shared memory (the constant taps of a block then stay constant-bank operands
+        // instead of being held in registers across unrolled blocks).  The window is
+        // released when the half tile is done.
+#pragma unroll 1
+        for (int blk = 0; blk < 64 / FF; ++blk) {
+            const int c0 = 64 * half + blk * FF;          // tile column of the block's first output
+            const int wrow = c0 / FF;                     // window row of x[floor(c0/F) - N_up]
+            float x_r[2 * NUP + 1], x_i[2 * NUP + 1];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) { xr[w] = pr[w * 128]; xi[w] = pi[w * 128]; }
+            for (int w = 0; w <= 2 * NUP; ++w) {
+                x_r[w] = wre[(wrow + w) * 128 + col];
+                x_i[w] = wim[(wrow + w) * 128 + col];
+            }
 #pragma unroll
-    for (int j = 0; j < CH; ++j) {
-        const int ph = (PH0 + j) % F;
-        const int b = (PH0 + j) / F + 2 * NUP;       // (floor(q/F) + N_up) - (floor(q0/F) - N_up)
-        if (ph == 0) {                               // z_0 = g[t F]: 1 at t = N_up, 0 elsewhere
-            vr[j] += xr[b - NUP];
-            vi[j] += xi[b - NUP];
-            continue;
+            for (int sub = 0; sub < FF / 8; ++sub) {
+                uint32_t rr[16];
+                if (has_acc) {
+                    tmem_ld8x2_async(tb + blk * FF + sub * 8, rr);
+                    tmem_wait16(rr);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) rr[j] = 0u;
+                }
+                float re[8], im[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    re[j] = __uint_as_float(rr[j]);
+                    im[j] = __uint_as_float(rr[8 + j]);
+                    const int ph = sub * 8 + j;
+                    if (ph == 0) {
+                        re[j] += x_r[NUP];
+                        im[j] += x_i[NUP];
+                        continue;
+                    }
+                    float sr = 0.f, si = 0.f;
+#pragma unroll
+                    for (int t = 0; t <= 2 * NUP; ++t) {
+                        if (t * F + ph > 2 * F * NUP) continue;
+                        const float zc = c_upz[OFF + ph * kUpTaps + t];
+                        sr = fmaf(zc, x_r[2 * NUP - t], sr);
+                        si = fmaf(zc, x_i[2 * NUP - t], si);
+                    }
+                    re[j] += sr;
+                    im[j] += si;
+                }
+                const int cb = blk * FF + sub * 8;        // column within the half tile
+                if (TOP) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float pw = re[j] * re[j] + im[j] * im[j];
+                        if (pw > best) { best = pw; bk = 64 * half + cb + j; bre = re[j]; bim = im[j]; }
+                    }
+                    if (STORE_Z && zvalid) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) { zr[cb + j] = re[j]; zi[cb + j] = im[j]; }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const long long q = q0 + cb + j;
+                        if (q >= lo && q <= hi) {
+                            o_re[(q - lo) * Mpad + m] = re[j];
+                            o_im[(q - lo) * Mpad + m] = im[j];
+                        }
+                    }
+                }
+            }
         }
-        float sr = 0.f, si = 0.f;
-#pragma unroll
-        for (int t = 0; t <= 2 * NUP; ++t) {
-            if (t * F + ph > 2 * F * NUP) continue;   // beyond the kernel: identically zero
-            const float zc = c_upz[OFF + ph * kUpTaps + t];
-            sr = fmaf(zc, xr[b - t], sr);
-            si = fmaf(zc, xi[b - t], si);
-        }
-        vr[j] += sr;
-        vi[j] += si;
+        mbar_arrive(wempty);
+        return make_float4(best, __int_as_float(bk), bre, bim);
     }
+    constexpr int NWR = (F >= 8 && F <= 32) ? 1 : NWH;
+    float xr[NWR], xi[NWR];
+    if (F) {
+        const int r0 = (64 * half) / FF;
+        const float* pr = wre + r0 * 128 + col;
+        const float* pi = wim + r0 * 128 + col;
+#pragma unroll
+        for (int w = 0; w < NWR; ++w) { xr[w] = pr[w * 128]; xi[w] = pi[w * 128]; }
+        mbar_arrive(wempty);
+    }
+    // 8-column chunks, the TMEM load of chunk k + 1 in flight while chunk k is computed
+    uint32_t cur[16], nxt[16];
+    if (has_acc) {
+        tmem_ld8x2_async(tb, cur);
+        tmem_wait16(cur);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) cur[j] = 0u;
+    }
+#pragma unroll
+    for (int cc = 0; cc < 64; cc += 8) {
+        if (has_acc && cc + 8 < 64) tmem_ld8x2_async(tb + cc + 8, nxt);
+        float re[8], im[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { re[j] = __uint_as_float(cur[j]); im[j] = __uint_as_float(cur[8 + j]); }
+        if (F) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int cr = cc + j;
+                const int ph = cr % FF;
+                const int b = cr / FF + 2 * NUP;
+                if (ph == 0) {                           // z_0 = g[t F]: 1 at t = N_up, 0 elsewhere
+                    re[j] += xr[b - NUP];
+                    im[j] += xi[b - NUP];
+                    continue;
+                }
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int t = 0; t <= 2 * NUP; ++t) {
+                    if (t * F + ph > 2 * F * NUP) continue;   // beyond the kernel: identically zero
+                    const float zc = c_upz[OFF + ph * kUpTaps + t];
+                    sr = fmaf(zc, xr[b - t], sr);
+                    si = fmaf(zc, xi[b - t], si);
+                }
+                re[j] += sr;
+                im[j] += si;
+            }
+        }
+        if (TOP) {
+            // chunk argmax as a pairwise tree (the earlier column wins ties), then into the running one
+            float p[8];
+            int k[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { p[j] = re[j] * re[j] + im[j] * im[j]; k[j] = j; }
+#pragma unroll
+            for (int s = 1; s < 8; s *= 2) {
+#pragma unroll
+                for (int j = 0; j < 8; j += 2 * s) {
+                    const bool later = p[j + s] > p[j];
+                    p[j] = later ? p[j + s] : p[j];
+                    k[j] = later ? k[j + s] : k[j];
+                }
+            }
+            float cre = re[0], cim = im[0];
+#pragma unroll
+            for (int j = 1; j < 8; ++j) {
+                cre = (k[0] == j) ? re[j] : cre;
+                cim = (k[0] == j) ? im[j] : cim;
+            }
+            if (p[0] > best) { best = p[0]; bk = 64 * half + cc + k[0]; bre = cre; bim = cim; }
+            if (STORE_Z && zvalid) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) { zr[cc + j] = re[j]; zi[cc + j] = im[j]; }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const long long q = q0 + cc + j;
+                if (q >= lo && q <= hi) {
+                    o_re[(q - lo) * Mpad + m] = re[j];
+                    o_im[(q - lo) * Mpad + m] = im[j];
+                }
+            }
+        }
+        if (has_acc && cc + 8 < 64) {
+            tmem_wait16(nxt);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) cur[j] = nxt[j];
+        }
+    }
+    return make_float4(best, __int_as_float(bk), bre, bim);
 }
 
-template <int NUP>
-__device__ __forceinline__ void add_up_dispatch(int F, int c, float (&vr)[16], float (&vi)[16], const float* wre,
-                                                const float* wim, int col) {
-    const int wb = c / F;                            // floor(q0/F) - floor(Q_tile/F)
-    const int ph0 = c & (F - 1);
-    switch (F) {
-        case 2: add_up_s<16, 2, NUP, 0>(vr, vi, wre, wim, wb, col); break;
-        case 4: add_up_s<16, 4, NUP, 0>(vr, vi, wre, wim, wb, col); break;
-        case 8: add_up_s<16, 8, NUP, 0>(vr, vi, wre, wim, wb, col); break;
-        case 16: add_up_s<16, 16, NUP, 0>(vr, vi, wre, wim, wb, col); break;
-        case 32:
-            if (ph0 == 0) add_up_s<16, 32, NUP, 0>(vr, vi, wre, wim, wb, col);
-            else add_up_s<16, 32, NUP, 16>(vr, vi, wre, wim, wb, col);
-            break;
-        case 64:
-            if (ph0 == 0) add_up_s<16, 64, NUP, 0>(vr, vi, wre, wim, wb, col);
-            else if (ph0 == 16) add_up_s<16, 64, NUP, 16>(vr, vi, wre, wim, wb, col);
-            else if (ph0 == 32) add_up_s<16, 64, NUP, 32>(vr, vi, wre, wim, wb, col);
-            else add_up_s<16, 64, NUP, 48>(vr, vi, wre, wim, wb, col);
-            break;
-        default: break;
-    }
-}
-
-template <bool BF16, bool TOP, bool STORE_Z>
+// F (the factor to the level below, 0 at the lowest level) is a template
+// parameter so that each instantiation gets the register allocation its
+// epilogue needs (up to 96 registers hold the window at F = 2); 10 warps, three
+// of which share one SM sub-partition's 16K registers, leave 168 per thread.
+template <bool BF16, bool TOP, bool STORE_Z, int F>
 __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
     k_level_tc(const LevelJob* __restrict__ jobs, const LevelMaps* __restrict__ maps,
                const int* __restrict__ tile_base, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
                int det0, int n_det_push, long long window, Partial* __restrict__ part, long long part_tmpl_stride,
                int n_slots, float* __restrict__ zout, int* __restrict__ err) {
-    constexpr int NUP = 8;
     using C = LevCfg<BF16>;
     constexpr int EPI = 32 * C::EPI_WARPS;
     extern __shared__ uint8_t smem_raw[];
@@ -465,16 +585,6 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                 const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
                 const long long Q0 = fdiv(fdiv(k_a - jb.Lambda, jb.D), 128) * 128;
                 const int yrow = det * 2 * jb.y_rows + (int)((Q0 + 128LL * tt) & (jb.y_rows - 1));
-                if (jb.F) {   // the level below's window for this tile (rows outside the planes read 0)
-                    if (!mbar_wait(wempty, wphase ^ 1, err, 37)) { ok = false; break; }
-                    const long long lo_in = fdiv(k_a - jb.Lambda_lo, jb.D_lo);
-                    const long long a_t = fdiv(Q0 + 128LL * tt, jb.F) - 8 - lo_in;
-                    const int base_row = det * 2 * jb.acc_in_rows;
-                    mbar_expect_tx(wfull, 2u * jb.nwt * 128 * 4);
-                    tma_load_2d(win_re, &mp->accin, wfull, tm * 128, (int)(base_row + a_t));
-                    tma_load_2d(win_im, &mp->accin, wfull, tm * 128, (int)(base_row + jb.acc_in_rows + a_t));
-                    wphase ^= 1;
-                }
                 for (int kc = 0; kc < jb.Kp; kc += kTcK) {
                     if (!mbar_wait(empty + stage, phase ^ 1, err, 31)) { ok = false; break; }
                     uint8_t* sb = smem + stage * C::STAGE_BYTES;
@@ -488,6 +598,19 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                     tma_load_2d(sb + C::NA * C::TILE_A, &mp->yhi, full + stage, kc, yrow);
                     tma_load_2d(sb + C::NA * C::TILE_A + C::TILE_B, &mp->ylo, full + stage, kc, yrow);
                     if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                }
+                // The level below's window for this tile (rows outside the planes read 0).  It is
+                // fetched after the tile's operand stages so that the MMAs of this tile overlap
+                // the epilogue of the previous one, which still holds the (single) window buffer.
+                if (F != 0 && ok) {
+                    if (!mbar_wait(wempty, wphase ^ 1, err, 37)) { ok = false; break; }
+                    const long long lo_in = fdiv(k_a - jb.Lambda_lo, jb.D_lo);
+                    const long long a_t = fdiv(Q0 + 128LL * tt, F != 0 ? F : 1) - 8 - lo_in;
+                    const int base_row = det * 2 * jb.acc_in_rows;
+                    mbar_expect_tx(wfull, 2u * jb.nwt * 128 * 4);
+                    tma_load_2d(win_re, &mp->accin, wfull, tm * 128, (int)(base_row + a_t));
+                    tma_load_2d(win_im, &mp->accin, wfull, tm * 128, (int)(base_row + jb.acc_in_rows + a_t));
+                    wphase ^= 1;
                 }
             }
             for (int s = 0; s < C::STAGES; ++s) {
@@ -566,52 +689,33 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
             const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + buf * 256;
             float best = -1.f, bre = 0.f, bim = 0.f;
             int bk = 0x7fffffff;
-            if (jb.F) {
+            if (F != 0) {
                 const bool wgot = mbar_wait(wfull, wph, err, 39);
                 if (!__all_sync(0xffffffffu, wgot)) break;
                 wph ^= 1;
             }
-#pragma unroll 1
-            for (int c = half * 64; c < half * 64 + 64; c += 16) {
-                float re[16], im[16];
-                if (jb.Kp > 0) {
-                    tmem_ld16(base + c, re);
-                    tmem_ld16(base + 128 + c, im);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) { re[j] = 0.f; im[j] = 0.f; }
-                }
-                const long long q0 = Q0 + 128LL * tt + c;
-                if (jb.F) add_up_dispatch<NUP>(jb.F, c, re, im, win_re, win_im, rowm);
-                if (TOP) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float p = re[j] * re[j] + im[j] * im[j];
-                        if (p > best) { best = p; bk = c + j; bre = re[j]; bim = im[j]; }
-                    }
-                    if (STORE_Z && m < jb.M) {
-                        const int n = (int)(k_b - k_a);
-                        float* zr = zout + (long long)(2 * m) * n + tt * kTcTileN + c;
-                        float* zi = zr + n;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) { zr[j] = re[j]; zi[j] = im[j]; }
-                    }
-                } else {
-                    float* o_re = jb.acc_out + det * jb.acc_out_det_stride;
-                    float* o_im = o_re + (long long)jb.acc_out_rows * jb.Mpad;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const long long q = q0 + j;
-                        if (q >= lo && q <= hi) {
-                            o_re[(q - lo) * jb.Mpad + m] = re[j];
-                            o_im[(q - lo) * jb.Mpad + m] = im[j];
-                        }
-                    }
-                }
+            float *o_re = nullptr, *o_im = nullptr, *zr = nullptr, *zi = nullptr;
+            bool zvalid = false;
+            if (!TOP) {
+                o_re = jb.acc_out + det * jb.acc_out_det_stride;
+                o_im = o_re + (long long)jb.acc_out_rows * jb.Mpad;
+            } else if (STORE_Z && m < jb.M) {
+                const int n = (int)(k_b - k_a);
+                zr = zout + (long long)(2 * m) * n + tt * kTcTileN + 64 * half;
+                zi = zr + n;
+                zvalid = true;
             }
+            const long long q0 = Q0 + 128LL * tt + 64 * half;
+            const uint32_t tb = base + 64 * half;
+            const bool has_acc = jb.Kp > 0;
+            const float4 r = epi_half<F, TOP, STORE_Z>(tb, has_acc, win_re, win_im, rowm, half, wempty, o_re, o_im,
+                                                       q0, lo, hi, jb.Mpad, m, zr, zi, zvalid);
+            best = r.x;
+            bk = __float_as_int(r.y);
+            bre = r.z;
+            bim = r.w;
             tc_fence_before();
             mbar_arrive(tempty + buf);
-            if (jb.F) mbar_arrive(wempty);          // the window may be refilled
             if (TOP && !STORE_Z) {
                 // the later half hands its tile argmax to the earlier half (which wins ties)
                 float4* xb = xchg + buf * 128;

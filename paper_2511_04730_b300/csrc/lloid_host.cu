@@ -152,10 +152,14 @@ struct lloid_ctx {
     FirTcJob* d_firtc = nullptr; FirMaps* d_firmaps = nullptr; int* d_firtc_base = nullptr;
     int n_firtc = 0, firtc_tiles = 0, firtc_smem = 0, firtc_strip = 0;
     static constexpr int kMaxDepth = 8;
-    LevelJob* d_lev[kMaxDepth] = {}; LevelMaps* d_levmaps[kMaxDepth] = {}; int* d_lev_base[kMaxDepth] = {};
-    int n_lev[kMaxDepth] = {}, lev_tiles[kMaxDepth] = {};
+    // one table per (depth, F slot): F = 0 (lowest level), 2, 4, ..., 64 -> slot 0..6
+    static constexpr int kFSlots = 7;
+    static constexpr int kLevTables = kMaxDepth * kFSlots;
+    LevelJob* d_lev[kLevTables] = {}; LevelMaps* d_levmaps[kLevTables] = {}; int* d_lev_base[kLevTables] = {};
+    int n_lev[kLevTables] = {}, lev_tiles[kLevTables] = {};
     int max_depth = 0;
-    std::vector<int> top_job_of_bank;  // bank id -> index in the depth-0 table
+    std::vector<int> top_job_of_bank;  // bank id -> index in its top-level table
+    std::vector<int> top_slot_of_bank; // bank id -> F slot of its top level (split path)
     // split path streams: index 0 = f0, index r + 1 = rate_D[r]; hi/lo halves, double-mapped
     uint16_t* s_hi[kMaxRates + 1] = {};
     uint16_t* s_lo[kMaxRates + 1] = {};
@@ -341,7 +345,7 @@ void free_jobs(lloid_ctx* ctx) {
     ctx->job_allocs.clear();
     ctx->d_fir = nullptr; ctx->d_up = nullptr; ctx->d_rec = nullptr; ctx->d_finj = nullptr;
     ctx->d_firtc = nullptr; ctx->d_firmaps = nullptr; ctx->d_firtc_base = nullptr;
-    for (int d = 0; d < lloid_ctx::kMaxDepth; ++d) {
+    for (int d = 0; d < lloid_ctx::kLevTables; ++d) {
         ctx->d_lev[d] = nullptr; ctx->d_levmaps[d] = nullptr; ctx->d_lev_base[d] = nullptr;
         ctx->n_lev[d] = 0; ctx->lev_tiles[d] = 0;
     }
@@ -400,6 +404,30 @@ struct StageTimer {
 
 
 // Job tables of the split (tensor-core) path for pushes of n samples.
+// Opt every k_level_tc instantiation of one precision into its shared memory.
+template <bool BF16, bool TOP, bool SZ, int F>
+cudaError_t level_attr1(int smem) {
+    return cudaFuncSetAttribute(k_level_tc<BF16, TOP, SZ, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+template <bool BF16, bool TOP, bool SZ>
+cudaError_t level_attr_f(int smem) {
+    cudaError_t e = cudaSuccess;
+    const cudaError_t r[] = {level_attr1<BF16, TOP, SZ, 0>(smem), level_attr1<BF16, TOP, SZ, 2>(smem),
+                             level_attr1<BF16, TOP, SZ, 4>(smem), level_attr1<BF16, TOP, SZ, 8>(smem),
+                             level_attr1<BF16, TOP, SZ, 16>(smem), level_attr1<BF16, TOP, SZ, 32>(smem),
+                             level_attr1<BF16, TOP, SZ, 64>(smem)};
+    for (cudaError_t x : r)
+        if (x != cudaSuccess) e = x;
+    return e;
+}
+template <bool BF16>
+cudaError_t level_smem_attr(int smem) {
+    cudaError_t e = level_attr_f<BF16, false, false>(smem);
+    if (e == cudaSuccess) e = level_attr_f<BF16, true, false>(smem);
+    if (e == cudaSuccess) e = level_attr_f<BF16, true, true>(smem);
+    return e;
+}
+
 lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     const lloid_config& c = ctx->cfg;
     const bool bf = c.precision == LLOID_BF16_SPLIT;
@@ -407,12 +435,13 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     std::vector<FirTcJob> fj;
     std::vector<FirMaps> fm;
     std::vector<int> fb;
-    std::vector<LevelJob> lj[lloid_ctx::kMaxDepth];
-    std::vector<LevelMaps> lm[lloid_ctx::kMaxDepth];
-    std::vector<int> lb[lloid_ctx::kMaxDepth];
-    int lt[lloid_ctx::kMaxDepth] = {};
+    std::vector<LevelJob> lj[lloid_ctx::kLevTables];
+    std::vector<LevelMaps> lm[lloid_ctx::kLevTables];
+    std::vector<int> lb[lloid_ctx::kLevTables];
+    int lt[lloid_ctx::kLevTables] = {};
     int ft = 0, strip = 128, max_depth = 0;
     ctx->top_job_of_bank.assign(ctx->next_bank_id, -1);
+    ctx->top_slot_of_bank.assign(ctx->next_bank_id, 0);
     for (auto& kv : ctx->banks) {
         BankRT* b = kv.second;
         const int nl = (int)b->lev.size();
@@ -458,7 +487,16 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             q.tiles_m = b->Mpad / kTcTileM;
             if (depth == 0) q.tiles_t = (int)(n / kTcTileN);
             else q.tiles_t = (int)((((n - 1 + 2LL * L.Lambda) / L.D + 2) + 127 + 127) / 128);
-            q.D = L.D; q.Lambda = L.Lambda; q.y_rows = L.R; q.map = (int)lj[depth].size();
+            q.D = L.D; q.Lambda = L.Lambda; q.y_rows = L.R;
+            int fslot = 0;
+            if (q.F) {
+                while ((2 << fslot) < q.F) ++fslot;
+                ++fslot;
+                if ((1 << fslot) != q.F || fslot >= lloid_ctx::kFSlots)
+                    return fail(ctx, LLOID_EINVAL, "bank %d: upsampling factor %d is not 2..64", b->id, q.F);
+            }
+            const int tab = depth * lloid_ctx::kFSlots + fslot;
+            q.map = (int)lj[tab].size();
             LevelMaps mp;
             std::memset(&mp, 0, sizeof mp);
             if (j > 0) {
@@ -479,16 +517,16 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                          encode_map(&mp.cim_lo, bf, L.d_cim_lo, L.Kp, b->Mpad, kTcTileM);
                 if (!ok) return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (level, bank %d)", b->id);
             }
-            if (depth == 0) ctx->top_job_of_bank[b->id] = (int)lj[0].size();
-            lj[depth].push_back(q); lm[depth].push_back(mp); lb[depth].push_back(lt[depth]);
-            lt[depth] += q.tiles_m * q.tiles_t;
+            if (depth == 0) { ctx->top_job_of_bank[b->id] = (int)lj[tab].size(); ctx->top_slot_of_bank[b->id] = fslot; }
+            lj[tab].push_back(q); lm[tab].push_back(mp); lb[tab].push_back(lt[tab]);
+            lt[tab] += q.tiles_m * q.tiles_t;
         }
     }
     lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_firtc, fj)) || (st = upload_vec(ctx, &ctx->d_firmaps, fm)) ||
         (st = upload_vec(ctx, &ctx->d_firtc_base, fb)))
         return st;
-    for (int d = 0; d < lloid_ctx::kMaxDepth; ++d) {
+    for (int d = 0; d < lloid_ctx::kLevTables; ++d) {
         ctx->d_lev[d] = nullptr; ctx->d_levmaps[d] = nullptr; ctx->d_lev_base[d] = nullptr;
         ctx->n_lev[d] = (int)lj[d].size(); ctx->lev_tiles[d] = lt[d];
         if (lj[d].empty()) continue;
@@ -507,15 +545,8 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     if (bf) CK(cudaFuncSetAttribute(k_fir_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
     else CK(cudaFuncSetAttribute(k_fir_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
     const int lsmem = bf ? LevCfg<true>::SMEM : LevCfg<false>::SMEM;
-    if (bf) {
-        CK(cudaFuncSetAttribute(k_level_tc<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
-        CK(cudaFuncSetAttribute(k_level_tc<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
-        CK(cudaFuncSetAttribute(k_level_tc<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
-    } else {
-        CK(cudaFuncSetAttribute(k_level_tc<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
-        CK(cudaFuncSetAttribute(k_level_tc<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
-        CK(cudaFuncSetAttribute(k_level_tc<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
-    }
+    if (bf) CK(level_smem_attr<true>(lsmem));
+    else CK(level_smem_attr<false>(lsmem));
     return LLOID_OK;
 }
 
@@ -613,8 +644,35 @@ lloid_status launch_recon_f32(lloid_ctx* ctx, long long k_a, long long n, int de
     return LLOID_OK;
 }
 
-// One ladder depth of the split path (depth 0 = f0: |z|^2 and window maxima).
-lloid_status launch_level(lloid_ctx* ctx, int depth, long long k_a, long long n, int det0, int n_det_push,
+template <bool BF16, bool TOP, bool SZ, int F>
+void launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps, const int* base,
+                int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W, Partial* part,
+                long long part_stride, int n_slots, float* zout, int* err) {
+    k_level_tc<BF16, TOP, SZ, F><<<g, LevCfg<BF16>::THREADS, smem, st>>>(jobs, maps, base, n_jobs, tiles, k_a, k_b,
+                                                                      det0, nd, W, part, part_stride, n_slots, zout,
+                                                                      err);
+}
+template <bool BF16, bool TOP, bool SZ>
+void launch_lv_f(int F, dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps,
+                 const int* base, int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W,
+                 Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
+#define LV_F(FV) launch_lv1<BF16, TOP, SZ, FV>(g, smem, st, jobs, maps, base, n_jobs, tiles, k_a, k_b, det0, nd, W, \
+                                               part, part_stride, n_slots, zout, err)
+    switch (F) {
+        case 0: LV_F(0); break;
+        case 2: LV_F(2); break;
+        case 4: LV_F(4); break;
+        case 8: LV_F(8); break;
+        case 16: LV_F(16); break;
+        case 32: LV_F(32); break;
+        default: LV_F(64); break;
+    }
+#undef LV_F
+}
+
+// One ladder depth and upsampling factor of the split path (depth 0 = f0:
+// |z|^2 and window maxima); fslot 0 = no level below, else F = 2^fslot.
+lloid_status launch_level(lloid_ctx* ctx, int depth, int fslot, long long k_a, long long n, int det0, int n_det_push,
                           bool store_z, const LevelJob* jobs, const LevelMaps* maps, const int* base, int n_jobs,
                           int tiles, float* zout) {
     if (tiles == 0 || n_jobs == 0) return LLOID_OK;
@@ -624,10 +682,10 @@ lloid_status launch_level(lloid_ctx* ctx, int depth, long long k_a, long long n,
     dim3 g(std::min(total, ctx->n_sm));
     const int smem = bf ? LevCfg<true>::SMEM : LevCfg<false>::SMEM;
     Partial* part = store_z ? nullptr : ctx->d_part;
-#define LAUNCH_LV(BFV, TOPV, SZ)                                                                                   \
-    k_level_tc<BFV, TOPV, SZ><<<g, LevCfg<BFV>::THREADS, smem, ctx->stream>>>(jobs, maps, base, n_jobs, tiles, k_a, k_a + n, det0,  \
-                                                              n_det_push, ctx->cfg.window_samples, part, part_stride, \
-                                                              ctx->n_slots, zout, ctx->d_err)
+    const int F = fslot ? 1 << fslot : 0;
+#define LAUNCH_LV(BFV, TOPV, SZ)                                                                                     \
+    launch_lv_f<BFV, TOPV, SZ>(F, g, smem, ctx->stream, jobs, maps, base, n_jobs, tiles, k_a, k_a + n, det0,          \
+                               n_det_push, ctx->cfg.window_samples, part, part_stride, ctx->n_slots, zout, ctx->d_err)
     if (depth > 0) { if (bf) LAUNCH_LV(true, false, false); else LAUNCH_LV(false, false, false); }
     else if (store_z) { if (bf) LAUNCH_LV(true, true, true); else LAUNCH_LV(false, true, true); }
     else { if (bf) LAUNCH_LV(true, true, false); else LAUNCH_LV(false, true, false); }
@@ -715,15 +773,19 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
         {
             StageTimer tm(ctx, 3);
             for (int d = ctx->max_depth - 1; d >= 1; --d)
-                if ((st = launch_level(ctx, d, k_a, n, det0, nd, false, ctx->d_lev[d], ctx->d_levmaps[d],
-                                       ctx->d_lev_base[d], ctx->n_lev[d], ctx->lev_tiles[d], nullptr)))
-                    return st;
+                for (int fs = 0; fs < lloid_ctx::kFSlots; ++fs) {
+                    const int tb = d * lloid_ctx::kFSlots + fs;
+                    if ((st = launch_level(ctx, d, fs, k_a, n, det0, nd, false, ctx->d_lev[tb], ctx->d_levmaps[tb],
+                                           ctx->d_lev_base[tb], ctx->n_lev[tb], ctx->lev_tiles[tb], nullptr)))
+                        return st;
+                }
         }
         // top level (f0) + a5 window maxima
         {
             StageTimer tm(ctx, 4);
-            st = launch_level(ctx, 0, k_a, n, det0, nd, false, ctx->d_lev[0], ctx->d_levmaps[0], ctx->d_lev_base[0],
-                              ctx->n_lev[0], ctx->lev_tiles[0], nullptr);
+            for (int fs = 0; fs < lloid_ctx::kFSlots && !st; ++fs)
+                st = launch_level(ctx, 0, fs, k_a, n, det0, nd, false, ctx->d_lev[fs], ctx->d_levmaps[fs],
+                                  ctx->d_lev_base[fs], ctx->n_lev[fs], ctx->lev_tiles[fs], nullptr);
         }
         if (st) return st;
     }
@@ -1395,7 +1457,8 @@ lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* o
         st = launch_recon_f32(ctx, k_a, n, det, 1, true, ctx->d_rec + idx, db, 1, tiles, out);
     } else {
         const int tiles = (b->Mpad / kTcTileM) * (int)(n / kTcTileN);
-        st = launch_level(ctx, 0, k_a, n, det, 1, true, ctx->d_lev[0] + idx, ctx->d_levmaps[0], db, 1, tiles, out);
+        const int fs = ctx->top_slot_of_bank[bank];
+        st = launch_level(ctx, 0, fs, k_a, n, det, 1, true, ctx->d_lev[fs] + idx, ctx->d_levmaps[fs], db, 1, tiles, out);
     }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     cudaFree(db);
