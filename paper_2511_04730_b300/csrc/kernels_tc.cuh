@@ -136,28 +136,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Asynchronous TMEM loads: 8 columns of re (taddr) and of im (taddr + 128)
-// into r[0..7] and r[8..15]; the registers are valid only after
-// tmem_wait16(r), which names them as operands so that no use of them can be
-// scheduled before the wait.
-__device__ __forceinline__ void tmem_ld8x2_async(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15])
-                 : "r"(taddr + 128));
-}
-__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15])
-                 :
-                 : "memory");
-}
-
 template <bool BF16>
 struct TcCfg {
     static constexpr int NA = BF16 ? 4 : 2;                 // A tiles per stage
@@ -171,6 +149,27 @@ struct TcCfg {
 // ---------------------------------------------------------------------------
 // Host helpers
 // ---------------------------------------------------------------------------
+// v = hi + lo with both halves FP16 (or BF16): hi = round(v), lo = round(v - hi).
+inline void split_hilo_host(bool bf16, const std::vector<double>& v, std::vector<uint16_t>* hi,
+                            std::vector<uint16_t>* lo) {
+    hi->resize(v.size());
+    lo->resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        const float x = (float)v[i];
+        if (bf16) {
+            __nv_bfloat16 bh = __float2bfloat16_rn(x);
+            __nv_bfloat16 bl = __float2bfloat16_rn(x - __bfloat162float(bh));
+            std::memcpy(&(*hi)[i], &bh, 2);
+            std::memcpy(&(*lo)[i], &bl, 2);
+        } else {
+            __half hh = __float2half_rn(x);
+            __half hl = __float2half_rn(x - __half2float(hh));
+            std::memcpy(&(*hi)[i], &hh, 2);
+            std::memcpy(&(*lo)[i], &hl, 2);
+        }
+    }
+}
+
 // FP16: C rounded to FP16 (hi only).  BF16: C = hi + lo, both BF16.
 inline void pack_coeffs_tc(bool bf16, const std::vector<double>& cre, const std::vector<double>& cim, int Mpad,
                            int Kpad, std::vector<uint16_t>* hre, std::vector<uint16_t>* him,

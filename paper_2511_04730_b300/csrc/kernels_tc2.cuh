@@ -14,9 +14,14 @@
 //
 // k_level_tc (a3 + a4 + a5): for ladder level j (rate r_j, lowest first)
 //   Acc_j[q] = C_j Y_j[q] + Up_F(Acc_{j-1})[q], Up of Eq. 8 in its centred
-//   reading; Acc is kept transposed ([q][template], templates contiguous) so
-//   that the epilogue's reads and writes coalesce.  The top level (f0) forms
-//   |z|^2 and the per-tile argmax instead of storing Acc.
+//   reading.  Both terms are tensor-core products accumulated into the same
+//   TMEM tile: Up_F restricted to one 128-sample tile is a fixed matrix U
+//   (output q x window row w, entries z_{q mod F}[t] of Eq. 7), so
+//   Up_F(Acc_{j-1}) = Acc_{j-1}[window] U^T, with the window and U each split
+//   into 16-bit hi + lo halves (three products).  Acc is stored as hi/lo
+//   planes, template-major with time contiguous, which is the K-major layout
+//   the next level's MMA reads.  The top level (f0) forms |z|^2 and the
+//   per-tile argmax instead of storing Acc.
 #pragma once
 #include "kernels_tc.cuh"
 
@@ -46,11 +51,10 @@ struct FirTcJob {
 };
 
 struct LevelJob {
-    const float* acc_in;           // level below, transposed [2][rows][Mpad], detector 0
-    float* acc_out;                // this level (non-top), transposed, detector 0
-    long long acc_in_det_stride, acc_out_det_stride;   // elements
-    const float* upz;              // unused (sub-kernels live in c_upz)
-    int acc_in_rows, acc_out_rows; // rows per re/im plane
+    uint16_t* acc_out;             // non-top: hi/lo planes [det][re hi, re lo, im hi, im lo][Mpad][acc_cols]
+                                   // (column 0 = sample floor8(lo) - 128)
+    long long acc_out_det_stride;  // elements
+    int acc_cols;                  // plane row length (multiple of 128)
     int Kp;                        // Kpad of the level (0: no slice at this rate)
     int M, Mpad, tmpl0;
     int tiles_m, tiles_t;
@@ -58,22 +62,27 @@ struct LevelJob {
     int F, D_lo, Lambda_lo;        // factor to the level below (0: lowest level)
     int y_rows;                    // level ring rows
     int map;                       // index into the level tensor-map array
-    int nwt;                       // up-window rows per 128-sample tile: 127/F + 2 N_up + 1
 };
 
 struct FirMaps { CUtensorMap a, a_lo; };
 
-// Eq. 7 polyphase sub-kernels z_phi[t] = g[t F + phi] (t = 0..16, N_up = 8) for
-// F = 2, 4, ..., 64, packed F after F (offset 17 (F - 2)); filled once per
-// device.  Indexed with compile-time constants, so each tap is one FFMA with a
-// constant-bank operand.
-constexpr int kUpTaps = 17;
-constexpr int kUpTable = kUpTaps * (2 + 4 + 8 + 16 + 32 + 64);
-__constant__ float c_upz[kUpTable];
-// accin: the level below's transposed Acc planes as FP32 rows of Mpad
-// templates (plane rows stacked det-major: [det][re, im][rows]); box 128
-// templates x nwt rows, loaded once per tile into shared memory.
-struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo, accin; };
+// accw: the level below's hi/lo planes (rows [det][plane][Mpad], columns =
+// samples), box 32 samples x 128 templates, 64-byte swizzle; uhi/ulo: the
+// Eq. 8 tile matrices U_F of this level's factor, rows [shift][128 outputs],
+// columns = window rows, same box and swizzle; accst: this level's own planes
+// for the epilogue's TMA stores, box 64 samples x 32 templates, 128-byte swizzle.
+struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo, accw, uhi, ulo, accst; };
+
+// Window of the level below read by one 128-sample tile (N_up = 8): rows
+// floor(Q/F) - N_up - r .. floor(Q/F) + 127/F + N_up, where the shift r =
+// floor(Q/F) mod 8 aligns the first row to 16 bytes (r = 0 for F <= 16, r in
+// {0, 4} for F = 32, {0, 2, 4, 6} for F = 64); whole 32-row stages.
+constexpr int kWinK = 32;
+__host__ __device__ constexpr int win_rows(int F) { return F ? 127 / F + 17 : 0; }
+__host__ __device__ constexpr int win_shift_max(int F) { return F == 64 ? 6 : (F == 32 ? 4 : 0); }
+__host__ __device__ constexpr int win_chunks(int F) {
+    return F ? (win_rows(F) + win_shift_max(F) + kWinK - 1) / kWinK : 0;
+}
 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t desc_nosw(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -103,6 +112,17 @@ __device__ __forceinline__ int job_of(const int* __restrict__ base, int n, int t
 __device__ __forceinline__ long long fdiv(long long a, long long b) {
     long long q = a / b;
     return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+// K-major, 64-byte swizzle (rows of 32 16-bit values), 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)4u << 61;                 // SWIZZLE_64B
+    return d;
 }
 
 template <typename T>
@@ -323,240 +343,60 @@ __global__ void __launch_bounds__(192, 1)
 // ---------------------------------------------------------------------------
 // a3 + a4 + a5 per ladder level
 // ---------------------------------------------------------------------------
-template <bool BF16>
+template <bool BF16, bool TOP>
 struct LevCfg {
     static constexpr int NA = BF16 ? 4 : 2;
-    static constexpr int STAGES = BF16 ? 1 : 2;
+    // below the top, 64 KB of shared memory stage the Acc planes for the TMA stores
+    static constexpr int STAGES = TOP ? (BF16 ? 2 : 3) : (BF16 ? 1 : 2);
     static constexpr int TILE_A = kTcTileM * kTcK * 2;
     static constexpr int TILE_B = kTcTileN * kTcK * 2;
     static constexpr int STAGE_BYTES = NA * TILE_A + 2 * TILE_B;
-    static constexpr int XCHG = 2 * 128 * 16;          // tile-argmax exchange between the column halves
-    static constexpr int NWT_MAX = 80;                 // up-window rows for F = 2
-    static constexpr int WIN = 2 * NWT_MAX * 128 * 4;  // re + im windows of the level below
-    static constexpr int SMEM = STAGES * STAGE_BYTES + WIN + XCHG + 1024 + 256;
+    static constexpr int WTILE = 128 * kWinK * 2;      // one window plane or one U half: 128 rows x 64 B
+    static constexpr int WSTAGE = 6 * WTILE;           // re hi, re lo, im hi, im lo, U hi, U lo
+    static_assert(WSTAGE <= STAGE_BYTES, "a window stage fits a stage slot");
     static constexpr int EPI_WARPS = 8;                 // two per TMEM lane quarter, 64 columns each
+    static constexpr int STG_BUF = 32 * 128;           // 32 templates x 64 samples x 2 B, 128-byte swizzle
+    static constexpr int STG = TOP ? 0 : EPI_WARPS * 2 * STG_BUF;
+    static constexpr int XCHG = 2 * 128 * 16;          // tile-argmax exchange between the column halves
+    static constexpr int SMEM = STAGES * STAGE_BYTES + STG + XCHG + 1024 + 256;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
 };
 
-// One epilogue thread: template m (TMEM lane), columns 64 h .. 64 h + 63 of
-// the tile.  Acc[q] = (C Y)[q] + Up_F(Acc_below)[q] with Eq. 8 in its centred
-// reading, Up[q] = sum_{t=0}^{2 N_up} z_{q mod F}[t] x[floor(q/F) + N_up - t].
-// The shared-memory window holds x from floor(Q_tile/F) - N_up on (row w);
-// output column c of the tile reads rows floor(c/F) + 2 N_up - t.  The rows
-// this half needs are copied to registers first and the window is released
-// at once, so that the next tile's window streams in while this one
-// finishes.  Tiles start at multiples of 128 and F divides 64, so every
-// register index is a compile-time constant.
-template <int F, bool TOP, bool STORE_Z>
-__device__ __forceinline__ float4 epi_half(uint32_t tb, bool has_acc, const float* __restrict__ wre,
-                                        const float* __restrict__ wim, int col, int half, uint64_t* wempty,
-                                        float* o_re, float* o_im, long long q0, long long lo, long long hi, int Mpad,
-                                        int m, float* zr, float* zi, bool zvalid) {
-    float best = -1.f, bre = 0.f, bim = 0.f;
-    int bk = 0x7fffffff;
-    constexpr int NUP = 8;
-    constexpr int FF = F ? F : 1;
-    constexpr int NWH = F ? 63 / FF + 2 * NUP + 1 : 1;
-    constexpr int OFF = F ? kUpTaps * (F - 2) : 0;
-    if constexpr (F >= 8 && F <= 32) {
-        // One F-block of outputs per iteration, rolled, with its 2 N_up + 1 window rows read
-        // from shared memory (the constant taps of a block then stay constant-bank operands
-        // instead of being held in registers across unrolled blocks).  The window is
-        // released when the half tile is done.
-#pragma unroll 1
-        for (int blk = 0; blk < 64 / FF; ++blk) {
-            const int c0 = 64 * half + blk * FF;          // tile column of the block's first output
-            const int wrow = c0 / FF;                     // window row of x[floor(c0/F) - N_up]
-            float x_r[2 * NUP + 1], x_i[2 * NUP + 1];
-#pragma unroll
-            for (int w = 0; w <= 2 * NUP; ++w) {
-                x_r[w] = wre[(wrow + w) * 128 + col];
-                x_i[w] = wim[(wrow + w) * 128 + col];
-            }
-#pragma unroll
-            for (int sub = 0; sub < FF / 8; ++sub) {
-                uint32_t rr[16];
-                if (has_acc) {
-                    tmem_ld8x2_async(tb + blk * FF + sub * 8, rr);
-                    tmem_wait16(rr);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) rr[j] = 0u;
-                }
-                float re[8], im[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    re[j] = __uint_as_float(rr[j]);
-                    im[j] = __uint_as_float(rr[8 + j]);
-                    const int ph = sub * 8 + j;
-                    if (ph == 0) {
-                        re[j] += x_r[NUP];
-                        im[j] += x_i[NUP];
-                        continue;
-                    }
-                    float sr = 0.f, si = 0.f;
-#pragma unroll
-                    for (int t = 0; t <= 2 * NUP; ++t) {
-                        if (t * F + ph > 2 * F * NUP) continue;
-                        const float zc = c_upz[OFF + ph * kUpTaps + t];
-                        sr = fmaf(zc, x_r[2 * NUP - t], sr);
-                        si = fmaf(zc, x_i[2 * NUP - t], si);
-                    }
-                    re[j] += sr;
-                    im[j] += si;
-                }
-                const int cb = blk * FF + sub * 8;        // column within the half tile
-                if (TOP) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float pw = re[j] * re[j] + im[j] * im[j];
-                        if (pw > best) { best = pw; bk = 64 * half + cb + j; bre = re[j]; bim = im[j]; }
-                    }
-                    if (STORE_Z && zvalid) {
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) { zr[cb + j] = re[j]; zi[cb + j] = im[j]; }
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const long long q = q0 + cb + j;
-                        if (q >= lo && q <= hi) {
-                            o_re[(q - lo) * Mpad + m] = re[j];
-                            o_im[(q - lo) * Mpad + m] = im[j];
-                        }
-                    }
-                }
-            }
-        }
-        mbar_arrive(wempty);
-        return make_float4(best, __int_as_float(bk), bre, bim);
-    }
-    constexpr int NWR = (F >= 8 && F <= 32) ? 1 : NWH;
-    float xr[NWR], xi[NWR];
-    if (F) {
-        const int r0 = (64 * half) / FF;
-        const float* pr = wre + r0 * 128 + col;
-        const float* pi = wim + r0 * 128 + col;
-#pragma unroll
-        for (int w = 0; w < NWR; ++w) { xr[w] = pr[w * 128]; xi[w] = pi[w * 128]; }
-        mbar_arrive(wempty);
-    }
-    // 8-column chunks, the TMEM load of chunk k + 1 in flight while chunk k is computed
-    uint32_t cur[16], nxt[16];
-    if (has_acc) {
-        tmem_ld8x2_async(tb, cur);
-        tmem_wait16(cur);
-    } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) cur[j] = 0u;
-    }
-#pragma unroll
-    for (int cc = 0; cc < 64; cc += 8) {
-        if (has_acc && cc + 8 < 64) tmem_ld8x2_async(tb + cc + 8, nxt);
-        float re[8], im[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) { re[j] = __uint_as_float(cur[j]); im[j] = __uint_as_float(cur[8 + j]); }
-        if (F) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int cr = cc + j;
-                const int ph = cr % FF;
-                const int b = cr / FF + 2 * NUP;
-                if (ph == 0) {                           // z_0 = g[t F]: 1 at t = N_up, 0 elsewhere
-                    re[j] += xr[b - NUP];
-                    im[j] += xi[b - NUP];
-                    continue;
-                }
-                float sr = 0.f, si = 0.f;
-#pragma unroll
-                for (int t = 0; t <= 2 * NUP; ++t) {
-                    if (t * F + ph > 2 * F * NUP) continue;   // beyond the kernel: identically zero
-                    const float zc = c_upz[OFF + ph * kUpTaps + t];
-                    sr = fmaf(zc, xr[b - t], sr);
-                    si = fmaf(zc, xi[b - t], si);
-                }
-                re[j] += sr;
-                im[j] += si;
-            }
-        }
-        if (TOP) {
-            // chunk argmax as a pairwise tree (the earlier column wins ties), then into the running one
-            float p[8];
-            int k[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) { p[j] = re[j] * re[j] + im[j] * im[j]; k[j] = j; }
-#pragma unroll
-            for (int s = 1; s < 8; s *= 2) {
-#pragma unroll
-                for (int j = 0; j < 8; j += 2 * s) {
-                    const bool later = p[j + s] > p[j];
-                    p[j] = later ? p[j + s] : p[j];
-                    k[j] = later ? k[j + s] : k[j];
-                }
-            }
-            float cre = re[0], cim = im[0];
-#pragma unroll
-            for (int j = 1; j < 8; ++j) {
-                cre = (k[0] == j) ? re[j] : cre;
-                cim = (k[0] == j) ? im[j] : cim;
-            }
-            if (p[0] > best) { best = p[0]; bk = 64 * half + cc + k[0]; bre = cre; bim = cim; }
-            if (STORE_Z && zvalid) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) { zr[cc + j] = re[j]; zi[cc + j] = im[j]; }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const long long q = q0 + cc + j;
-                if (q >= lo && q <= hi) {
-                    o_re[(q - lo) * Mpad + m] = re[j];
-                    o_im[(q - lo) * Mpad + m] = im[j];
-                }
-            }
-        }
-        if (has_acc && cc + 8 < 64) {
-            tmem_wait16(nxt);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) cur[j] = nxt[j];
-        }
-    }
-    return make_float4(best, __int_as_float(bk), bre, bim);
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-// F (the factor to the level below, 0 at the lowest level) is a template
-// parameter so that each instantiation gets the register allocation its
-// epilogue needs (up to 96 registers hold the window at F = 2); 10 warps, three
-// of which share one SM sub-partition's 16K registers, leave 168 per thread.
+// F: the factor to the level below (0 at the lowest level), a template
+// parameter so that the window stages and their MMAs are unrolled.
 template <bool BF16, bool TOP, bool STORE_Z, int F>
-__global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
+__global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
     k_level_tc(const LevelJob* __restrict__ jobs, const LevelMaps* __restrict__ maps,
                const int* __restrict__ tile_base, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
                int det0, int n_det_push, long long window, Partial* __restrict__ part, long long part_tmpl_stride,
                int n_slots, float* __restrict__ zout, int* __restrict__ err) {
-    using C = LevCfg<BF16>;
+    using C = LevCfg<BF16, TOP>;
     constexpr int EPI = 32 * C::EPI_WARPS;
+    constexpr int NWC = win_chunks(F);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* win_re = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES);
-    float* win_im = win_re + C::NWT_MAX * 128;
-    float4* xchg = reinterpret_cast<float4*>(smem + C::STAGES * C::STAGE_BYTES + C::WIN);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES + C::WIN + C::XCHG);
+    uint8_t* stg = smem + C::STAGES * C::STAGE_BYTES;
+    float4* xchg = reinterpret_cast<float4*>(stg + C::STG);
+    uint64_t* full = reinterpret_cast<uint64_t*>(stg + C::STG + C::XCHG);
     uint64_t* empty = full + C::STAGES;
     uint64_t* tfull = empty + C::STAGES;
     uint64_t* tempty = tfull + 2;
     uint64_t* drain = tempty + 2;
-    uint64_t* wfull = drain + 1;
-    uint64_t* wempty = wfull + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wempty + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(tfull + b, 1); mbar_init(tempty + b, EPI); }
         mbar_init(drain, 1);
-        mbar_init(wfull, 1);
-        mbar_init(wempty, EPI);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -573,7 +413,7 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
             int stage = 0;
-            uint32_t phase = 0, wphase = 0;
+            uint32_t phase = 0;
             bool ok = true;
             for (int it = blockIdx.x; it < total && ok; it += gridDim.x) {
                 const int det = det0 + it / tiles_per_det;
@@ -583,8 +423,8 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                 const LevelMaps* mp = maps + jb.map;
                 const int local = t - tile_base[jx];
                 const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
-                const long long Q0 = fdiv(fdiv(k_a - jb.Lambda, jb.D), 128) * 128;
-                const int yrow = det * 2 * jb.y_rows + (int)((Q0 + 128LL * tt) & (jb.y_rows - 1));
+                const long long Qt = fdiv(fdiv(k_a - jb.Lambda, jb.D), 128) * 128 + 128LL * tt;
+                const int yrow = det * 2 * jb.y_rows + (int)(Qt & (jb.y_rows - 1));
                 for (int kc = 0; kc < jb.Kp; kc += kTcK) {
                     if (!mbar_wait(empty + stage, phase ^ 1, err, 31)) { ok = false; break; }
                     uint8_t* sb = smem + stage * C::STAGE_BYTES;
@@ -599,25 +439,32 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                     tma_load_2d(sb + C::NA * C::TILE_A + C::TILE_B, &mp->ylo, full + stage, kc, yrow);
                     if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
                 }
-                // The level below's window for this tile (rows outside the planes read 0).  It is
-                // fetched after the tile's operand stages so that the MMAs of this tile overlap
-                // the epilogue of the previous one, which still holds the (single) window buffer.
-                if (F != 0 && ok) {
-                    if (!mbar_wait(wempty, wphase ^ 1, err, 37)) { ok = false; break; }
-                    const long long lo_in = fdiv(k_a - jb.Lambda_lo, jb.D_lo);
-                    const long long a_t = fdiv(Q0 + 128LL * tt, F != 0 ? F : 1) - 8 - lo_in;
-                    const int base_row = det * 2 * jb.acc_in_rows;
-                    mbar_expect_tx(wfull, 2u * jb.nwt * 128 * 4);
-                    tma_load_2d(win_re, &mp->accin, wfull, tm * 128, (int)(base_row + a_t));
-                    tma_load_2d(win_im, &mp->accin, wfull, tm * 128, (int)(base_row + jb.acc_in_rows + a_t));
-                    wphase ^= 1;
+                if (F != 0) {
+                    // window of the level below: its planes start at sample X0 = floor8(lo_below) - 128;
+                    // the first row read is floor(Qt/F) - N_up - r (a multiple of 8 past X0)
+                    const long long X0 = fdiv(fdiv(k_a - jb.Lambda_lo, jb.D_lo), 8) * 8 - 128;
+                    const long long qf = fdiv(Qt, F != 0 ? F : 1);
+                    const int r = (int)(qf & 7);
+                    const int a = (int)(qf - 8 - r - X0);
+                    const int prow = det * 4 * jb.Mpad + tm * 128;
+#pragma unroll 1
+                    for (int ch = 0; ch < NWC && ok; ++ch) {
+                        if (!mbar_wait(empty + stage, phase ^ 1, err, 32)) { ok = false; break; }
+                        uint8_t* sb = smem + stage * C::STAGE_BYTES;
+                        mbar_expect_tx(full + stage, C::WSTAGE);
+#pragma unroll
+                        for (int pl = 0; pl < 4; ++pl)
+                            tma_load_2d(sb + pl * C::WTILE, &mp->accw, full + stage, a + kWinK * ch, prow + pl * jb.Mpad);
+                        tma_load_2d(sb + 4 * C::WTILE, &mp->uhi, full + stage, kWinK * ch, r * 128);
+                        tma_load_2d(sb + 5 * C::WTILE, &mp->ulo, full + stage, kWinK * ch, r * 128);
+                        if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                    }
                 }
             }
             for (int s = 0; s < C::STAGES; ++s) {
-                if (!mbar_wait(empty + stage, phase ^ 1, err, 32)) break;
+                if (!mbar_wait(empty + stage, phase ^ 1, err, 38)) break;
                 if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
             }
-            mbar_wait(wempty, wphase ^ 1, err, 38);    // the last window was consumed
         }
     } else if (warp == 1) {
         if (lane == 0) {   // ------------------------------------------------ MMA issuer
@@ -656,8 +503,29 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                     umma_commit(empty + stage);
                     if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
                 }
+#pragma unroll 1
+                for (int ch = 0; ch < NWC && ok; ++ch) {
+                    if (!mbar_wait(full + stage, phase, err, 30)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sb = smem_u32(smem + stage * C::STAGE_BYTES);
+                    const uint32_t w_rh = sb, w_rl = sb + C::WTILE, w_ih = sb + 2 * C::WTILE, w_il = sb + 3 * C::WTILE;
+                    const uint32_t u_h = sb + 4 * C::WTILE, u_l = sb + 5 * C::WTILE;
+#pragma unroll
+                    for (int k = 0; k < kWinK / 16; ++k) {
+                        const uint32_t off = k * 32;
+                        const uint32_t acc0 = (Kp > 0 || ch > 0 || k > 0) ? 1u : 0u;
+                        umma_f16(d_re, desc_sw64(w_rh + off), desc_sw64(u_h + off), idesc, acc0);
+                        umma_f16(d_re, desc_sw64(w_rl + off), desc_sw64(u_h + off), idesc, 1u);
+                        umma_f16(d_re, desc_sw64(w_rh + off), desc_sw64(u_l + off), idesc, 1u);
+                        umma_f16(d_im, desc_sw64(w_ih + off), desc_sw64(u_h + off), idesc, acc0);
+                        umma_f16(d_im, desc_sw64(w_il + off), desc_sw64(u_h + off), idesc, 1u);
+                        umma_f16(d_im, desc_sw64(w_ih + off), desc_sw64(u_l + off), idesc, 1u);
+                    }
+                    umma_commit(empty + stage);
+                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                }
                 if (!ok) break;
-                umma_commit(tfull + buf);     // with Kp == 0 this only signals the epilogue
+                umma_commit(tfull + buf);
             }
             umma_commit(drain);
             mbar_wait(drain, 0, err, 35);
@@ -669,7 +537,6 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
         const int qd = warp & 3;
         const int half = (warp - 2) >> 2;
         const int rowm = qd * 32 + lane;
-        uint32_t wph = 0;
         int i = 0;
         for (int it = blockIdx.x; it < total; it += gridDim.x, ++i) {
             const int det = det0 + it / tiles_per_det;
@@ -683,37 +550,83 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
             if (!__all_sync(0xffffffffu, got)) break;
             tc_fence_after();
             const long long lo = fdiv(k_a - jb.Lambda, jb.D);
-            const long long hi = fdiv(k_b - 1 + jb.Lambda, jb.D);
             const long long Q0 = fdiv(lo, 128) * 128;
             const int m = tm * kTcTileM + rowm;
             const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + buf * 256;
+            const bool has_acc = jb.Kp > 0 || F != 0;
             float best = -1.f, bre = 0.f, bim = 0.f;
             int bk = 0x7fffffff;
-            if (F != 0) {
-                const bool wgot = mbar_wait(wfull, wph, err, 39);
-                if (!__all_sync(0xffffffffu, wgot)) break;
-                wph ^= 1;
+            if (TOP) {
+#pragma unroll 1
+                for (int c = half * 64; c < half * 64 + 64; c += 16) {
+                    float re[16], im[16];
+                    if (has_acc) {
+                        tmem_ld16(base + c, re);
+                        tmem_ld16(base + 128 + c, im);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) { re[j] = 0.f; im[j] = 0.f; }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float p = re[j] * re[j] + im[j] * im[j];
+                        if (p > best) { best = p; bk = c + j; bre = re[j]; bim = im[j]; }
+                    }
+                    if (STORE_Z && m < jb.M) {
+                        const int n = (int)(k_b - k_a);
+                        float* zr = zout + (long long)(2 * m) * n + tt * kTcTileN + c;
+                        float* zi = zr + n;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) { zr[j] = re[j]; zi[j] = im[j]; }
+                    }
+                }
+            } else {
+                // Acc of this warp's 32 templates x 64 samples as four hi/lo planes: each plane
+                // through a 128-byte-swizzled staging buffer and one TMA store (box 64 x 32).
+                // Plane columns start at X0 = floor8(lo) - 128, so no store starts left of 0.
+                const LevelMaps* mp = maps + jb.map;
+                const long long X0 = fdiv(lo, 8) * 8 - 128;
+                const int x = (int)(Q0 + 128LL * tt + 64 * half - X0);
+                const int y0 = det * 4 * jb.Mpad + tm * 128 + qd * 32;
+                uint8_t* wbuf = stg + (warp - 2) * 2 * C::STG_BUF;
+#pragma unroll 1
+                for (int part = 0; part < 2; ++part) {          // re, im
+                    float v0[32], v1[32];
+                    if (has_acc) {
+                        tmem_ld32(base + part * 128 + 64 * half, v0);
+                        tmem_ld32(base + part * 128 + 64 * half + 32, v1);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) { v0[j] = 0.f; v1[j] = 0.f; }
+                    }
+                    uint32_t hp[32], lp[32];
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const float a0 = k < 16 ? v0[2 * k] : v1[2 * k - 32];
+                        const float a1 = k < 16 ? v0[2 * k + 1] : v1[2 * k - 31];
+                        uint16_t h0, l0, h1, l1;
+                        split_hilo<BF16>(a0, h0, l0);
+                        split_hilo<BF16>(a1, h1, l1);
+                        hp[k] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                        lp[k] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+                    }
+#pragma unroll
+                    for (int sub = 0; sub < 2; ++sub) {          // hi, lo
+                        uint8_t* b = wbuf + sub * C::STG_BUF;
+                        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                        __syncwarp();
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const uint32_t* src = sub ? lp : hp;
+                            *reinterpret_cast<uint4*>(b + lane * 128 + ((k ^ (lane & 7)) << 4)) =
+                                make_uint4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
+                        }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) tma_store_2d(&mp->accst, b, x, y0 + (2 * part + sub) * jb.Mpad);
+                    }
+                }
             }
-            float *o_re = nullptr, *o_im = nullptr, *zr = nullptr, *zi = nullptr;
-            bool zvalid = false;
-            if (!TOP) {
-                o_re = jb.acc_out + det * jb.acc_out_det_stride;
-                o_im = o_re + (long long)jb.acc_out_rows * jb.Mpad;
-            } else if (STORE_Z && m < jb.M) {
-                const int n = (int)(k_b - k_a);
-                zr = zout + (long long)(2 * m) * n + tt * kTcTileN + 64 * half;
-                zi = zr + n;
-                zvalid = true;
-            }
-            const long long q0 = Q0 + 128LL * tt + 64 * half;
-            const uint32_t tb = base + 64 * half;
-            const bool has_acc = jb.Kp > 0;
-            const float4 r = epi_half<F, TOP, STORE_Z>(tb, has_acc, win_re, win_im, rowm, half, wempty, o_re, o_im,
-                                                       q0, lo, hi, jb.Mpad, m, zr, zi, zvalid);
-            best = r.x;
-            bk = __float_as_int(r.y);
-            bre = r.z;
-            bim = r.w;
             tc_fence_before();
             mbar_arrive(tempty + buf);
             if (TOP && !STORE_Z) {
@@ -732,6 +645,7 @@ __global__ void __launch_bounds__(LevCfg<BF16>::THREADS, 1)
                 }
             }
         }
+        if (!TOP && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();

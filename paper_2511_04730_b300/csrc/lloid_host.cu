@@ -67,8 +67,8 @@ struct LevelRT {
     void *d_cre = nullptr, *d_cim = nullptr, *d_cre_lo = nullptr, *d_cim_lo = nullptr;  // [Mpad][Kp]
     uint16_t *d_yhi = nullptr, *d_ylo = nullptr;   // operand ring [n_det][2R][Kp]
     int R = 0;
-    float* d_acc = nullptr;            // transposed [n_det][2][acc_rows][Mpad] (below the top)
-    int acc_rows = 0;
+    uint16_t* d_accp = nullptr;        // below the top: hi/lo planes [n_det][4][Mpad][acc_cols]
+    int acc_cols = 0;
 };
 struct FirSliceRT {
     int level = 0, col = 0, Np = 0, Kp = 0, Mtiles = 0;
@@ -160,6 +160,8 @@ struct lloid_ctx {
     int max_depth = 0;
     std::vector<int> top_job_of_bank;  // bank id -> index in its top-level table
     std::vector<int> top_slot_of_bank; // bank id -> F slot of its top level (split path)
+    uint16_t* d_u_hi[kFSlots] = {};    // Eq. 8 tile matrices per F slot (hi, lo halves)
+    uint16_t* d_u_lo[kFSlots] = {};
     // split path streams: index 0 = f0, index r + 1 = rate_D[r]; hi/lo halves, double-mapped
     uint16_t* s_hi[kMaxRates + 1] = {};
     uint16_t* s_lo[kMaxRates + 1] = {};
@@ -277,17 +279,31 @@ bool encode_map(CUtensorMap* m, bool bf16, const void* base, long long cols, lon
     return r == CUDA_SUCCESS;
 }
 
-// 2-D FP32 map without swizzle: rows of `cols` floats, box box_cols x box_rows.
-bool encode_map_f32(CUtensorMap* m, const void* base, long long cols, long long rows, int box_cols, int box_rows) {
+// 2-D 16-bit map with 64-byte swizzle: rows of `cols` values, box 32 x 128.
+bool encode_map_sw64(CUtensorMap* m, bool bf16, const void* base, long long cols, long long rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
-    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kWinK, 128};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// 2-D 16-bit map for the epilogue's TMA stores: box 64 x 32, 128-byte swizzle.
+bool encode_map_store(CUtensorMap* m, bool bf16, const void* base, long long cols, long long rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, 32};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -406,25 +422,26 @@ struct StageTimer {
 // Job tables of the split (tensor-core) path for pushes of n samples.
 // Opt every k_level_tc instantiation of one precision into its shared memory.
 template <bool BF16, bool TOP, bool SZ, int F>
-cudaError_t level_attr1(int smem) {
-    return cudaFuncSetAttribute(k_level_tc<BF16, TOP, SZ, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t level_attr1() {
+    return cudaFuncSetAttribute(k_level_tc<BF16, TOP, SZ, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                LevCfg<BF16, TOP>::SMEM);
 }
 template <bool BF16, bool TOP, bool SZ>
-cudaError_t level_attr_f(int smem) {
+cudaError_t level_attr_f() {
     cudaError_t e = cudaSuccess;
-    const cudaError_t r[] = {level_attr1<BF16, TOP, SZ, 0>(smem), level_attr1<BF16, TOP, SZ, 2>(smem),
-                             level_attr1<BF16, TOP, SZ, 4>(smem), level_attr1<BF16, TOP, SZ, 8>(smem),
-                             level_attr1<BF16, TOP, SZ, 16>(smem), level_attr1<BF16, TOP, SZ, 32>(smem),
-                             level_attr1<BF16, TOP, SZ, 64>(smem)};
+    const cudaError_t r[] = {level_attr1<BF16, TOP, SZ, 0>(), level_attr1<BF16, TOP, SZ, 2>(),
+                             level_attr1<BF16, TOP, SZ, 4>(), level_attr1<BF16, TOP, SZ, 8>(),
+                             level_attr1<BF16, TOP, SZ, 16>(), level_attr1<BF16, TOP, SZ, 32>(),
+                             level_attr1<BF16, TOP, SZ, 64>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
 }
 template <bool BF16>
-cudaError_t level_smem_attr(int smem) {
-    cudaError_t e = level_attr_f<BF16, false, false>(smem);
-    if (e == cudaSuccess) e = level_attr_f<BF16, true, false>(smem);
-    if (e == cudaSuccess) e = level_attr_f<BF16, true, true>(smem);
+cudaError_t level_smem_attr() {
+    cudaError_t e = level_attr_f<BF16, false, false>();
+    if (e == cudaSuccess) e = level_attr_f<BF16, true, false>();
+    if (e == cudaSuccess) e = level_attr_f<BF16, true, true>();
     return e;
 }
 
@@ -478,11 +495,11 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             LevelJob q{};
             if (j > 0) {
                 const LevelRT& P = b->lev[j - 1];
-                q.acc_in = P.d_acc; q.acc_in_det_stride = 2LL * P.acc_rows * b->Mpad; q.acc_in_rows = P.acc_rows;
                 q.F = P.D / L.D; q.D_lo = P.D; q.Lambda_lo = P.Lambda;
-                q.upz = nullptr;   // the kernels read the constant tables
             }
-            if (j < nl - 1) { q.acc_out = L.d_acc; q.acc_out_det_stride = 2LL * L.acc_rows * b->Mpad; q.acc_out_rows = L.acc_rows; }
+            if (j < nl - 1) {
+                q.acc_out = L.d_accp; q.acc_out_det_stride = 4LL * b->Mpad * L.acc_cols; q.acc_cols = L.acc_cols;
+            }
             q.Kp = L.Kp; q.M = b->M; q.Mpad = b->Mpad; q.tmpl0 = b->tmpl0;
             q.tiles_m = b->Mpad / kTcTileM;
             if (depth == 0) q.tiles_t = (int)(n / kTcTileN);
@@ -501,10 +518,10 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             std::memset(&mp, 0, sizeof mp);
             if (j > 0) {
                 const LevelRT& P = b->lev[j - 1];
-                q.nwt = 127 / q.F + 2 * c.n_up + 1;
-                if (q.nwt > LevCfg<false>::NWT_MAX)
-                    return fail(ctx, LLOID_EINVAL, "upsampling window of %d rows exceeds %d", q.nwt, LevCfg<false>::NWT_MAX);
-                if (!encode_map_f32(&mp.accin, P.d_acc, b->Mpad, (long long)nd * 2 * P.acc_rows, 128, q.nwt))
+                const int kw = win_chunks(q.F) * kWinK;
+                if (!encode_map_sw64(&mp.accw, bf, P.d_accp, P.acc_cols, (long long)nd * 4 * b->Mpad) ||
+                    !encode_map_sw64(&mp.uhi, bf, ctx->d_u_hi[fslot], kw, 8 * 128) ||
+                    !encode_map_sw64(&mp.ulo, bf, ctx->d_u_lo[fslot], kw, 8 * 128))
                     return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (window, bank %d)", b->id);
             }
             if (L.Kp > 0) {
@@ -517,6 +534,8 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                          encode_map(&mp.cim_lo, bf, L.d_cim_lo, L.Kp, b->Mpad, kTcTileM);
                 if (!ok) return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (level, bank %d)", b->id);
             }
+            if (j < nl - 1 && !encode_map_store(&mp.accst, bf, L.d_accp, L.acc_cols, (long long)nd * 4 * b->Mpad))
+                return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (planes, bank %d)", b->id);
             if (depth == 0) { ctx->top_job_of_bank[b->id] = (int)lj[tab].size(); ctx->top_slot_of_bank[b->id] = fslot; }
             lj[tab].push_back(q); lm[tab].push_back(mp); lb[tab].push_back(lt[tab]);
             lt[tab] += q.tiles_m * q.tiles_t;
@@ -544,9 +563,8 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     if (fsmem > 227 * 1024) return fail(ctx, LLOID_EINVAL, "FIR shared memory %d exceeds the limit", fsmem);
     if (bf) CK(cudaFuncSetAttribute(k_fir_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
     else CK(cudaFuncSetAttribute(k_fir_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
-    const int lsmem = bf ? LevCfg<true>::SMEM : LevCfg<false>::SMEM;
-    if (bf) CK(level_smem_attr<true>(lsmem));
-    else CK(level_smem_attr<false>(lsmem));
+    if (bf) CK(level_smem_attr<true>());
+    else CK(level_smem_attr<false>());
     return LLOID_OK;
 }
 
@@ -648,7 +666,7 @@ template <bool BF16, bool TOP, bool SZ, int F>
 void launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps, const int* base,
                 int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W, Partial* part,
                 long long part_stride, int n_slots, float* zout, int* err) {
-    k_level_tc<BF16, TOP, SZ, F><<<g, LevCfg<BF16>::THREADS, smem, st>>>(jobs, maps, base, n_jobs, tiles, k_a, k_b,
+    k_level_tc<BF16, TOP, SZ, F><<<g, LevCfg<BF16, TOP>::THREADS, LevCfg<BF16, TOP>::SMEM, st>>>(jobs, maps, base, n_jobs, tiles, k_a, k_b,
                                                                       det0, nd, W, part, part_stride, n_slots, zout,
                                                                       err);
 }
@@ -680,7 +698,7 @@ lloid_status launch_level(lloid_ctx* ctx, int depth, int fslot, long long k_a, l
     const long long part_stride = (long long)ctx->cfg.n_detectors * ctx->n_slots;
     const int total = tiles * n_det_push;
     dim3 g(std::min(total, ctx->n_sm));
-    const int smem = bf ? LevCfg<true>::SMEM : LevCfg<false>::SMEM;
+    const int smem = 0;   // each instantiation launches with its own LevCfg<BF16, TOP>::SMEM
     Partial* part = store_z ? nullptr : ctx->d_part;
     const int F = fslot ? 1 << fslot : 0;
 #define LAUNCH_LV(BFV, TOPV, SZ)                                                                                     \
@@ -889,10 +907,10 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
         L.Kp = (L.K + 63) / 64 * 64;
         const long long cnt = (c.max_block - 1 + 2LL * L.Lambda) / L.D + 2;
         L.R = (int)next_pow2(cnt + 128 + 64);
-        if (j < nl - 1) L.acc_rows = (int)cnt + 2;
+        if (j < nl - 1) L.acc_cols = 128 * (int)((cnt + 127 + 127) / 128 + 2);   // every column a tile writes
         need += (size_t)b->Mpad * L.Kp * es * (bf ? 4 : 2);
         need += (size_t)nd * 2 * L.R * L.Kp * es * 2;
-        need += (size_t)nd * 2 * L.acc_rows * b->Mpad * 4;
+        need += (size_t)nd * 4 * b->Mpad * L.acc_cols * 2;
     }
     for (auto& f : fs) need += (size_t)f.Mtiles * 128 * f.Kp * es * (bf ? 2 : 1);
     *need_out = need;
@@ -950,8 +968,8 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
             if ((st = dalloc(ctx, &L.d_ylo, rb, &b->allocs, &b->bytes))) return st;
             CK(cudaStreamSynchronize(ctx->stream));
         }
-        if (L.acc_rows > 0) {
-            if ((st = dalloc(ctx, &L.d_acc, (size_t)nd * 2 * L.acc_rows * b->Mpad * 4, &b->allocs, &b->bytes)))
+        if (L.acc_cols > 0) {   // zeroed: columns no tile has written read as 0
+            if ((st = dalloc(ctx, &L.d_accp, (size_t)nd * 4 * b->Mpad * L.acc_cols * 2, &b->allocs, &b->bytes)))
                 return st;
         }
     }
@@ -1131,21 +1149,34 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
             if ((st = dalloc(ctx, &ctx->s_hi[r], bytes, nullptr, &ctx->state_bytes))) return st;
             if ((st = dalloc(ctx, &ctx->s_lo[r], bytes, nullptr, &ctx->state_bytes))) return st;
         }
-        // Eq. 7 sub-kernels z_phi[t] = g[t F + phi], t = 0..2 N_up, g of Eq. 4 with c = F N_up
-        // (the sinc's zeros at multiples of F written as exact zeros)
-        std::vector<float> z(kUpTable, 0.f);
-        for (int F = 2; F <= 64; F *= 2) {
+        // Eq. 8 tile matrices: for a 128-sample tile starting at Q (F | Q) and window row w
+        // holding sample floor(Q/F) - N_up - r + w of the level below,
+        //   U_F[r][q][w] = z_{q mod F}[t],  t = floor(q/F) + 2 N_up + r - w in [0, 2 N_up],
+        // with the sub-kernels z_phi[t] = g[t F + phi] of Eq. 7 (g of Eq. 4, c = F N_up, the
+        // sinc's zeros at multiples of F written as exact zeros).  Stored as 16-bit hi + lo.
+        for (int fs = 1; fs < lloid_ctx::kFSlots; ++fs) {
+            const int F = 1 << fs;
             const int cF = F * c.n_up;
+            const int kw = win_chunks(F) * kWinK;
             std::vector<double> g = sinc_windowed(F, cF);
-            for (int ph = 0; ph < F; ++ph)
-                for (int t = 0; t < kUpTaps; ++t) {
-                    const long long k = (long long)t * F + ph;
-                    double v = (k <= 2LL * cF) ? g[k] : 0.0;
-                    if ((k - cF) % F == 0 && k != cF) v = 0.0;
-                    z[(size_t)kUpTaps * (F - 2) + (size_t)ph * kUpTaps + t] = (float)v;
-                }
+            std::vector<double> u((size_t)8 * 128 * kw, 0.0);
+            for (int r = 0; r < 8; ++r)
+                for (int q = 0; q < 128; ++q)
+                    for (int w = 0; w < kw; ++w) {
+                        const int t = q / F + 2 * c.n_up + r - w;
+                        if (t < 0 || t > 2 * c.n_up) continue;
+                        const long long k = (long long)t * F + q % F;
+                        if (k > 2LL * cF || ((k - cF) % F == 0 && k != cF)) continue;
+                        u[((size_t)r * 128 + q) * kw + w] = g[k];
+                    }
+            std::vector<uint16_t> uh(u.size()), ul(u.size());
+            split_hilo_host(c.precision == LLOID_BF16_SPLIT, u, &uh, &ul);
+            if ((st = dalloc(ctx, &ctx->d_u_hi[fs], uh.size() * 2, nullptr, &ctx->state_bytes)) ||
+                (st = dalloc(ctx, &ctx->d_u_lo[fs], ul.size() * 2, nullptr, &ctx->state_bytes)))
+                return st;
+            CK(cudaMemcpy(ctx->d_u_hi[fs], uh.data(), uh.size() * 2, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(ctx->d_u_lo[fs], ul.data(), ul.size() * 2, cudaMemcpyHostToDevice));
         }
-        CK(cudaMemcpyToSymbol(c_upz, z.data(), z.size() * sizeof(float)));
     }
     ctx->pos.assign(nd, 0);
     ctx->fin.assign(nd, -1);
@@ -1186,6 +1217,7 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
     cudaFree(ctx->d_err);
     for (int r = 0; r <= kMaxRates; ++r) { cudaFree(ctx->s_hi[r]); cudaFree(ctx->s_lo[r]); }
+    for (int f = 0; f < lloid_ctx::kFSlots; ++f) { cudaFree(ctx->d_u_hi[f]); cudaFree(ctx->d_u_lo[f]); }
 
     if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
     for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
