@@ -70,7 +70,7 @@ struct FirMaps { CUtensorMap a, a_lo; };
 // samples), box 32 samples x 128 templates, 64-byte swizzle; uhi/ulo: the
 // Eq. 8 tile matrices U_F of this level's factor, rows [shift][128 outputs],
 // columns = window rows, same box and swizzle; accst: this level's own planes
-// for the epilogue's TMA stores, box 64 samples x 32 templates, 128-byte swizzle.
+// for the epilogue's TMA stores, box 32 samples x 32 templates, 64-byte swizzle.
 struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo, accw, uhi, ulo, accst; };
 
 // Window of the level below read by one 128-sample tile (N_up = 8): rows
@@ -346,8 +346,7 @@ __global__ void __launch_bounds__(192, 1)
 template <bool BF16, bool TOP>
 struct LevCfg {
     static constexpr int NA = BF16 ? 4 : 2;
-    // below the top, 64 KB of shared memory stage the Acc planes for the TMA stores
-    static constexpr int STAGES = TOP ? (BF16 ? 2 : 3) : (BF16 ? 1 : 2);
+    static constexpr int STAGES = BF16 ? 2 : 3;
     static constexpr int TILE_A = kTcTileM * kTcK * 2;
     static constexpr int TILE_B = kTcTileN * kTcK * 2;
     static constexpr int STAGE_BYTES = NA * TILE_A + 2 * TILE_B;
@@ -355,9 +354,9 @@ struct LevCfg {
     static constexpr int WSTAGE = 6 * WTILE;           // re hi, re lo, im hi, im lo, U hi, U lo
     static_assert(WSTAGE <= STAGE_BYTES, "a window stage fits a stage slot");
     static constexpr int EPI_WARPS = 8;                 // two per TMEM lane quarter, 64 columns each
-    static constexpr int STG_BUF = 32 * 128;           // 32 templates x 64 samples x 2 B, 128-byte swizzle
-    static constexpr int STG = TOP ? 0 : EPI_WARPS * 2 * STG_BUF;
-    static constexpr int XCHG = 2 * 128 * 16;          // tile-argmax exchange between the column halves
+    static constexpr int STG_BUF = 32 * 64;            // 32 templates x 32 samples x 2 B, 64-byte swizzle
+    static constexpr int STG = TOP ? 0 : EPI_WARPS * 2 * STG_BUF;   // below the top: staging for the TMA stores
+    static constexpr int XCHG = TOP ? 2 * 128 * 16 : 0;   // top: tile-argmax exchange between the column halves
     static constexpr int SMEM = STAGES * STAGE_BYTES + STG + XCHG + 1024 + 256;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
 };
@@ -581,49 +580,49 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                     }
                 }
             } else {
-                // Acc of this warp's 32 templates x 64 samples as four hi/lo planes: each plane
-                // through a 128-byte-swizzled staging buffer and one TMA store (box 64 x 32).
-                // Plane columns start at X0 = floor8(lo) - 128, so no store starts left of 0.
+                // Acc of this warp's 32 templates x 64 samples as four hi/lo planes, 32 samples at a
+                // time: each half through a 64-byte-swizzled staging buffer and one TMA store (box
+                // 32 x 32).  Plane columns start at X0 = floor8(lo) - 128, so no store starts left of 0.
                 const LevelMaps* mp = maps + jb.map;
                 const long long X0 = fdiv(lo, 8) * 8 - 128;
-                const int x = (int)(Q0 + 128LL * tt + 64 * half - X0);
+                const int x0 = (int)(Q0 + 128LL * tt + 64 * half - X0);
                 const int y0 = det * 4 * jb.Mpad + tm * 128 + qd * 32;
                 uint8_t* wbuf = stg + (warp - 2) * 2 * C::STG_BUF;
 #pragma unroll 1
                 for (int part = 0; part < 2; ++part) {          // re, im
-                    float v0[32], v1[32];
-                    if (has_acc) {
-                        tmem_ld32(base + part * 128 + 64 * half, v0);
-                        tmem_ld32(base + part * 128 + 64 * half + 32, v1);
-                    } else {
+#pragma unroll 1
+                    for (int g = 0; g < 2; ++g) {               // samples 32 g .. 32 g + 31 of the half
+                        float v[32];
+                        if (has_acc) {
+                            tmem_ld32(base + part * 128 + 64 * half + 32 * g, v);
+                        } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) { v0[j] = 0.f; v1[j] = 0.f; }
-                    }
-                    uint32_t hp[32], lp[32];
+                            for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                        }
+                        uint32_t hp[16], lp[16];
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const float a0 = k < 16 ? v0[2 * k] : v1[2 * k - 32];
-                        const float a1 = k < 16 ? v0[2 * k + 1] : v1[2 * k - 31];
-                        uint16_t h0, l0, h1, l1;
-                        split_hilo<BF16>(a0, h0, l0);
-                        split_hilo<BF16>(a1, h1, l1);
-                        hp[k] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                        lp[k] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-                    }
-#pragma unroll
-                    for (int sub = 0; sub < 2; ++sub) {          // hi, lo
-                        uint8_t* b = wbuf + sub * C::STG_BUF;
-                        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                        for (int k = 0; k < 16; ++k) {
+                            uint16_t h0, l0, h1, l1;
+                            split_hilo<BF16>(v[2 * k], h0, l0);
+                            split_hilo<BF16>(v[2 * k + 1], h1, l1);
+                            hp[k] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                            lp[k] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+                        }
+                        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                         __syncwarp();
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const uint32_t* src = sub ? lp : hp;
-                            *reinterpret_cast<uint4*>(b + lane * 128 + ((k ^ (lane & 7)) << 4)) =
-                                make_uint4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
+                        for (int k = 0; k < 4; ++k) {
+                            const int off = lane * 64 + ((k ^ ((lane >> 1) & 3)) << 4);
+                            *reinterpret_cast<uint4*>(wbuf + off) = make_uint4(hp[4 * k], hp[4 * k + 1], hp[4 * k + 2], hp[4 * k + 3]);
+                            *reinterpret_cast<uint4*>(wbuf + C::STG_BUF + off) =
+                                make_uint4(lp[4 * k], lp[4 * k + 1], lp[4 * k + 2], lp[4 * k + 3]);
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         __syncwarp();
-                        if (lane == 0) tma_store_2d(&mp->accst, b, x, y0 + (2 * part + sub) * jb.Mpad);
+                        if (lane == 0) {
+                            tma_store_2d(&mp->accst, wbuf, x0 + 32 * g, y0 + (2 * part) * jb.Mpad);
+                            tma_store_2d(&mp->accst, wbuf + C::STG_BUF, x0 + 32 * g, y0 + (2 * part + 1) * jb.Mpad);
+                        }
                     }
                 }
             }

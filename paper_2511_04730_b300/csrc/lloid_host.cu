@@ -140,6 +140,10 @@ struct lloid_ctx {
     long long trig_cap = 0;
     long long* d_total = nullptr;
     long long* h_total = nullptr;
+    int* h_err = nullptr;                  // pinned copy of d_err taken by a pull
+    TriggerOut* h_trig = nullptr;          // pinned first part of a pulled list
+    long long h_trig_cap = 0, last_pull = 0;
+    cudaEvent_t pull_ev = nullptr;
 
     // job tables for the current push length
     bool jobs_dirty = true;
@@ -293,17 +297,17 @@ bool encode_map_sw64(CUtensorMap* m, bool bf16, const void* base, long long cols
     return r == CUDA_SUCCESS;
 }
 
-// 2-D 16-bit map for the epilogue's TMA stores: box 64 x 32, 128-byte swizzle.
+// 2-D 16-bit map for the epilogue's TMA stores: box 32 x 32, 64-byte swizzle.
 bool encode_map_store(CUtensorMap* m, bool bf16, const void* base, long long cols, long long rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {64, 32};
+    cuuint32_t box[2] = {32, 32};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                     const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -855,19 +859,22 @@ lloid_status push_common(lloid_ctx* ctx, int det0, int nd, long long t0, const f
     return LLOID_OK;
 }
 
-lloid_status wait_done(lloid_ctx* ctx, int timeout_ms) {
+// Wait for an event: polled without sleeping for the first 2 ms (a pull usually
+// waits well under that), then every 50 us; timeout_ms < 0 waits without limit.
+lloid_status wait_event(lloid_ctx* ctx, cudaEvent_t ev, int timeout_ms) {
     auto t_start = std::chrono::steady_clock::now();
     for (;;) {
-        cudaError_t e = cudaEventQuery(ctx->done_ev);
+        cudaError_t e = cudaEventQuery(ev);
         if (e == cudaSuccess) return LLOID_OK;
         if (e != cudaErrorNotReady) return fail(ctx, LLOID_ECUDA, "device error: %s", cudaGetErrorString(e));
-        if (timeout_ms >= 0) {
-            auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t_start);
-            if (el.count() >= timeout_ms) return fail(ctx, LLOID_ETIMEOUT, "GPU work not done after %d ms", timeout_ms);
-        }
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
+        auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t_start);
+        if (timeout_ms >= 0 && el.count() >= 1000LL * timeout_ms)
+            return fail(ctx, LLOID_ETIMEOUT, "GPU work not done after %d ms", timeout_ms);
+        if (el.count() < 2000) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
 }
+lloid_status wait_done(lloid_ctx* ctx, int timeout_ms) { return wait_event(ctx, ctx->done_ev, timeout_ms); }
 
 // Split path: ladder levels, 8-phase expanded bases for the tensor-core FIR,
 // per-level coefficient blocks, operand rings and Acc planes.  Uploads
@@ -1192,6 +1199,8 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
     ctx->tiles_per_window = (int)(c.window_samples / kTileT);
     ctx->n_slots = (int)next_pow2(((c.max_block + c.window_samples - 1) / c.window_samples + 2) * ctx->tiles_per_window);
     CK(cudaHostAlloc((void**)&ctx->h_total, sizeof(long long), cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&ctx->h_err, sizeof(int), cudaHostAllocDefault));
+    CK(cudaEventCreateWithFlags(&ctx->pull_ev, cudaEventDisableTiming));
     if ((st = dalloc(ctx, &ctx->d_err, sizeof(int), nullptr, &ctx->state_bytes))) return st;
     if ((st = dalloc(ctx, &ctx->d_total, sizeof(long long), nullptr, &ctx->state_bytes))) return st;
     if ((st = ensure_template_capacity(ctx, 1024))) return st;
@@ -1215,6 +1224,8 @@ void lloid_destroy(lloid_ctx* ctx) {
     for (int i = 0; i < 2; ++i) { cudaFreeHost(ctx->h_stage[i]); if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]); }
     cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_tmpl0_of);
     cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
+    cudaFreeHost(ctx->h_err); cudaFreeHost(ctx->h_trig);
+    if (ctx->pull_ev) cudaEventDestroy(ctx->pull_ev);
     cudaFree(ctx->d_err);
     for (int r = 0; r <= kMaxRates; ++r) { cudaFree(ctx->s_hi[r]); cudaFree(ctx->s_lo[r]); }
     for (int f = 0; f < lloid_ctx::kFSlots; ++f) { cudaFree(ctx->d_u_hi[f]); cudaFree(ctx->d_u_lo[f]); }
@@ -1422,40 +1433,68 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
     for (long long f : ctx->fin) { fin_min = std::min(fin_min, f); fin_max = std::max(fin_max, f); }
     if (w1 > fin_min) return fail(ctx, LLOID_ENOTREADY, "window %lld needs data through sample %lld", w1, (w1 + 1) * W);
     if (w0 + kWindowRing <= fin_max) return fail(ctx, LLOID_EEXPIRED, "window %lld is no longer retained", (long long)w0);
-    lloid_status st = wait_done(ctx, timeout_ms);
-    if (st) return st;
-    if ((st = check_kernel_err(ctx))) return st;
     const int nd = ctx->cfg.n_detectors;
     const int M_used = ctx->M_used;
-    if (M_used == 0) return LLOID_OK;
+    lloid_status st;
+    if (M_used == 0) {
+        if ((st = wait_done(ctx, timeout_ms))) return st;
+        return check_kernel_err(ctx);
+    }
     const long long total = n_windows * nd * M_used;
     const int chunks = (int)((total + 1023) / 1024);
     if (chunks > ctx->counts_cap) {
+        CK(cudaStreamSynchronize(ctx->stream));
         cudaFree(ctx->d_counts);
         CK(cudaMalloc(&ctx->d_counts, chunks * sizeof(int)));
         ctx->counts_cap = chunks;
     }
     if (total > ctx->trig_cap) {
+        CK(cudaStreamSynchronize(ctx->stream));
         cudaFree(ctx->d_trig);
         CK(cudaMalloc(&ctx->d_trig, total * sizeof(TriggerOut)));
         ctx->trig_cap = total;
     }
-    StageTimer tmg(ctx, 6);
-    k_gather_count<<<chunks, 1024, 0, ctx->stream>>>(ctx->d_slab, ctx->M_cap, M_used, nd, w0, (int)n_windows,
-                                                     kWindowRing, ctx->d_counts);
-    CKL();
-    k_gather_scatter<<<chunks, 1024, 0, ctx->stream>>>(ctx->d_slab, ctx->M_cap, M_used, nd, w0, (int)n_windows,
-                                                       kWindowRing, ctx->d_counts, chunks, ctx->d_bank_of,
-                                                       ctx->d_tmpl0_of, W, ctx->d_trig, ctx->trig_cap, ctx->d_total);
-    CKL();
+    // Everything below is enqueued behind the pushes; the host waits once, for the
+    // error flag, the count and a first part of the list (sized from the last pull)
+    // in pinned memory, and copies the rest only when the list is longer.
+    const long long want = std::min<long long>(total, std::max<long long>(256, 2 * ctx->last_pull + 64));
+    if (want > ctx->h_trig_cap) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaFreeHost(ctx->h_trig);
+        ctx->h_trig = nullptr;
+        const long long cap2 = std::max<long long>(want, 2 * ctx->h_trig_cap);
+        CK(cudaHostAlloc((void**)&ctx->h_trig, cap2 * sizeof(TriggerOut), cudaHostAllocDefault));
+        ctx->h_trig_cap = cap2;
+    }
+    {
+        StageTimer tmg(ctx, 6);
+        k_gather_count<<<chunks, 1024, 0, ctx->stream>>>(ctx->d_slab, ctx->M_cap, M_used, nd, w0, (int)n_windows,
+                                                         kWindowRing, ctx->d_counts);
+        CKL();
+        k_gather_scatter<<<chunks, 1024, 0, ctx->stream>>>(ctx->d_slab, ctx->M_cap, M_used, nd, w0, (int)n_windows,
+                                                           kWindowRing, ctx->d_counts, chunks, ctx->d_bank_of,
+                                                           ctx->d_tmpl0_of, W, ctx->d_trig, ctx->trig_cap,
+                                                           ctx->d_total);
+        CKL();
+    }
+    CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_trig, ctx->d_trig, want * sizeof(TriggerOut), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ctx->pull_ev, ctx->stream));
+    if ((st = wait_event(ctx, ctx->pull_ev, timeout_ms))) return st;
+    if (*ctx->h_err)
+        return fail(ctx, LLOID_ETIMEOUT, "a kernel wait expired (code %d); results of the last pushes are invalid",
+                    *ctx->h_err);
     const long long cnt = *ctx->h_total;
     *n_out = cnt;
+    ctx->last_pull = cnt;
     if (cnt > cap) return fail(ctx, LLOID_ERANGE, "%lld triggers, capacity %lld", cnt, (long long)cap);
     static_assert(sizeof(TriggerOut) == sizeof(lloid_trigger), "trigger layout");
-    if (cnt > 0) {
-        CK(cudaMemcpyAsync(out, ctx->d_trig, cnt * sizeof(lloid_trigger), cudaMemcpyDeviceToHost, ctx->stream));
+    const long long head = std::min(cnt, want);
+    if (head > 0) std::memcpy(out, ctx->h_trig, head * sizeof(lloid_trigger));
+    if (cnt > head) {
+        CK(cudaMemcpyAsync(out + head, ctx->d_trig + head, (cnt - head) * sizeof(lloid_trigger),
+                           cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
     return LLOID_OK;
