@@ -249,6 +249,25 @@ def algorithmic_work(slices, M, f0=F0, n_up=8):
             "at_f0": rec_by.get(f0, 0.0) + up_by.get(f0, 0.0) + cmp_}
 
 
+# DRAM read + write bytes per launch of each stage's kernel, from the ncu
+# capture summarised in profiles/k_level_tc_k_fir_tc_bank1000.md; valid only
+# while the tensor-core kernel sources hash to the prefix it was taken with.
+TRAFFIC_SOURCES = ("kernels_tc.cuh", "kernels_tc2.cuh", "lloid_common.cuh")
+TRAFFIC_SHA = "e0a6821a59bb3b91"
+TRAFFIC = {("bank1000", "fp16_split", 8, 2): {"upsample": 82.1e6, "recon": 159.2e6, "fir": 255.8e6}}
+
+
+def measured_traffic(workload, precision, block_seconds, n_det, stage):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2511_04730_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != TRAFFIC_SHA:
+        return None
+    return TRAFFIC.get((workload, precision, block_seconds, n_det), {}).get(stage)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -535,8 +554,11 @@ def run_lloid(args, rank, world, dist):
     launches_dom = max(1.0, stages[dom][1] / args.steps)
     alg = per_dets * det_s / launches_dom          # one launch's share of the stage's work
     achieved = alg / (dur_ms / 1000.0) / 1e12
+    traffic = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, dom)
     roofline = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                                   "profiles/k_level_tc_k_fir_tc_bank1000.md") if traffic else None,
                 "algorithmic_flop_per_launch": alg, "launch_ms": dur_ms}
     per_stage = {}
     for st_name in ("fir", "upsample", "recon"):

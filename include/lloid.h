@@ -208,7 +208,7 @@ LLOID_API lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank
                              int64_t* t0, int64_t* n_samples);
 
 /* Checkpoint of the streaming state (SGNL snapshots its state periodically,
- * Section II.D.4): every per-detector stream ring, every bank's history ring,
+ * Section II.D.5): every per-detector stream ring, every bank's history ring,
  * the window partials and retained trigger windows, and the stream
  * positions, written to the host buffer buf[*len] after waiting for the
  * context's stream.  With buf == NULL, *len receives the size and the call
