@@ -27,6 +27,9 @@
 
 namespace lloid {
 
+// Both kernels run a static schedule built on the host: sched[0 .. grid] are
+// per-CTA offsets into the tile ids that follow; a tile id `it` is detector
+// det0 + it % n_det_push and tile it / n_det_push of the launch's job table.
 constexpr int kFirNC = 128;       // max c-groups per FIR tile (1024 outputs)
 constexpr int kEpiThreads = 128;  // epilogue warps 2..5
 
@@ -146,10 +149,9 @@ __device__ __forceinline__ void split_hilo(float v, uint16_t& hi, uint16_t& lo) 
 // ---------------------------------------------------------------------------
 template <bool BF16>
 struct FirCfg {
-    static constexpr int STAGES = 4;
+    static constexpr int MAX_STAGES = 8;                       // runtime count: as many as shared memory allows
     static constexpr int TILE_A = 128 * kTcK * 2;              // 16 KB
     static constexpr int STAGE_BYTES = (BF16 ? 2 : 1) * TILE_A;
-    static constexpr int STAGE_AREA = STAGES * STAGE_BYTES;
     static constexpr int EPI_LD = 24;                          // staging row pitch (halves): conflict-free, 16 B aligned
     static constexpr int EPI_BYTES = 2 * 256 * EPI_LD * 2;     // staging [256 q][16 bases (+pad)] hi + lo
 };
@@ -157,18 +159,18 @@ struct FirCfg {
 template <bool BF16>
 __global__ void __launch_bounds__(192, 1)
     k_fir_tc(const FirTcJob* __restrict__ jobs, const FirMaps* __restrict__ maps, const int* __restrict__ tile_base,
-             int n_jobs, int tiles_per_det, long long k_a, int det0, int n_det_push, int strip_bytes,
-             int* __restrict__ err) {
+             const int* __restrict__ sched, int n_jobs, int tiles_per_det, long long k_a, int det0, int n_det_push, int strip_bytes,
+             int n_stages, int* __restrict__ err) {
     using C = FirCfg<BF16>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stage_area = smem;
-    uint8_t* strip_area = smem + C::STAGE_AREA;                // 2 buffers x (hi, lo) x strip_bytes
+    uint8_t* strip_area = smem + n_stages * C::STAGE_BYTES;                // 2 buffers x (hi, lo) x strip_bytes
     uint16_t* epi = reinterpret_cast<uint16_t*>(strip_area + 4 * strip_bytes);
     uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(epi) + C::EPI_BYTES);
     uint64_t* a_full = bars;
-    uint64_t* a_empty = a_full + C::STAGES;
-    uint64_t* s_full = a_empty + C::STAGES;
+    uint64_t* a_empty = a_full + n_stages;
+    uint64_t* s_full = a_empty + n_stages;
     uint64_t* s_empty = s_full + 2;
     uint64_t* t_full = s_empty + 2;
     uint64_t* t_empty = t_full + 2;
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(192, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) { mbar_init(a_full + s, 1); mbar_init(a_empty + s, 1); }
+        for (int s = 0; s < n_stages; ++s) { mbar_init(a_full + s, 1); mbar_init(a_empty + s, 1); }
         for (int b = 0; b < 2; ++b) {
             mbar_init(s_full + b, 1); mbar_init(s_empty + b, 1);
             mbar_init(t_full + b, 1); mbar_init(t_empty + b, kEpiThreads);
@@ -194,16 +196,16 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int total = tiles_per_det * n_det_push;
 
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
             int stage = 0, sb = 0;
             uint32_t phase = 0, sphase = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < total && ok; it += gridDim.x) {
-                const int det = det0 + it / tiles_per_det;
-                const int t = it % tiles_per_det;
+            for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1] && ok; ++k) {
+                const int it = sched[gridDim.x + 1 + k];
+                const int det = det0 + it % n_det_push;
+                const int t = it / n_det_push;
                 const int jx = job_of(tile_base, n_jobs, t);
                 const FirTcJob& jb = jobs[jx];
                 const int local = t - tile_base[jx];
@@ -226,12 +228,12 @@ __global__ void __launch_bounds__(192, 1)
                     mbar_expect_tx(a_full + stage, C::STAGE_BYTES);
                     tma_load_2d(st, &mp->a, a_full + stage, kc, mt * 128);
                     if (BF16) tma_load_2d(st + C::TILE_A, &mp->a_lo, a_full + stage, kc, mt * 128);
-                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                    if (++stage == n_stages) { stage = 0; phase ^= 1; }
                 }
             }
-            for (int s = 0; s < C::STAGES; ++s) {                 // drain the A stages
+            for (int s = 0; s < n_stages; ++s) {                 // drain the A stages
                 if (!mbar_wait(a_empty + stage, phase ^ 1, err, 23)) break;
-                if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                if (++stage == n_stages) { stage = 0; phase ^= 1; }
             }
             for (int s = 0; s < 2; ++s) {                         // and the strips
                 if (!mbar_wait(s_empty + sb, sphase ^ 1, err, 24)) break;
@@ -243,8 +245,8 @@ __global__ void __launch_bounds__(192, 1)
             int stage = 0, sb = 0, i = 0;
             uint32_t phase = 0, sphase = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < total && ok; it += gridDim.x, ++i) {
-                const int t = it % tiles_per_det;
+            for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1] && ok; ++k, ++i) {
+                const int t = sched[gridDim.x + 1 + k] / n_det_push;
                 const int jx = job_of(tile_base, n_jobs, t);
                 const int Kp = jobs[jx].Kp, NC = jobs[jx].NC;
                 const uint32_t idesc = idesc_f16(BF16, 128, NC);
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(192, 1)
                         if (BF16) umma_f16(d, desc_sw128(a + C::TILE_A + 32 * k), bh, idesc, 1u);
                     }
                     umma_commit(a_empty + stage);
-                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                    if (++stage == n_stages) { stage = 0; phase ^= 1; }
                 }
                 if (!ok) break;
                 umma_commit(s_empty + sb);
@@ -287,9 +289,10 @@ __global__ void __launch_bounds__(192, 1)
         const int row = qd * 32 + lane;                 // A' row in the tile = 8 l + t
         const int l_loc = row >> 3, tph = row & 7;
         int i = 0;
-        for (int it = blockIdx.x; it < total; it += gridDim.x, ++i) {
-            const int det = det0 + it / tiles_per_det;
-            const int t = it % tiles_per_det;
+        for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1]; ++k, ++i) {
+            const int it = sched[gridDim.x + 1 + k];
+            const int det = det0 + it % n_det_push;
+            const int t = it / n_det_push;
             const int jx = job_of(tile_base, n_jobs, t);
             const FirTcJob& jb = jobs[jx];
             const int local = t - tile_base[jx];
@@ -313,7 +316,9 @@ __global__ void __launch_bounds__(192, 1)
                     epi[256 * C::EPI_LD + (8 * j + tph) * C::EPI_LD + l_loc] = l;
                 }
                 epi_sync();
-                // 256 rows x 32 B (hi) + 256 x 32 B (lo) as 16-byte stores, both ring mappings
+                // 256 rows x 32 B (hi) + 256 x 32 B (lo) as 16-byte stores.  Only the first of the
+                // ring's two mappings is written: the level kernel reads 128-row boxes that start
+                // at multiples of 128 in a power-of-two ring, which never wrap.
                 for (int e = et; e < 2 * 256 * 2; e += kEpiThreads) {
                     const int part = e >> 9;             // 0 hi, 1 lo
                     const int r = (e >> 1) & 255, h16 = e & 1;
@@ -323,7 +328,6 @@ __global__ void __launch_bounds__(192, 1)
                     uint16_t* dst = part ? yl : yh;
                     const long long rr = q & (jb.y_rows - 1);
                     *reinterpret_cast<uint4*>(dst + rr * jb.y_ld + h16 * 8) = val;
-                    *reinterpret_cast<uint4*>(dst + (rr + jb.y_rows) * jb.y_ld + h16 * 8) = val;
                 }
                 epi_sync();
             }
@@ -374,7 +378,7 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
 template <bool BF16, bool TOP, bool STORE_Z, int F>
 __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
     k_level_tc(const LevelJob* __restrict__ jobs, const LevelMaps* __restrict__ maps,
-               const int* __restrict__ tile_base, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
+               const int* __restrict__ tile_base, const int* __restrict__ sched, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
                int det0, int n_det_push, long long window, Partial* __restrict__ part, long long part_tmpl_stride,
                int n_slots, float* __restrict__ zout, int* __restrict__ err) {
     using C = LevCfg<BF16, TOP>;
@@ -407,16 +411,16 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int total = tiles_per_det * n_det_push;
 
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < total && ok; it += gridDim.x) {
-                const int det = det0 + it / tiles_per_det;
-                const int t = it % tiles_per_det;
+            for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1] && ok; ++k) {
+                const int it = sched[gridDim.x + 1 + k];
+                const int det = det0 + it % n_det_push;
+                const int t = it / n_det_push;
                 const int jx = job_of(tile_base, n_jobs, t);
                 const LevelJob& jb = jobs[jx];
                 const LevelMaps* mp = maps + jb.map;
@@ -471,8 +475,8 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
             int stage = 0, i = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < total && ok; it += gridDim.x, ++i) {
-                const int t = it % tiles_per_det;
+            for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1] && ok; ++k, ++i) {
+                const int t = sched[gridDim.x + 1 + k] / n_det_push;
                 const int jx = job_of(tile_base, n_jobs, t);
                 const int Kp = jobs[jx].Kp;
                 const int buf = i & 1;
@@ -537,9 +541,10 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
         const int half = (warp - 2) >> 2;
         const int rowm = qd * 32 + lane;
         int i = 0;
-        for (int it = blockIdx.x; it < total; it += gridDim.x, ++i) {
-            const int det = det0 + it / tiles_per_det;
-            const int t = it % tiles_per_det;
+        for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1]; ++k, ++i) {
+            const int it = sched[gridDim.x + 1 + k];
+            const int det = det0 + it % n_det_push;
+            const int t = it / n_det_push;
             const int jx = job_of(tile_base, n_jobs, t);
             const LevelJob& jb = jobs[jx];
             const int local = t - tile_base[jx];

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <queue>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -154,12 +155,16 @@ struct lloid_ctx {
     FinJob* d_finj = nullptr; int n_fin = 0;
     // split path job tables: FIR over all slices, levels per depth below the top
     FirTcJob* d_firtc = nullptr; FirMaps* d_firmaps = nullptr; int* d_firtc_base = nullptr;
-    int n_firtc = 0, firtc_tiles = 0, firtc_smem = 0, firtc_strip = 0;
+    int n_firtc = 0, firtc_tiles = 0, firtc_smem = 0, firtc_strip = 0, firtc_stages = 0;
     static constexpr int kMaxDepth = 8;
     // one table per (depth, F slot): F = 0 (lowest level), 2, 4, ..., 64 -> slot 0..6
     static constexpr int kFSlots = 7;
     static constexpr int kLevTables = kMaxDepth * kFSlots;
     LevelJob* d_lev[kLevTables] = {}; LevelMaps* d_levmaps[kLevTables] = {}; int* d_lev_base[kLevTables] = {};
+    // tile schedules ([grid + 1] offsets, then tile ids) for pushes of one detector [0]
+    // and of all detectors [1]
+    int* d_lev_sched[kLevTables][2] = {}; int lev_grid[kLevTables][2] = {};
+    int* d_fir_sched[2] = {}; int fir_grid[2] = {};
     int n_lev[kLevTables] = {}, lev_tiles[kLevTables] = {};
     int max_depth = 0;
     std::vector<int> top_job_of_bank;  // bank id -> index in its top-level table
@@ -368,7 +373,9 @@ void free_jobs(lloid_ctx* ctx) {
     for (int d = 0; d < lloid_ctx::kLevTables; ++d) {
         ctx->d_lev[d] = nullptr; ctx->d_levmaps[d] = nullptr; ctx->d_lev_base[d] = nullptr;
         ctx->n_lev[d] = 0; ctx->lev_tiles[d] = 0;
+        ctx->d_lev_sched[d][0] = ctx->d_lev_sched[d][1] = nullptr;
     }
+    ctx->d_fir_sched[0] = ctx->d_fir_sched[1] = nullptr;
     ctx->n_firtc = ctx->firtc_tiles = 0;
 }
 
@@ -379,6 +386,38 @@ lloid_status upload_vec(lloid_ctx* ctx, T** dst, const std::vector<T>& v) {
     ctx->job_allocs.push_back(*dst);
     if (!v.empty()) CK(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
     return LLOID_OK;
+}
+
+// Static schedule of one launch over tiles t of a job table (cost[t]) for nd
+// detectors: tile id it = t * nd + detector offset.  Longest tiles first, each
+// to the least-loaded CTA (LPT); each CTA then runs its tiles in id order, so
+// the detectors of one tile run side by side and share its operands in L2.
+std::vector<int> build_sched(const std::vector<double>& cost, int nd, int n_sm, int* grid_out) {
+    const long long total = (long long)cost.size() * nd;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(total, n_sm));
+    std::vector<int> order((size_t)total);
+    for (long long i = 0; i < total; ++i) order[(size_t)i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a / nd] > cost[b / nd]; });
+    std::vector<std::vector<int>> per(grid);
+    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> load;
+    for (int g = 0; g < grid; ++g) load.push({0.0, g});
+    for (int it : order) {
+        auto top = load.top();
+        load.pop();
+        per[top.second].push_back(it);
+        load.push({top.first + cost[it / nd], top.second});
+    }
+    std::vector<int> h(grid + 1, 0);
+    for (int g = 0; g < grid; ++g) {
+        std::sort(per[g].begin(), per[g].end());
+        h[g + 1] = h[g] + (int)per[g].size();
+    }
+    for (int g = 0; g < grid; ++g) h.insert(h.end(), per[g].begin(), per[g].end());
+    *grid_out = grid;
+    return h;
+}
+lloid_status upload_sched(lloid_ctx* ctx, const std::vector<double>& cost, int nd, int** d_out, int* grid_out) {
+    return upload_vec(ctx, d_out, build_sched(cost, nd, ctx->n_sm, grid_out));
 }
 
 bool split_precision(const lloid_ctx* ctx) { return ctx->cfg.precision != LLOID_FP32; }
@@ -557,12 +596,37 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             (st = upload_vec(ctx, &ctx->d_lev_base[d], lb[d])))
             return st;
     }
+    {   // schedules: cost ~ MMAs of a tile plus a fixed epilogue share
+        const int mk = bf ? 3 : 2;
+        std::vector<double> fc;
+        for (const FirTcJob& f : fj)
+            for (int k = 0; k < f.Mtiles * f.ctiles; ++k) fc.push_back(mk * f.Kp / 16.0 + 16.0);
+        for (int v = 0; v < 2; ++v) {
+            const int ndv = v ? nd : 1;
+            if ((st = upload_sched(ctx, fc, ndv, &ctx->d_fir_sched[v], &ctx->fir_grid[v]))) return st;
+        }
+        for (int d = 0; d < lloid_ctx::kLevTables; ++d) {
+            if (lj[d].empty()) continue;
+            std::vector<double> lc;
+            for (const LevelJob& q : lj[d])
+                for (int k = 0; k < q.tiles_m * q.tiles_t; ++k)
+                    lc.push_back((bf ? 6 : 4) * q.Kp / 16.0 + 12.0 * win_chunks(q.F) + 16.0);
+            for (int v = 0; v < 2; ++v) {
+                const int ndv = v ? nd : 1;
+                if ((st = upload_sched(ctx, lc, ndv, &ctx->d_lev_sched[d][v], &ctx->lev_grid[d][v]))) return st;
+            }
+        }
+    }
     ctx->n_firtc = (int)fj.size();
     ctx->firtc_tiles = ft;
     ctx->firtc_strip = strip;
     ctx->max_depth = max_depth;
-    const int fsmem = (bf ? FirCfg<true>::STAGE_AREA : FirCfg<false>::STAGE_AREA) + 4 * strip +
-                      FirCfg<false>::EPI_BYTES + 256 + 1024;   // EPI_BYTES is the same for both
+    // as many A' stages as fit next to the strips, the epilogue staging and the barriers
+    const int fixed = 4 * strip + FirCfg<false>::EPI_BYTES + 256 + 1024;   // EPI_BYTES is the same for both
+    const int sbytes = bf ? FirCfg<true>::STAGE_BYTES : FirCfg<false>::STAGE_BYTES;
+    ctx->firtc_stages = std::min(FirCfg<false>::MAX_STAGES, (227 * 1024 - fixed) / sbytes);
+    if (ctx->firtc_stages < 2) return fail(ctx, LLOID_EINVAL, "FIR strips of %d bytes leave no room for 2 stages", strip);
+    const int fsmem = ctx->firtc_stages * sbytes + fixed;
     ctx->firtc_smem = fsmem;
     if (fsmem > 227 * 1024) return fail(ctx, LLOID_EINVAL, "FIR shared memory %d exceeds the limit", fsmem);
     if (bf) CK(cudaFuncSetAttribute(k_fir_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
@@ -668,17 +732,17 @@ lloid_status launch_recon_f32(lloid_ctx* ctx, long long k_a, long long n, int de
 
 template <bool BF16, bool TOP, bool SZ, int F>
 void launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps, const int* base,
-                int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W, Partial* part,
-                long long part_stride, int n_slots, float* zout, int* err) {
-    k_level_tc<BF16, TOP, SZ, F><<<g, LevCfg<BF16, TOP>::THREADS, LevCfg<BF16, TOP>::SMEM, st>>>(jobs, maps, base, n_jobs, tiles, k_a, k_b,
+                const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W,
+                Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
+    k_level_tc<BF16, TOP, SZ, F><<<g, LevCfg<BF16, TOP>::THREADS, LevCfg<BF16, TOP>::SMEM, st>>>(jobs, maps, base, sched, n_jobs, tiles, k_a, k_b,
                                                                       det0, nd, W, part, part_stride, n_slots, zout,
                                                                       err);
 }
 template <bool BF16, bool TOP, bool SZ>
 void launch_lv_f(int F, dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps,
-                 const int* base, int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W,
-                 Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
-#define LV_F(FV) launch_lv1<BF16, TOP, SZ, FV>(g, smem, st, jobs, maps, base, n_jobs, tiles, k_a, k_b, det0, nd, W, \
+                 const int* base, const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0,
+                 int nd, long long W, Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
+#define LV_F(FV) launch_lv1<BF16, TOP, SZ, FV>(g, smem, st, jobs, maps, base, sched, n_jobs, tiles, k_a, k_b, det0, nd, W, \
                                                part, part_stride, n_slots, zout, err)
     switch (F) {
         case 0: LV_F(0); break;
@@ -695,18 +759,17 @@ void launch_lv_f(int F, dim3 g, int smem, cudaStream_t st, const LevelJob* jobs,
 // One ladder depth and upsampling factor of the split path (depth 0 = f0:
 // |z|^2 and window maxima); fslot 0 = no level below, else F = 2^fslot.
 lloid_status launch_level(lloid_ctx* ctx, int depth, int fslot, long long k_a, long long n, int det0, int n_det_push,
-                          bool store_z, const LevelJob* jobs, const LevelMaps* maps, const int* base, int n_jobs,
-                          int tiles, float* zout) {
+                          bool store_z, const LevelJob* jobs, const LevelMaps* maps, const int* base,
+                          const int* sched, int grid, int n_jobs, int tiles, float* zout) {
     if (tiles == 0 || n_jobs == 0) return LLOID_OK;
     const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
     const long long part_stride = (long long)ctx->cfg.n_detectors * ctx->n_slots;
-    const int total = tiles * n_det_push;
-    dim3 g(std::min(total, ctx->n_sm));
+    dim3 g(grid);
     const int smem = 0;   // each instantiation launches with its own LevCfg<BF16, TOP>::SMEM
     Partial* part = store_z ? nullptr : ctx->d_part;
     const int F = fslot ? 1 << fslot : 0;
 #define LAUNCH_LV(BFV, TOPV, SZ)                                                                                     \
-    launch_lv_f<BFV, TOPV, SZ>(F, g, smem, ctx->stream, jobs, maps, base, n_jobs, tiles, k_a, k_a + n, det0,          \
+    launch_lv_f<BFV, TOPV, SZ>(F, g, smem, ctx->stream, jobs, maps, base, sched, n_jobs, tiles, k_a, k_a + n, det0,   \
                                n_det_push, ctx->cfg.window_samples, part, part_stride, ctx->n_slots, zout, ctx->d_err)
     if (depth > 0) { if (bf) LAUNCH_LV(true, false, false); else LAUNCH_LV(false, false, false); }
     else if (store_z) { if (bf) LAUNCH_LV(true, true, true); else LAUNCH_LV(false, true, true); }
@@ -777,18 +840,20 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
         // a2 basis FIR on the tensor cores
         if (ctx->firtc_tiles) {
             StageTimer tm(ctx, 2);
-            const int total = ctx->firtc_tiles * nd;
-            dim3 g(std::min(total, ctx->n_sm));
+            const int v = nd == 1 ? 0 : 1;
+            if (nd != 1 && nd != ctx->cfg.n_detectors) return fail(ctx, LLOID_EINVAL, "push of %d detectors", nd);
+            dim3 g(ctx->fir_grid[v]);
             if (ctx->cfg.precision == LLOID_BF16_SPLIT)
                 k_fir_tc<true><<<g, 192, ctx->firtc_smem, ctx->stream>>>(ctx->d_firtc, ctx->d_firmaps,
-                                                                         ctx->d_firtc_base, ctx->n_firtc,
-                                                                         ctx->firtc_tiles, k_a, det0, nd,
-                                                                         ctx->firtc_strip, ctx->d_err);
+                                                                         ctx->d_firtc_base, ctx->d_fir_sched[v],
+                                                                         ctx->n_firtc, ctx->firtc_tiles, k_a, det0,
+                                                                         nd, ctx->firtc_strip, ctx->firtc_stages, ctx->d_err);
             else
                 k_fir_tc<false><<<g, 192, ctx->firtc_smem, ctx->stream>>>(ctx->d_firtc, ctx->d_firmaps,
-                                                                          ctx->d_firtc_base, ctx->n_firtc,
-                                                                          ctx->firtc_tiles, k_a, det0, nd,
-                                                                          ctx->firtc_strip, ctx->d_err);
+                                                                          ctx->d_firtc_base, ctx->d_fir_sched[v],
+                                                                          ctx->n_firtc, ctx->firtc_tiles, k_a, det0,
+                                                                          nd, ctx->firtc_strip, ctx->firtc_stages,
+                                                                          ctx->d_err);
             CKL();
         }
         // a3 + a4: reconstruction rate by rate with the Eq. 7-8 ladder, lowest rate first
@@ -797,17 +862,21 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
             for (int d = ctx->max_depth - 1; d >= 1; --d)
                 for (int fs = 0; fs < lloid_ctx::kFSlots; ++fs) {
                     const int tb = d * lloid_ctx::kFSlots + fs;
+                    const int v = nd == 1 ? 0 : 1;
                     if ((st = launch_level(ctx, d, fs, k_a, n, det0, nd, false, ctx->d_lev[tb], ctx->d_levmaps[tb],
-                                           ctx->d_lev_base[tb], ctx->n_lev[tb], ctx->lev_tiles[tb], nullptr)))
+                                           ctx->d_lev_base[tb], ctx->d_lev_sched[tb][v], ctx->lev_grid[tb][v],
+                                           ctx->n_lev[tb], ctx->lev_tiles[tb], nullptr)))
                         return st;
                 }
         }
         // top level (f0) + a5 window maxima
         {
             StageTimer tm(ctx, 4);
+            const int v = nd == 1 ? 0 : 1;
             for (int fs = 0; fs < lloid_ctx::kFSlots && !st; ++fs)
                 st = launch_level(ctx, 0, fs, k_a, n, det0, nd, false, ctx->d_lev[fs], ctx->d_levmaps[fs],
-                                  ctx->d_lev_base[fs], ctx->n_lev[fs], ctx->lev_tiles[fs], nullptr);
+                                  ctx->d_lev_base[fs], ctx->d_lev_sched[fs][v], ctx->lev_grid[fs][v], ctx->n_lev[fs],
+                                  ctx->lev_tiles[fs], nullptr);
         }
         if (st) return st;
     }
@@ -1519,6 +1588,7 @@ lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* o
     if (st0) return st0;
     const int idx = ctx->top_job_of_bank[bank];
     int* db = nullptr;
+    int* dsched = nullptr;
     CK(cudaMalloc(&db, sizeof(int)));
     CK(cudaMemsetAsync(db, 0, sizeof(int), ctx->stream));
     const long long k_a = ctx->pos[det] - n;
@@ -1529,10 +1599,16 @@ lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* o
     } else {
         const int tiles = (b->Mpad / kTcTileM) * (int)(n / kTcTileN);
         const int fs = ctx->top_slot_of_bank[bank];
-        st = launch_level(ctx, 0, fs, k_a, n, det, 1, true, ctx->d_lev[fs] + idx, ctx->d_levmaps[fs], db, 1, tiles, out);
+        int grid = 0;
+        const std::vector<int> hs = build_sched(std::vector<double>(tiles, 1.0), 1, ctx->n_sm, &grid);
+        CK(cudaMalloc(&dsched, hs.size() * sizeof(int)));
+        CK(cudaMemcpyAsync(dsched, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        st = launch_level(ctx, 0, fs, k_a, n, det, 1, true, ctx->d_lev[fs] + idx, ctx->d_levmaps[fs], db, dsched, grid,
+                          1, tiles, out);
     }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     cudaFree(db);
+    cudaFree(dsched);
     if (st) return st;
     if (e != cudaSuccess) return fail(ctx, LLOID_ECUDA, "snr_block: %s", cudaGetErrorString(e));
     if ((st = check_kernel_err(ctx))) return st;
