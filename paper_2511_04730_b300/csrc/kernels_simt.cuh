@@ -30,6 +30,8 @@ __global__ void k_ingest(const float* __restrict__ src, long long src_det_stride
                          long long ring_det_stride, int mask, long long k_a, int n, int det0,
                          uint16_t* __restrict__ s_hi, uint16_t* __restrict__ s_lo, long long s_det_stride,
                          int s_len, int mode) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int det = blockIdx.y;
     const float* s = src + det * src_det_stride;
     float* r = ring + (det0 + det) * ring_det_stride;
@@ -68,6 +70,8 @@ struct DownParams {
 
 __global__ void k_downsample(DownParams p, const float* __restrict__ ring0, long long ring0_det_stride,
                              int mask0, long long k_a, int n, int n_down, int det0) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int r = blockIdx.z;
     if (r >= p.n_rates) return;
     const int D = p.D[r];
@@ -328,6 +332,8 @@ __global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ job
                                                   long long part_tmpl_stride, int n_slots, int tiles_per_window,
                                                   long long w0, float threshold, SlabEntry* __restrict__ slab_base,
                                                   int ring, int n_det_total, long long slab_det_stride, int det0) {
+    pdl_launch_dependents();
+    pdl_wait();
     const FinJob jb = jobs[blockIdx.x];
     const int det = det0 + blockIdx.y;
     const long long w = w0 + blockIdx.z;
@@ -396,6 +402,8 @@ __device__ __forceinline__ const SlabEntry& slab_at(const SlabEntry* slab, long 
 
 __global__ void k_gather_count(const SlabEntry* __restrict__ slab, long long cap, int M_used, int n_det,
                                long long w0, int n_win, int ring, int* __restrict__ counts) {
+    pdl_launch_dependents();
+    pdl_wait();
     const long long total = (long long)n_win * n_det * M_used;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int v = 0;
@@ -411,6 +419,8 @@ __global__ void k_gather_scatter(const SlabEntry* __restrict__ slab, long long c
                                  long long w0, int n_win, int ring, const int* __restrict__ counts, int n_chunks,
                                  const int* __restrict__ bank_of, const int* __restrict__ tmpl0_of, long long W,
                                  TriggerOut* __restrict__ out, long long out_cap, long long* __restrict__ total_out) {
+    pdl_launch_dependents();
+    pdl_wait();
     __shared__ int red[1024 / 32];
     __shared__ int base_s;
     // exclusive prefix of the chunk counts

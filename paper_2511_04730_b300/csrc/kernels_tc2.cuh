@@ -72,9 +72,8 @@ struct FirMaps { CUtensorMap a, a_lo; };
 // accw: the level below's hi/lo planes (rows [det][plane][Mpad], columns =
 // samples), box 32 samples x 128 templates, 64-byte swizzle; uhi/ulo: the
 // Eq. 8 tile matrices U_F of this level's factor, rows [shift][128 outputs],
-// columns = window rows, same box and swizzle; accst: this level's own planes
-// for the epilogue's TMA stores, box 32 samples x 32 templates, 64-byte swizzle.
-struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo, accw, uhi, ulo, accst; };
+// columns = window rows, same box and swizzle.
+struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo, accw, uhi, ulo; };
 
 // Window of the level below read by one 128-sample tile (N_up = 8): rows
 // floor(Q/F) - N_up - r .. floor(Q/F) + 127/F + N_up, where the shift r =
@@ -144,6 +143,24 @@ __device__ __forceinline__ void split_hilo(float v, uint16_t& hi, uint16_t& lo) 
     }
 }
 
+// Two values at once: hi = round(a, b) as a packed pair, lo = round((a, b) - hi).
+template <bool BF16>
+__device__ __forceinline__ void split_hilo2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    if (BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a2 on the tensor cores
 // ---------------------------------------------------------------------------
@@ -162,6 +179,7 @@ __global__ void __launch_bounds__(192, 1)
              const int* __restrict__ sched, int n_jobs, int tiles_per_det, long long k_a, int det0, int n_det_push, int strip_bytes,
              int n_stages, int* __restrict__ err) {
     using C = FirCfg<BF16>;
+    pdl_launch_dependents();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stage_area = smem;
@@ -196,6 +214,7 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();   // inputs of this launch are written by the previous kernels of the stream
 
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
@@ -358,20 +377,13 @@ struct LevCfg {
     static constexpr int WSTAGE = 6 * WTILE;           // re hi, re lo, im hi, im lo, U hi, U lo
     static_assert(WSTAGE <= STAGE_BYTES, "a window stage fits a stage slot");
     static constexpr int EPI_WARPS = 8;                 // two per TMEM lane quarter, 64 columns each
-    static constexpr int STG_BUF = 32 * 64;            // 32 templates x 32 samples x 2 B, 64-byte swizzle
-    static constexpr int STG = TOP ? 0 : EPI_WARPS * 2 * STG_BUF;   // below the top: staging for the TMA stores
+    static constexpr int STG_PITCH = 80;               // 32 samples x 2 B + 16 B pad: conflict-free rows
+    static constexpr int STG_BUF = 32 * STG_PITCH;     // one warp's 32 templates x 32 samples
+    static constexpr int STG = TOP ? 0 : EPI_WARPS * STG_BUF;   // below the top: per-warp transpose buffers
     static constexpr int XCHG = TOP ? 2 * 128 * 16 : 0;   // top: tile-argmax exchange between the column halves
     static constexpr int SMEM = STAGES * STAGE_BYTES + STG + XCHG + 1024 + 256;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
 };
-
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(smem_u32(src)), "r"(c0), "r"(c1)
-                 : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
 
 // F: the factor to the level below (0 at the lowest level), a template
 // parameter so that the window stages and their MMAs are unrolled.
@@ -382,6 +394,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                int det0, int n_det_push, long long window, Partial* __restrict__ part, long long part_tmpl_stride,
                int n_slots, float* __restrict__ zout, int* __restrict__ err) {
     using C = LevCfg<BF16, TOP>;
+    pdl_launch_dependents();
     constexpr int EPI = 32 * C::EPI_WARPS;
     constexpr int NWC = win_chunks(F);
     extern __shared__ uint8_t smem_raw[];
@@ -411,6 +424,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();   // inputs of this launch are written by the previous kernels of the stream
 
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
@@ -586,13 +600,16 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                 }
             } else {
                 // Acc of this warp's 32 templates x 64 samples as four hi/lo planes, 32 samples at a
-                // time: each half through a 64-byte-swizzled staging buffer and one TMA store (box
-                // 32 x 32).  Plane columns start at X0 = floor8(lo) - 128, so no store starts left of 0.
-                const LevelMaps* mp = maps + jb.map;
+                // time, transposed through a padded shared-memory buffer so that each global store
+                // instruction writes 8 template rows x 64 contiguous bytes.  Plane columns start at
+                // X0 = floor8(lo) - 128 (a tile never writes left of column 0).
                 const long long X0 = fdiv(lo, 8) * 8 - 128;
-                const int x0 = (int)(Q0 + 128LL * tt + 64 * half - X0);
-                const int y0 = det * 4 * jb.Mpad + tm * 128 + qd * 32;
-                uint8_t* wbuf = stg + (warp - 2) * 2 * C::STG_BUF;
+                const long long x0 = Q0 + 128LL * tt + 64 * half - X0;
+                const long long pstride = (long long)jb.Mpad * jb.acc_cols;
+                uint16_t* pbase = jb.acc_out + det * jb.acc_out_det_stride +
+                                  (long long)(tm * 128 + qd * 32) * jb.acc_cols;
+                uint8_t* wbuf = stg + (warp - 2) * C::STG_BUF;
+                const int rr = lane >> 2, cq = lane & 3;        // read-back: row within 8, 16-byte chunk
 #pragma unroll 1
                 for (int part = 0; part < 2; ++part) {          // re, im
 #pragma unroll 1
@@ -606,27 +623,23 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                         }
                         uint32_t hp[16], lp[16];
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            uint16_t h0, l0, h1, l1;
-                            split_hilo<BF16>(v[2 * k], h0, l0);
-                            split_hilo<BF16>(v[2 * k + 1], h1, l1);
-                            hp[k] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                            lp[k] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-                        }
-                        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                        __syncwarp();
+                        for (int k = 0; k < 16; ++k) split_hilo2<BF16>(v[2 * k], v[2 * k + 1], hp[k], lp[k]);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int off = lane * 64 + ((k ^ ((lane >> 1) & 3)) << 4);
-                            *reinterpret_cast<uint4*>(wbuf + off) = make_uint4(hp[4 * k], hp[4 * k + 1], hp[4 * k + 2], hp[4 * k + 3]);
-                            *reinterpret_cast<uint4*>(wbuf + C::STG_BUF + off) =
-                                make_uint4(lp[4 * k], lp[4 * k + 1], lp[4 * k + 2], lp[4 * k + 3]);
-                        }
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0) {
-                            tma_store_2d(&mp->accst, wbuf, x0 + 32 * g, y0 + (2 * part) * jb.Mpad);
-                            tma_store_2d(&mp->accst, wbuf + C::STG_BUF, x0 + 32 * g, y0 + (2 * part + 1) * jb.Mpad);
+                        for (int sub = 0; sub < 2; ++sub) {      // hi, lo
+                            const uint32_t* src = sub ? lp : hp;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                *reinterpret_cast<uint4*>(wbuf + lane * C::STG_PITCH + k * 16) =
+                                    make_uint4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
+                            __syncwarp();
+                            uint16_t* pl = pbase + (2 * part + sub) * pstride + x0 + 32 * g + 8 * cq;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int r = 8 * i + rr;
+                                const uint4 val = *reinterpret_cast<const uint4*>(wbuf + r * C::STG_PITCH + cq * 16);
+                                *reinterpret_cast<uint4*>(pl + (long long)r * jb.acc_cols) = val;
+                            }
+                            __syncwarp();
                         }
                     }
                 }
@@ -649,7 +662,6 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                 }
             }
         }
-        if (!TOP && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();

@@ -27,6 +27,13 @@ __device__ __forceinline__ void split_hilo_rt(float v, int mode, uint16_t& hi, u
     }
 }
 
+// Programmatic dependent launch: a kernel lets the next one in the stream be
+// scheduled as soon as all its CTAs have started, and waits for the previous
+// one to finish (and its writes to be visible) before touching its results.
+// Both are no-ops for a launch without the programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 constexpr int kTileT = 128;      // time tile of the reconstruction = window granule
 constexpr int kMaxRates = 8;     // downsampled streams f0/2 ... f0/256
 

@@ -302,20 +302,6 @@ bool encode_map_sw64(CUtensorMap* m, bool bf16, const void* base, long long cols
     return r == CUDA_SUCCESS;
 }
 
-// 2-D 16-bit map for the epilogue's TMA stores: box 32 x 32, 64-byte swizzle.
-bool encode_map_store(CUtensorMap* m, bool bf16, const void* base, long long cols, long long rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {32, 32};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
-                    const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
 lloid_status ensure_template_capacity(lloid_ctx* ctx, long long need) {
     if (need <= ctx->M_cap) return LLOID_OK;
     const int nd = ctx->cfg.n_detectors;
@@ -386,6 +372,24 @@ lloid_status upload_vec(lloid_ctx* ctx, T** dst, const std::vector<T>& v) {
     ctx->job_allocs.push_back(*dst);
     if (!v.empty()) CK(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
     return LLOID_OK;
+}
+
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the previous one drains; it waits (griddepcontrol.wait) before it
+// reads anything the previous kernels wrote.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
 // Static schedule of one launch over tiles t of a job table (cost[t]) for nd
@@ -577,8 +581,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                          encode_map(&mp.cim_lo, bf, L.d_cim_lo, L.Kp, b->Mpad, kTcTileM);
                 if (!ok) return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (level, bank %d)", b->id);
             }
-            if (j < nl - 1 && !encode_map_store(&mp.accst, bf, L.d_accp, L.acc_cols, (long long)nd * 4 * b->Mpad))
-                return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (planes, bank %d)", b->id);
+
             if (depth == 0) { ctx->top_job_of_bank[b->id] = (int)lj[tab].size(); ctx->top_slot_of_bank[b->id] = fslot; }
             lj[tab].push_back(q); lm[tab].push_back(mp); lb[tab].push_back(lt[tab]);
             lt[tab] += q.tiles_m * q.tiles_t;
@@ -731,27 +734,27 @@ lloid_status launch_recon_f32(lloid_ctx* ctx, long long k_a, long long n, int de
 }
 
 template <bool BF16, bool TOP, bool SZ, int F>
-void launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps, const int* base,
+cudaError_t launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps, const int* base,
                 const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W,
                 Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
-    k_level_tc<BF16, TOP, SZ, F><<<g, LevCfg<BF16, TOP>::THREADS, LevCfg<BF16, TOP>::SMEM, st>>>(jobs, maps, base, sched, n_jobs, tiles, k_a, k_b,
+    return launch_pdl(k_level_tc<BF16, TOP, SZ, F>, g, dim3(LevCfg<BF16, TOP>::THREADS), LevCfg<BF16, TOP>::SMEM, st, jobs, maps, base, sched, n_jobs, tiles, k_a, k_b,
                                                                       det0, nd, W, part, part_stride, n_slots, zout,
                                                                       err);
 }
 template <bool BF16, bool TOP, bool SZ>
-void launch_lv_f(int F, dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps,
+cudaError_t launch_lv_f(int F, dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps,
                  const int* base, const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0,
                  int nd, long long W, Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
 #define LV_F(FV) launch_lv1<BF16, TOP, SZ, FV>(g, smem, st, jobs, maps, base, sched, n_jobs, tiles, k_a, k_b, det0, nd, W, \
                                                part, part_stride, n_slots, zout, err)
     switch (F) {
-        case 0: LV_F(0); break;
-        case 2: LV_F(2); break;
-        case 4: LV_F(4); break;
-        case 8: LV_F(8); break;
-        case 16: LV_F(16); break;
-        case 32: LV_F(32); break;
-        default: LV_F(64); break;
+        case 0: return LV_F(0);
+        case 2: return LV_F(2);
+        case 4: return LV_F(4);
+        case 8: return LV_F(8);
+        case 16: return LV_F(16);
+        case 32: return LV_F(32);
+        default: return LV_F(64);
     }
 #undef LV_F
 }
@@ -768,14 +771,16 @@ lloid_status launch_level(lloid_ctx* ctx, int depth, int fslot, long long k_a, l
     const int smem = 0;   // each instantiation launches with its own LevCfg<BF16, TOP>::SMEM
     Partial* part = store_z ? nullptr : ctx->d_part;
     const int F = fslot ? 1 << fslot : 0;
+    cudaError_t le = cudaSuccess;
 #define LAUNCH_LV(BFV, TOPV, SZ)                                                                                     \
-    launch_lv_f<BFV, TOPV, SZ>(F, g, smem, ctx->stream, jobs, maps, base, sched, n_jobs, tiles, k_a, k_a + n, det0,   \
+    le = launch_lv_f<BFV, TOPV, SZ>(F, g, smem, ctx->stream, jobs, maps, base, sched, n_jobs, tiles, k_a, k_a + n, det0,   \
                                n_det_push, ctx->cfg.window_samples, part, part_stride, ctx->n_slots, zout, ctx->d_err)
     if (depth > 0) { if (bf) LAUNCH_LV(true, false, false); else LAUNCH_LV(false, false, false); }
     else if (store_z) { if (bf) LAUNCH_LV(true, true, true); else LAUNCH_LV(false, true, true); }
     else { if (bf) LAUNCH_LV(true, true, false); else LAUNCH_LV(false, true, false); }
 #undef LAUNCH_LV
-    CKL();
+    CK(le);
+    ++ctx->launches;
     return LLOID_OK;
 }
 
@@ -789,11 +794,10 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     {
         StageTimer tm(ctx, 0);
         dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 1024), nd);
-        k_ingest<<<grid, 256, 0, ctx->stream>>>(src, src_det_stride, ctx->ring0, ctx->ring0_len,
-                                                (int)(ctx->ring0_len - 1), k_a, n_i, det0, ctx->s_hi[0],
-                                                ctx->s_lo[0], 2 * ctx->s_len[0], (int)ctx->s_len[0],
-                                                ctx->cfg.precision);
-        CKL();
+        CK(launch_pdl(k_ingest, grid, dim3(256), 0, ctx->stream, src, src_det_stride, ctx->ring0, ctx->ring0_len,
+                      (int)(ctx->ring0_len - 1), k_a, n_i, det0, ctx->s_hi[0], ctx->s_lo[0], 2 * ctx->s_len[0],
+                      (int)ctx->s_len[0], (int)ctx->cfg.precision));
+        ++ctx->launches;
     }
     // a1 downsample to every rate
     {
@@ -808,9 +812,9 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
         }
         p.mode = ctx->cfg.precision;
         dim3 grid((unsigned)((n / 2 + 7) / 8), nd, ctx->n_rates);
-        k_downsample<<<grid, 256, 0, ctx->stream>>>(p, ctx->ring0, ctx->ring0_len, (int)(ctx->ring0_len - 1), k_a,
-                                                    n_i, ctx->cfg.n_down, det0);
-        CKL();
+        CK(launch_pdl(k_downsample, grid, dim3(256), 0, ctx->stream, p, (const float*)ctx->ring0, ctx->ring0_len,
+                      (int)(ctx->ring0_len - 1), k_a, n_i, (int)ctx->cfg.n_down, det0));
+        ++ctx->launches;
     }
     if (ctx->banks.empty()) return LLOID_OK;
     if (!split_precision(ctx)) {
@@ -844,16 +848,15 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
             if (nd != 1 && nd != ctx->cfg.n_detectors) return fail(ctx, LLOID_EINVAL, "push of %d detectors", nd);
             dim3 g(ctx->fir_grid[v]);
             if (ctx->cfg.precision == LLOID_BF16_SPLIT)
-                k_fir_tc<true><<<g, 192, ctx->firtc_smem, ctx->stream>>>(ctx->d_firtc, ctx->d_firmaps,
-                                                                         ctx->d_firtc_base, ctx->d_fir_sched[v],
-                                                                         ctx->n_firtc, ctx->firtc_tiles, k_a, det0,
-                                                                         nd, ctx->firtc_strip, ctx->firtc_stages, ctx->d_err);
+                CK(launch_pdl(k_fir_tc<true>, g, dim3(192), ctx->firtc_smem, ctx->stream, (const FirTcJob*)ctx->d_firtc,
+                              (const FirMaps*)ctx->d_firmaps, (const int*)ctx->d_firtc_base,
+                              (const int*)ctx->d_fir_sched[v], ctx->n_firtc, ctx->firtc_tiles, k_a, det0, nd,
+                              ctx->firtc_strip, ctx->firtc_stages, ctx->d_err));
             else
-                k_fir_tc<false><<<g, 192, ctx->firtc_smem, ctx->stream>>>(ctx->d_firtc, ctx->d_firmaps,
-                                                                          ctx->d_firtc_base, ctx->d_fir_sched[v],
-                                                                          ctx->n_firtc, ctx->firtc_tiles, k_a, det0,
-                                                                          nd, ctx->firtc_strip, ctx->firtc_stages,
-                                                                          ctx->d_err);
+                CK(launch_pdl(k_fir_tc<false>, g, dim3(192), ctx->firtc_smem, ctx->stream, (const FirTcJob*)ctx->d_firtc,
+                              (const FirMaps*)ctx->d_firmaps, (const int*)ctx->d_firtc_base,
+                              (const int*)ctx->d_fir_sched[v], ctx->n_firtc, ctx->firtc_tiles, k_a, det0, nd,
+                              ctx->firtc_strip, ctx->firtc_stages, ctx->d_err));
             CKL();
         }
         // a3 + a4: reconstruction rate by rate with the Eq. 7-8 ladder, lowest rate first
@@ -886,11 +889,11 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     const long long w_first = k_a / W, w_end = (k_a + n) / W;   // windows completed by this push
     if (w_end > w_first && ctx->n_fin > 0) {
         dim3 grid(ctx->n_fin, nd, (unsigned)(w_end - w_first));
-        k_finalize<<<grid, 256, 0, ctx->stream>>>(ctx->d_finj, ctx->d_part,
-                                                  (long long)ctx->cfg.n_detectors * ctx->n_slots, ctx->n_slots,
-                                                  ctx->tiles_per_window, w_first, ctx->cfg.snr_threshold, ctx->d_slab,
-                                                  kWindowRing, ctx->cfg.n_detectors, ctx->M_cap, det0);
-        CKL();
+        CK(launch_pdl(k_finalize, grid, dim3(256), 0, ctx->stream, (const FinJob*)ctx->d_finj,
+                      (const Partial*)ctx->d_part, (long long)ctx->cfg.n_detectors * ctx->n_slots, ctx->n_slots,
+                      ctx->tiles_per_window, w_first, ctx->cfg.snr_threshold, ctx->d_slab, (int)kWindowRing,
+                      ctx->cfg.n_detectors, (long long)ctx->M_cap, det0));
+        ++ctx->launches;
     }
     return LLOID_OK;
 }
@@ -1537,14 +1540,14 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
     }
     {
         StageTimer tmg(ctx, 6);
-        k_gather_count<<<chunks, 1024, 0, ctx->stream>>>(ctx->d_slab, ctx->M_cap, M_used, nd, w0, (int)n_windows,
-                                                         kWindowRing, ctx->d_counts);
-        CKL();
-        k_gather_scatter<<<chunks, 1024, 0, ctx->stream>>>(ctx->d_slab, ctx->M_cap, M_used, nd, w0, (int)n_windows,
-                                                           kWindowRing, ctx->d_counts, chunks, ctx->d_bank_of,
-                                                           ctx->d_tmpl0_of, W, ctx->d_trig, ctx->trig_cap,
-                                                           ctx->d_total);
-        CKL();
+        CK(launch_pdl(k_gather_count, dim3(chunks), dim3(1024), 0, ctx->stream, (const SlabEntry*)ctx->d_slab,
+                      (long long)ctx->M_cap, M_used, nd, (long long)w0, (int)n_windows, (int)kWindowRing,
+                      ctx->d_counts));
+        CK(launch_pdl(k_gather_scatter, dim3(chunks), dim3(1024), 0, ctx->stream, (const SlabEntry*)ctx->d_slab,
+                      (long long)ctx->M_cap, M_used, nd, (long long)w0, (int)n_windows, (int)kWindowRing,
+                      (const int*)ctx->d_counts, chunks, (const int*)ctx->d_bank_of, (const int*)ctx->d_tmpl0_of,
+                      W, ctx->d_trig, ctx->trig_cap, ctx->d_total));
+        ctx->launches += 2;
     }
     CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
