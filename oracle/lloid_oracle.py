@@ -23,6 +23,10 @@ What it computes (every array is float64, every step written out plainly):
     threshold, its time and phase, and the per-bank maximum (Section II.D.1).
 (D) ``svd_bank``         -- per-slice SVD of the real/imaginary-stacked
     templates keeping 99.99 % of the slice energy (Eq. 3).
+(E) ``autocorrelation`` and ``xi2`` -- the signal-consistency statistic of
+    Eq. 10 (Section II.D.2) for each trigger:
+      xi2 = sum_{t=-d}^{d} |z[k+t] - z[k] R(t)|^2 / sum_{t=-d}^{d} (2 - 2 |R(t)|^2),
+    R the template's complex autocorrelation with R(0) = 1.
 
 Readings of points the paper leaves open (each is also listed in the design doc):
 * discrete unit-variance form of Eq. 1 (no factor 2): E|z|^2 = 2 in white
@@ -38,11 +42,17 @@ Readings of points the paper leaves open (each is also listed in the design doc):
   renormalised (g[c] = 1 makes it interpolating);
 * the ladder is the bank's distinct slice rates plus f0;
 * triggers: windows [max(0, wW - overlap), (w + 1) W), "exceeds" is strict,
-  ties go to the earliest sample, the bank maximum to the lowest template.
+  ties go to the earliest sample, the bank maximum to the lowest template;
+* Eq. 10: R(t) = sum_j hbar[j] conj(hbar[j - t]) / sum_j |hbar[j]|^2 (the
+  complex template's autocorrelation, so that a noise-free signal gives
+  z[k + t] = z[k] R(t) and white noise gives E xi2 = 1 under the E|z|^2 = 2
+  normalisation the denominator 2 - 2|R|^2 implies); the sums run over the
+  full autocorrelation length 2 d + 1 centred on the peak, and z before the
+  start of the stream is 0.
 
-Parity status: (A), Eq. 4, Eq. 7-8, the reconstruction and the trigger rules
-are pinned by closed forms, special cases and brute force in
-``tests/test_oracle_pins.py``.  (B) as an approximation of (A) has no exact
+Parity status: (A), Eq. 4, Eq. 7-8, the reconstruction, the trigger rules and
+Eq. 10 are pinned by closed forms, special cases, invariants and brute force
+in ``tests/test_oracle_pins.py``.  (B) as an approximation of (A) has no exact
 pin in the paper: it is held to 1 % relative SNR at injections (parity
 unpinned beyond that tolerance).
 """
@@ -343,3 +353,38 @@ def triggers(z_rows: np.ndarray, window: int, overlap: int = 0, threshold: float
                 out.append(Trigger(detector, bank, i, w, kk + t_offset, math.sqrt(best[i]),
                                    math.atan2(im[i, kk], re[i, kk]), re[i, kk], im[i, kk], i == top))
     return out
+
+
+# ----------------------------------------------------------------------------
+# (E) signal-based consistency, Eq. 10 (Section II.D.2)
+# ----------------------------------------------------------------------------
+
+def autocorrelation(h_c: np.ndarray, h_s: np.ndarray, half: int) -> np.ndarray:
+    """R(t) for t = -half .. half (index t + half): the complex template
+    hbar = h_c + i h_s correlated with itself,
+    R(t) = sum_j hbar[j] conj(hbar[j - t]) / sum_j |hbar[j]|^2, hbar = 0
+    outside its samples; R(0) = 1."""
+    h = np.asarray(h_c, dtype=np.float64) + 1j * np.asarray(h_s, dtype=np.float64)
+    n = h.size
+    norm = float(np.sum(np.abs(h) ** 2))
+    out = np.empty(2 * half + 1, dtype=np.complex128)
+    for t in range(-half, half + 1):
+        # pairs (j, j - t) with both inside [0, n)
+        lo, hi = max(0, t), min(n, n + t)
+        out[t + half] = np.sum(h[lo:hi] * np.conj(h[lo - t:hi - t])) / norm if hi > lo else 0.0
+    return out
+
+
+def xi2(z: np.ndarray, k: int, R: np.ndarray) -> float:
+    """Eq. 10 at a peak: z is one template's complex SNR series (index =
+    sample), k the peak sample, R its autocorrelation for t = -d .. d.  Samples
+    before the start of the series are 0; the series must reach k + d."""
+    half = (R.size - 1) // 2
+    if k + half >= z.size:
+        raise ValueError("the series does not reach k + d")
+    num = 0.0
+    for t in range(-half, half + 1):
+        zt = z[k + t] if k + t >= 0 else 0.0
+        num += abs(zt - z[k] * R[t + half]) ** 2
+    den = float(np.sum(2.0 - 2.0 * np.abs(R) ** 2))
+    return num / den

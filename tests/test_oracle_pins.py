@@ -302,3 +302,63 @@ def test_triggers_hand_built():
     tr = O.triggers(z, W_, overlap=2, threshold=4.0)
     w1 = [(t.tmpl, t.sample) for t in tr if t.window == 1]
     assert w1 == [(0, 6), (1, 12), (2, 7)]
+
+
+# --------------------------------------------------------------------------
+# Eq. 10: autocorrelation and the signal-consistency statistic
+# --------------------------------------------------------------------------
+
+def test_autocorrelation_against_library_correlate(bank64):
+    """R(0) = 1, R(-t) = conj R(t), and R equals numpy's full correlation of
+    the complex template normalised at lag 0 (an independent route)."""
+    rows = bank64[0].full()
+    for i in (0, 33, 63):
+        h = rows[2 * i] + 1j * rows[2 * i + 1]
+        R = O.autocorrelation(rows[2 * i], rows[2 * i + 1], 175)
+        assert abs(R[175] - 1.0) < 1e-14
+        assert np.max(np.abs(R[::-1] - np.conj(R))) < 1e-14
+        c = np.correlate(h, h, mode="full")          # c[n - 1 + t] = sum_j h[j + t] conj(h[j])
+        n = h.size
+        ref = c[n - 1 - 175:n + 175] / c[n - 1]
+        assert np.max(np.abs(R - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("i,amp,phase", [(0, 12.0, 0.3), (40, 20.0, 2.0)])
+def test_xi2_noise_free_signal_is_consistent(bank64, i, amp, phase):
+    """A noise-free injection of the template itself gives z[k + t] = z[k] R(t)
+    up to the template's tiny non-analytic part: xi2 ~ 0; the same data seen
+    through another template gives a large xi2."""
+    b = bank64[0]
+    rows = b.full()
+    T = 32 * F0
+    d = np.zeros(T)
+    W.add_injection(d, b, W.Injection(i, 20 * F0, amp, phase))
+    z = O.brute_force_snr(d, rows[2 * i:2 * i + 2])
+    zc = z[0] + 1j * z[1]
+    k = int(np.argmax(np.abs(zc)))
+    assert k == 20 * F0
+    assert O.xi2(zc, k, O.autocorrelation(rows[2 * i], rows[2 * i + 1], 350)) < 1e-6
+    j = (i + 7) % 64
+    zj = O.brute_force_snr(d, rows[2 * j:2 * j + 2])
+    zj = zj[0] + 1j * zj[1]
+    kj = int(np.argmax(np.abs(zj)))
+    assert O.xi2(zj, kj, O.autocorrelation(rows[2 * j], rows[2 * j + 1], 350)) > 0.5
+
+
+def test_xi2_white_noise_mean_is_one(bank64):
+    """In white noise E|z(t) - z(0) R(t)|^2 = 2 - 2|R(t)|^2 at any sample, so
+    the mean of xi2 over many positions is 1 (within 4 standard errors)."""
+    b = bank64[0]
+    rows = b.full()
+    rng = np.random.default_rng(5)
+    T = 32 * F0
+    d = rng.standard_normal(T)
+    i = 10
+    z = O.brute_force_snr(d, rows[2 * i:2 * i + 2])
+    zc = z[0] + 1j * z[1]
+    R = O.autocorrelation(rows[2 * i], rows[2 * i + 1], 350)
+    v = np.array([O.xi2(zc, int(k), R) for k in rng.integers(9000, T - 400, 400)])
+    assert abs(v.mean() - 1.0) < 4 * v.std() / np.sqrt(v.size)
+    # doubling the data quadruples xi2 (numerator quadratic in z, denominator fixed)
+    k = 12345
+    assert abs(O.xi2(2 * zc, k, R) - 4 * O.xi2(zc, k, R)) < 1e-12 * O.xi2(zc, k, R) + 1e-15
