@@ -120,6 +120,17 @@ typedef struct {
     int32_t n_templates;       /* M (>= 1) */
     int32_t n_slices;          /* S (>= 1) */
     const lloid_slice* slices; /* host, [n_slices], any order, non-overlapping */
+    /* Signal-consistency test (Eq. 10, Section II.D.2), optional: with
+     * ac_half = d > 0 every trigger of the bank gets
+     *   xi2 = sum_{t=-d}^{d} |z(k*+t) - z(k*) R(t)|^2 / sum_{t=-d}^{d} (2 - 2|R(t)|^2)
+     * around its peak k*, where R is the template's complex autocorrelation
+     * normalised to R(0) = 1 (the paper uses 2 d + 1 = 351 or 701 samples).
+     * Windows of such a bank can be pulled once every detector's stream has
+     * passed the window's end by d samples.  ac_half = 0: no xi2 (autocorr
+     * unused). */
+    int32_t ac_half;           /* d, 0 .. 2048 */
+    int32_t pad1;
+    const double* autocorr;    /* host, [M][2 d + 1][2]: Re, Im of R_i(t), t = -d .. d */
 } lloid_bank_desc;
 
 /* A trigger (Section II.D.1): template `tmpl` of bank `bank` in detector
@@ -137,6 +148,8 @@ typedef struct {
     float phase;
     float re;
     float im;
+    float xi2;                 /* Eq. 10 statistic; < 0 when the bank has no autocorrelation */
+    int32_t pad;
 } lloid_trigger;
 
 /* Fill *cfg with the defaults above (n_detectors = 1, max_block = 16384,

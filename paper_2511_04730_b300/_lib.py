@@ -39,7 +39,8 @@ class LloidSlice(ctypes.Structure):
 
 class LloidBankDesc(ctypes.Structure):
     _fields_ = [("n_templates", ctypes.c_int32), ("n_slices", ctypes.c_int32),
-                ("slices", ctypes.POINTER(LloidSlice))]
+                ("slices", ctypes.POINTER(LloidSlice)), ("ac_half", ctypes.c_int32), ("pad1", ctypes.c_int32),
+                ("autocorr", ctypes.POINTER(ctypes.c_double))]
 
 
 class LloidTrigger(ctypes.Structure):
@@ -47,6 +48,7 @@ class LloidTrigger(ctypes.Structure):
         ("detector", ctypes.c_int32), ("bank", ctypes.c_int32), ("tmpl", ctypes.c_int32),
         ("is_bank_max", ctypes.c_int32), ("window", ctypes.c_int64), ("sample", ctypes.c_int64),
         ("snr", ctypes.c_float), ("phase", ctypes.c_float), ("re", ctypes.c_float), ("im", ctypes.c_float),
+        ("xi2", ctypes.c_float), ("pad", ctypes.c_int32),
     ]
 
 

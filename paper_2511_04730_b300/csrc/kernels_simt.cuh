@@ -318,6 +318,17 @@ __global__ void __launch_bounds__(256) k_recon_f32(const ReconJob* __restrict__ 
                     zout[(long long)(2 * m + 1) * n + t0 + lane * 4 + q] = aim[i][q];
                 }
             }
+            if (jb.zring != nullptr) {   // Eq. 10 history: 4 samples of z as half2, one 16-byte store
+                uint32_t h[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __half2 v = __floats2half2_rn(are[i][q], aim[i][q]);
+                    h[q] = *reinterpret_cast<const uint32_t*>(&v);
+                }
+                const long long pos = (k_a + t0 + lane * 4) & (jb.zring_len - 1);
+                *reinterpret_cast<uint4*>(jb.zring + det * jb.zring_det_stride + (long long)m * jb.zring_len + pos) =
+                    make_uint4(h[0], h[1], h[2], h[3]);
+            }
         }
     }
 }
@@ -358,6 +369,8 @@ __global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ job
         e.im = bim;
         e.k_off = bk;
         e.flags = (e.snr > threshold) ? 1 : 0;
+        e.xi2 = -1.f;
+        e.pad = 0;
         out[jb.tmpl0 + m] = e;
         if (best > tbest || (best == tbest && m < tidx)) { tbest = best; tidx = m; }
     }
@@ -388,6 +401,8 @@ struct TriggerOut {       // identical layout to lloid_trigger
     int32_t detector, bank, tmpl, is_bank_max;
     long long window, sample;
     float snr, phase, re, im;
+    float xi2;
+    int32_t pad;
 };
 
 // Entries e = (wl * n_det + det) * M_used + m for windows w0 .. w0 + n_win - 1.
@@ -470,9 +485,58 @@ __global__ void k_gather_scatter(const SlabEntry* __restrict__ slab, long long c
             o.window = window;
             o.sample = window * W + en.k_off;
             o.snr = en.snr; o.phase = en.phase; o.re = en.re; o.im = en.im;
+            o.xi2 = en.xi2;
+            o.pad = 0;
             out[pos] = o;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 10 for the triggers of windows w0 .. w0 + gridDim.z - 1 of one detector:
+// one warp per (template, window); the lanes stride t = -d .. d.
+// xi2 = sum_t |z[k* + t] - z[k*] R(t)|^2 / sum_t (2 - 2 |R(t)|^2), with z from
+// the bank's half2 ring (samples before the stream start read as 0).
+// grid (tiles of 8 templates over all jobs, 1, windows), 256 threads.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_xi2(const Xi2Job* __restrict__ jobs, const int* __restrict__ tile_base,
+                                             int n_jobs, long long w0, long long W, int det,
+                                             SlabEntry* __restrict__ slab_base, int ring, int n_det_total,
+                                             long long slab_det_stride) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int t = blockIdx.x;
+    const int jx = find_job(tile_base, n_jobs, t);
+    const Xi2Job& jb = jobs[jx];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = (t - tile_base[jx]) * 8 + warp;
+    if (m >= jb.M) return;
+    const long long w = w0 + blockIdx.z;
+    SlabEntry* e = slab_base + (size_t)(w % ring) * n_det_total * slab_det_stride + det * slab_det_stride +
+                   jb.tmpl0 + m;
+    if ((e->flags & 1) == 0) return;
+    const long long k = w * W + e->k_off;
+    const float zr0 = e->re, zi0 = e->im;
+    const uint32_t* zr = jb.zring + det * jb.zdet_stride + (long long)m * jb.zlen;
+    const float2* R = jb.ac + (long long)m * (2 * jb.half + 1);
+    float acc = 0.f;
+    for (int tt = lane; tt <= 2 * jb.half; tt += 32) {
+        const long long s = k + tt - jb.half;
+        float zx = 0.f, zy = 0.f;
+        if (s >= 0) {
+            const uint32_t u = zr[s & (jb.zlen - 1)];
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+            zx = f.x;
+            zy = f.y;
+        }
+        const float2 r = R[tt];
+        const float ex = zx - (zr0 * r.x - zi0 * r.y);
+        const float ey = zy - (zr0 * r.y + zi0 * r.x);
+        acc = fmaf(ex, ex, fmaf(ey, ey, acc));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) e->xi2 = acc / jb.den[m];
 }
 
 }  // namespace lloid

@@ -65,6 +65,9 @@ struct LevelJob {
     int F, D_lo, Lambda_lo;        // factor to the level below (0: lowest level)
     int y_rows;                    // level ring rows
     int map;                       // index into the level tensor-map array
+    uint32_t* zring;               // top level of an Eq. 10 bank: [det][Mpad][zring_len] z as half2, else null
+    long long zring_det_stride;
+    int zring_len;
 };
 
 struct FirMaps { CUtensorMap a, a_lo; };
@@ -596,6 +599,19 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                         float* zi = zr + n;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) { zr[j] = re[j]; zi[j] = im[j]; }
+                    }
+                    if (jb.zring != nullptr) {   // Eq. 10 history: z as half2, four 16-byte stores
+                        uint32_t h[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const __half2 v = __floats2half2_rn(re[j], im[j]);
+                            h[j] = *reinterpret_cast<const uint32_t*>(&v);
+                        }
+                        const long long pos = (Q0 + 128LL * tt + c) & (jb.zring_len - 1);
+                        uint4* dst = reinterpret_cast<uint4*>(jb.zring + det * jb.zring_det_stride +
+                                                              (long long)m * jb.zring_len + pos);
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) dst[g] = make_uint4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
                     }
                 }
             } else {

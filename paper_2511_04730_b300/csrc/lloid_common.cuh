@@ -84,6 +84,9 @@ struct ReconJob {
     int Kpad, Mpad, M;
     int tmpl0;                   // first global template id of the bank
     int tiles_m, tiles_t;
+    uint32_t* zring;             // Eq. 10 banks: [det][Mpad][zring_len] z as half2, else null
+    long long zring_det_stride;
+    int zring_len;
 };
 
 // Per (template, detector, time tile) partial maximum of |z|^2.
@@ -95,6 +98,19 @@ struct SlabEntry {
     float snr, phase, re, im;
     int32_t k_off;               // sample - window start
     int32_t flags;               // bit 0 valid (|z| > threshold), bit 1 bank max
+    float xi2;                   // Eq. 10, < 0 until computed (or without autocorrelation)
+    int32_t pad;
+};
+
+// Eq. 10 for one bank: its templates' autocorrelations and the ring of its
+// recent SNR samples (written by the top-level reconstruction).
+struct Xi2Job {
+    int tmpl0, M, half;          // first global template id, templates, d
+    const float2* ac;            // [M][2 d + 1] R_i(t)
+    const float* den;            // [M] sum_t (2 - 2 |R_i(t)|^2)
+    const uint32_t* zring;       // [det][Mpad][zlen] z as packed half2 (re low, im high)
+    long long zdet_stride;       // elements
+    int zlen;                    // power of two
 };
 
 struct FinJob {

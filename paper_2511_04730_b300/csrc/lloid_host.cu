@@ -88,6 +88,12 @@ struct BankRT {
     void* d_yhat = nullptr;      // [n_det][Kpad][max_block]
     void* d_yhat_lo = nullptr;
     long long yhat_det_stride = 0;
+    // Eq. 10: autocorrelations R_i(t) [Mpad][2 d + 1], their denominators, and the
+    // ring of recent z samples [det][Mpad][zlen] (half2) the reconstruction writes
+    int ac_half = 0, zlen = 0;
+    float2* d_ac = nullptr;
+    float* d_ac_den = nullptr;
+    uint32_t* d_zring = nullptr;
     size_t bytes = 0;
     std::vector<void*> allocs;
 };
@@ -169,6 +175,10 @@ struct lloid_ctx {
     int max_depth = 0;
     std::vector<int> top_job_of_bank;  // bank id -> index in its top-level table
     std::vector<int> top_slot_of_bank; // bank id -> F slot of its top level (split path)
+    // Eq. 10 table: tiles of 8 templates over the banks with autocorrelations
+    Xi2Job* d_xi2 = nullptr; int* d_xi2_base = nullptr; int n_xi2 = 0, xi2_tiles = 0;
+    int xi2_half_max = 0;              // largest d of the loaded banks (pull readiness)
+    std::vector<long long> xi2_next;   // per detector: first window whose xi2 is not computed yet
     uint16_t* d_u_hi[kFSlots] = {};    // Eq. 8 tile matrices per F slot (hi, lo halves)
     uint16_t* d_u_lo[kFSlots] = {};
     // split path streams: index 0 = f0, index r + 1 = rate_D[r]; hi/lo halves, double-mapped
@@ -363,6 +373,7 @@ void free_jobs(lloid_ctx* ctx) {
     }
     ctx->d_fir_sched[0] = ctx->d_fir_sched[1] = nullptr;
     ctx->n_firtc = ctx->firtc_tiles = 0;
+    ctx->d_xi2 = nullptr; ctx->d_xi2_base = nullptr; ctx->n_xi2 = ctx->xi2_tiles = 0;
 }
 
 template <typename T>
@@ -548,6 +559,9 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                 q.acc_out = L.d_accp; q.acc_out_det_stride = 4LL * b->Mpad * L.acc_cols; q.acc_cols = L.acc_cols;
             }
             q.Kp = L.Kp; q.M = b->M; q.Mpad = b->Mpad; q.tmpl0 = b->tmpl0;
+            if (depth == 0 && b->d_zring) {
+                q.zring = b->d_zring; q.zring_det_stride = (long long)b->Mpad * b->zlen; q.zring_len = b->zlen;
+            }
             q.tiles_m = b->Mpad / kTcTileM;
             if (depth == 0) q.tiles_t = (int)(n / kTcTileN);
             else q.tiles_t = (int)((((n - 1 + 2LL * L.Lambda) / L.D + 2) + 127 + 127) / 128);
@@ -649,6 +663,22 @@ lloid_status build_jobs(lloid_ctx* ctx, long long n) {
     lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_finj, fin))) return st;
     ctx->n_fin = (int)fin.size();
+    {   // Eq. 10: one tile per 8 templates of every bank with autocorrelations
+        std::vector<Xi2Job> xj;
+        std::vector<int> xb;
+        int xt = 0;
+        for (auto& kv : ctx->banks) {
+            const BankRT* b = kv.second;
+            if (b->ac_half <= 0) continue;
+            Xi2Job x{};
+            x.tmpl0 = b->tmpl0; x.M = b->M; x.half = b->ac_half; x.ac = b->d_ac; x.den = b->d_ac_den;
+            x.zring = b->d_zring; x.zdet_stride = (long long)b->Mpad * b->zlen; x.zlen = b->zlen;
+            xj.push_back(x); xb.push_back(xt); xt += (b->M + 7) / 8;
+        }
+        if ((st = upload_vec(ctx, &ctx->d_xi2, xj)) || (st = upload_vec(ctx, &ctx->d_xi2_base, xb))) return st;
+        ctx->n_xi2 = (int)xj.size();
+        ctx->xi2_tiles = xt;
+    }
     if (split_precision(ctx)) {
         if ((st = build_jobs_split(ctx, n))) return st;
         CK(cudaStreamSynchronize(ctx->stream));
@@ -699,6 +729,7 @@ lloid_status build_jobs(lloid_ctx* ctx, long long n) {
         r.Kpad = b->Kpad; r.Mpad = b->Mpad; r.M = b->M; r.tmpl0 = b->tmpl0;
         r.tiles_m = b->Mpad / 64;
         r.tiles_t = (int)(n / 128);
+        r.zring = b->d_zring; r.zring_det_stride = (long long)b->Mpad * b->zlen; r.zring_len = b->zlen;
         ctx->top_job_of_bank[b->id] = (int)rj.size();
         rj.push_back(r); rb.push_back(rt); rt += r.tiles_m * r.tiles_t;
     }
@@ -895,6 +926,19 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
                       ctx->cfg.n_detectors, (long long)ctx->M_cap, det0));
         ++ctx->launches;
     }
+    // Eq. 10 for the windows whose triggers now have d samples of z past the window end
+    if (ctx->n_xi2 > 0) {
+        const long long w_ready = (k_a + n - ctx->xi2_half_max) / W;   // windows < w_ready are ready
+        for (int d = det0; d < det0 + nd; ++d) {
+            long long w_lo = std::max(ctx->xi2_next[d], w_ready - (long long)kWindowRing);
+            if (w_ready <= w_lo) continue;
+            CK(launch_pdl(k_xi2, dim3(ctx->xi2_tiles, 1, (unsigned)(w_ready - w_lo)), dim3(256), 0, ctx->stream,
+                          (const Xi2Job*)ctx->d_xi2, (const int*)ctx->d_xi2_base, ctx->n_xi2, w_lo, W, d,
+                          ctx->d_slab, (int)kWindowRing, ctx->cfg.n_detectors, (long long)ctx->M_cap));
+            ++ctx->launches;
+            ctx->xi2_next[d] = w_ready;
+        }
+    }
     return LLOID_OK;
 }
 
@@ -1066,11 +1110,14 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
     const int nd = c.n_detectors;
     hdr->clear();
     seg->clear();
-    long long h[] = {0x4C4C4F4944535431LL, 1, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
+    long long h[] = {0x4C4C4F4944535431LL, 2, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
                      c.max_block, c.max_history, c.min_rate, (long long)ctx->banks.size(), ctx->M_used,
                      ctx->M_cap, ctx->n_slots};
     hdr->assign(h, h + sizeof h / sizeof h[0]);
-    for (int d = 0; d < nd; ++d) { hdr->push_back(ctx->pos[d]); hdr->push_back(ctx->fin[d]); hdr->push_back(ctx->last_n[d]); }
+    for (int d = 0; d < nd; ++d) {
+        hdr->push_back(ctx->pos[d]); hdr->push_back(ctx->fin[d]); hdr->push_back(ctx->last_n[d]);
+        hdr->push_back(ctx->xi2_next[d]);
+    }
     seg->push_back({ctx->ring0, (size_t)nd * ctx->ring0_len * 4});
     for (int r = 0; r < ctx->n_rates; ++r) seg->push_back({ctx->rate_ring[r], (size_t)nd * ctx->rate_len[r] * 4});
     for (int r = 0; r <= kMaxRates; ++r)
@@ -1083,6 +1130,8 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
     for (auto& kv : ctx->banks) {
         const BankRT* b = kv.second;
         hdr->push_back(kv.first); hdr->push_back(b->M); hdr->push_back(b->tmpl0); hdr->push_back((long long)b->sl.size());
+        hdr->push_back(b->ac_half);
+        if (b->d_zring) seg->push_back({b->d_zring, (size_t)nd * b->Mpad * b->zlen * 4});
         for (const auto& sl : b->sl) {
             hdr->push_back(sl.rate); hdr->push_back(sl.J); hdr->push_back(sl.N); hdr->push_back(sl.L);
             if (sl.d_yring) seg->push_back({sl.d_yring, (size_t)nd * sl.L * sl.y_len * 4});
@@ -1259,6 +1308,7 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
     }
     ctx->pos.assign(nd, 0);
     ctx->fin.assign(nd, -1);
+    ctx->xi2_next.assign(nd, 0);
     for (int i = 0; i < 64; ++i) ctx->last_n[i] = 0;
     if ((st = dalloc(ctx, &ctx->d_stage, (size_t)nd * c.max_block * 4, nullptr, &ctx->state_bytes))) return st;
     for (int i = 0; i < 2; ++i) {
@@ -1340,6 +1390,8 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
             long long ya = y.j_start, yb = y.j_start + (long long)y.n_taps * (c.f0 / y.rate);
             if (xa < yb && ya < xb) return fail(ctx, LLOID_EINVAL, "slices %d and %d overlap", a, b);
         }
+    if (bd->ac_half < 0 || bd->ac_half > 2048 || (bd->ac_half > 0 && !bd->autocorr))
+        return fail(ctx, LLOID_EINVAL, "ac_half %d must be in 0..2048 with autocorr given", bd->ac_half);
     // ---- ladder: distinct rates plus f0, ascending
     std::vector<int> ladder = rates;
     ladder.push_back(c.f0);
@@ -1393,6 +1445,12 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
         cleanup();
         return st;
     }
+    b->ac_half = bd->ac_half;
+    if (b->ac_half > 0) {
+        b->zlen = (int)next_pow2(c.max_block + c.window_samples + 2LL * b->ac_half + 256);
+        need += (size_t)b->Mpad * (2 * b->ac_half + 1) * sizeof(float2) + (size_t)b->Mpad * 4 +
+                (size_t)nd * b->Mpad * b->zlen * 4;
+    }
     if (c.hbm_budget_bytes && ctx->state_bytes + ctx->bank_bytes + need > c.hbm_budget_bytes) {
         cleanup();
         return fail(ctx, LLOID_EBUDGET, "bank needs %zu bytes; %zu of %zu in use", need,
@@ -1435,6 +1493,34 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
         b->yhat_det_stride = (long long)b->Kpad * c.max_block;
         if ((st = dalloc(ctx, (char**)&b->d_yhat, (size_t)nd * b->yhat_det_stride * 4, &b->allocs, &b->bytes))) { cleanup(); return st; }
     }
+    // ---- Eq. 10 tables and the z ring (zeroed: samples before the stream start are 0)
+    if (b->ac_half > 0) {
+        const int na = 2 * b->ac_half + 1;
+        std::vector<float2> ac((size_t)b->Mpad * na, make_float2(0.f, 0.f));
+        std::vector<float> den(b->Mpad, 1.f);
+        for (int i = 0; i < M; ++i) {
+            double sden = 0.0;
+            for (int t = 0; t < na; ++t) {
+                const double re = bd->autocorr[((size_t)i * na + t) * 2], im = bd->autocorr[((size_t)i * na + t) * 2 + 1];
+                ac[(size_t)i * na + t] = make_float2((float)re, (float)im);
+                sden += 2.0 - 2.0 * (re * re + im * im);
+            }
+            if (!(sden > 0.0)) {
+                cleanup();
+                return fail(ctx, LLOID_EINVAL, "template %d: sum of 2 - 2|R|^2 is not positive", i);
+            }
+            den[i] = (float)sden;
+        }
+        if ((st = dalloc(ctx, &b->d_ac, ac.size() * sizeof(float2), &b->allocs, &b->bytes)) ||
+            (st = dalloc(ctx, &b->d_ac_den, den.size() * 4, &b->allocs, &b->bytes)) ||
+            (st = dalloc(ctx, &b->d_zring, (size_t)nd * b->Mpad * b->zlen * 4, &b->allocs, &b->bytes))) {
+            cleanup();
+            return st;
+        }
+        CK(cudaMemcpyAsync(b->d_ac, ac.data(), ac.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(b->d_ac_den, den.data(), den.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     // ---- template ids, window state
     b->tmpl0 = ctx->M_used;
     if ((st = ensure_template_capacity(ctx, (long long)ctx->M_used + M))) { cleanup(); return st; }
@@ -1460,6 +1546,7 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
     *bank_id = id;
     ctx->banks[id] = b.release();
     ctx->jobs_dirty = true;
+    ctx->xi2_half_max = std::max(ctx->xi2_half_max, bd->ac_half);
     return LLOID_OK;
 }
 
@@ -1478,6 +1565,8 @@ lloid_status lloid_unload_bank(lloid_ctx* ctx, int32_t bank_id) {
     delete it->second;
     ctx->banks.erase(it);
     ctx->jobs_dirty = true;
+    ctx->xi2_half_max = 0;
+    for (auto& kv : ctx->banks) ctx->xi2_half_max = std::max(ctx->xi2_half_max, kv.second->ac_half);
     return LLOID_OK;
 }
 
@@ -1504,6 +1593,12 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
     long long fin_min = ctx->fin[0], fin_max = ctx->fin[0];
     for (long long f : ctx->fin) { fin_min = std::min(fin_min, f); fin_max = std::max(fin_max, f); }
     if (w1 > fin_min) return fail(ctx, LLOID_ENOTREADY, "window %lld needs data through sample %lld", w1, (w1 + 1) * W);
+    if (ctx->xi2_half_max > 0) {   // Eq. 10 needs d samples of z past the window's end
+        for (int d = 0; d < ctx->cfg.n_detectors; ++d)
+            if (w1 >= ctx->xi2_next[d])
+                return fail(ctx, LLOID_ENOTREADY, "window %lld needs data through sample %lld for xi2", w1,
+                            (w1 + 1) * W + ctx->xi2_half_max);
+    }
     if (w0 + kWindowRing <= fin_max) return fail(ctx, LLOID_EEXPIRED, "window %lld is no longer retained", (long long)w0);
     const int nd = ctx->cfg.n_detectors;
     const int M_used = ctx->M_used;
@@ -1662,7 +1757,7 @@ lloid_status lloid_restore_state(lloid_ctx* ctx, const void* buf, size_t len) {
     std::vector<long long> saved((size_t)nh);
     std::memcpy(saved.data(), in + sizeof nh, (size_t)nh * sizeof(long long));
     const int nd = ctx->cfg.n_detectors;
-    const size_t pos_at = 15, pos_end = 15 + 3 * (size_t)nd;
+    const size_t pos_at = 15, pos_end = 15 + 4 * (size_t)nd;
     for (size_t i = 0; i < hdr.size(); ++i) {
         if (i >= pos_at && i < pos_end) continue;
         if (saved[i] != hdr[i]) return fail(ctx, LLOID_EINVAL, "checkpoint does not match this context (word %zu)", i);
@@ -1676,9 +1771,10 @@ lloid_status lloid_restore_state(lloid_ctx* ctx, const void* buf, size_t len) {
         o += x.bytes;
     }
     for (int d = 0; d < nd; ++d) {
-        ctx->pos[d] = saved[pos_at + 3 * d];
-        ctx->fin[d] = saved[pos_at + 3 * d + 1];
-        ctx->last_n[d] = saved[pos_at + 3 * d + 2];
+        ctx->pos[d] = saved[pos_at + 4 * d];
+        ctx->fin[d] = saved[pos_at + 4 * d + 1];
+        ctx->last_n[d] = saved[pos_at + 4 * d + 2];
+        ctx->xi2_next[d] = saved[pos_at + 4 * d + 3];
     }
     CK(cudaEventRecord(ctx->done_ev, ctx->stream));
     return LLOID_OK;

@@ -38,6 +38,8 @@ struct TrigOut {   // the layout of lloid_trigger
     int32_t detector, bank, tmpl, is_bank_max;
     long long window, sample;
     float snr, phase, re, im;
+    float xi2;
+    int32_t pad;
 };
 
 // Pair p = wl * M + i: the maximum of |z_i|^2 over window wl (earliest sample on ties).
@@ -131,6 +133,8 @@ __global__ void k_na_scatter(const float4* __restrict__ pairs, long long n_pairs
     o.window = w0 + wl;
     o.sample = (w0 + wl) * W + __float_as_int(e.y);
     o.snr = sqrtf(e.x); o.phase = atan2f(e.w, e.z); o.re = e.z; o.im = e.w;
+    o.xi2 = -1.f;      // no autocorrelation on this path
+    o.pad = 0;
     out[pos] = o;
 }
 

@@ -16,7 +16,7 @@ from . import _lib
 TRIGGER_DTYPE = np.dtype([
     ("detector", np.int32), ("bank", np.int32), ("tmpl", np.int32), ("is_bank_max", np.int32),
     ("window", np.int64), ("sample", np.int64), ("snr", np.float32), ("phase", np.float32),
-    ("re", np.float32), ("im", np.float32),
+    ("re", np.float32), ("im", np.float32), ("xi2", np.float32), ("pad", np.int32),
 ])
 assert TRIGGER_DTYPE.itemsize == ctypes.sizeof(_lib.LloidTrigger)
 
@@ -90,9 +90,11 @@ class Context:
         self.close()
 
     # -- banks ----------------------------------------------------------------
-    def load_bank(self, slices: Iterable) -> int:
+    def load_bank(self, slices: Iterable, autocorr=None) -> int:
         """Load an SVD bank given as objects with rate, j_start, bases [L, N]
-        and coeffs [2M, L] (float64).  Returns the bank id."""
+        and coeffs [2M, L] (float64); optional autocorr [M, 2d + 1] complex
+        (R_i(t), t = -d .. d) enables the Eq. 10 statistic for its triggers.
+        Returns the bank id."""
         slices = list(slices)
         keep = []
         arr = (_lib.LloidSlice * len(slices))()
@@ -110,6 +112,14 @@ class Context:
             if c.shape != (n_rows, b.shape[0]):
                 raise ValueError("coeffs must be [2M, L] with one 2M for the bank")
         desc = _lib.LloidBankDesc(n_rows // 2, len(slices), arr)
+        if autocorr is not None:
+            ac = np.asarray(autocorr, dtype=np.complex128)
+            if ac.ndim != 2 or ac.shape[0] != n_rows // 2 or ac.shape[1] % 2 != 1:
+                raise ValueError("autocorr must be [M, 2d + 1] complex")
+            acf = np.ascontiguousarray(ac.view(np.float64).reshape(ac.shape[0], ac.shape[1], 2))
+            keep.append(acf)
+            desc.ac_half = (ac.shape[1] - 1) // 2
+            desc.autocorr = acf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         bid = ctypes.c_int32()
         self._check(self._lib.lloid_load_bank(self._h, ctypes.byref(desc), ctypes.byref(bid)))
         self.banks[bid.value] = n_rows // 2

@@ -87,3 +87,24 @@ def build_svd_bank(bank, plan, energy: float = 0.9999, max_basis: Optional[int] 
             continue
         out.append(SliceArrays(int(rate), int(J), np.ascontiguousarray(bases), np.ascontiguousarray(coeffs), kept))
     return out
+
+
+def template_autocorrelation(bank, half: int, chunk: int = 16) -> np.ndarray:
+    """R_i(t), t = -half .. half, of every template of a ``workloads.ChirpBank``
+    (Eq. 10): the complex template hbar = h_c + i h_s correlated with itself
+    through FFTs, R(t) = sum_j hbar[j] conj(hbar[j - t]) / sum_j |hbar[j]|^2.
+    Returns [M, 2 half + 1] complex128."""
+    M = bank.mchirp.size
+    out = np.empty((M, 2 * half + 1), dtype=np.complex128)
+    for a in range(0, M, chunk):
+        idx = list(range(a, min(M, a + chunk)))
+        lo = int(min(bank.j_lo[i] for i in idx))
+        hi = int(max(bank.j_hi[i] for i in idx))
+        r = bank.rows(np.arange(lo, hi), idx)
+        h = r[0::2] + 1j * r[1::2]
+        n = 1 << int(math.ceil(math.log2(2 * h.shape[1] + 1)))
+        H = np.fft.fft(h, n, axis=1)
+        c = np.fft.ifft(H * np.conj(H), axis=1)           # c[t] = sum_j h[j + t] conj(h[j])
+        lags = np.arange(-half, half + 1)
+        out[a:a + len(idx)] = c[:, lags % n] / c[:, :1].real
+    return out
