@@ -23,6 +23,12 @@ What it computes (every array is float64, every step written out plainly):
     threshold, its time and phase, and the per-bank maximum (Section II.D.1).
 (D) ``svd_bank``         -- per-slice SVD of the real/imaginary-stacked
     templates keeping 99.99 % of the slice energy (Eq. 3).
+(F) ``coincident_events`` -- coincidence across detectors and clustering per
+    bank (Sections II.D.3-4): per (bank, window, template) the loudest
+    detector's trigger is the reference and every other detector's trigger
+    within the coincidence window joins it; with two or more detectors it is
+    an event of network SNR sqrt(sum rho^2); per (bank, window) only the
+    event of highest network SNR is kept.
 (E) ``autocorrelation`` and ``xi2`` -- the signal-consistency statistic of
     Eq. 10 (Section II.D.2) for each trigger:
       xi2 = sum_{t=-d}^{d} |z[k+t] - z[k] R(t)|^2 / sum_{t=-d}^{d} (2 - 2 |R(t)|^2),
@@ -43,6 +49,11 @@ Readings of points the paper leaves open (each is also listed in the design doc):
 * the ladder is the bank's distinct slice rates plus f0;
 * triggers: windows [max(0, wW - overlap), (w + 1) W), "exceeds" is strict,
   ties go to the earliest sample, the bank maximum to the lowest template;
+* coincidence: one window (samples) for every detector pair, inclusive
+  (|k_a - k_b| <= delta); the reference is the loudest detector (lowest index
+  on ties); a coincidence needs two or more detectors; clustering keeps the
+  highest network SNR per (bank, window), lowest template on ties; windows do
+  not overlap, so triggers in different windows never coincide;
 * Eq. 10: R(t) = sum_j hbar[j] conj(hbar[j - t]) / sum_j |hbar[j]|^2 (the
   complex template's autocorrelation, so that a noise-free signal gives
   z[k + t] = z[k] R(t) and white noise gives E xi2 = 1 under the E|z|^2 = 2
@@ -388,3 +399,43 @@ def xi2(z: np.ndarray, k: int, R: np.ndarray) -> float:
         num += abs(zt - z[k] * R[t + half]) ** 2
     den = float(np.sum(2.0 - 2.0 * np.abs(R) ** 2))
     return num / den
+
+
+# ----------------------------------------------------------------------------
+# (F) coincidence and clustering, Sections II.D.3-4
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Event:
+    window: int
+    bank: int
+    tmpl: int
+    n_ifo: int
+    ifo_mask: int
+    net_snr: float
+    ref_detector: int
+    ref_sample: int
+
+
+def coincident_events(trigs: Sequence[Trigger], delta: int) -> List[Event]:
+    """Events of a trigger list (any detectors, banks, windows)."""
+    by_key = {}
+    for t in trigs:
+        by_key.setdefault((t.bank, t.window, t.tmpl), {})[t.detector] = t
+    best = {}
+    for (bank, w, i), per_det in by_key.items():
+        dets = sorted(per_det)
+        ref = dets[0]
+        for d in dets[1:]:
+            if per_det[d].snr > per_det[ref].snr:
+                ref = d
+        k0 = per_det[ref].sample
+        members = [d for d in dets if abs(per_det[d].sample - k0) <= delta]
+        if len(members) < 2:
+            continue
+        net = math.sqrt(sum(per_det[d].snr ** 2 for d in members))
+        ev = Event(w, bank, i, len(members), sum(1 << d for d in members), net, ref, k0)
+        cur = best.get((bank, w))
+        if cur is None or net > cur.net_snr or (net == cur.net_snr and i < cur.tmpl):
+            best[(bank, w)] = ev
+    return [best[k] for k in sorted(best)]

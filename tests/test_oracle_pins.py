@@ -362,3 +362,44 @@ def test_xi2_white_noise_mean_is_one(bank64):
     # doubling the data quadruples xi2 (numerator quadratic in z, denominator fixed)
     k = 12345
     assert abs(O.xi2(2 * zc, k, R) - 4 * O.xi2(zc, k, R)) < 1e-12 * O.xi2(zc, k, R) + 1e-15
+
+
+# --------------------------------------------------------------------------
+# Coincidence and clustering (Sections II.D.3-4) on hand-built trigger lists
+# --------------------------------------------------------------------------
+
+def _t(det, tmpl, w, k, snr, bank=0):
+    return O.Trigger(det, bank, tmpl, w, k, snr, 0.0, snr, 0.0, False)
+
+
+def test_coincidence_hand_built():
+    D = 66
+    trigs = [
+        # window 0, template 3: H (det 0) and L (det 1) exactly D apart -> coincident
+        _t(0, 3, 0, 1000, 6.0), _t(1, 3, 0, 1000 + D, 8.0),
+        # template 4: D + 1 apart -> not coincident, no event
+        _t(0, 4, 0, 500, 9.0), _t(1, 4, 0, 500 + D + 1, 9.5),
+        # template 5: three detectors, V (det 2) too far from the loudest (det 2 is the loudest!)
+        _t(0, 5, 0, 300, 5.0), _t(1, 5, 0, 310, 5.5), _t(2, 5, 0, 300 + 200, 7.0),
+        # window 1: only single-detector triggers -> no event
+        _t(0, 3, 1, 2100, 12.0),
+        # bank 1, window 0: two events, equal network SNR -> lowest template wins
+        _t(0, 7, 0, 100, 3.0, bank=1), _t(1, 7, 0, 101, 4.0, bank=1),
+        _t(0, 2, 0, 900, 4.0, bank=1), _t(1, 2, 0, 899, 3.0, bank=1),
+    ]
+    ev = O.coincident_events(trigs, D)
+    assert [(e.bank, e.window) for e in ev] == [(0, 0), (1, 0)]
+    e0, e1 = ev
+    # bank 0: template 3 (sqrt(36 + 64) = 10) beats template 5, whose loudest detector (V) has
+    # no partner within D (H and L are 200 / 190 samples away), so template 5 has no event
+    assert (e0.tmpl, e0.n_ifo, e0.ifo_mask, e0.ref_detector, e0.ref_sample) == (3, 2, 0b11, 1, 1000 + D)
+    assert abs(e0.net_snr - 10.0) < 1e-12
+    assert (e1.tmpl, e1.net_snr, e1.ifo_mask) == (2, 5.0, 0b11)
+
+
+def test_coincidence_of_a_loud_reference_with_three_detectors():
+    trigs = [_t(0, 1, 2, 4500, 6.0), _t(1, 1, 2, 4530, 9.0), _t(2, 1, 2, 4470, 2.0)]
+    (e,) = O.coincident_events(trigs, 66)
+    # all within 66 of the loudest (det 1 at 4530): 4500 (30), 4470 (60)
+    assert (e.n_ifo, e.ifo_mask, e.ref_detector) == (3, 0b111, 1)
+    assert abs(e.net_snr - math.sqrt(36 + 81 + 4)) < 1e-12
