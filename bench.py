@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--seconds", type=int, default=1024)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--xi2-half", type=int, default=350,
+                   help="Eq. 10 autocorrelation half-length d for the xi2 measurement (0: skip it)")
     p.add_argument("--no-fp32-compare", action="store_true")
     p.add_argument("--latency-steps", type=int, default=32)
     p.add_argument("--workload", default="bank1000", choices=["bank1000", "banks20", "banks500"])
@@ -397,8 +399,10 @@ def run_lloid(args, rank, world, dist):
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
 
-    def run_steps(ctx, k_steps, pos, host=False, lat=None):
-        """k_steps timed steps; returns (ms per step list, pos, launches, h2d, d2h)."""
+    def run_steps(ctx, k_steps, pos, host=False, lat=None, lag=0):
+        """k_steps timed steps; returns (ms per step list, pos, launches, h2d, d2h).
+        lag = 1: pull the windows that became ready (xi2 needs d samples of the
+        next block), i.e. the previous block's last window and this block's others."""
         ext = torch.cuda.ExternalStream(ctx.stream_ptr, device=f"cuda:{dev}")
         ms, h2d, d2h = [], 0, 0
         l0 = ctx.launch_count()
@@ -416,7 +420,8 @@ def run_lloid(args, rank, world, dist):
                     h2d += blk.nbytes
                 else:
                     ctx.push_all(pos, d_blocks[k])
-                tr = ctx.pull(pos // F0, n_windows=B // F0)      # the windows this block completes
+                w_lo = max(0, pos // F0 - lag)
+                tr = ctx.pull(w_lo, n_windows=(pos + B) // F0 - lag - w_lo)   # the windows this block completes
                 d2h += 8 + tr.nbytes
                 b.record(ext)
                 b.synchronize()
@@ -464,6 +469,30 @@ def run_lloid(args, rank, world, dist):
         per_ctx[prec]["stages"] = ctx.stage_times(reset=True)
         per_ctx[prec]["ms_timed_stages"] = ms_t
         ctx.close()
+
+    # Eq. 10 (a NEXT row): the same steps with autocorrelations loaded for every bank
+    xi2 = None
+    if args.xi2_half > 0:
+        from paper_2511_04730_b300.svdbank import template_autocorrelation
+        t_ac = time.perf_counter()
+        acs = [template_autocorrelation(w.banks[i], args.xi2_half) for i in mine]
+        t_ac = time.perf_counter() - t_ac
+        ctx = make_ctx(args.precision, timing=True)
+        for x, ac in zip(banks_sb, acs):
+            ctx.load_bank(x, autocorr=ac)
+        pos = 0
+        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, lag=1)
+        ctx.stage_times(reset=True)
+        torch.cuda.synchronize()
+        ms_x, pos, _, _, d2h_x = run_steps(ctx, args.steps, pos, lag=1)
+        st_x = ctx.stage_times(reset=True)
+        ctx.close()
+        units_x = M * args.block_seconds * n_det
+        xi2 = {"value": units_x * args.steps / (sum(ms_x) / 1000.0), "unit": UNIT,
+               "ms_per_step": statistics.mean(ms_x), "autocorr_samples": 2 * args.xi2_half + 1,
+               "finalize_plus_xi2_ms_per_step": round(st_x["finalize"][0] / args.steps, 4),
+               "recon_ms_per_step": round(st_x["recon"][0] / args.steps, 4),
+               "d2h_bytes_per_step": d2h_x // args.steps, "autocorr_build_s": round(t_ac, 1)}
 
     # accuracy of the measured path against the FP32 path (same stream, same blocks)
     max_dsnr = None
@@ -595,6 +624,7 @@ def run_lloid(args, rank, world, dist):
                                       "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
                                       "n": len(lat)} if lat else None),
             "stage_ms_per_step": stage_ms,
+            "xi2": xi2,
             "ms_per_step_with_stage_events": statistics.mean(main["ms_timed_stages"]),
             "kernels": recon_info,
             "paths": {p: units * args.steps / (sum(v["ms"]) / 1000.0) for p, v in per_ctx.items()},

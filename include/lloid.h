@@ -95,7 +95,9 @@ typedef struct {
     int32_t device;            /* CUDA device ordinal */
     size_t hbm_budget_bytes;   /* 0 = no budget; else cap on bank + state bytes */
     void* cuda_stream;         /* cudaStream_t to order work on, or NULL */
-    uint32_t flags;            /* reserved, 0 */
+    uint32_t flags;            /* LLOID_FLAG_* bits */
+    int32_t coinc_window;      /* coincidence window in samples (Section II.D.3): maximum light
+                                  travel time plus buffer, default 66 = (0.0273 + 0.005) s x 2048 */
 } lloid_config;
 
 /* One time slice of a bank (Eq. 3): the leading L bases and their
@@ -151,6 +153,23 @@ typedef struct {
     float xi2;                 /* Eq. 10 statistic; < 0 when the bank has no autocorrelation */
     int32_t pad;
 } lloid_trigger;
+
+/* A coincident event after clustering (Sections II.D.3-4): in window
+ * `window` of bank `bank`, template `tmpl` triggered in the n_ifo >= 2
+ * detectors of ifo_mask within coinc_window samples of its loudest trigger
+ * (detector ref_detector, sample ref_sample); net_snr = sqrt(sum of their
+ * snr^2) is the largest of the bank's events in that window (lowest template
+ * on ties), so there is at most one event per (bank, window). */
+typedef struct {
+    int64_t window;
+    int32_t bank;
+    int32_t tmpl;
+    int32_t n_ifo;
+    uint32_t ifo_mask;
+    float net_snr;
+    int32_t ref_detector;
+    int64_t ref_sample;
+} lloid_event;
 
 /* Fill *cfg with the defaults above (n_detectors = 1, max_block = 16384,
  * max_history = 128 s, min_rate = 32, precision FP32). */
@@ -211,6 +230,15 @@ LLOID_API lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid
  * one compaction pass and one wait for all of them. */
 LLOID_API lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_trigger* out,
                                                  int64_t cap, int64_t* n_out, int32_t timeout_ms);
+
+/* Coincident events of windows w0 .. w0 + n_windows - 1 (1 <= n_windows <=
+ * 16), ordered by window then bank: at most one per (bank, window), formed on
+ * the GPU from the windows' triggers of all detectors (Sections II.D.3-4).
+ * A window's events are ready once its triggers are (for banks with
+ * autocorrelations, d samples past the window's end in every detector);
+ * same waiting, ENOTREADY, ERANGE and EEXPIRED rules as the trigger pulls. */
+LLOID_API lloid_status lloid_pull_events(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_event* out,
+                                         int64_t cap, int64_t* n_out, int32_t timeout_ms);
 
 /* Debug and parity aid: recompute the full-rate SNR rows of the most recent
  * push of detector `det` for bank `bank` into the DEVICE array out

@@ -26,6 +26,7 @@ class LloidConfig(ctypes.Structure):
         ("snr_threshold", ctypes.c_float), ("precision", ctypes.c_int32), ("max_block", ctypes.c_int64),
         ("max_history", ctypes.c_int64), ("min_rate", ctypes.c_int32), ("device", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+        ("coinc_window", ctypes.c_int32),
     ]
 
 
@@ -52,6 +53,14 @@ class LloidTrigger(ctypes.Structure):
     ]
 
 
+class LloidEvent(ctypes.Structure):
+    _fields_ = [
+        ("window", ctypes.c_int64), ("bank", ctypes.c_int32), ("tmpl", ctypes.c_int32), ("n_ifo", ctypes.c_int32),
+        ("ifo_mask", ctypes.c_uint32), ("net_snr", ctypes.c_float), ("ref_detector", ctypes.c_int32),
+        ("ref_sample", ctypes.c_int64),
+    ]
+
+
 # (name, restype, argtypes) for every entry point of include/lloid.h
 SIGNATURES = [
     ("lloid_config_default", None, [ctypes.POINTER(LloidConfig)]),
@@ -67,6 +76,9 @@ SIGNATURES = [
                                              ctypes.c_int]),
     ("lloid_pull_triggers", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(LloidTrigger),
                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("lloid_pull_events", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.POINTER(LloidEvent), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.c_int32]),
     ("lloid_pull_triggers_range", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                  ctypes.POINTER(LloidTrigger), ctypes.c_int64,
                                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),

@@ -539,4 +539,79 @@ __global__ void __launch_bounds__(256) k_xi2(const Xi2Job* __restrict__ jobs, co
     if (lane == 0) e->xi2 = acc / jb.den[m];
 }
 
+// ---------------------------------------------------------------------------
+// Coincidence and clustering (Sections II.D.3-4) for windows w0 .. w0 +
+// gridDim.y - 1: one CTA per (bank, window), threads over templates.  For a
+// template, the loudest detector's trigger (lowest detector on ties) is the
+// reference; triggers of the other detectors within `delta` samples join; two
+// or more detectors make an event of network SNR sqrt(sum snr^2).  The CTA
+// keeps the bank's event of largest network SNR (lowest template on ties).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_coinc(const FinJob* __restrict__ jobs, long long w0, int n_det,
+                                               int delta, const SlabEntry* __restrict__ slab_base, int ring,
+                                               long long slab_det_stride, EventEntry* __restrict__ ev_base,
+                                               int ev_cap) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const FinJob jb = jobs[blockIdx.x];
+    const long long w = w0 + blockIdx.y;
+    const SlabEntry* slab = slab_base + (size_t)(w % ring) * n_det * slab_det_stride;
+    float best = -1.f;
+    int bm = 0x7fffffff, bn = 0, bref = 0, bk = 0;
+    uint32_t bmask = 0;
+    for (int m = threadIdx.x; m < jb.M; m += blockDim.x) {
+        int ref = -1;
+        float rs = 0.f;
+        for (int d = 0; d < n_det; ++d) {
+            const SlabEntry& e = slab[d * slab_det_stride + jb.tmpl0 + m];
+            if ((e.flags & 1) && (ref < 0 || e.snr > rs)) { ref = d; rs = e.snr; }
+        }
+        if (ref < 0) continue;
+        const int k0 = slab[ref * slab_det_stride + jb.tmpl0 + m].k_off;
+        float s2 = 0.f;
+        int n = 0;
+        uint32_t mask = 0;
+        for (int d = 0; d < n_det; ++d) {
+            const SlabEntry& e = slab[d * slab_det_stride + jb.tmpl0 + m];
+            if ((e.flags & 1) && abs(e.k_off - k0) <= delta) {
+                s2 = fmaf(e.snr, e.snr, s2);
+                ++n;
+                mask |= 1u << d;
+            }
+        }
+        if (n < 2) continue;
+        const float net = sqrtf(s2);
+        if (net > best || (net == best && m < bm)) { best = net; bm = m; bn = n; bref = ref; bk = k0; bmask = mask; }
+    }
+    __shared__ float sb[8];
+    __shared__ int sm[8], sn[8], sr[8], sk[8];
+    __shared__ uint32_t smask[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int om = __shfl_xor_sync(0xffffffffu, bm, o), on = __shfl_xor_sync(0xffffffffu, bn, o);
+        const int orf = __shfl_xor_sync(0xffffffffu, bref, o), ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const uint32_t omk = __shfl_xor_sync(0xffffffffu, bmask, o);
+        if (ob > best || (ob == best && om < bm)) { best = ob; bm = om; bn = on; bref = orf; bk = ok; bmask = omk; }
+    }
+    if (lane == 0) { sb[wid] = best; sm[wid] = bm; sn[wid] = bn; sr[wid] = bref; sk[wid] = bk; smask[wid] = bmask; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
+            if (sb[i] > best || (sb[i] == best && sm[i] < bm)) {
+                best = sb[i]; bm = sm[i]; bn = sn[i]; bref = sr[i]; bk = sk[i]; bmask = smask[i];
+            }
+        EventEntry ev;
+        ev.net_snr = best;
+        ev.tmpl = bm;
+        ev.n_ifo = bn;
+        ev.ifo_mask = bmask;
+        ev.ref_det = bref;
+        ev.ref_k_off = bk;
+        ev.pad[0] = ev.pad[1] = 0;
+        ev_base[(size_t)(w % ring) * ev_cap + jb.bank] = ev;
+    }
+}
+
 }  // namespace lloid

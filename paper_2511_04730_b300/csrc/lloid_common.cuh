@@ -114,7 +114,18 @@ struct Xi2Job {
 };
 
 struct FinJob {
-    int tmpl0, M;
+    int tmpl0, M, bank;
+};
+
+// One (bank, window) slot of the clustered coincident events.
+struct EventEntry {
+    float net_snr;               // < 0: no event
+    int32_t tmpl;                // bank-local
+    int32_t n_ifo;
+    uint32_t ifo_mask;
+    int32_t ref_det;
+    int32_t ref_k_off;           // sample - window start of the reference trigger
+    int32_t pad[2];
 };
 
 }  // namespace lloid

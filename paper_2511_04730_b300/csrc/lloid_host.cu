@@ -134,6 +134,10 @@ struct lloid_ctx {
     int* d_bank_of = nullptr;          // [M_cap]
     int* d_tmpl0_of = nullptr;         // [bank_cap]
     int bank_cap = 0;
+    // coincident events (Sections II.D.3-4): [kWindowRing][bank_cap], net_snr <= 0 = none
+    EventEntry* d_events = nullptr;
+    EventEntry* h_events = nullptr;    // pinned staging of a pull
+    long long coinc_next = 0;          // first window whose events are not formed yet
     std::vector<int> h_bank_of, h_tmpl0_of;
 
     // window state
@@ -659,7 +663,7 @@ lloid_status build_jobs(lloid_ctx* ctx, long long n) {
     CK(cudaStreamSynchronize(ctx->stream));
     free_jobs(ctx);
     std::vector<FinJob> fin;
-    for (auto& kv : ctx->banks) fin.push_back(FinJob{kv.second->tmpl0, kv.second->M});
+    for (auto& kv : ctx->banks) fin.push_back(FinJob{kv.second->tmpl0, kv.second->M, kv.second->id});
     lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_finj, fin))) return st;
     ctx->n_fin = (int)fin.size();
@@ -939,6 +943,25 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
             ctx->xi2_next[d] = w_ready;
         }
     }
+    // coincidence and clustering for the windows every detector has ready
+    {
+        long long w_all = -1;
+        for (int d = 0; d < ctx->cfg.n_detectors; ++d) {
+            const bool pushed = d >= det0 && d < det0 + nd;
+            long long r = ctx->n_xi2 > 0 ? ctx->xi2_next[d] : (pushed ? (k_a + n) / W : ctx->fin[d] + 1);
+            w_all = (w_all < 0) ? r : std::min(w_all, r);
+        }
+        const int ndt = ctx->cfg.n_detectors;
+        long long w_lo = std::max(ctx->coinc_next, w_all - (long long)kWindowRing);
+        if (ndt >= 2 && ndt <= 32 && ctx->n_fin > 0 && w_all > w_lo) {
+            CK(launch_pdl(k_coinc, dim3(ctx->n_fin, (unsigned)(w_all - w_lo)), dim3(256), 0, ctx->stream,
+                          (const FinJob*)ctx->d_finj, w_lo, ndt, (int)ctx->cfg.coinc_window,
+                          (const SlabEntry*)ctx->d_slab, (int)kWindowRing, (long long)ctx->M_cap, ctx->d_events,
+                          ctx->bank_cap));
+            ++ctx->launches;
+        }
+        if (w_all > ctx->coinc_next) ctx->coinc_next = w_all;
+    }
     return LLOID_OK;
 }
 
@@ -1110,7 +1133,7 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
     const int nd = c.n_detectors;
     hdr->clear();
     seg->clear();
-    long long h[] = {0x4C4C4F4944535431LL, 2, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
+    long long h[] = {0x4C4C4F4944535431LL, 3, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
                      c.max_block, c.max_history, c.min_rate, (long long)ctx->banks.size(), ctx->M_used,
                      ctx->M_cap, ctx->n_slots};
     hdr->assign(h, h + sizeof h / sizeof h[0]);
@@ -1118,6 +1141,7 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
         hdr->push_back(ctx->pos[d]); hdr->push_back(ctx->fin[d]); hdr->push_back(ctx->last_n[d]);
         hdr->push_back(ctx->xi2_next[d]);
     }
+    hdr->push_back(ctx->coinc_next);
     seg->push_back({ctx->ring0, (size_t)nd * ctx->ring0_len * 4});
     for (int r = 0; r < ctx->n_rates; ++r) seg->push_back({ctx->rate_ring[r], (size_t)nd * ctx->rate_len[r] * 4});
     for (int r = 0; r <= kMaxRates; ++r)
@@ -1127,6 +1151,7 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
         }
     seg->push_back({ctx->d_part, (size_t)ctx->M_cap * nd * ctx->n_slots * sizeof(Partial)});
     seg->push_back({ctx->d_slab, (size_t)kWindowRing * nd * ctx->M_cap * sizeof(SlabEntry)});
+    if (ctx->d_events) seg->push_back({ctx->d_events, (size_t)kWindowRing * ctx->bank_cap * sizeof(EventEntry)});
     for (auto& kv : ctx->banks) {
         const BankRT* b = kv.second;
         hdr->push_back(kv.first); hdr->push_back(b->M); hdr->push_back(b->tmpl0); hdr->push_back((long long)b->sl.size());
@@ -1180,6 +1205,7 @@ void lloid_config_default(lloid_config* c) {
     c->hbm_budget_bytes = 0;
     c->cuda_stream = nullptr;
     c->flags = 0;
+    c->coinc_window = 66;   // (0.0273 + 0.005) s at 2048 Hz
 }
 
 const char* lloid_strerror(lloid_status st) {
@@ -1234,7 +1260,7 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
     if (!is_pow2(c.f0) || c.n_detectors < 1 || c.n_detectors > 64 || c.n_down < 1 || c.n_up < 1 ||
         c.window_samples <= 0 || c.window_samples % kTileT || c.max_block <= 0 || c.max_block % kTileT ||
         c.max_history < 0 || !is_pow2(c.min_rate) || c.min_rate > c.f0 || c.f0 / c.min_rate > 256 ||
-        c.precision < 0 || c.precision > 2 || !(c.snr_threshold >= 0.f))
+        c.precision < 0 || c.precision > 2 || !(c.snr_threshold >= 0.f) || c.coinc_window < 0)
         return fail(nullptr, LLOID_EINVAL, "bad configuration");
     if (c.window_overlap != 0) return LLOID_EINVAL;
     if (c.precision != LLOID_FP32 && (c.max_block % kTcTileN || c.n_up != 8 || c.f0 / c.min_rate > 64))
@@ -1347,6 +1373,7 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_tmpl0_of);
     cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
     cudaFreeHost(ctx->h_err); cudaFreeHost(ctx->h_trig);
+    cudaFree(ctx->d_events); cudaFreeHost(ctx->h_events);
     if (ctx->pull_ev) cudaEventDestroy(ctx->pull_ev);
     cudaFree(ctx->d_err);
     for (int r = 0; r <= kMaxRates; ++r) { cudaFree(ctx->s_hi[r]); cudaFree(ctx->s_lo[r]); }
@@ -1527,6 +1554,22 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
     b->id = ctx->next_bank_id++;
     if (b->id >= ctx->bank_cap) {
         int ncap = std::max(64, 2 * ctx->bank_cap);
+        {   // event slots follow the bank capacity
+            EventEntry* ne = nullptr;
+            CK(cudaMalloc(&ne, (size_t)kWindowRing * ncap * sizeof(EventEntry)));
+            CK(cudaMemsetAsync(ne, 0, (size_t)kWindowRing * ncap * sizeof(EventEntry), ctx->stream));
+            if (ctx->d_events)
+                CK(cudaMemcpy2DAsync(ne, ncap * sizeof(EventEntry), ctx->d_events, ctx->bank_cap * sizeof(EventEntry),
+                                     ctx->bank_cap * sizeof(EventEntry), kWindowRing, cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            cudaFree(ctx->d_events);
+            ctx->d_events = ne;
+            cudaFreeHost(ctx->h_events);
+            ctx->h_events = nullptr;
+            CK(cudaHostAlloc((void**)&ctx->h_events, (size_t)kWindowRing * ncap * sizeof(EventEntry),
+                             cudaHostAllocDefault));
+        }
         int* nt = nullptr;
         CK(cudaMalloc(&nt, ncap * sizeof(int)));
         cudaFree(ctx->d_tmpl0_of);
@@ -1559,6 +1602,9 @@ lloid_status lloid_unload_bank(lloid_ctx* ctx, int32_t bank_id) {
     CK(cudaMemset2DAsync(ctx->d_slab + it->second->tmpl0, ctx->M_cap * sizeof(SlabEntry), 0,
                          (size_t)it->second->M * sizeof(SlabEntry), (size_t)kWindowRing * ctx->cfg.n_detectors,
                          ctx->stream));
+    if (ctx->d_events)
+        CK(cudaMemset2DAsync(ctx->d_events + bank_id, ctx->bank_cap * sizeof(EventEntry), 0, sizeof(EventEntry),
+                             kWindowRing, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (void* p : it->second->allocs) cudaFree(p);
     ctx->bank_bytes -= it->second->bytes;
@@ -1667,6 +1713,48 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
     return LLOID_OK;
 }
 
+lloid_status lloid_pull_events(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_event* out, int64_t cap,
+                               int64_t* n_out, int32_t timeout_ms) {
+    if (!ctx) return LLOID_EINVAL;
+    if (!n_out || (cap > 0 && !out) || w0 < 0 || n_windows < 1 || n_windows > kWindowRing)
+        return fail(ctx, LLOID_EINVAL, "bad output arguments");
+    *n_out = 0;
+    const long long w1 = w0 + n_windows - 1;
+    const long long W = ctx->cfg.window_samples;
+    if (w1 >= ctx->coinc_next)
+        return fail(ctx, LLOID_ENOTREADY, "events of window %lld are not formed yet", (long long)w1);
+    long long fin_max = ctx->fin[0];
+    for (long long f : ctx->fin) fin_max = std::max(fin_max, f);
+    if (w0 + kWindowRing <= fin_max) return fail(ctx, LLOID_EEXPIRED, "window %lld is no longer retained", (long long)w0);
+    if (!ctx->d_events) return LLOID_OK;
+    const size_t row = (size_t)ctx->bank_cap * sizeof(EventEntry);
+    for (long long w = w0; w <= w1; ++w)
+        CK(cudaMemcpyAsync(ctx->h_events + (w - w0) * ctx->bank_cap, ctx->d_events + (w % kWindowRing) * ctx->bank_cap,
+                           row, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ctx->pull_ev, ctx->stream));
+    lloid_status st;
+    if ((st = wait_event(ctx, ctx->pull_ev, timeout_ms))) return st;
+    if (*ctx->h_err)
+        return fail(ctx, LLOID_ETIMEOUT, "a kernel wait expired (code %d); results of the last pushes are invalid",
+                    *ctx->h_err);
+    long long cnt = 0;
+    for (long long w = w0; w <= w1; ++w)
+        for (int bk = 0; bk < ctx->bank_cap; ++bk) {
+            const EventEntry& e = ctx->h_events[(w - w0) * ctx->bank_cap + bk];
+            if (!(e.net_snr > 0.f) || ctx->banks.find(bk) == ctx->banks.end()) continue;
+            if (cnt < cap) {
+                lloid_event& o = out[cnt];
+                o.window = w; o.bank = bk; o.tmpl = e.tmpl; o.n_ifo = e.n_ifo; o.ifo_mask = e.ifo_mask;
+                o.net_snr = e.net_snr; o.ref_detector = e.ref_det; o.ref_sample = w * W + e.ref_k_off;
+            }
+            ++cnt;
+        }
+    *n_out = cnt;
+    if (cnt > cap) return fail(ctx, LLOID_ERANGE, "%lld events, capacity %lld", cnt, (long long)cap);
+    return LLOID_OK;
+}
+
 lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid_trigger* out, int64_t cap, int64_t* n_out,
                                  int32_t timeout_ms) {
     return lloid_pull_triggers_range(ctx, window, 1, out, cap, n_out, timeout_ms);
@@ -1757,7 +1845,7 @@ lloid_status lloid_restore_state(lloid_ctx* ctx, const void* buf, size_t len) {
     std::vector<long long> saved((size_t)nh);
     std::memcpy(saved.data(), in + sizeof nh, (size_t)nh * sizeof(long long));
     const int nd = ctx->cfg.n_detectors;
-    const size_t pos_at = 15, pos_end = 15 + 4 * (size_t)nd;
+    const size_t pos_at = 15, pos_end = 15 + 4 * (size_t)nd + 1;
     for (size_t i = 0; i < hdr.size(); ++i) {
         if (i >= pos_at && i < pos_end) continue;
         if (saved[i] != hdr[i]) return fail(ctx, LLOID_EINVAL, "checkpoint does not match this context (word %zu)", i);
@@ -1776,6 +1864,7 @@ lloid_status lloid_restore_state(lloid_ctx* ctx, const void* buf, size_t len) {
         ctx->last_n[d] = saved[pos_at + 4 * d + 2];
         ctx->xi2_next[d] = saved[pos_at + 4 * d + 3];
     }
+    ctx->coinc_next = saved[pos_at + 4 * (size_t)nd];
     CK(cudaEventRecord(ctx->done_ev, ctx->stream));
     return LLOID_OK;
 }

@@ -19,6 +19,11 @@ TRIGGER_DTYPE = np.dtype([
     ("re", np.float32), ("im", np.float32), ("xi2", np.float32), ("pad", np.int32),
 ])
 assert TRIGGER_DTYPE.itemsize == ctypes.sizeof(_lib.LloidTrigger)
+EVENT_DTYPE = np.dtype([
+    ("window", np.int64), ("bank", np.int32), ("tmpl", np.int32), ("n_ifo", np.int32), ("ifo_mask", np.uint32),
+    ("net_snr", np.float32), ("ref_detector", np.int32), ("ref_sample", np.int64),
+])
+assert EVENT_DTYPE.itemsize == ctypes.sizeof(_lib.LloidEvent)
 
 
 class LloidError(RuntimeError):
@@ -41,7 +46,7 @@ class Context:
     def __init__(self, n_detectors: int = 1, precision: str = "fp32", max_block: int = 16384,
                  max_history: Optional[int] = None, window: int = 2048, threshold: float = 4.0,
                  device: int = 0, stream=None, hbm_budget: int = 0, f0: int = 2048, min_rate: int = 32,
-                 n_down: int = 32, n_up: int = 8, stage_timing: bool = False):
+                 n_down: int = 32, n_up: int = 8, stage_timing: bool = False, coinc_window: Optional[int] = None):
         self._lib = _lib.load()
         cfg = default_config()
         cfg.f0, cfg.n_detectors, cfg.n_down, cfg.n_up = f0, n_detectors, n_down, n_up
@@ -51,6 +56,8 @@ class Context:
         if max_history is not None:
             cfg.max_history = max_history
         cfg.min_rate, cfg.device, cfg.hbm_budget_bytes = min_rate, device, hbm_budget
+        if coinc_window is not None:
+            cfg.coinc_window = coinc_window
         cfg.cuda_stream = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         cfg.flags = _lib.FLAG_STAGE_TIMING if stage_timing else 0
         self.cfg = cfg
@@ -189,6 +196,22 @@ class Context:
                                                      out.size, ctypes.byref(n_out), timeout_ms)
             if st == -8:   # ERANGE: grow the reusable buffer and retry
                 self._pull_buf = np.empty(int(n_out.value) * 2, dtype=TRIGGER_DTYPE)
+                continue
+            self._check(st)
+            return out[: n_out.value].copy()
+
+    def pull_events(self, window: int, n_windows: int = 1, timeout_ms: int = -1) -> np.ndarray:
+        """Coincident events (at most one per bank and window) of windows
+        window .. window + n_windows - 1 as a numpy structured array (EVENT_DTYPE)."""
+        n_out = ctypes.c_int64()
+        cap = 256
+        while True:
+            out = np.empty(cap, dtype=EVENT_DTYPE)
+            st = self._lib.lloid_pull_events(self._h, window, n_windows,
+                                             out.ctypes.data_as(ctypes.POINTER(_lib.LloidEvent)), cap,
+                                             ctypes.byref(n_out), timeout_ms)
+            if st == -8:
+                cap = int(n_out.value)
                 continue
             self._check(st)
             return out[: n_out.value].copy()

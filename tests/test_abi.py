@@ -47,11 +47,15 @@ def test_struct_layout_matches_c(lib):
 #include "lloid.h"
 #define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
 int main(void) {
-  printf("lloid_config %zu\nlloid_slice %zu\nlloid_bank_desc %zu\nlloid_trigger %zu\n",
-         sizeof(lloid_config), sizeof(lloid_slice), sizeof(lloid_bank_desc), sizeof(lloid_trigger));
+  printf("lloid_config %zu\nlloid_slice %zu\nlloid_bank_desc %zu\nlloid_trigger %zu\nlloid_event %zu\n",
+         sizeof(lloid_config), sizeof(lloid_slice), sizeof(lloid_bank_desc), sizeof(lloid_trigger),
+         sizeof(lloid_event));
   P(lloid_config, max_block) P(lloid_config, hbm_budget_bytes) P(lloid_config, cuda_stream) P(lloid_config, flags)
+  P(lloid_config, coinc_window)
   P(lloid_slice, j_start) P(lloid_slice, bases) P(lloid_slice, coeffs)
-  P(lloid_trigger, window) P(lloid_trigger, sample) P(lloid_trigger, snr) P(lloid_trigger, im)
+  P(lloid_bank_desc, ac_half) P(lloid_bank_desc, autocorr)
+  P(lloid_trigger, window) P(lloid_trigger, sample) P(lloid_trigger, snr) P(lloid_trigger, im) P(lloid_trigger, xi2)
+  P(lloid_event, window) P(lloid_event, net_snr) P(lloid_event, ref_sample)
   return 0;
 }
 '''
@@ -63,7 +67,7 @@ int main(void) {
         out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
     got = dict(line.rsplit(" ", 1) for line in out if line)
     m = {"lloid_config": _lib.LloidConfig, "lloid_slice": _lib.LloidSlice,
-         "lloid_bank_desc": _lib.LloidBankDesc, "lloid_trigger": _lib.LloidTrigger}
+         "lloid_bank_desc": _lib.LloidBankDesc, "lloid_trigger": _lib.LloidTrigger, "lloid_event": _lib.LloidEvent}
     for k, v in got.items():
         if "." in k:
             t, f = k.split(".")
@@ -78,6 +82,8 @@ def test_host_only_calls(lib):
     lib.lloid_config_default(ctypes.byref(cfg))
     # the paper's constants (Section II.C.2, II.D.1)
     assert (cfg.f0, cfg.n_down, cfg.n_up, cfg.window_samples) == (2048, 32, 8, 2048)
+    # coincidence window: maximum light travel time plus buffer (Section II.D.3), at 2048 Hz
+    assert cfg.coinc_window == int((0.0273 + 0.005) * 2048)
     assert cfg.snr_threshold == 4.0 and cfg.window_overlap == 0
     assert lib.lloid_strerror(-4) == b"discontinuous push (t0 is not the stream end)"
     assert lib.lloid_strerror(0) == b"ok"
