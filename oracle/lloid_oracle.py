@@ -29,6 +29,10 @@ What it computes (every array is float64, every step written out plainly):
     within the coincidence window joins it; with two or more detectors it is
     an event of network SNR sqrt(sum rho^2); per (bank, window) only the
     event of highest network SNR is kept.
+(G) ``background_counts`` -- the per-(bank, detector) background histogram
+    of Section II.D.5: SNR and xi2 of the single-detector triggers (those not
+    in their template's coincidence) binned on given edges, only while two
+    or more detectors operate.
 (E) ``autocorrelation`` and ``xi2`` -- the signal-consistency statistic of
     Eq. 10 (Section II.D.2) for each trigger:
       xi2 = sum_{t=-d}^{d} |z[k+t] - z[k] R(t)|^2 / sum_{t=-d}^{d} (2 - 2 |R(t)|^2),
@@ -54,6 +58,12 @@ Readings of points the paper leaves open (each is also listed in the design doc):
   on ties); a coincidence needs two or more detectors; clustering keeps the
   highest network SNR per (bank, window), lowest template on ties; windows do
   not overlap, so triggers in different windows never coincide;
+* background: a trigger is single unless it is a member of its template's
+  coincidence (two or more detectors within the window of the loudest);
+  bins are given as ascending float32 edges e_0 < ... < e_n, a value x goes to
+  the number of edges e_1 .. e_{n-1} that are <= x (so the first and last bins
+  take everything outside the edges); the comparisons are made in float32,
+  as on the GPU;
 * Eq. 10: R(t) = sum_j hbar[j] conj(hbar[j - t]) / sum_j |hbar[j]|^2 (the
   complex template's autocorrelation, so that a noise-free signal gives
   z[k + t] = z[k] R(t) and white noise gives E xi2 = 1 under the E|z|^2 = 2
@@ -439,3 +449,43 @@ def coincident_events(trigs: Sequence[Trigger], delta: int) -> List[Event]:
         if cur is None or net > cur.net_snr or (net == cur.net_snr and i < cur.tmpl):
             best[(bank, w)] = ev
     return [best[k] for k in sorted(best)]
+
+
+# ----------------------------------------------------------------------------
+# (G) background collection, Section II.D.5
+# ----------------------------------------------------------------------------
+
+def _bin(x: float, edges: np.ndarray) -> int:
+    x32 = np.float32(x)
+    b = 0
+    for e in edges[1:-1]:
+        if np.float32(e) <= x32:
+            b += 1
+    return b
+
+
+def background_counts(trigs: Sequence[Trigger], xi2_of, n_det: int, delta: int, snr_edges: np.ndarray,
+                      xi2_edges: np.ndarray) -> dict:
+    """{(bank, detector): counts [n_snr, n_xi2]} over the single-detector
+    triggers; xi2_of(trigger) gives its xi2."""
+    out = {}
+    if n_det < 2:
+        return out
+    by_key = {}
+    for t in trigs:
+        by_key.setdefault((t.bank, t.window, t.tmpl), {})[t.detector] = t
+    for (bank, w, i), per_det in by_key.items():
+        dets = sorted(per_det)
+        ref = dets[0]
+        for d in dets[1:]:
+            if per_det[d].snr > per_det[ref].snr:
+                ref = d
+        k0 = per_det[ref].sample
+        members = [d for d in dets if abs(per_det[d].sample - k0) <= delta]
+        coincident = set(members) if len(members) >= 2 else set()
+        for d in dets:
+            if d in coincident:
+                continue
+            h = out.setdefault((bank, d), np.zeros((len(snr_edges) - 1, len(xi2_edges) - 1), dtype=np.int64))
+            h[_bin(per_det[d].snr, snr_edges), _bin(xi2_of(per_det[d]), xi2_edges)] += 1
+    return out

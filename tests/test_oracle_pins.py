@@ -403,3 +403,30 @@ def test_coincidence_of_a_loud_reference_with_three_detectors():
     # all within 66 of the loudest (det 1 at 4530): 4500 (30), 4470 (60)
     assert (e.n_ifo, e.ifo_mask, e.ref_detector) == (3, 0b111, 1)
     assert abs(e.net_snr - math.sqrt(36 + 81 + 4)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Background collection (Section II.D.5) on a hand-built trigger list
+# --------------------------------------------------------------------------
+
+def test_background_counts_hand_built():
+    snr_e = np.array([4.0, 6.0, 10.0, 100.0], dtype=np.float32)
+    xi2_e = np.array([0.1, 1.0, 10.0], dtype=np.float32)
+    trigs = [
+        _t(0, 3, 0, 1000, 6.0), _t(1, 3, 0, 1030, 8.0),        # coincident pair: not background
+        _t(0, 4, 0, 500, 5.0), _t(1, 4, 0, 900, 11.0),          # too far apart: both single
+        _t(2, 4, 0, 880, 200.0),                                # joins det 1?  no: det 2 is the loudest,
+                                                                # det 1 (20 away) joins it, det 0 stays single
+        _t(0, 5, 1, 2100, 4.5),                                 # alone in its template: single
+    ]
+    xi2 = {(0, 3): 0.5, (1, 3): 0.5, (0, 4): 0.05, (1, 4): 2.0, (2, 4): 50.0, (0, 5): 1.0}
+    h = O.background_counts(trigs, lambda t: xi2[(t.detector, t.tmpl)], 3, 66, snr_e, xi2_e)
+    assert sorted(h) == [(0, 0)]
+    expect = np.zeros((3, 2), dtype=np.int64)
+    expect[0, 0] += 1        # det 0, template 4: snr 5 -> bin 0, xi2 0.05 -> bin 0 (below the first edge)
+    expect[0, 1] += 1        # det 0, template 5: snr 4.5 -> bin 0, xi2 1.0 -> bin 1 (an edge counts upward)
+    assert np.array_equal(h[(0, 0)], expect)
+    assert O.background_counts(trigs, lambda t: 1.0, 1, 66, snr_e, xi2_e) == {}
+    # edges decide in float32: a value equal to an edge goes to the upper bin
+    assert O._bin(6.0, snr_e) == 1 and O._bin(np.nextafter(np.float32(6.0), np.float32(0)), snr_e) == 0
+    assert O._bin(1e9, snr_e) == 2 and O._bin(-5.0, snr_e) == 0
