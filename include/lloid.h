@@ -240,6 +240,21 @@ LLOID_API lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int
 LLOID_API lloid_status lloid_pull_events(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_event* out,
                                          int64_t cap, int64_t* n_out, int32_t timeout_ms);
 
+/* Background collection (Section II.D.5): from now on every window adds its
+ * single-detector triggers (those that are not members of their template's
+ * coincidence) to a persistent histogram per bank and detector over SNR and
+ * xi2 (-1 for banks without autocorrelations), only while two or more
+ * detectors are configured.  Edges are ascending (n_snr + 1 and n_xi2 + 1
+ * values); a value goes to the bin of the last edge <= it, values outside
+ * the edges to the first or last bin.  Calling again resets every bank's
+ * counts. */
+LLOID_API lloid_status lloid_set_background_bins(lloid_ctx* ctx, const float* snr_edges, int32_t n_snr,
+                                                 const float* xi2_edges, int32_t n_xi2);
+
+/* Copy bank `bank`'s counts [n_detectors][n_snr][n_xi2] into out[cap] (after
+ * the context's queued work); the snapshot the paper takes every four hours. */
+LLOID_API lloid_status lloid_get_background(lloid_ctx* ctx, int32_t bank, uint32_t* out, int64_t cap);
+
 /* Debug and parity aid: recompute the full-rate SNR rows of the most recent
  * push of detector `det` for bank `bank` into the DEVICE array out
  * [2M][n_last] (row 2i = real part of template i) with the same kernels and

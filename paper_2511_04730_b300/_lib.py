@@ -76,6 +76,10 @@ SIGNATURES = [
                                              ctypes.c_int]),
     ("lloid_pull_triggers", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(LloidTrigger),
                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("lloid_set_background_bins", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
+    ("lloid_get_background", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32),
+                                            ctypes.c_int64]),
     ("lloid_pull_events", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.POINTER(LloidEvent), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.c_int32]),

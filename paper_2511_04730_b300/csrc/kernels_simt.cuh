@@ -614,4 +614,51 @@ __global__ void __launch_bounds__(256) k_coinc(const FinJob* __restrict__ jobs, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Background collection (Section II.D.5) for windows w0 .. w0 + gridDim.y - 1:
+// a thread per template (grid.z covers the largest bank); every trigger that
+// is not a member of its template's coincidence (same rule as k_coinc) adds 1
+// to bin (snr, xi2) of its bank and detector.  Bins: the number of inner
+// edges <= the value (float comparisons, as the host wrote the edges).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int edge_bin(float x, const float* __restrict__ e, int n) {
+    int b = 0;
+    for (int i = 1; i < n; ++i) b += (e[i] <= x) ? 1 : 0;
+    return b;
+}
+
+__global__ void __launch_bounds__(256) k_background(const FinJob* __restrict__ jobs, long long w0, int n_det,
+                                                    int delta, const SlabEntry* __restrict__ slab_base, int ring,
+                                                    long long slab_det_stride, const float* __restrict__ snr_e,
+                                                    int n_snr, const float* __restrict__ xi2_e, int n_xi2) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const FinJob jb = jobs[blockIdx.x];
+    const int m = blockIdx.z * blockDim.x + threadIdx.x;
+    if (jb.bg == nullptr || m >= jb.M) return;
+    const long long w = w0 + blockIdx.y;
+    const SlabEntry* slab = slab_base + (size_t)(w % ring) * n_det * slab_det_stride + jb.tmpl0 + m;
+    int ref = -1;
+    float rs = 0.f;
+    for (int d = 0; d < n_det; ++d) {
+        const SlabEntry& e = slab[d * slab_det_stride];
+        if ((e.flags & 1) && (ref < 0 || e.snr > rs)) { ref = d; rs = e.snr; }
+    }
+    if (ref < 0) return;
+    const int k0 = slab[ref * slab_det_stride].k_off;
+    uint32_t mask = 0;
+    int n = 0;
+    for (int d = 0; d < n_det; ++d) {
+        const SlabEntry& e = slab[d * slab_det_stride];
+        if ((e.flags & 1) && abs(e.k_off - k0) <= delta) { mask |= 1u << d; ++n; }
+    }
+    if (n < 2) mask = 0;
+    for (int d = 0; d < n_det; ++d) {
+        const SlabEntry& e = slab[d * slab_det_stride];
+        if (!(e.flags & 1) || (mask >> d & 1u)) continue;
+        const int bs = edge_bin(e.snr, snr_e, n_snr), bx = edge_bin(e.xi2, xi2_e, n_xi2);
+        atomicAdd(jb.bg + ((size_t)d * n_snr + bs) * n_xi2 + bx, 1u);
+    }
+}
+
 }  // namespace lloid

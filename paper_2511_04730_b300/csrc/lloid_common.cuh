@@ -115,6 +115,7 @@ struct Xi2Job {
 
 struct FinJob {
     int tmpl0, M, bank;
+    uint32_t* bg;                // background counts [det][n_snr][n_xi2], or null
 };
 
 // One (bank, window) slot of the clustered coincident events.

@@ -94,6 +94,7 @@ struct BankRT {
     float2* d_ac = nullptr;
     float* d_ac_den = nullptr;
     uint32_t* d_zring = nullptr;
+    uint32_t* d_bg = nullptr;          // background counts [det][n_snr][n_xi2] (own allocation)
     size_t bytes = 0;
     std::vector<void*> allocs;
 };
@@ -138,6 +139,9 @@ struct lloid_ctx {
     EventEntry* d_events = nullptr;
     EventEntry* h_events = nullptr;    // pinned staging of a pull
     long long coinc_next = 0;          // first window whose events are not formed yet
+    // background bins (Section II.D.5): snr edges then xi2 edges
+    float* d_bg_edges = nullptr;
+    int bg_nsnr = 0, bg_nxi2 = 0;
     std::vector<int> h_bank_of, h_tmpl0_of;
 
     // window state
@@ -663,7 +667,7 @@ lloid_status build_jobs(lloid_ctx* ctx, long long n) {
     CK(cudaStreamSynchronize(ctx->stream));
     free_jobs(ctx);
     std::vector<FinJob> fin;
-    for (auto& kv : ctx->banks) fin.push_back(FinJob{kv.second->tmpl0, kv.second->M, kv.second->id});
+    for (auto& kv : ctx->banks) fin.push_back(FinJob{kv.second->tmpl0, kv.second->M, kv.second->id, kv.second->d_bg});
     lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_finj, fin))) return st;
     ctx->n_fin = (int)fin.size();
@@ -959,6 +963,16 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
                           (const SlabEntry*)ctx->d_slab, (int)kWindowRing, (long long)ctx->M_cap, ctx->d_events,
                           ctx->bank_cap));
             ++ctx->launches;
+            if (ctx->bg_nsnr > 0) {
+                int mmax = 1;
+                for (auto& kv : ctx->banks) mmax = std::max(mmax, kv.second->M);
+                CK(launch_pdl(k_background, dim3(ctx->n_fin, (unsigned)(w_all - w_lo), (unsigned)((mmax + 255) / 256)),
+                              dim3(256), 0, ctx->stream, (const FinJob*)ctx->d_finj, w_lo, ndt,
+                              (int)ctx->cfg.coinc_window, (const SlabEntry*)ctx->d_slab, (int)kWindowRing,
+                              (long long)ctx->M_cap, (const float*)ctx->d_bg_edges, ctx->bg_nsnr,
+                              (const float*)(ctx->d_bg_edges + ctx->bg_nsnr + 1), ctx->bg_nxi2));
+                ++ctx->launches;
+            }
         }
         if (w_all > ctx->coinc_next) ctx->coinc_next = w_all;
     }
@@ -1157,6 +1171,7 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
         hdr->push_back(kv.first); hdr->push_back(b->M); hdr->push_back(b->tmpl0); hdr->push_back((long long)b->sl.size());
         hdr->push_back(b->ac_half);
         if (b->d_zring) seg->push_back({b->d_zring, (size_t)nd * b->Mpad * b->zlen * 4});
+        if (b->d_bg) seg->push_back({b->d_bg, (size_t)nd * ctx->bg_nsnr * ctx->bg_nxi2 * 4});
         for (const auto& sl : b->sl) {
             hdr->push_back(sl.rate); hdr->push_back(sl.J); hdr->push_back(sl.N); hdr->push_back(sl.L);
             if (sl.d_yring) seg->push_back({sl.d_yring, (size_t)nd * sl.L * sl.y_len * 4});
@@ -1363,9 +1378,11 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->banks) {
         for (void* p : kv.second->allocs) cudaFree(p);
+        cudaFree(kv.second->d_bg);
         delete kv.second;
     }
     free_jobs(ctx);
+    cudaFree(ctx->d_bg_edges);
     cudaFree(ctx->ring0);
     for (int r = 0; r < ctx->n_rates; ++r) { cudaFree(ctx->rate_ring[r]); cudaFree(ctx->w_down[r]); }
     cudaFree(ctx->d_stage);
@@ -1461,7 +1478,11 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
     b->Mpad = (M + 127) / 128 * 128;
     const int nd = c.n_detectors;
     lloid_status st;
-    auto cleanup = [&]() { for (void* p : b->allocs) cudaFree(p); };
+    auto cleanup = [&]() {
+        for (void* p : b->allocs) cudaFree(p);
+        cudaFree(b->d_bg);
+        b->d_bg = nullptr;
+    };
     // ---- budget check before any large allocation
     size_t need = 0;
     if (!split) {
@@ -1548,6 +1569,13 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
         CK(cudaMemcpyAsync(b->d_ac_den, den.data(), den.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
+    if (ctx->bg_nsnr > 0) {
+        const size_t bb = (size_t)nd * ctx->bg_nsnr * ctx->bg_nxi2 * 4;
+        void* q = nullptr;
+        if (cudaMalloc(&q, bb) != cudaSuccess) { cleanup(); return fail(ctx, LLOID_ENOMEM, "background counts"); }
+        CK(cudaMemsetAsync(q, 0, bb, ctx->stream));
+        b->d_bg = (uint32_t*)q;
+    }
     // ---- template ids, window state
     b->tmpl0 = ctx->M_used;
     if ((st = ensure_template_capacity(ctx, (long long)ctx->M_used + M))) { cleanup(); return st; }
@@ -1607,6 +1635,7 @@ lloid_status lloid_unload_bank(lloid_ctx* ctx, int32_t bank_id) {
                              kWindowRing, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (void* p : it->second->allocs) cudaFree(p);
+    cudaFree(it->second->d_bg);
     ctx->bank_bytes -= it->second->bytes;
     delete it->second;
     ctx->banks.erase(it);
@@ -1710,6 +1739,47 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
                            cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
+    return LLOID_OK;
+}
+
+lloid_status lloid_set_background_bins(lloid_ctx* ctx, const float* snr_edges, int32_t n_snr, const float* xi2_edges,
+                                       int32_t n_xi2) {
+    if (!ctx) return LLOID_EINVAL;
+    if (!snr_edges || !xi2_edges || n_snr < 1 || n_xi2 < 1 || n_snr > 4096 || n_xi2 > 4096)
+        return fail(ctx, LLOID_EINVAL, "background bins need 1..4096 bins and their edges");
+    for (int i = 0; i < n_snr; ++i)
+        if (!(snr_edges[i] < snr_edges[i + 1])) return fail(ctx, LLOID_EINVAL, "snr edges are not ascending");
+    for (int i = 0; i < n_xi2; ++i)
+        if (!(xi2_edges[i] < xi2_edges[i + 1])) return fail(ctx, LLOID_EINVAL, "xi2 edges are not ascending");
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<float> e(snr_edges, snr_edges + n_snr + 1);
+    e.insert(e.end(), xi2_edges, xi2_edges + n_xi2 + 1);
+    cudaFree(ctx->d_bg_edges);
+    ctx->d_bg_edges = nullptr;
+    CK(cudaMalloc(&ctx->d_bg_edges, e.size() * 4));
+    CK(cudaMemcpy(ctx->d_bg_edges, e.data(), e.size() * 4, cudaMemcpyHostToDevice));
+    ctx->bg_nsnr = n_snr;
+    ctx->bg_nxi2 = n_xi2;
+    const size_t bb = (size_t)ctx->cfg.n_detectors * n_snr * n_xi2 * 4;
+    for (auto& kv : ctx->banks) {
+        cudaFree(kv.second->d_bg);
+        kv.second->d_bg = nullptr;
+        CK(cudaMalloc(&kv.second->d_bg, bb));
+        CK(cudaMemset(kv.second->d_bg, 0, bb));
+    }
+    ctx->jobs_dirty = true;
+    return LLOID_OK;
+}
+
+lloid_status lloid_get_background(lloid_ctx* ctx, int32_t bank, uint32_t* out, int64_t cap) {
+    if (!ctx) return LLOID_EINVAL;
+    auto it = ctx->banks.find(bank);
+    if (it == ctx->banks.end()) return fail(ctx, LLOID_EINVAL, "no bank %d", bank);
+    if (ctx->bg_nsnr == 0) return fail(ctx, LLOID_EINVAL, "no background bins set");
+    const long long n = (long long)ctx->cfg.n_detectors * ctx->bg_nsnr * ctx->bg_nxi2;
+    if (!out || cap < n) return fail(ctx, LLOID_ERANGE, "need %lld counts", n);
+    CK(cudaMemcpyAsync(out, it->second->d_bg, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return LLOID_OK;
 }
 

@@ -200,6 +200,22 @@ class Context:
             self._check(st)
             return out[: n_out.value].copy()
 
+    def set_background_bins(self, snr_edges, xi2_edges):
+        """Start background collection (Section II.D.5) on these ascending edges."""
+        se = np.ascontiguousarray(snr_edges, dtype=np.float32)
+        xe = np.ascontiguousarray(xi2_edges, dtype=np.float32)
+        self._bg_shape = (self.n_detectors, se.size - 1, xe.size - 1)
+        self._check(self._lib.lloid_set_background_bins(
+            self._h, se.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), se.size - 1,
+            xe.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), xe.size - 1))
+
+    def background(self, bank: int) -> np.ndarray:
+        """Counts [n_detectors, n_snr, n_xi2] of a bank's single-detector triggers."""
+        out = np.zeros(self._bg_shape, dtype=np.uint32)
+        self._check(self._lib.lloid_get_background(self._h, bank, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                                   out.size))
+        return out
+
     def pull_events(self, window: int, n_windows: int = 1, timeout_ms: int = -1) -> np.ndarray:
         """Coincident events (at most one per bank and window) of windows
         window .. window + n_windows - 1 as a numpy structured array (EVENT_DTYPE)."""

@@ -91,3 +91,36 @@ def test_events_need_two_detectors(P, case):
         with pytest.raises(P.LloidError) as e:
             ctx.pull_events(8)
         assert e.value.name == "LLOID_ENOTREADY"
+
+
+def test_background_counts_match_the_rules(P, case):
+    """Background histogram (Section II.D.5) of a three-detector stream with
+    xi2: the GPU's counts equal the oracle's rules applied to the GPU's own
+    triggers (exact integers; bins decided on the same float32 values)."""
+    from paper_2511_04730_b300.svdbank import template_autocorrelation
+    w, strains, _ = case
+    sb = P.build_svd_bank(w.banks[0], w.plans[0])
+    R = template_autocorrelation(w.banks[0], 175)
+    snr_e = np.geomspace(3.0, 100.0, 9).astype(np.float32)
+    xi2_e = np.geomspace(0.05, 50.0, 7).astype(np.float32)
+    B = 4096
+    trig = []
+    with P.Context(n_detectors=3, precision="fp16_split", max_block=B, max_history=64 * F0,
+                   coinc_window=DELTA, threshold=3.0) as ctx:
+        bid = ctx.load_bank(sb, autocorr=R)
+        ctx.set_background_bins(snr_e, xi2_e)
+        nw = 0
+        for t in range(0, strains.shape[1], B):
+            ctx.push_all(t, np.ascontiguousarray(strains[:, t:t + B], dtype=np.float32))
+            ready = (t + B - 175) // F0
+            if ready > nw:
+                trig.append(ctx.pull(nw, n_windows=ready - nw))
+                nw = ready
+        counts = ctx.background(bid)
+    trig = np.concatenate(trig)
+    xi2 = {(int(r["detector"]), int(r["tmpl"]), int(r["window"])): float(r["xi2"]) for r in trig}
+    ref = O.background_counts(_as_oracle(trig), lambda t: xi2[(t.detector, t.tmpl, t.window)], 3, DELTA,
+                              snr_e, xi2_e)
+    assert counts.sum() > 100
+    for d in range(3):
+        assert np.array_equal(counts[d].astype(np.int64), ref.get((bid, d), np.zeros_like(counts[d], dtype=np.int64)))
