@@ -29,6 +29,12 @@ What it computes (every array is float64, every step written out plainly):
     within the coincidence window joins it; with two or more detectors it is
     an event of network SNR sqrt(sum rho^2); per (bank, window) only the
     event of highest network SNR is kept.
+(H) ``Whitener``         -- PSD estimation and whitening of Section II.B.2:
+    blocks of N input samples (an N - 2Z Hann-windowed segment between Z
+    zeros) advancing by N/2 - Z, FFT, downsampling by keeping the bins below
+    the output Nyquist, per-bin median of the last n_med instantaneous PSDs,
+    running geometric mean, x e^gamma, whitening, inverse FFT at the output
+    rate, Tukey window, overlap-add; output lags the input by N/2.
 (G) ``background_counts`` -- the per-(bank, detector) background histogram
     of Section II.D.5: SNR and xi2 of the single-detector triggers (those not
     in their template's coincidence) binned on given edges, only while two
@@ -64,6 +70,19 @@ Readings of points the paper leaves open (each is also listed in the design doc):
   the number of edges e_1 .. e_{n-1} that are <= x (so the first and last bins
   take everything outside the edges); the comparisons are made in float32,
   as on the GPU;
+* whitening: periodic Hann of length L = N - 2Z (hop L/2 windows sum to one);
+  instantaneous PSD |X_k|^2 / sum w^2; the median of the last n_med (n_med
+  odd; while fewer exist, of the largest odd number of the newest ones)
+  divided by kappa_k = exp(E[log median of k unit exponentials] + gamma) is a
+  geometric-mean estimate of the bin's exponential distribution (E[log] of it
+  equals that of a single sample, log mean - gamma);
+  running geometric mean log G <- log G + (log g - log G) / min(i, n_avg) over
+  the i-th estimate (n_avg = 64: the paper does not give it); PSD = G e^gamma;
+  Y_k = X_k / sqrt(PSD_k) sqrt(N_out / N) / N_out for k <= N_out / 2 (the
+  Nyquist bin's real part), inverse real FFT of size N_out, Tukey window with
+  cosine tapers of Z_out samples at each end; a block whose segment holds a
+  non-finite sample adds nothing and does not update the PSD; output sample
+  j corresponds to input sample j rate_in / rate_out - Z;
 * Eq. 10: R(t) = sum_j hbar[j] conj(hbar[j - t]) / sum_j |hbar[j]|^2 (the
   complex template's autocorrelation, so that a noise-free signal gives
   z[k + t] = z[k] R(t) and white noise gives E xi2 = 1 under the E|z|^2 = 2
@@ -489,3 +508,95 @@ def background_counts(trigs: Sequence[Trigger], xi2_of, n_det: int, delta: int, 
             h = out.setdefault((bank, d), np.zeros((len(snr_edges) - 1, len(xi2_edges) - 1), dtype=np.int64))
             h[_bin(per_det[d].snr, snr_edges), _bin(xi2_of(per_det[d]), xi2_edges)] += 1
     return out
+
+
+# ----------------------------------------------------------------------------
+# (H) PSD estimation and whitening, Section II.B.2
+# ----------------------------------------------------------------------------
+
+def median_log_factor(k: int) -> float:
+    """kappa_k = exp(E[log M] + gamma) for M the median of k (odd) independent
+    unit exponentials.  M has density c (1 - e^-x)^m e^-(m+1)x, m = (k-1)/2,
+    c = k!/(m!)^2; expanding (1 - e^-x)^m and using
+    int_0^inf log(x) e^-ax dx = -(gamma + log a)/a:
+    E[log M] = -c sum_j C(m, j) (-1)^j (gamma + log(m+1+j)) / (m+1+j)."""
+    m = (k - 1) // 2
+    c = math.factorial(k) / math.factorial(m) ** 2
+    e = 0.0
+    for j in range(m + 1):
+        a = m + 1 + j
+        e -= c * math.comb(m, j) * (-1) ** j * (np.euler_gamma + math.log(a)) / a
+    return math.exp(e + np.euler_gamma)
+
+
+def hann_periodic(L: int) -> np.ndarray:
+    n = np.arange(L)
+    return np.sin(np.pi * n / L) ** 2
+
+
+def tukey(n: int, taper: int) -> np.ndarray:
+    """Flat 1 with cosine tapers of `taper` samples at each end."""
+    w = np.ones(n)
+    if taper > 0:
+        t = np.arange(taper)
+        ramp = 0.5 * (1.0 - np.cos(np.pi * (t + 0.5) / taper))
+        w[:taper] = ramp
+        w[n - taper:] = ramp[::-1]
+    return w
+
+
+class Whitener:
+    """One detector's whitening stream (FP64)."""
+
+    def __init__(self, rate_in: int, rate_out: int, n_fft: int, z_pad: int, n_med: int = 7, n_avg: int = 64):
+        self.r_in, self.r_out, self.N, self.Z = rate_in, rate_out, n_fft, z_pad
+        self.n_med, self.n_avg = n_med, n_avg
+        self.L = n_fft - 2 * z_pad
+        self.hop = n_fft // 2 - z_pad
+        self.N_out = n_fft * rate_out // rate_in
+        self.Z_out = z_pad * rate_out // rate_in
+        self.hop_out = self.hop * rate_out // rate_in
+        self.w = hann_periodic(self.L)
+        self.W2 = float(np.sum(self.w ** 2))
+        self.T = tukey(self.N_out, self.Z_out)
+        self.buf = np.zeros(0)
+        self.hist = []               # recent instantaneous PSDs (n_med)
+        self.logG = None
+        self.n_est = 0
+        self.acc = np.zeros(self.N_out)
+
+    def psd(self) -> np.ndarray:
+        return np.exp(self.logG) * math.exp(np.euler_gamma)
+
+    def _update_psd(self, p_inst: np.ndarray) -> None:
+        self.hist = (self.hist + [p_inst])[-self.n_med:]
+        k = len(self.hist) if len(self.hist) % 2 else len(self.hist) - 1
+        med = np.median(np.stack(self.hist[-k:]), axis=0)
+        g = med / median_log_factor(k)
+        self.n_est += 1
+        if self.logG is None:
+            self.logG = np.log(g)
+        else:
+            self.logG = self.logG + (np.log(g) - self.logG) / min(self.n_est, self.n_avg)
+
+    def push(self, x: np.ndarray) -> np.ndarray:
+        """Append input samples (a multiple of the hop); return the output
+        samples that became final."""
+        self.buf = np.concatenate([self.buf, np.asarray(x, dtype=np.float64)])
+        out = []
+        while self.buf.size >= self.L:
+            seg = self.buf[:self.L]
+            self.buf = self.buf[self.hop:]
+            b = np.zeros(self.N)
+            b[self.Z:self.Z + self.L] = self.w * seg
+            k_out = self.N_out // 2
+            y = np.zeros(self.N_out)
+            if np.all(np.isfinite(seg)):
+                X = np.fft.rfft(b)[:k_out + 1]
+                self._update_psd(np.abs(X) ** 2 / self.W2)
+                Y = X / np.sqrt(self.psd()) * math.sqrt(self.N_out / self.N) / self.N_out
+                y = np.fft.irfft(Y * self.N_out, n=self.N_out)   # numpy's irfft divides by N_out
+            self.acc += self.T * y
+            out.append(self.acc[:self.hop_out].copy())
+            self.acc = np.concatenate([self.acc[self.hop_out:], np.zeros(self.hop_out)])
+        return np.concatenate(out) if out else np.zeros(0)

@@ -430,3 +430,86 @@ def test_background_counts_hand_built():
     # edges decide in float32: a value equal to an edge goes to the upper bin
     assert O._bin(6.0, snr_e) == 1 and O._bin(np.nextafter(np.float32(6.0), np.float32(0)), snr_e) == 0
     assert O._bin(1e9, snr_e) == 2 and O._bin(-5.0, snr_e) == 0
+
+
+# --------------------------------------------------------------------------
+# PSD estimation and whitening (Section II.B.2)
+# --------------------------------------------------------------------------
+
+def test_median_log_factor_closed_form_against_quadrature():
+    from scipy import integrate
+    assert abs(O.median_log_factor(1) - 1.0) < 1e-15          # E[log X] = -gamma for one exponential
+    assert abs(O.median_log_factor(3) - 9.0 / 8.0) < 1e-14    # exp(2 log 3 - 3 log 2)
+    for k in (5, 7, 9):
+        m = (k - 1) // 2
+        c = math.factorial(k) / math.factorial(m) ** 2
+        f = lambda x: math.log(x) * c * (-math.expm1(-x)) ** m * math.exp(-(m + 1) * x)
+        e = integrate.quad(f, 0.0, 1.0, limit=200)[0] + integrate.quad(f, 1.0, math.inf, limit=200)[0]
+        assert abs(O.median_log_factor(k) - math.exp(e + np.euler_gamma)) < 1e-9
+
+
+def test_hann_windows_sum_to_one_and_tukey_shape():
+    w = O.hann_periodic(512)
+    assert np.max(np.abs(w[:256] + w[256:] - 1.0)) < 1e-15
+    t = O.tukey(100, 10)
+    assert np.all(t[10:90] == 1.0) and np.array_equal(t[:10], t[90:][::-1])
+    assert np.all(np.diff(t[:10]) > 0) and 0 < t[0] < t[9] < 1
+    # raised-cosine taper: t[i] + t[9 - i] = 1 (mirror symmetry about the half point)
+    assert np.max(np.abs(t[:10] + t[:10][::-1] - 1.0)) < 1e-15
+
+
+def _whiten(x, wh, hop):
+    return np.concatenate([wh.push(x[i:i + hop]) for i in range(0, x.size, hop)])
+
+
+def test_whitening_white_and_coloured_noise():
+    """After the PSD settles: unit variance for white noise of any level, and
+    coloured noise comes out white (no correlation at small lags)."""
+    from scipy.signal import lfilter
+    fi, fo = 4096, 512
+    rng = np.random.default_rng(2)
+    x = 3.0 * rng.standard_normal(120 * fi)
+    y = _whiten(x, O.Whitener(fi, fo, 4 * fi, fi), 2 * fi - fi)[30 * fo:]
+    assert abs(y.var() - 1.0) < 0.05
+    xc = lfilter([1.0, 0.9], [1.0, -0.5], rng.standard_normal(120 * fi))
+    yc = _whiten(xc, O.Whitener(fi, fo, 4 * fi, fi), fi)[30 * fo:]
+    assert abs(yc.var() - 1.0) < 0.05
+    for lag in (1, 2, 3):
+        assert abs(np.corrcoef(yc[:-lag], yc[lag:])[0, 1]) < 0.03
+    # the raw input was strongly correlated
+    assert np.corrcoef(xc[:-1], xc[1:])[0, 1] > 0.5
+
+
+def test_whitening_latency_and_alignment():
+    """Output sample j is input sample j rate_in / rate_out - Z: an impulse in
+    white noise (PSD settled) comes out at (t0 + Z) rate_out / rate_in, and the
+    output reaches it N/2 input samples after the input did."""
+    fi, fo = 4096, 512
+    N, Z = 4 * fi, fi
+    rng = np.random.default_rng(3)
+    x = 0.01 * rng.standard_normal(40 * fi)
+    t0 = 30 * fi + 800
+    x[t0] += 50.0
+    wh = O.Whitener(fi, fo, N, Z)
+    hop = N // 2 - Z
+    outs, got_at = [], None
+    for i in range(0, x.size, hop):
+        o = wh.push(x[i:i + hop])
+        outs.append(o)
+        if got_at is None and sum(v.size for v in outs) > (t0 + Z) * fo // fi:
+            got_at = i + hop
+    y = np.concatenate(outs)
+    assert int(np.argmax(np.abs(y))) == (t0 + Z) * fo // fi
+    assert got_at - t0 <= N // 2 + hop
+
+
+def test_whitening_skips_blocks_with_gaps():
+    fi, fo = 4096, 512
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(30 * fi)
+    x[20 * fi + 5] = np.nan
+    wh = O.Whitener(fi, fo, 4 * fi, fi)
+    y = _whiten(x, wh, fi)
+    assert np.all(np.isfinite(y))
+    # the two blocks whose 2 s segments hold the gap add nothing and estimate nothing
+    assert wh.n_est == (30 * fi - (4 * fi - 2 * fi)) // fi + 1 - 2
