@@ -255,6 +255,56 @@ LLOID_API lloid_status lloid_set_background_bins(lloid_ctx* ctx, const float* sn
  * the context's queued work); the snapshot the paper takes every four hours. */
 LLOID_API lloid_status lloid_get_background(lloid_ctx* ctx, int32_t bank, uint32_t* out, int64_t cap);
 
+/* ---------------------------------------------------------------------------
+ * PSD estimation and whitening (Section II.B.2), the front end before
+ * lloid_push_strain: blocks of n_fft input samples (an n_fft - 2 z_pad
+ * Hann-windowed segment between z_pad zeros) advance by hop = n_fft/2 - z_pad;
+ * each is Fourier transformed, downsampled by keeping the bins below the
+ * output Nyquist, used to update the PSD estimate (per bin: median of the
+ * last n_med instantaneous estimates, turned into a geometric-mean estimate
+ * by a constant factor and averaged in log over up to n_avg blocks; times
+ * e^gamma for the arithmetic mean) and whitened with it, inverse transformed
+ * at rate_out, Tukey-tapered (z_pad rate_out / rate_in samples at each end)
+ * and overlap-added.  Output sample j corresponds to input sample
+ * j rate_in / rate_out - z_pad, so the output lags the input by n_fft / 2
+ * samples.  A block whose segment holds a non-finite sample (a gap) neither
+ * updates the PSD nor adds output.  The forward and inverse transforms are
+ * cuFFT calls; windowing, PSD, whitening and overlap-add are this library's
+ * kernels.
+ * ------------------------------------------------------------------------- */
+typedef struct lloid_whitener lloid_whitener;
+
+typedef struct {
+    int32_t rate_in;           /* input rate (Hz), power of two */
+    int32_t rate_out;          /* output rate, power of two <= rate_in */
+    int32_t n_fft;             /* N: input samples per block, power of two */
+    int32_t z_pad;             /* Z: 0 <= Z < N/2, N/2 - Z a multiple of rate_in / rate_out */
+    int32_t n_med;             /* odd, 1 .. 31 */
+    int32_t n_avg;             /* >= 1 */
+    int32_t n_detectors;       /* 1 .. 64 */
+    int32_t device;
+    int64_t max_push;          /* largest push (input samples, a multiple of the hop) */
+    void* cuda_stream;         /* cudaStream_t or NULL */
+} lloid_whitener_config;
+
+/* 16384 Hz -> 2048 Hz, N = 4 s, Z = 1 s, n_med = 7 (Section II.B.2), n_avg = 64,
+ * one detector, max_push = 16 s. */
+LLOID_API void lloid_whitener_config_default(lloid_whitener_config* cfg);
+LLOID_API lloid_status lloid_whitener_create(const lloid_whitener_config* cfg, lloid_whitener** out);
+LLOID_API void lloid_whitener_destroy(lloid_whitener* wh);
+
+/* Append n input samples of detector det (n a multiple of the hop, at most
+ * max_push) and write the output samples that became final (n / hop x
+ * hop rate_out / rate_in of them once the first segment has filled) to
+ * out[cap] (device memory if out_is_device, else host); *n_out = their count.
+ * Asynchronous on the whitener's stream when the output is on the device. */
+LLOID_API lloid_status lloid_whiten(lloid_whitener* wh, int32_t det, const float* in, int64_t n, int in_is_device,
+                                    float* out, int64_t cap, int64_t* n_out, int out_is_device);
+
+/* The current PSD estimate of detector det: n_fft rate_out / rate_in / 2 + 1
+ * bins (0 .. rate_out / 2 Hz), in units of the input's per-sample variance. */
+LLOID_API lloid_status lloid_whitener_psd(lloid_whitener* wh, int32_t det, float* out, int64_t cap);
+
 /* Debug and parity aid: recompute the full-rate SNR rows of the most recent
  * push of detector `det` for bank `bank` into the DEVICE array out
  * [2M][n_last] (row 2i = real part of template i) with the same kernels and

@@ -61,6 +61,14 @@ class LloidEvent(ctypes.Structure):
     ]
 
 
+class LloidWhitenerConfig(ctypes.Structure):
+    _fields_ = [
+        ("rate_in", ctypes.c_int32), ("rate_out", ctypes.c_int32), ("n_fft", ctypes.c_int32), ("z_pad", ctypes.c_int32),
+        ("n_med", ctypes.c_int32), ("n_avg", ctypes.c_int32), ("n_detectors", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("max_push", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
 # (name, restype, argtypes) for every entry point of include/lloid.h
 SIGNATURES = [
     ("lloid_config_default", None, [ctypes.POINTER(LloidConfig)]),
@@ -80,6 +88,13 @@ SIGNATURES = [
                                                  ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     ("lloid_get_background", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32),
                                             ctypes.c_int64]),
+    ("lloid_whitener_config_default", None, [ctypes.POINTER(LloidWhitenerConfig)]),
+    ("lloid_whitener_create", ctypes.c_int, [ctypes.POINTER(LloidWhitenerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    ("lloid_whitener_destroy", None, [ctypes.c_void_p]),
+    ("lloid_whiten", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
+    ("lloid_whitener_psd", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.c_int64]),
     ("lloid_pull_events", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.POINTER(LloidEvent), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.c_int32]),

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblloid_b300.so")
-SOURCES = ["lloid_host.cu", "lloid_noalloc.cu"]
+SOURCES = ["lloid_host.cu", "lloid_noalloc.cu", "lloid_whiten.cu"]
 HEADERS = ["lloid_common.cuh", "kernels_simt.cuh", "kernels_tc.cuh", "kernels_tc2.cuh"]
 
 NVCC_FLAGS = [
@@ -36,7 +36,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
     cmd = [nvcc, *NVCC_FLAGS, *extra, "-I", os.path.join(ROOT, "include"),
-           *[os.path.join(CSRC, f) for f in SOURCES], "-o", LIB + ".tmp", "-lcudart"]
+           *[os.path.join(CSRC, f) for f in SOURCES], "-o", LIB + ".tmp", "-lcudart", "-lcufft"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

@@ -307,3 +307,63 @@ def triggers_from_snr_noalloc(z, t0: int, window: int = 2048, threshold: float =
         raise LloidError(st, "lloid_triggers_from_snr_noalloc failed")
     k = int(n_out.item())
     return np.frombuffer(out[: min(k, cap) * TRIGGER_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=TRIGGER_DTYPE)
+
+
+class Whitener:
+    """PSD estimation and whitening (Section II.B.2) on the GPU
+    (``lloid_whitener_create``); output feeds ``Context.push``."""
+
+    def __init__(self, rate_in: int = 16384, rate_out: int = 2048, n_fft: Optional[int] = None,
+                 z_pad: Optional[int] = None, n_med: int = 7, n_avg: int = 64, n_detectors: int = 1,
+                 max_push: Optional[int] = None, device: int = 0):
+        self._lib = _lib.load()
+        cfg = _lib.LloidWhitenerConfig()
+        self._lib.lloid_whitener_config_default(ctypes.byref(cfg))
+        cfg.rate_in, cfg.rate_out = rate_in, rate_out
+        cfg.n_fft = 4 * rate_in if n_fft is None else n_fft
+        cfg.z_pad = rate_in if z_pad is None else z_pad
+        cfg.n_med, cfg.n_avg, cfg.n_detectors, cfg.device = n_med, n_avg, n_detectors, device
+        cfg.max_push = 16 * rate_in if max_push is None else max_push
+        self.hop = cfg.n_fft // 2 - cfg.z_pad
+        self.ratio = rate_in // rate_out
+        self.n_bins = cfg.n_fft // self.ratio // 2 + 1
+        h = ctypes.c_void_p()
+        st = self._lib.lloid_whitener_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise LloidError(st, "lloid_whitener_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lloid_whitener_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def whiten(self, det: int, block: np.ndarray) -> np.ndarray:
+        """Append input samples (a multiple of the hop); return the final output samples."""
+        x = np.ascontiguousarray(block, dtype=np.float32)
+        out = np.empty(x.size // self.ratio + 1, dtype=np.float32)
+        n_out = ctypes.c_int64()
+        st = self._lib.lloid_whiten(self._h, det, x.ctypes.data_as(ctypes.c_void_p), x.size, 0,
+                                    out.ctypes.data_as(ctypes.c_void_p), out.size, ctypes.byref(n_out), 0)
+        if st != 0:
+            raise LloidError(st, "lloid_whiten")
+        return out[: n_out.value].copy()
+
+    def psd(self, det: int = 0) -> np.ndarray:
+        out = np.empty(self.n_bins, dtype=np.float32)
+        st = self._lib.lloid_whitener_psd(self._h, det, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size)
+        if st != 0:
+            raise LloidError(st, "lloid_whitener_psd")
+        return out
