@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--seconds", type=int, default=1024)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--whiten-seconds", type=int, default=64,
+                   help="seconds of 16384 Hz strain per detector for the whitening measurement (0: skip it)")
     p.add_argument("--xi2-half", type=int, default=350,
                    help="Eq. 10 autocorrelation half-length d for the xi2 measurement (0: skip it)")
     p.add_argument("--no-fp32-compare", action="store_true")
@@ -494,6 +496,36 @@ def run_lloid(args, rank, world, dist):
                "recon_ms_per_step": round(st_x["recon"][0] / args.steps, 4),
                "d2h_bytes_per_step": d2h_x // args.steps, "autocorr_build_s": round(t_ac, 1)}
 
+    # PSD estimation and whitening (a NEXT row): 16384 Hz -> 2048 Hz, N = 4 s, Z = 1 s, 16 s pushes
+    whiten = None
+    if args.whiten_seconds > 0 and rank == 0:
+        fi, push = 16384, 16 * 16384
+        wx = np.random.default_rng(9).standard_normal((n_det, args.whiten_seconds * fi)).astype(np.float32)
+        dwx = torch.from_numpy(wx).to(f"cuda:{dev}")
+        wout = torch.empty(push // 8 + 1, dtype=torch.float32, device=f"cuda:{dev}")
+        torch.cuda.synchronize()                 # the whitener works on its own stream
+        with P.Whitener(fi, F0, n_detectors=n_det, max_push=push) as wg:
+            lib = wg._lib
+            import ctypes
+            n_out = ctypes.c_int64()
+
+            def wpass(lo, hi):
+                for i in range(lo, hi, push):
+                    for det in range(n_det):
+                        st = lib.lloid_whiten(wg._h, det, ctypes.c_void_p(dwx[det, i:i + push].data_ptr()), push, 1,
+                                              ctypes.c_void_p(wout.data_ptr()), wout.numel(), ctypes.byref(n_out), 1)
+                        assert st == 0, st
+            half = (args.whiten_seconds // 2) * fi // push * push
+            wpass(0, half)                       # warm-up: plans, PSD settles
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            wpass(half, wx.shape[1] // push * push)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            secs = (wx.shape[1] // push * push - half) / fi * n_det
+        whiten = {"value": secs / dt, "unit": "detector-seconds whitened/s", "input_rate": fi, "output_rate": F0,
+                  "n_fft_s": 4, "z_s": 1, "push_s": 16, "seconds": secs}
+
     # accuracy of the measured path against the FP32 path (same stream, same blocks)
     max_dsnr = None
     if args.precision != "fp32" and not args.no_fp32_compare:
@@ -625,6 +657,7 @@ def run_lloid(args, rank, world, dist):
                                       "n": len(lat)} if lat else None),
             "stage_ms_per_step": stage_ms,
             "xi2": xi2,
+            "whiten": whiten,
             "ms_per_step_with_stage_events": statistics.mean(main["ms_timed_stages"]),
             "kernels": recon_info,
             "paths": {p: units * args.steps / (sum(v["ms"]) / 1000.0) for p, v in per_ctx.items()},
