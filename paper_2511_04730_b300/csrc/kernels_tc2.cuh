@@ -382,7 +382,7 @@ struct LevCfg {
     static constexpr int EPI_WARPS = 8;                 // two per TMEM lane quarter, 64 columns each
     static constexpr int STG_PITCH = 80;               // 32 samples x 2 B + 16 B pad: conflict-free rows
     static constexpr int STG_BUF = 32 * STG_PITCH;     // one warp's 32 templates x 32 samples
-    static constexpr int STG = TOP ? 0 : EPI_WARPS * STG_BUF;   // below the top: per-warp transpose buffers
+    static constexpr int STG = EPI_WARPS * STG_BUF;    // per-warp transpose buffers (planes; the top's SNR history)
     static constexpr int XCHG = TOP ? 2 * 128 * 16 : 0;   // top: tile-argmax exchange between the column halves
     static constexpr int SMEM = STAGES * STAGE_BYTES + STG + XCHG + 1024 + 256;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
     pdl_launch_dependents();
     constexpr int EPI = 32 * C::EPI_WARPS;
     constexpr int NWC = win_chunks(F);
+    constexpr int NK16 = (win_rows(F) + win_shift_max(F) + 15) / 16;   // K steps of 16 rows that U can reach
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stg = smem + C::STAGES * C::STAGE_BYTES;
@@ -532,6 +533,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                     const uint32_t u_h = sb + 4 * C::WTILE, u_l = sb + 5 * C::WTILE;
 #pragma unroll
                     for (int k = 0; k < kWinK / 16; ++k) {
+                        if (ch * (kWinK / 16) + k >= NK16) break;   // rows past the window: U is zero there
                         const uint32_t off = k * 32;
                         const uint32_t acc0 = (Kp > 0 || ch > 0 || k > 0) ? 1u : 0u;
                         umma_f16(d_re, desc_sw64(w_rh + off), desc_sw64(u_h + off), idesc, acc0);
@@ -600,18 +602,32 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
 #pragma unroll
                         for (int j = 0; j < 16; ++j) { zr[j] = re[j]; zi[j] = im[j]; }
                     }
-                    if (jb.zring != nullptr) {   // Eq. 10 history: z as half2, four 16-byte stores
+                    if (jb.zring != nullptr) {
+                        // Eq. 10 history: z as half2, transposed through the warp's buffer so that
+                        // each store instruction writes 8 template rows x 64 contiguous bytes
+                        uint8_t* wbuf = stg + (warp - 2) * C::STG_BUF;
                         uint32_t h[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const __half2 v = __floats2half2_rn(re[j], im[j]);
                             h[j] = *reinterpret_cast<const uint32_t*>(&v);
                         }
-                        const long long pos = (Q0 + 128LL * tt + c) & (jb.zring_len - 1);
-                        uint4* dst = reinterpret_cast<uint4*>(jb.zring + det * jb.zring_det_stride +
-                                                              (long long)m * jb.zring_len + pos);
 #pragma unroll
-                        for (int g = 0; g < 4; ++g) dst[g] = make_uint4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
+                        for (int g = 0; g < 4; ++g)
+                            *reinterpret_cast<uint4*>(wbuf + lane * C::STG_PITCH + g * 16) =
+                                make_uint4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
+                        __syncwarp();
+                        const int rr = lane >> 2, cq = lane & 3;
+                        const long long pos = (Q0 + 128LL * tt + c + 4 * cq) & (jb.zring_len - 1);
+                        uint32_t* zbase = jb.zring + det * jb.zring_det_stride +
+                                          (long long)(tm * kTcTileM + qd * 32) * jb.zring_len + pos;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int r = 8 * i + rr;
+                            *reinterpret_cast<uint4*>(zbase + (long long)r * jb.zring_len) =
+                                *reinterpret_cast<const uint4*>(wbuf + r * C::STG_PITCH + cq * 16);
+                        }
+                        __syncwarp();
                     }
                 }
             } else {
