@@ -52,8 +52,22 @@ __global__ void k_ingest(const float* __restrict__ src, long long src_det_stride
 // ---------------------------------------------------------------------------
 // a1: d_D[q] = sum_k w'[k] d[D q + c - k], w' = sqrt(D) g / sum(g) (Eq. 4),
 // for the n/D new samples q in [k_a/D - N_down, k_b/D - N_down) of every rate.
-// One warp per output sample; lanes stride the 2c+1 taps.
+// A block of 256 threads takes QB = clamp(256 / D, 1, 128) consecutive outputs
+// of one rate and one detector, so that every block does about the same number
+// of multiply-adds at every rate and all blocks of a push fit on the GPU at
+// once.  With m = 2c - k the sum reads d[D (q0 + i) - c + m]: the input span of
+// the block is staged in shared memory split by phase,
+// x_p[j] = d[D q0 - c + m0 + D j + p], so that the taps a warp reads together
+// land in distinct banks; the tap weights come through L1.  Thread t takes
+// output i = t mod QB and every G-th tap, G = 256 / QB, starting at t / QB;
+// taps go through in chunks of kDownMC.  The G partial sums of an output are
+// added by warp shuffles and then across warps, always in the same order.
+// Staging loads are issued 16 per thread before any is stored, so a chunk
+// costs one or two memory round trips; six blocks fit on an SM.
 // ---------------------------------------------------------------------------
+constexpr int kDownThreads = 256;
+constexpr int kDownMC = 4096;    // taps per shared-memory chunk (a multiple of every D <= 256)
+__host__ __device__ constexpr int down_qb(int D) { return D >= 256 ? 1 : (D <= 2 ? 128 : 256 / D); }
 struct DownParams {
     const float* w[kMaxRates];
     float* dst[kMaxRates];
@@ -64,37 +78,75 @@ struct DownParams {
     uint16_t* s_lo[kMaxRates];
     long long s_det_stride[kMaxRates];
     int s_len[kMaxRates];
+    int blk0[kMaxRates + 1];            // first block of each rate along grid x
     int n_rates;
     int mode;                           // 0 FP32 only, 1 FP16, 2 BF16
 };
+// Shared memory of k_downsample: phase rows D x Jp with Jp <= QB + kDownMC / D + 1,
+// so at most D QB + D + kDownMC words (D QB = 256), and one partial sum per thread.
+__host__ __device__ constexpr int down_smem_bytes(int D_max) {
+    return 4 * (256 + D_max + kDownMC + kDownThreads);
+}
 
-__global__ void k_downsample(DownParams p, const float* __restrict__ ring0, long long ring0_det_stride,
-                             int mask0, long long k_a, int n, int n_down, int det0) {
+__global__ void __launch_bounds__(kDownThreads, 6) k_downsample(DownParams p, const float* __restrict__ ring0,
+                                                             long long ring0_det_stride, int mask0, long long k_a,
+                                                             int n, int n_down, int det0) {
+    constexpr int NT = kDownThreads, U = 16;
     pdl_launch_dependents();
-    pdl_wait();
-    const int r = blockIdx.z;
-    if (r >= p.n_rates) return;
-    const int D = p.D[r];
+    extern __shared__ float dsm[];
+    int r = 0;
+    while (r + 1 < p.n_rates && (int)blockIdx.x >= p.blk0[r + 1]) ++r;
+    const int D = p.D[r], lgD = __ffs(D) - 1;
+    const int QB = down_qb(D), G = NT / QB;
     const int nq = n / D;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (qi >= nq) return;
+    const int i0 = ((int)blockIdx.x - p.blk0[r]) * QB;
     const int det = det0 + blockIdx.y;
-    const long long q = k_a / D - n_down + qi;
-    const int c = D * n_down;
-    const int taps = 2 * c + 1;
+    const int c = D * n_down, taps = 2 * c + 1;
+    const int Jp = (QB + kDownMC / D) | 1;           // odd pitch of a phase row
+    float* xs = dsm;                                 // [D][Jp]
+    float* part = dsm + D * Jp;                      // [NT]
+    const int i = threadIdx.x & (QB - 1), g = threadIdx.x / QB;
+    const long long q0 = k_a / D - n_down + i0;
     const float* src = ring0 + det * ring0_det_stride;
-    const float* w = p.w[r];
-    const long long base = (long long)D * q + c;
+    const float* wr = p.w[r] + taps - 1;             // wr[-m] = w'[2c - m]
+    pdl_wait();
     float acc = 0.f;
-    for (int k = lane; k < taps; k += 32) acc = fmaf(__ldg(w + k), src[(base - k) & mask0], acc);
+    for (int m0 = 0; m0 < taps; m0 += kDownMC) {
+        const int L = min(kDownMC, taps - m0);
+        const long long e0 = (long long)D * q0 - c + m0;
+        const int nx = D * (QB - 1) + L;             // staged words: offsets D i + m - m0 of the chunk
+        for (int eb = 0; eb < nx; eb += NT * U) {
+            float v[U];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-        p.dst[r][det * p.dst_det_stride[r] + (q & p.dst_mask[r])] = acc;
+            for (int u = 0; u < U; ++u) {
+                const int e = eb + u * NT + threadIdx.x;
+                v[u] = e < nx ? src[(e0 + e) & mask0] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = eb + u * NT + threadIdx.x;
+                if (e < nx) xs[(e & (D - 1)) * Jp + (e >> lgD)] = v[u];
+            }
+        }
+        __syncthreads();
+        const float* wc = wr - m0;
+#pragma unroll 4
+        for (int m = g; m < L; m += G) acc = fmaf(__ldg(wc - m), xs[(m & (D - 1)) * Jp + (m >> lgD) + i], acc);
+        __syncthreads();
+    }
+    // Lanes o apart (o = QB, 2 QB, ... < 32) hold the same output.
+    for (int o = QB; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    const int S = QB > 32 ? QB : 32;                 // threads i, i + S, ... hold the remaining partials
+    if ((int)threadIdx.x < QB && i0 + i < nq) {
+        float v = part[i];
+        for (int t = i + S; t < NT; t += S) v += part[t];
+        const long long q = q0 + i;
+        p.dst[r][det * p.dst_det_stride[r] + (q & p.dst_mask[r])] = v;
         if (p.mode) {
             uint16_t h, l;
-            split_hilo_rt(acc, p.mode, h, l);
+            split_hilo_rt(v, p.mode, h, l);
             const long long ps = q & (p.s_len[r] - 1);
             const long long o = det * p.s_det_stride[r];
             p.s_hi[r][o + ps] = h; p.s_hi[r][o + ps + p.s_len[r]] = h;

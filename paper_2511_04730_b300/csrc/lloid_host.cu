@@ -114,6 +114,7 @@ struct lloid_ctx {
     long long ring0_len = 0;
     int n_rates = 0;
     int rate_D[kMaxRates] = {};
+    int down_smem = 0;                   // dynamic shared memory of k_downsample
     float* rate_ring[kMaxRates] = {};
     long long rate_len[kMaxRates] = {};
     float* w_down[kMaxRates] = {};
@@ -850,10 +851,19 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
             p.s_det_stride[r] = 2 * ctx->s_len[r + 1]; p.s_len[r] = (int)ctx->s_len[r + 1];
         }
         p.mode = ctx->cfg.precision;
-        dim3 grid((unsigned)((n / 2 + 7) / 8), nd, ctx->n_rates);
-        CK(launch_pdl(k_downsample, grid, dim3(256), 0, ctx->stream, p, (const float*)ctx->ring0, ctx->ring0_len,
-                      (int)(ctx->ring0_len - 1), k_a, n_i, (int)ctx->cfg.n_down, det0));
-        ++ctx->launches;
+        int blocks = 0;
+        for (int r = 0; r < ctx->n_rates; ++r) {
+            p.blk0[r] = blocks;
+            const int qb = down_qb(ctx->rate_D[r]);
+            blocks += (int)((n / ctx->rate_D[r] + qb - 1) / qb);
+        }
+        p.blk0[ctx->n_rates] = blocks;
+        if (blocks > 0) {
+            CK(launch_pdl(k_downsample, dim3((unsigned)blocks, nd), dim3(kDownThreads), ctx->down_smem, ctx->stream, p,
+                          (const float*)ctx->ring0, ctx->ring0_len, (int)(ctx->ring0_len - 1), k_a, n_i,
+                          (int)ctx->cfg.n_down, det0));
+            ++ctx->launches;
+        }
     }
     if (ctx->banks.empty()) return LLOID_OK;
     if (!split_precision(ctx)) {
@@ -1309,6 +1319,8 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         if ((st = dalloc(ctx, &ctx->w_down[r], w.size() * 4, nullptr, &ctx->state_bytes))) return st;
         CK(cudaMemcpyAsync(ctx->w_down[r], w.data(), w.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     }
+    ctx->down_smem = down_smem_bytes(ctx->n_rates ? ctx->rate_D[ctx->n_rates - 1] : 1);
+    CK(cudaFuncSetAttribute(k_downsample, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->down_smem));
     if (c.precision != LLOID_FP32) {
         // hi/lo double-mapped streams for the tensor-core FIR (index 0 = f0)
         for (int r = 0; r <= ctx->n_rates; ++r) {
