@@ -389,59 +389,129 @@ __global__ void __launch_bounds__(256) k_recon_f32(const ReconJob* __restrict__ 
 // a5: finalise window w for one (bank, detector): reduce the tile partials of
 // every template, threshold, and flag the bank's loudest template.
 // ---------------------------------------------------------------------------
-// grid (bank, detector, window): windows w0 .. w0 + gridDim.z - 1; window w's
-// slab is slab_base + (w mod ring) * n_det_total * slab_det_stride.
-__global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ jobs, const Partial* __restrict__ part,
-                                                  long long part_tmpl_stride, int n_slots, int tiles_per_window,
-                                                  long long w0, float threshold, SlabEntry* __restrict__ slab_base,
-                                                  int ring, int n_det_total, long long slab_det_stride, int det0) {
-    pdl_launch_dependents();
-    pdl_wait();
-    const FinJob jb = jobs[blockIdx.x];
-    const int det = det0 + blockIdx.y;
-    const long long w = w0 + blockIdx.z;
-    SlabEntry* slab = slab_base + (size_t)(w % ring) * n_det_total * slab_det_stride;
-    const int s0 = (int)((w * tiles_per_window) & (n_slots - 1));
-    SlabEntry* out = slab + det * slab_det_stride;
-    float tbest = -1.f;
-    int tidx = 0x7fffffff;
-    for (int m = threadIdx.x; m < jb.M; m += blockDim.x) {
-        const Partial* p = part + (long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots;
-        float best = -1.f, bre = 0.f, bim = 0.f;
-        int bk = 0x7fffffff;
-        for (int s = 0; s < tiles_per_window; ++s) {
-            float4 v = p[(s0 + s) & (n_slots - 1)];
-            int k = __float_as_int(v.y);
-            if (better(v.x, k, best, bk)) { best = v.x; bk = k; bre = v.z; bim = v.w; }
-        }
-        SlabEntry e;
-        e.snr = sqrtf(best);
-        e.phase = atan2f(bim, bre);
-        e.re = bre;
-        e.im = bim;
-        e.k_off = bk;
-        e.flags = (e.snr > threshold) ? 1 : 0;
-        e.xi2 = -1.f;
-        e.pad = 0;
-        out[jb.tmpl0 + m] = e;
-        if (best > tbest || (best == tbest && m < tidx)) { tbest = best; tidx = m; }
-    }
+// grid (chunk, detector, window): a chunk is kFinTB templates of one bank; a
+// half-warp reduces one template's tile partials (16 lanes read them side by
+// side).  Windows w0 .. w0 + gridDim.z - 1; window w's slab is
+// slab_base + (w mod ring) * n_det_total * slab_det_stride.  The bank's loudest
+// template (largest max |z|^2, lowest index on ties) is found across chunks by
+// an atomic max on an order-preserving 64-bit key; the last chunk block to
+// finish flags it and clears the key and the counter for the next push.
+constexpr int kFinTB = 64;          // templates per k_finalize block
+constexpr int kCoincTB = 256;       // templates per k_coinc block
+struct FinChunk { int job, m0; };
+
+// Key whose unsigned order is (x ascending, m descending): float bits mapped to
+// an unsigned total order in the high word, ~m in the low word.
+__device__ __forceinline__ unsigned long long max_key(float x, int m) {
+    uint32_t u = __float_as_uint(x);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)u << 32) | (uint32_t)(0xffffffffu - (uint32_t)m);
+}
+__device__ __forceinline__ int max_key_index(unsigned long long k) {
+    return (int)(0xffffffffu - (uint32_t)(k & 0xffffffffu));
+}
+
+// Block-wide argmax of (v, idx) (largest v, lowest idx on ties) in thread 0.
+__device__ __forceinline__ void block_argmax(float& v, int& idx) {
     __shared__ float sb[32];
     __shared__ int si[32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        float ob = __shfl_xor_sync(0xffffffffu, tbest, o);
-        int oi = __shfl_xor_sync(0xffffffffu, tidx, o);
-        if (ob > tbest || (ob == tbest && oi < tidx)) { tbest = ob; tidx = oi; }
+        const float ob = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ob > v || (ob == v && oi < idx)) { v = ob; idx = oi; }
     }
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { sb[wid] = tbest; si[wid] = tidx; }
+    if (lane == 0) { sb[wid] = v; si[wid] = idx; }
     __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
+            if (sb[i] > v || (sb[i] == v && si[i] < idx)) { v = sb[i]; idx = si[i]; }
+}
+
+__global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ jobs, const FinChunk* __restrict__ chunks,
+                                                  const Partial* __restrict__ part, long long part_tmpl_stride,
+                                                  int n_slots, int tiles_per_window, long long w0, float threshold,
+                                                  SlabEntry* __restrict__ slab_base, int ring, int n_det_total,
+                                                  long long slab_det_stride, int det0,
+                                                  unsigned long long* __restrict__ red) {
+    constexpr int P = kFinTB / 16;
+    pdl_launch_dependents();
+    pdl_wait();
+    const FinChunk ch = chunks[blockIdx.x];
+    const FinJob jb = jobs[ch.job];
+    const int det = det0 + blockIdx.y;
+    const long long w = w0 + blockIdx.z;
+    SlabEntry* out = slab_base + (size_t)(w % ring) * n_det_total * slab_det_stride + det * slab_det_stride;
+    const int s0 = (int)((w * tiles_per_window) & (n_slots - 1));
+    const int hw = threadIdx.x >> 4, l16 = threadIdx.x & 15;
+    const Partial none = make_float4(-1.f, __int_as_float(0x7fffffff), 0.f, 0.f);
+    Partial v[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {            // every first-round load in flight at once
+        const int m = ch.m0 + 16 * p + hw;
+        v[p] = (m < jb.M && l16 < tiles_per_window)
+                   ? part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots +
+                          ((s0 + l16) & (n_slots - 1))]
+                   : none;
+    }
+    float tbest = -1.f;
+    int tidx = 0x7fffffff;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int m = ch.m0 + 16 * p + hw;
+        float best = v[p].x, bre = v[p].z, bim = v[p].w;
+        int bk = __float_as_int(v[p].y);
+        if (m < jb.M) {
+            const Partial* pt = part + (long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots;
+            for (int s = l16 + 16; s < tiles_per_window; s += 16) {
+                const float4 u = pt[(s0 + s) & (n_slots - 1)];
+                const int k = __float_as_int(u.y);
+                if (better(u.x, k, best, bk)) { best = u.x; bk = k; bre = u.z; bim = u.w; }
+            }
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {   // within the half-warp
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            const float ore = __shfl_xor_sync(0xffffffffu, bre, o), oim = __shfl_xor_sync(0xffffffffu, bim, o);
+            if (better(ob, ok, best, bk)) { best = ob; bk = ok; bre = ore; bim = oim; }
+        }
+        if (m < jb.M) {
+            if (l16 == 0) {
+                SlabEntry e;
+                e.snr = sqrtf(best);
+                e.phase = atan2f(bim, bre);
+                e.re = bre;
+                e.im = bim;
+                e.k_off = bk;
+                e.flags = (e.snr > threshold) ? 1 : 0;
+                e.xi2 = -1.f;
+                e.pad = 0;
+                out[jb.tmpl0 + m] = e;
+            }
+            if (best > tbest || (best == tbest && m < tidx)) { tbest = best; tidx = m; }
+        }
+    }
+    __threadfence();                          // slab entries visible before this block counts itself done
+    block_argmax(tbest, tidx);
     if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int i = 1; i < nw; ++i)
-            if (sb[i] > tbest || (sb[i] == tbest && si[i] < tidx)) { tbest = sb[i]; tidx = si[i]; }
-        if (tidx < jb.M && (out[jb.tmpl0 + tidx].flags & 1)) out[jb.tmpl0 + tidx].flags |= 2;
+        const size_t slot = ((size_t)ch.job * n_det_total + det) * ring + (size_t)(w % ring);
+        unsigned long long* key = red + 2 * slot;
+        unsigned long long* cnt = key + 1;
+        if (tidx < jb.M) atomicMax(key, max_key(tbest, tidx));
+        __threadfence();
+        const unsigned long long n_chunks = (unsigned long long)((jb.M + kFinTB - 1) / kFinTB);
+        if (atomicAdd(cnt, 1ull) == n_chunks - 1) {   // last chunk of this (bank, detector, window)
+            __threadfence();
+            const unsigned long long k = atomicExch(key, 0ull);
+            atomicExch(cnt, 0ull);
+            const int m = max_key_index(k);
+            if (k != 0ull && m >= 0 && m < jb.M) {
+                int* f = &out[jb.tmpl0 + m].flags;
+                if (atomicAdd(f, 0) & 1) atomicOr(f, 2);
+            }
+        }
     }
 }
 
@@ -593,76 +663,80 @@ __global__ void __launch_bounds__(256) k_xi2(const Xi2Job* __restrict__ jobs, co
 
 // ---------------------------------------------------------------------------
 // Coincidence and clustering (Sections II.D.3-4) for windows w0 .. w0 +
-// gridDim.y - 1: one CTA per (bank, window), threads over templates.  For a
-// template, the loudest detector's trigger (lowest detector on ties) is the
-// reference; triggers of the other detectors within `delta` samples join; two
-// or more detectors make an event of network SNR sqrt(sum snr^2).  The CTA
-// keeps the bank's event of largest network SNR (lowest template on ties).
+// gridDim.y - 1: grid (chunk of kCoincTB templates of one bank, window), a
+// thread per template.  For a template, the loudest detector's trigger (lowest
+// detector on ties) is the reference; triggers of the other detectors within
+// `delta` samples join; two or more detectors make an event of network SNR
+// sqrt(sum snr^2).  The bank keeps its event of largest network SNR (lowest
+// template on ties): an atomic max on an order-preserving key across chunks;
+// the last chunk block to finish rebuilds that template's event, stores it and
+// clears the key and the counter for the next push.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_coinc(const FinJob* __restrict__ jobs, long long w0, int n_det,
-                                               int delta, const SlabEntry* __restrict__ slab_base, int ring,
-                                               long long slab_det_stride, EventEntry* __restrict__ ev_base,
-                                               int ev_cap) {
+struct CoincHit { float net; int n, ref, k0; uint32_t mask; };
+__device__ __forceinline__ CoincHit coinc_of(const SlabEntry* __restrict__ slab, long long slab_det_stride, int t,
+                                             int n_det, int delta) {
+    CoincHit h{-1.f, 0, -1, 0, 0u};
+    float rs = 0.f;
+    for (int d = 0; d < n_det; ++d) {
+        const SlabEntry& e = slab[d * slab_det_stride + t];
+        if ((e.flags & 1) && (h.ref < 0 || e.snr > rs)) { h.ref = d; rs = e.snr; }
+    }
+    if (h.ref < 0) return h;
+    h.k0 = slab[h.ref * slab_det_stride + t].k_off;
+    float s2 = 0.f;
+    for (int d = 0; d < n_det; ++d) {
+        const SlabEntry& e = slab[d * slab_det_stride + t];
+        if ((e.flags & 1) && abs(e.k_off - h.k0) <= delta) {
+            s2 = fmaf(e.snr, e.snr, s2);
+            ++h.n;
+            h.mask |= 1u << d;
+        }
+    }
+    if (h.n >= 2) h.net = sqrtf(s2);
+    return h;
+}
+
+__global__ void __launch_bounds__(256) k_coinc(const FinJob* __restrict__ jobs, const FinChunk* __restrict__ chunks,
+                                               long long w0, int n_det, int delta,
+                                               const SlabEntry* __restrict__ slab_base, int ring,
+                                               long long slab_det_stride, EventEntry* __restrict__ ev_base, int ev_cap,
+                                               unsigned long long* __restrict__ red) {
     pdl_launch_dependents();
     pdl_wait();
-    const FinJob jb = jobs[blockIdx.x];
+    const FinChunk ch = chunks[blockIdx.x];
+    const FinJob jb = jobs[ch.job];
     const long long w = w0 + blockIdx.y;
     const SlabEntry* slab = slab_base + (size_t)(w % ring) * n_det * slab_det_stride;
     float best = -1.f;
-    int bm = 0x7fffffff, bn = 0, bref = 0, bk = 0;
-    uint32_t bmask = 0;
-    for (int m = threadIdx.x; m < jb.M; m += blockDim.x) {
-        int ref = -1;
-        float rs = 0.f;
-        for (int d = 0; d < n_det; ++d) {
-            const SlabEntry& e = slab[d * slab_det_stride + jb.tmpl0 + m];
-            if ((e.flags & 1) && (ref < 0 || e.snr > rs)) { ref = d; rs = e.snr; }
-        }
-        if (ref < 0) continue;
-        const int k0 = slab[ref * slab_det_stride + jb.tmpl0 + m].k_off;
-        float s2 = 0.f;
-        int n = 0;
-        uint32_t mask = 0;
-        for (int d = 0; d < n_det; ++d) {
-            const SlabEntry& e = slab[d * slab_det_stride + jb.tmpl0 + m];
-            if ((e.flags & 1) && abs(e.k_off - k0) <= delta) {
-                s2 = fmaf(e.snr, e.snr, s2);
-                ++n;
-                mask |= 1u << d;
-            }
-        }
-        if (n < 2) continue;
-        const float net = sqrtf(s2);
-        if (net > best || (net == best && m < bm)) { best = net; bm = m; bn = n; bref = ref; bk = k0; bmask = mask; }
+    int bm = 0x7fffffff;
+    const int m = ch.m0 + (int)threadIdx.x;
+    if (m < jb.M) {
+        const CoincHit h = coinc_of(slab, slab_det_stride, jb.tmpl0 + m, n_det, delta);
+        if (h.n >= 2) { best = h.net; bm = m; }
     }
-    __shared__ float sb[8];
-    __shared__ int sm[8], sn[8], sr[8], sk[8];
-    __shared__ uint32_t smask[8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int om = __shfl_xor_sync(0xffffffffu, bm, o), on = __shfl_xor_sync(0xffffffffu, bn, o);
-        const int orf = __shfl_xor_sync(0xffffffffu, bref, o), ok = __shfl_xor_sync(0xffffffffu, bk, o);
-        const uint32_t omk = __shfl_xor_sync(0xffffffffu, bmask, o);
-        if (ob > best || (ob == best && om < bm)) { best = ob; bm = om; bn = on; bref = orf; bk = ok; bmask = omk; }
-    }
-    if (lane == 0) { sb[wid] = best; sm[wid] = bm; sn[wid] = bn; sr[wid] = bref; sk[wid] = bk; smask[wid] = bmask; }
-    __syncthreads();
+    block_argmax(best, bm);
     if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
-            if (sb[i] > best || (sb[i] == best && sm[i] < bm)) {
-                best = sb[i]; bm = sm[i]; bn = sn[i]; bref = sr[i]; bk = sk[i]; bmask = smask[i];
+        const size_t slot = (size_t)ch.job * ring + (size_t)(w % ring);
+        unsigned long long* key = red + 2 * slot;
+        unsigned long long* cnt = key + 1;
+        if (bm < jb.M) atomicMax(key, max_key(best, bm));
+        __threadfence();
+        const unsigned long long n_chunks = (unsigned long long)((jb.M + kCoincTB - 1) / kCoincTB);
+        if (atomicAdd(cnt, 1ull) == n_chunks - 1) {
+            __threadfence();
+            const unsigned long long k = atomicExch(key, 0ull);
+            atomicExch(cnt, 0ull);
+            EventEntry ev;
+            ev.net_snr = -1.f; ev.tmpl = 0x7fffffff; ev.n_ifo = 0; ev.ifo_mask = 0; ev.ref_det = 0; ev.ref_k_off = 0;
+            ev.pad[0] = ev.pad[1] = 0;
+            const int bt = max_key_index(k);
+            if (k != 0ull && bt >= 0 && bt < jb.M) {
+                const CoincHit h = coinc_of(slab, slab_det_stride, jb.tmpl0 + bt, n_det, delta);
+                ev.net_snr = h.net; ev.tmpl = bt; ev.n_ifo = h.n; ev.ifo_mask = h.mask; ev.ref_det = h.ref;
+                ev.ref_k_off = h.k0;
             }
-        EventEntry ev;
-        ev.net_snr = best;
-        ev.tmpl = bm;
-        ev.n_ifo = bn;
-        ev.ifo_mask = bmask;
-        ev.ref_det = bref;
-        ev.ref_k_off = bk;
-        ev.pad[0] = ev.pad[1] = 0;
-        ev_base[(size_t)(w % ring) * ev_cap + jb.bank] = ev;
+            ev_base[(size_t)(w % ring) * ev_cap + jb.bank] = ev;
+        }
     }
 }
 

@@ -168,6 +168,13 @@ struct lloid_ctx {
     UpJob* d_up = nullptr; int* d_up_base = nullptr; int n_up = 0, up_tiles = 0, up_smem = 0;
     ReconJob* d_rec = nullptr; int* d_rec_base = nullptr; int n_rec = 0, rec_tiles = 0;
     FinJob* d_finj = nullptr; int n_fin = 0;
+    // chunk tables of k_finalize (kFinTB templates) and k_coinc (kCoincTB), and their
+    // cross-chunk reductions: a (key, count) pair per (job, detector, window slot) and
+    // per (job, window slot), zero between launches
+    FinChunk* d_fin_chunks = nullptr; int n_fin_chunks = 0;
+    FinChunk* d_coinc_chunks = nullptr; int n_coinc_chunks = 0;
+    unsigned long long* d_fin_red = nullptr;
+    unsigned long long* d_coinc_red = nullptr;
     // split path job tables: FIR over all slices, levels per depth below the top
     FirTcJob* d_firtc = nullptr; FirMaps* d_firmaps = nullptr; int* d_firtc_base = nullptr;
     int n_firtc = 0, firtc_tiles = 0, firtc_smem = 0, firtc_strip = 0, firtc_stages = 0;
@@ -374,6 +381,8 @@ void free_jobs(lloid_ctx* ctx) {
     for (void* p : ctx->job_allocs) cudaFree(p);
     ctx->job_allocs.clear();
     ctx->d_fir = nullptr; ctx->d_up = nullptr; ctx->d_rec = nullptr; ctx->d_finj = nullptr;
+    ctx->d_fin_chunks = ctx->d_coinc_chunks = nullptr; ctx->n_fin_chunks = ctx->n_coinc_chunks = 0;
+    ctx->d_fin_red = ctx->d_coinc_red = nullptr;
     ctx->d_firtc = nullptr; ctx->d_firmaps = nullptr; ctx->d_firtc_base = nullptr;
     for (int d = 0; d < lloid_ctx::kLevTables; ++d) {
         ctx->d_lev[d] = nullptr; ctx->d_levmaps[d] = nullptr; ctx->d_lev_base[d] = nullptr;
@@ -672,6 +681,21 @@ lloid_status build_jobs(lloid_ctx* ctx, long long n) {
     lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_finj, fin))) return st;
     ctx->n_fin = (int)fin.size();
+    {
+        std::vector<FinChunk> fc, cc;
+        for (int j = 0; j < (int)fin.size(); ++j) {
+            for (int m0 = 0; m0 < fin[j].M; m0 += kFinTB) fc.push_back(FinChunk{j, m0});
+            for (int m0 = 0; m0 < fin[j].M; m0 += kCoincTB) cc.push_back(FinChunk{j, m0});
+        }
+        if ((st = upload_vec(ctx, &ctx->d_fin_chunks, fc))) return st;
+        if ((st = upload_vec(ctx, &ctx->d_coinc_chunks, cc))) return st;
+        ctx->n_fin_chunks = (int)fc.size();
+        ctx->n_coinc_chunks = (int)cc.size();
+        const std::vector<unsigned long long> zf((size_t)2 * fin.size() * ctx->cfg.n_detectors * kWindowRing, 0ull);
+        const std::vector<unsigned long long> zc((size_t)2 * fin.size() * kWindowRing, 0ull);
+        if ((st = upload_vec(ctx, &ctx->d_fin_red, zf))) return st;
+        if ((st = upload_vec(ctx, &ctx->d_coinc_red, zc))) return st;
+    }
     {   // Eq. 10: one tile per 8 templates of every bank with autocorrelations
         std::vector<Xi2Job> xj;
         std::vector<int> xb;
@@ -937,11 +961,12 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     StageTimer tmf(ctx, 5);
     const long long w_first = k_a / W, w_end = (k_a + n) / W;   // windows completed by this push
     if (w_end > w_first && ctx->n_fin > 0) {
-        dim3 grid(ctx->n_fin, nd, (unsigned)(w_end - w_first));
+        dim3 grid(ctx->n_fin_chunks, nd, (unsigned)(w_end - w_first));
         CK(launch_pdl(k_finalize, grid, dim3(256), 0, ctx->stream, (const FinJob*)ctx->d_finj,
-                      (const Partial*)ctx->d_part, (long long)ctx->cfg.n_detectors * ctx->n_slots, ctx->n_slots,
-                      ctx->tiles_per_window, w_first, ctx->cfg.snr_threshold, ctx->d_slab, (int)kWindowRing,
-                      ctx->cfg.n_detectors, (long long)ctx->M_cap, det0));
+                      (const FinChunk*)ctx->d_fin_chunks, (const Partial*)ctx->d_part,
+                      (long long)ctx->cfg.n_detectors * ctx->n_slots, ctx->n_slots, ctx->tiles_per_window, w_first,
+                      ctx->cfg.snr_threshold, ctx->d_slab, (int)kWindowRing, ctx->cfg.n_detectors,
+                      (long long)ctx->M_cap, det0, ctx->d_fin_red));
         ++ctx->launches;
     }
     // Eq. 10 for the windows whose triggers now have d samples of z past the window end
@@ -968,10 +993,10 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
         const int ndt = ctx->cfg.n_detectors;
         long long w_lo = std::max(ctx->coinc_next, w_all - (long long)kWindowRing);
         if (ndt >= 2 && ndt <= 32 && ctx->n_fin > 0 && w_all > w_lo) {
-            CK(launch_pdl(k_coinc, dim3(ctx->n_fin, (unsigned)(w_all - w_lo)), dim3(256), 0, ctx->stream,
-                          (const FinJob*)ctx->d_finj, w_lo, ndt, (int)ctx->cfg.coinc_window,
-                          (const SlabEntry*)ctx->d_slab, (int)kWindowRing, (long long)ctx->M_cap, ctx->d_events,
-                          ctx->bank_cap));
+            CK(launch_pdl(k_coinc, dim3(ctx->n_coinc_chunks, (unsigned)(w_all - w_lo)), dim3(256), 0, ctx->stream,
+                          (const FinJob*)ctx->d_finj, (const FinChunk*)ctx->d_coinc_chunks, w_lo, ndt,
+                          (int)ctx->cfg.coinc_window, (const SlabEntry*)ctx->d_slab, (int)kWindowRing,
+                          (long long)ctx->M_cap, ctx->d_events, ctx->bank_cap, ctx->d_coinc_red));
             ++ctx->launches;
             if (ctx->bg_nsnr > 0) {
                 int mmax = 1;
@@ -1288,6 +1313,8 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         c.precision < 0 || c.precision > 2 || !(c.snr_threshold >= 0.f) || c.coinc_window < 0)
         return fail(nullptr, LLOID_EINVAL, "bad configuration");
     if (c.window_overlap != 0) return LLOID_EINVAL;
+    if (c.max_block / c.window_samples + 1 > kWindowRing)
+        return fail(nullptr, LLOID_EINVAL, "a push may complete at most %d trigger windows", kWindowRing);
     if (c.precision != LLOID_FP32 && (c.max_block % kTcTileN || c.n_up != 8 || c.f0 / c.min_rate > 64))
         return fail(nullptr, LLOID_EINVAL, "tensor-core paths need max_block % 128 == 0 and n_up == 8");
     CK(cudaSetDevice(c.device));
