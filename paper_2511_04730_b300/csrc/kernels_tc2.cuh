@@ -106,14 +106,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
-__device__ __forceinline__ int job_of(const int* __restrict__ base, int n, int t) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (__ldg(base + mid) <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
+// Per-tile facts, written by the host with the job tables: x = job, y = tile index within the
+// job, z = K'pad of the job, w = its N (FIR c-groups per tile; 0 for a ladder level).  One load
+// replaces a search of the job table, and the MMA issuers read the next tile's entry while the
+// current tile's MMAs run.
+using TileInfo = int4;
 __device__ __forceinline__ long long fdiv(long long a, long long b) {
     long long q = a / b;
     return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
@@ -178,7 +175,7 @@ struct FirCfg {
 
 template <bool BF16>
 __global__ void __launch_bounds__(192, 1)
-    k_fir_tc(const FirTcJob* __restrict__ jobs, const FirMaps* __restrict__ maps, const int* __restrict__ tile_base,
+    k_fir_tc(const FirTcJob* __restrict__ jobs, const FirMaps* __restrict__ maps, const TileInfo* __restrict__ tinfo,
              const int* __restrict__ sched, int n_jobs, int tiles_per_det, long long k_a, int det0, int n_det_push, int strip_bytes,
              int n_stages, int* __restrict__ err) {
     using C = FirCfg<BF16>;
@@ -227,10 +224,9 @@ __global__ void __launch_bounds__(192, 1)
             for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1] && ok; ++k) {
                 const int it = sched[gridDim.x + 1 + k];
                 const int det = det0 + it % n_det_push;
-                const int t = it / n_det_push;
-                const int jx = job_of(tile_base, n_jobs, t);
-                const FirTcJob& jb = jobs[jx];
-                const int local = t - tile_base[jx];
+                const TileInfo ti = tinfo[it / n_det_push];
+                const FirTcJob& jb = jobs[ti.x];
+                const int local = ti.y;
                 const int mt = local % jb.Mtiles, ct = local / jb.Mtiles;
                 const long long qa = fdiv(k_a - 1 + jb.Lambda, jb.D) + 1;
                 const long long c0 = fdiv(qa, 8) + (long long)ct * jb.NC;
@@ -267,10 +263,14 @@ __global__ void __launch_bounds__(192, 1)
             int stage = 0, sb = 0, i = 0;
             uint32_t phase = 0, sphase = 0;
             bool ok = true;
-            for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1] && ok; ++k, ++i) {
-                const int t = sched[gridDim.x + 1 + k] / n_det_push;
-                const int jx = job_of(tile_base, n_jobs, t);
-                const int Kp = jobs[jx].Kp, NC = jobs[jx].NC;
+            const int kb = sched[blockIdx.x], ke = sched[blockIdx.x + 1];
+            TileInfo tnext = kb < ke ? tinfo[sched[gridDim.x + 1 + kb] / n_det_push] : TileInfo{};
+            int snext = kb + 1 < ke ? sched[gridDim.x + 1 + kb + 1] : 0;
+            for (int k = kb; k < ke && ok; ++k, ++i) {
+                const TileInfo tcur = tnext;             // the next entries load while this tile runs
+                if (k + 1 < ke) tnext = tinfo[snext / n_det_push];
+                if (k + 2 < ke) snext = sched[gridDim.x + 1 + k + 2];
+                const int Kp = tcur.z, NC = tcur.w;
                 const uint32_t idesc = idesc_f16(BF16, 128, NC);
                 const int buf = i & 1;
                 if (!mbar_wait(t_empty + buf, ((i >> 1) & 1) ^ 1, err, 25)) { ok = false; break; }
@@ -314,10 +314,9 @@ __global__ void __launch_bounds__(192, 1)
         for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1]; ++k, ++i) {
             const int it = sched[gridDim.x + 1 + k];
             const int det = det0 + it % n_det_push;
-            const int t = it / n_det_push;
-            const int jx = job_of(tile_base, n_jobs, t);
-            const FirTcJob& jb = jobs[jx];
-            const int local = t - tile_base[jx];
+            const TileInfo ti = tinfo[it / n_det_push];
+            const FirTcJob& jb = jobs[ti.x];
+            const int local = ti.y;
             const int mt = local % jb.Mtiles, ct = local / jb.Mtiles;
             const long long qa = fdiv(k_a - 1 + jb.Lambda, jb.D) + 1;
             const long long c0 = fdiv(qa, 8) + (long long)ct * jb.NC;
@@ -393,7 +392,7 @@ struct LevCfg {
 template <bool BF16, bool TOP, bool STORE_Z, int F>
 __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
     k_level_tc(const LevelJob* __restrict__ jobs, const LevelMaps* __restrict__ maps,
-               const int* __restrict__ tile_base, const int* __restrict__ sched, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
+               const TileInfo* __restrict__ tinfo, const int* __restrict__ sched, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
                int det0, int n_det_push, long long window, Partial* __restrict__ part, long long part_tmpl_stride,
                int n_slots, float* __restrict__ zout, int* __restrict__ err) {
     using C = LevCfg<BF16, TOP>;
@@ -438,11 +437,10 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
             for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1] && ok; ++k) {
                 const int it = sched[gridDim.x + 1 + k];
                 const int det = det0 + it % n_det_push;
-                const int t = it / n_det_push;
-                const int jx = job_of(tile_base, n_jobs, t);
-                const LevelJob& jb = jobs[jx];
+                const TileInfo ti = tinfo[it / n_det_push];
+                const LevelJob& jb = jobs[ti.x];
                 const LevelMaps* mp = maps + jb.map;
-                const int local = t - tile_base[jx];
+                const int local = ti.y;
                 const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
                 const long long Qt = fdiv(fdiv(k_a - jb.Lambda, jb.D), 128) * 128 + 128LL * tt;
                 const int yrow = det * 2 * jb.y_rows + (int)(Qt & (jb.y_rows - 1));
@@ -493,10 +491,14 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
             int stage = 0, i = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1] && ok; ++k, ++i) {
-                const int t = sched[gridDim.x + 1 + k] / n_det_push;
-                const int jx = job_of(tile_base, n_jobs, t);
-                const int Kp = jobs[jx].Kp;
+            const int kb = sched[blockIdx.x], ke = sched[blockIdx.x + 1];
+            TileInfo tnext = kb < ke ? tinfo[sched[gridDim.x + 1 + kb] / n_det_push] : TileInfo{};
+            int snext = kb + 1 < ke ? sched[gridDim.x + 1 + kb + 1] : 0;
+            for (int k = kb; k < ke && ok; ++k, ++i) {
+                const TileInfo tcur = tnext;             // the next entries load while this tile runs
+                if (k + 1 < ke) tnext = tinfo[snext / n_det_push];
+                if (k + 2 < ke) snext = sched[gridDim.x + 1 + k + 2];
+                const int Kp = tcur.z;
                 const int buf = i & 1;
                 if (!mbar_wait(tempty + buf, ((i >> 1) & 1) ^ 1, err, 33)) { ok = false; break; }
                 tc_fence_after();
@@ -563,10 +565,9 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
         for (int k = sched[blockIdx.x]; k < sched[blockIdx.x + 1]; ++k, ++i) {
             const int it = sched[gridDim.x + 1 + k];
             const int det = det0 + it % n_det_push;
-            const int t = it / n_det_push;
-            const int jx = job_of(tile_base, n_jobs, t);
-            const LevelJob& jb = jobs[jx];
-            const int local = t - tile_base[jx];
+            const TileInfo ti = tinfo[it / n_det_push];
+            const LevelJob& jb = jobs[ti.x];
+            const int local = ti.y;
             const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
             const int buf = i & 1;
             const bool got = mbar_wait(tfull + buf, (i >> 1) & 1, err, 36);

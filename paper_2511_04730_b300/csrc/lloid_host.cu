@@ -176,13 +176,14 @@ struct lloid_ctx {
     unsigned long long* d_fin_red = nullptr;
     unsigned long long* d_coinc_red = nullptr;
     // split path job tables: FIR over all slices, levels per depth below the top
-    FirTcJob* d_firtc = nullptr; FirMaps* d_firmaps = nullptr; int* d_firtc_base = nullptr;
+    FirTcJob* d_firtc = nullptr; FirMaps* d_firmaps = nullptr; TileInfo* d_firtc_base = nullptr;   // per tile
     int n_firtc = 0, firtc_tiles = 0, firtc_smem = 0, firtc_strip = 0, firtc_stages = 0;
     static constexpr int kMaxDepth = 8;
     // one table per (depth, F slot): F = 0 (lowest level), 2, 4, ..., 64 -> slot 0..6
     static constexpr int kFSlots = 7;
     static constexpr int kLevTables = kMaxDepth * kFSlots;
-    LevelJob* d_lev[kLevTables] = {}; LevelMaps* d_levmaps[kLevTables] = {}; int* d_lev_base[kLevTables] = {};
+    LevelJob* d_lev[kLevTables] = {}; LevelMaps* d_levmaps[kLevTables] = {};
+    TileInfo* d_lev_base[kLevTables] = {};   // per tile of each level table
     // tile schedules ([grid + 1] offsets, then tile ids) for pushes of one detector [0]
     // and of all detectors [1]
     int* d_lev_sched[kLevTables][2] = {}; int lev_grid[kLevTables][2] = {};
@@ -527,10 +528,10 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     const int nd = c.n_detectors;
     std::vector<FirTcJob> fj;
     std::vector<FirMaps> fm;
-    std::vector<int> fb;
+    std::vector<TileInfo> fb;
     std::vector<LevelJob> lj[lloid_ctx::kLevTables];
     std::vector<LevelMaps> lm[lloid_ctx::kLevTables];
-    std::vector<int> lb[lloid_ctx::kLevTables];
+    std::vector<TileInfo> lb[lloid_ctx::kLevTables];
     int lt[lloid_ctx::kLevTables] = {};
     int ft = 0, strip = 128, max_depth = 0;
     ctx->top_job_of_bank.assign(ctx->next_bank_id, -1);
@@ -563,7 +564,8 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             if (ok && bf) ok = encode_map(&mp.a_lo, bf, fsr.d_a_lo, fsr.Kp, (long long)fsr.Mtiles * 128, 128);
             if (!ok) return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (FIR bank %d)", b->id);
             strip = std::max(strip, (2 * (8 * f.NC + f.Kp) + 127) / 128 * 128);
-            fj.push_back(f); fm.push_back(mp); fb.push_back(ft); ft += f.Mtiles * f.ctiles;
+            for (int l = 0; l < f.Mtiles * f.ctiles; ++l) fb.push_back(TileInfo{(int)fj.size(), l, f.Kp, f.NC});
+            fj.push_back(f); fm.push_back(mp); ft += f.Mtiles * f.ctiles;
         }
         for (int j = 0; j < nl; ++j) {
             const LevelRT& L = b->lev[j];
@@ -615,7 +617,8 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             }
 
             if (depth == 0) { ctx->top_job_of_bank[b->id] = (int)lj[tab].size(); ctx->top_slot_of_bank[b->id] = fslot; }
-            lj[tab].push_back(q); lm[tab].push_back(mp); lb[tab].push_back(lt[tab]);
+            for (int l = 0; l < q.tiles_m * q.tiles_t; ++l) lb[tab].push_back(TileInfo{(int)lj[tab].size(), l, q.Kp, 0});
+            lj[tab].push_back(q); lm[tab].push_back(mp);
             lt[tab] += q.tiles_m * q.tiles_t;
         }
     }
@@ -798,7 +801,7 @@ lloid_status launch_recon_f32(lloid_ctx* ctx, long long k_a, long long n, int de
 }
 
 template <bool BF16, bool TOP, bool SZ, int F>
-cudaError_t launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps, const int* base,
+cudaError_t launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps, const TileInfo* base,
                 const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W,
                 Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
     return launch_pdl(k_level_tc<BF16, TOP, SZ, F>, g, dim3(LevCfg<BF16, TOP>::THREADS), LevCfg<BF16, TOP>::SMEM, st, jobs, maps, base, sched, n_jobs, tiles, k_a, k_b,
@@ -807,7 +810,7 @@ cudaError_t launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, 
 }
 template <bool BF16, bool TOP, bool SZ>
 cudaError_t launch_lv_f(int F, dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps,
-                 const int* base, const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0,
+                 const TileInfo* base, const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0,
                  int nd, long long W, Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
 #define LV_F(FV) launch_lv1<BF16, TOP, SZ, FV>(g, smem, st, jobs, maps, base, sched, n_jobs, tiles, k_a, k_b, det0, nd, W, \
                                                part, part_stride, n_slots, zout, err)
@@ -826,7 +829,7 @@ cudaError_t launch_lv_f(int F, dim3 g, int smem, cudaStream_t st, const LevelJob
 // One ladder depth and upsampling factor of the split path (depth 0 = f0:
 // |z|^2 and window maxima); fslot 0 = no level below, else F = 2^fslot.
 lloid_status launch_level(lloid_ctx* ctx, int depth, int fslot, long long k_a, long long n, int det0, int n_det_push,
-                          bool store_z, const LevelJob* jobs, const LevelMaps* maps, const int* base,
+                          bool store_z, const LevelJob* jobs, const LevelMaps* maps, const TileInfo* base,
                           const int* sched, int grid, int n_jobs, int tiles, float* zout) {
     if (tiles == 0 || n_jobs == 0) return LLOID_OK;
     const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
@@ -922,12 +925,12 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
             dim3 g(ctx->fir_grid[v]);
             if (ctx->cfg.precision == LLOID_BF16_SPLIT)
                 CK(launch_pdl(k_fir_tc<true>, g, dim3(192), ctx->firtc_smem, ctx->stream, (const FirTcJob*)ctx->d_firtc,
-                              (const FirMaps*)ctx->d_firmaps, (const int*)ctx->d_firtc_base,
+                              (const FirMaps*)ctx->d_firmaps, (const TileInfo*)ctx->d_firtc_base,
                               (const int*)ctx->d_fir_sched[v], ctx->n_firtc, ctx->firtc_tiles, k_a, det0, nd,
                               ctx->firtc_strip, ctx->firtc_stages, ctx->d_err));
             else
                 CK(launch_pdl(k_fir_tc<false>, g, dim3(192), ctx->firtc_smem, ctx->stream, (const FirTcJob*)ctx->d_firtc,
-                              (const FirMaps*)ctx->d_firmaps, (const int*)ctx->d_firtc_base,
+                              (const FirMaps*)ctx->d_firmaps, (const TileInfo*)ctx->d_firtc_base,
                               (const int*)ctx->d_fir_sched[v], ctx->n_firtc, ctx->firtc_tiles, k_a, det0, nd,
                               ctx->firtc_strip, ctx->firtc_stages, ctx->d_err));
             CKL();
@@ -1884,6 +1887,7 @@ lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* o
     const int idx = ctx->top_job_of_bank[bank];
     int* db = nullptr;
     int* dsched = nullptr;
+    TileInfo* dti = nullptr;
     CK(cudaMalloc(&db, sizeof(int)));
     CK(cudaMemsetAsync(db, 0, sizeof(int), ctx->stream));
     const long long k_a = ctx->pos[det] - n;
@@ -1896,14 +1900,19 @@ lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* o
         const int fs = ctx->top_slot_of_bank[bank];
         int grid = 0;
         const std::vector<int> hs = build_sched(std::vector<double>(tiles, 1.0), 1, ctx->n_sm, &grid);
+        std::vector<TileInfo> hti(tiles);
+        for (int l = 0; l < tiles; ++l) hti[l] = TileInfo{0, l, b->lev.back().Kp, 0};
         CK(cudaMalloc(&dsched, hs.size() * sizeof(int)));
+        CK(cudaMalloc(&dti, hti.size() * sizeof(TileInfo)));
         CK(cudaMemcpyAsync(dsched, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-        st = launch_level(ctx, 0, fs, k_a, n, det, 1, true, ctx->d_lev[fs] + idx, ctx->d_levmaps[fs], db, dsched, grid,
+        CK(cudaMemcpyAsync(dti, hti.data(), hti.size() * sizeof(TileInfo), cudaMemcpyHostToDevice, ctx->stream));
+        st = launch_level(ctx, 0, fs, k_a, n, det, 1, true, ctx->d_lev[fs] + idx, ctx->d_levmaps[fs], dti, dsched, grid,
                           1, tiles, out);
     }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     cudaFree(db);
     cudaFree(dsched);
+    cudaFree(dti);
     if (st) return st;
     if (e != cudaSuccess) return fail(ctx, LLOID_ECUDA, "snr_block: %s", cudaGetErrorString(e));
     if ((st = check_kernel_err(ctx))) return st;
