@@ -54,8 +54,8 @@ struct FirTcJob {
 };
 
 struct LevelJob {
-    uint16_t* acc_out;             // non-top: hi/lo planes [det][re hi, re lo, im hi, im lo][Mpad][acc_cols]
-                                   // (column 0 = sample floor8(lo) - 128)
+    uint16_t* acc_out;             // non-top: hi/lo planes [det][re hi, re lo, im hi, im lo][acc_cols / 8][Mpad][8]
+                                   // (time-blocked; column 0 = sample floor8(lo) - 128)
     long long acc_out_det_stride;  // elements
     int acc_cols;                  // plane row length (multiple of 128)
     int Kp;                        // Kpad of the level (0: no slice at this rate)
@@ -72,10 +72,12 @@ struct LevelJob {
 
 struct FirMaps { CUtensorMap a, a_lo; };
 
-// accw: the level below's hi/lo planes (rows [det][plane][Mpad], columns =
-// samples), box 32 samples x 128 templates, 64-byte swizzle; uhi/ulo: the
-// Eq. 8 tile matrices U_F of this level's factor, rows [shift][128 outputs],
-// columns = window rows, same box and swizzle.
+// accw: the level below's hi/lo planes, time-blocked [det x plane][x / 8][Mpad][8]
+// (4-D map whose innermost dimension is 32 templates x 8 samples = 512 B, box
+// 4 of those x 4 blocks, no swizzle: a box is four contiguous 2 KB runs and lands
+// in shared memory as the no-swizzle K-major layout of a 128 x 32 operand); uhi/ulo: the Eq. 8 tile matrices U_F of this level's
+// factor, rows [shift][128 outputs], columns = window rows, box 32 x 128, 64-byte
+// swizzle.
 struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo, accw, uhi, ulo; };
 
 // Window of the level below read by one 128-sample tile (N_up = 8): rows
@@ -98,6 +100,9 @@ __device__ __forceinline__ uint64_t desc_nosw(uint32_t saddr, uint32_t lbo, uint
     d |= (uint64_t)1u << 46;
     return d;   // layout type 0: no swizzle
 }
+// A window plane in shared memory: [4 blocks of 8 window rows][128 templates][8 x 16 bit], the
+// no-swizzle K-major layout with 8 x 16 B core matrices, 128 B apart along M and 2 KB along K.
+__device__ __forceinline__ uint64_t desc_win(uint32_t saddr) { return desc_nosw(saddr, 2048, 128); }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
@@ -473,7 +478,8 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                         mbar_expect_tx(full + stage, C::WSTAGE);
 #pragma unroll
                         for (int pl = 0; pl < 4; ++pl)
-                            tma_load_2d(sb + pl * C::WTILE, &mp->accw, full + stage, a + kWinK * ch, prow + pl * jb.Mpad);
+                            tma_load_4d(sb + pl * C::WTILE, &mp->accw, full + stage, 0, tm * 4, (a + kWinK * ch) >> 3,
+                                        det * 4 + pl);
                         tma_load_2d(sb + 4 * C::WTILE, &mp->uhi, full + stage, kWinK * ch, r * 128);
                         tma_load_2d(sb + 5 * C::WTILE, &mp->ulo, full + stage, kWinK * ch, r * 128);
                         if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
@@ -536,14 +542,15 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
 #pragma unroll
                     for (int k = 0; k < kWinK / 16; ++k) {
                         if (ch * (kWinK / 16) + k >= NK16) break;   // rows past the window: U is zero there
-                        const uint32_t off = k * 32;
+                        const uint32_t off = k * 32;            // U: 16 window rows into the 64-byte swizzle row
+                        const uint32_t woff = k * 4096;         // window: two 8-row blocks of 128 x 16 B
                         const uint32_t acc0 = (Kp > 0 || ch > 0 || k > 0) ? 1u : 0u;
-                        umma_f16(d_re, desc_sw64(w_rh + off), desc_sw64(u_h + off), idesc, acc0);
-                        umma_f16(d_re, desc_sw64(w_rl + off), desc_sw64(u_h + off), idesc, 1u);
-                        umma_f16(d_re, desc_sw64(w_rh + off), desc_sw64(u_l + off), idesc, 1u);
-                        umma_f16(d_im, desc_sw64(w_ih + off), desc_sw64(u_h + off), idesc, acc0);
-                        umma_f16(d_im, desc_sw64(w_il + off), desc_sw64(u_h + off), idesc, 1u);
-                        umma_f16(d_im, desc_sw64(w_ih + off), desc_sw64(u_l + off), idesc, 1u);
+                        umma_f16(d_re, desc_win(w_rh + woff), desc_sw64(u_h + off), idesc, acc0);
+                        umma_f16(d_re, desc_win(w_rl + woff), desc_sw64(u_h + off), idesc, 1u);
+                        umma_f16(d_re, desc_win(w_rh + woff), desc_sw64(u_l + off), idesc, 1u);
+                        umma_f16(d_im, desc_win(w_ih + woff), desc_sw64(u_h + off), idesc, acc0);
+                        umma_f16(d_im, desc_win(w_il + woff), desc_sw64(u_h + off), idesc, 1u);
+                        umma_f16(d_im, desc_win(w_ih + woff), desc_sw64(u_l + off), idesc, 1u);
                     }
                     umma_commit(empty + stage);
                     if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
@@ -632,17 +639,14 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                     }
                 }
             } else {
-                // Acc of this warp's 32 templates x 64 samples as four hi/lo planes, 32 samples at a
-                // time, transposed through a padded shared-memory buffer so that each global store
-                // instruction writes 8 template rows x 64 contiguous bytes.  Plane columns start at
+                // Acc of this warp's 32 templates x 64 samples as four hi/lo planes in the time-blocked
+                // layout [plane][x / 8][Mpad][8]: for each block of 8 samples the warp's 32 rows are
+                // 512 contiguous bytes, one 16-byte store per lane.  Plane columns start at
                 // X0 = floor8(lo) - 128 (a tile never writes left of column 0).
                 const long long X0 = fdiv(lo, 8) * 8 - 128;
-                const long long x0 = Q0 + 128LL * tt + 64 * half - X0;
+                const long long x0 = Q0 + 128LL * tt + 64 * half - X0;   // a multiple of 8
                 const long long pstride = (long long)jb.Mpad * jb.acc_cols;
-                uint16_t* pbase = jb.acc_out + det * jb.acc_out_det_stride +
-                                  (long long)(tm * 128 + qd * 32) * jb.acc_cols;
-                uint8_t* wbuf = stg + (warp - 2) * C::STG_BUF;
-                const int rr = lane >> 2, cq = lane & 3;        // read-back: row within 8, 16-byte chunk
+                uint16_t* pbase = jb.acc_out + det * jb.acc_out_det_stride + (long long)(tm * 128 + qd * 32 + lane) * 8;
 #pragma unroll 1
                 for (int part = 0; part < 2; ++part) {          // re, im
 #pragma unroll 1
@@ -657,22 +661,14 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                         uint32_t hp[16], lp[16];
 #pragma unroll
                         for (int k = 0; k < 16; ++k) split_hilo2<BF16>(v[2 * k], v[2 * k + 1], hp[k], lp[k]);
+                        const long long blk0 = (x0 + 32 * g) >> 3;
 #pragma unroll
-                        for (int sub = 0; sub < 2; ++sub) {      // hi, lo
-                            const uint32_t* src = sub ? lp : hp;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                *reinterpret_cast<uint4*>(wbuf + lane * C::STG_PITCH + k * 16) =
-                                    make_uint4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
-                            __syncwarp();
-                            uint16_t* pl = pbase + (2 * part + sub) * pstride + x0 + 32 * g + 8 * cq;
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const int r = 8 * i + rr;
-                                const uint4 val = *reinterpret_cast<const uint4*>(wbuf + r * C::STG_PITCH + cq * 16);
-                                *reinterpret_cast<uint4*>(pl + (long long)r * jb.acc_cols) = val;
-                            }
-                            __syncwarp();
+                        for (int bq = 0; bq < 4; ++bq) {
+                            const long long o = (blk0 + bq) * jb.Mpad * 8;
+                            *reinterpret_cast<uint4*>(pbase + (2 * part) * pstride + o) =
+                                make_uint4(hp[4 * bq], hp[4 * bq + 1], hp[4 * bq + 2], hp[4 * bq + 3]);
+                            *reinterpret_cast<uint4*>(pbase + (2 * part + 1) * pstride + o) =
+                                make_uint4(lp[4 * bq], lp[4 * bq + 1], lp[4 * bq + 2], lp[4 * bq + 3]);
                         }
                     }
                 }

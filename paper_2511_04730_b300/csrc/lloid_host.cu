@@ -68,7 +68,7 @@ struct LevelRT {
     void *d_cre = nullptr, *d_cim = nullptr, *d_cre_lo = nullptr, *d_cim_lo = nullptr;  // [Mpad][Kp]
     uint16_t *d_yhi = nullptr, *d_ylo = nullptr;   // operand ring [n_det][2R][Kp]
     int R = 0;
-    uint16_t* d_accp = nullptr;        // below the top: hi/lo planes [n_det][4][Mpad][acc_cols]
+    uint16_t* d_accp = nullptr;        // below the top: hi/lo planes [n_det][4][acc_cols / 8][Mpad][8]
     int acc_cols = 0;
 };
 struct FirSliceRT {
@@ -312,6 +312,22 @@ bool encode_map(CUtensorMap* m, bool bf16, const void* base, long long cols, lon
     CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                     const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// 4-D 16-bit map of time-blocked planes [planes][cols / 8][rows][8], each block of 8 samples
+// seen as rows / 32 runs of 256 values (512 B) so that the TMA moves a box in 16 long rows:
+// box 256 x 4 x (kWinK / 8) x 1 = 128 rows x 8 samples x 4 blocks, no swizzle.  rows % 128 == 0.
+bool encode_map_blocked(CUtensorMap* m, bool bf16, const void* base, long long cols, long long rows, long long planes) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {256, (cuuint64_t)(rows / 32), (cuuint64_t)(cols / 8), (cuuint64_t)planes};
+    cuuint64_t strides[3] = {512, (cuuint64_t)rows * 16, (cuuint64_t)(cols / 8) * rows * 16};
+    cuuint32_t box[4] = {256, 4, (cuuint32_t)(kWinK / 8), 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
+                    const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -600,7 +616,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             if (j > 0) {
                 const LevelRT& P = b->lev[j - 1];
                 const int kw = win_chunks(q.F) * kWinK;
-                if (!encode_map_sw64(&mp.accw, bf, P.d_accp, P.acc_cols, (long long)nd * 4 * b->Mpad) ||
+                if (!encode_map_blocked(&mp.accw, bf, P.d_accp, P.acc_cols, b->Mpad, (long long)nd * 4) ||
                     !encode_map_sw64(&mp.uhi, bf, ctx->d_u_hi[fslot], kw, 8 * 128) ||
                     !encode_map_sw64(&mp.ulo, bf, ctx->d_u_lo[fslot], kw, 8 * 128))
                     return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (window, bank %d)", b->id);
@@ -1185,7 +1201,7 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
     const int nd = c.n_detectors;
     hdr->clear();
     seg->clear();
-    long long h[] = {0x4C4C4F4944535431LL, 3, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
+    long long h[] = {0x4C4C4F4944535431LL, 4, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
                      c.max_block, c.max_history, c.min_rate, (long long)ctx->banks.size(), ctx->M_used,
                      ctx->M_cap, ctx->n_slots};
     hdr->assign(h, h + sizeof h / sizeof h[0]);
