@@ -75,9 +75,9 @@ struct FirMaps { CUtensorMap a, a_lo; };
 // accw: the level below's hi/lo planes, time-blocked [det x plane][x / 8][Mpad][8]
 // (4-D map whose innermost dimension is 32 templates x 8 samples = 512 B, box
 // 4 of those x 4 blocks, no swizzle: a box is four contiguous 2 KB runs and lands
-// in shared memory as the no-swizzle K-major layout of a 128 x 32 operand); uhi/ulo: the Eq. 8 tile matrices U_F of this level's
-// factor, rows [shift][128 outputs], columns = window rows, box 32 x 128, 64-byte
-// swizzle.
+// in shared memory as the no-swizzle K-major layout of a 128 x 32 operand);
+// uhi/ulo: the Eq. 8 tile matrices U_F of this level's factor, time-blocked the
+// same way, [shift][window row / 8][128 outputs][8], same box.
 struct LevelMaps { CUtensorMap cre, cim, cre_lo, cim_lo, yhi, ylo, accw, uhi, ulo; };
 
 // Window of the level below read by one 128-sample tile (N_up = 8): rows
@@ -119,17 +119,6 @@ using TileInfo = int4;
 __device__ __forceinline__ long long fdiv(long long a, long long b) {
     long long q = a / b;
     return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
-}
-
-// K-major, 64-byte swizzle (rows of 32 16-bit values), 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;
-    d |= (uint64_t)(512u >> 4) << 32;
-    d |= (uint64_t)1u << 46;
-    d |= (uint64_t)4u << 61;                 // SWIZZLE_64B
-    return d;
 }
 
 template <typename T>
@@ -470,7 +459,6 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                     const long long qf = fdiv(Qt, F != 0 ? F : 1);
                     const int r = (int)(qf & 7);
                     const int a = (int)(qf - 8 - r - X0);
-                    const int prow = det * 4 * jb.Mpad + tm * 128;
 #pragma unroll 1
                     for (int ch = 0; ch < NWC && ok; ++ch) {
                         if (!mbar_wait(empty + stage, phase ^ 1, err, 32)) { ok = false; break; }
@@ -480,8 +468,8 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                         for (int pl = 0; pl < 4; ++pl)
                             tma_load_4d(sb + pl * C::WTILE, &mp->accw, full + stage, 0, tm * 4, (a + kWinK * ch) >> 3,
                                         det * 4 + pl);
-                        tma_load_2d(sb + 4 * C::WTILE, &mp->uhi, full + stage, kWinK * ch, r * 128);
-                        tma_load_2d(sb + 5 * C::WTILE, &mp->ulo, full + stage, kWinK * ch, r * 128);
+                        tma_load_4d(sb + 4 * C::WTILE, &mp->uhi, full + stage, 0, 0, (kWinK * ch) >> 3, r);
+                        tma_load_4d(sb + 5 * C::WTILE, &mp->ulo, full + stage, 0, 0, (kWinK * ch) >> 3, r);
                         if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
                     }
                 }
@@ -542,15 +530,14 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
 #pragma unroll
                     for (int k = 0; k < kWinK / 16; ++k) {
                         if (ch * (kWinK / 16) + k >= NK16) break;   // rows past the window: U is zero there
-                        const uint32_t off = k * 32;            // U: 16 window rows into the 64-byte swizzle row
-                        const uint32_t woff = k * 4096;         // window: two 8-row blocks of 128 x 16 B
+                        const uint32_t woff = k * 4096;         // two 8-row blocks of 128 x 16 B (window and U)
                         const uint32_t acc0 = (Kp > 0 || ch > 0 || k > 0) ? 1u : 0u;
-                        umma_f16(d_re, desc_win(w_rh + woff), desc_sw64(u_h + off), idesc, acc0);
-                        umma_f16(d_re, desc_win(w_rl + woff), desc_sw64(u_h + off), idesc, 1u);
-                        umma_f16(d_re, desc_win(w_rh + woff), desc_sw64(u_l + off), idesc, 1u);
-                        umma_f16(d_im, desc_win(w_ih + woff), desc_sw64(u_h + off), idesc, acc0);
-                        umma_f16(d_im, desc_win(w_il + woff), desc_sw64(u_h + off), idesc, 1u);
-                        umma_f16(d_im, desc_win(w_ih + woff), desc_sw64(u_l + off), idesc, 1u);
+                        umma_f16(d_re, desc_win(w_rh + woff), desc_win(u_h + woff), idesc, acc0);
+                        umma_f16(d_re, desc_win(w_rl + woff), desc_win(u_h + woff), idesc, 1u);
+                        umma_f16(d_re, desc_win(w_rh + woff), desc_win(u_l + woff), idesc, 1u);
+                        umma_f16(d_im, desc_win(w_ih + woff), desc_win(u_h + woff), idesc, acc0);
+                        umma_f16(d_im, desc_win(w_il + woff), desc_win(u_h + woff), idesc, 1u);
+                        umma_f16(d_im, desc_win(w_ih + woff), desc_win(u_l + woff), idesc, 1u);
                     }
                     umma_commit(empty + stage);
                     if (++stage == C::STAGES) { stage = 0; phase ^= 1; }

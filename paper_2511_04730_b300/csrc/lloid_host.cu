@@ -331,20 +331,6 @@ bool encode_map_blocked(CUtensorMap* m, bool bf16, const void* base, long long c
     return r == CUDA_SUCCESS;
 }
 
-// 2-D 16-bit map with 64-byte swizzle: rows of `cols` values, box 32 x 128.
-bool encode_map_sw64(CUtensorMap* m, bool bf16, const void* base, long long cols, long long rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kWinK, 128};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
-                    const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
 lloid_status ensure_template_capacity(lloid_ctx* ctx, long long need) {
     if (need <= ctx->M_cap) return LLOID_OK;
     const int nd = ctx->cfg.n_detectors;
@@ -617,8 +603,8 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                 const LevelRT& P = b->lev[j - 1];
                 const int kw = win_chunks(q.F) * kWinK;
                 if (!encode_map_blocked(&mp.accw, bf, P.d_accp, P.acc_cols, b->Mpad, (long long)nd * 4) ||
-                    !encode_map_sw64(&mp.uhi, bf, ctx->d_u_hi[fslot], kw, 8 * 128) ||
-                    !encode_map_sw64(&mp.ulo, bf, ctx->d_u_lo[fslot], kw, 8 * 128))
+                    !encode_map_blocked(&mp.uhi, bf, ctx->d_u_hi[fslot], kw, 128, 8) ||
+                    !encode_map_blocked(&mp.ulo, bf, ctx->d_u_lo[fslot], kw, 128, 8))
                     return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (window, bank %d)", b->id);
             }
             if (L.Kp > 0) {
@@ -1380,7 +1366,8 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         // holding sample floor(Q/F) - N_up - r + w of the level below,
         //   U_F[r][q][w] = z_{q mod F}[t],  t = floor(q/F) + 2 N_up + r - w in [0, 2 N_up],
         // with the sub-kernels z_phi[t] = g[t F + phi] of Eq. 7 (g of Eq. 4, c = F N_up, the
-        // sinc's zeros at multiples of F written as exact zeros).  Stored as 16-bit hi + lo.
+        // sinc's zeros at multiples of F written as exact zeros).  Stored as 16-bit hi + lo,
+        // time-blocked like the planes: [r][w / 8][q][w mod 8].
         for (int fs = 1; fs < lloid_ctx::kFSlots; ++fs) {
             const int F = 1 << fs;
             const int cF = F * c.n_up;
@@ -1394,7 +1381,7 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
                         if (t < 0 || t > 2 * c.n_up) continue;
                         const long long k = (long long)t * F + q % F;
                         if (k > 2LL * cF || ((k - cF) % F == 0 && k != cF)) continue;
-                        u[((size_t)r * 128 + q) * kw + w] = g[k];
+                        u[(((size_t)r * (kw / 8) + w / 8) * 128 + q) * 8 + w % 8] = g[k];
                     }
             std::vector<uint16_t> uh(u.size()), ul(u.size());
             split_hilo_host(c.precision == LLOID_BF16_SPLIT, u, &uh, &ul);
