@@ -176,8 +176,11 @@ typedef struct {
 LLOID_API void lloid_config_default(lloid_config* cfg);
 
 /* Create a context on cfg->device.  Allocates the per-detector strain rings
- * and window buffers.  EINVAL on a bad configuration, ECUDA/ENOMEM on device
- * failure.  *out is NULL on failure. */
+ * and window buffers.  EINVAL on a bad configuration (checked before any
+ * device call), among them a max_block with which one push could complete
+ * more than 16 trigger windows (max_block / window_samples + 1 > 16: the
+ * retained-window ring holds 16); ECUDA/ENOMEM on device failure.  *out is
+ * NULL on failure. */
 LLOID_API lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out);
 
 /* Free every device and host resource of the context (NULL is a no-op). */

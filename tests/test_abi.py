@@ -90,6 +90,18 @@ def test_host_only_calls(lib):
     assert lib.lloid_last_error(None) == b"null context"
 
 
+def test_create_rejects_pushes_of_more_than_16_windows(lib):
+    """Configuration checks run before any device call: a push that could
+    complete 17 one-second windows is refused with LLOID_EINVAL."""
+    from paper_2511_04730_b300 import _lib
+    cfg = _lib.LloidConfig()
+    lib.lloid_config_default(ctypes.byref(cfg))
+    cfg.max_block = 16 * cfg.window_samples
+    h = ctypes.c_void_p()
+    assert lib.lloid_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    assert not h.value
+
+
 def test_product_path_has_no_oracle_import():
     """The product package never imports the oracle (test infrastructure)."""
     pkg = os.path.join(ROOT, "paper_2511_04730_b300")

@@ -180,6 +180,37 @@ def test_multirate_ladder_bank1000_segments(lloid, ladder_case, precision):
         assert err <= TOL[precision]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16_split"])
+def test_triggers_across_finalize_chunks(lloid, ladder_case, precision):
+    """96 templates: window maxima are finalised in chunks of 64 templates and
+    the bank maximum is found across the chunks.  Triggers of the windows of
+    the oracle's segments (absolute windows and samples) against the oracle's."""
+    bank, plan, d, segs, S = ladder_case
+    sb = lloid.build_svd_bank(bank, plan)
+    end = max(segs) + S
+    got = []
+    with _ctx(lloid, precision, max_history=64 * F0) as ctx:
+        ctx.load_bank(sb)
+        for t in range(0, end, 16384):
+            ctx.push(0, t, np.ascontiguousarray(d[t:t + 16384], dtype=np.float32))
+            got += [ctx.pull(win) for win in range(t // F0, (t + 16384) // F0)]
+    trig = np.concatenate(got)
+    n_checked = 0
+    for a, zo in segs.items():
+        w0, w1 = a // F0, (a + S) // F0
+        g = trig[(trig["window"] >= w0) & (trig["window"] < w1)]
+        otr = O.triggers(zo, F0, n_windows=w1, t_offset=a)
+        assert compare_triggers(g, otr, zo, TOL[precision], F0, t_offset=a) == []
+        for w in range(w0, w1):
+            rows = g[g["window"] == w]
+            if len(rows):
+                n_checked += 1
+                assert rows["is_bank_max"].sum() == 1
+                top = rows[rows["is_bank_max"] == 1][0]
+                assert top["snr"] >= rows["snr"].max() - TOL[precision]
+    assert n_checked > 0
+
+
 def test_error_codes(lloid, bank64_case):
     w, bank, plan, d, _ = bank64_case
     sb = lloid.build_svd_bank(bank, plan)
