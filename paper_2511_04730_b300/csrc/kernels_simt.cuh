@@ -92,7 +92,6 @@ __global__ void __launch_bounds__(kDownThreads, 6) k_downsample(DownParams p, co
                                                              long long ring0_det_stride, int mask0, long long k_a,
                                                              int n, int n_down, int det0) {
     constexpr int NT = kDownThreads, U = 16;
-    pdl_launch_dependents();
     extern __shared__ float dsm[];
     int r = 0;
     while (r + 1 < p.n_rates && (int)blockIdx.x >= p.blk0[r + 1]) ++r;
@@ -134,6 +133,9 @@ __global__ void __launch_bounds__(kDownThreads, 6) k_downsample(DownParams p, co
         for (int m = g; m < L; m += G) acc = fmaf(__ldg(wc - m), xs[(m & (D - 1)) * Jp + (m >> lgD) + i], acc);
         __syncthreads();
     }
+    // The next launch (the FIR, one wave of resident CTAs) may be scheduled once every block is
+    // past its multiply-adds: earlier, its CTAs would take the SMs that this grid still needs.
+    pdl_launch_dependents();
     // Lanes o apart (o = QB, 2 QB, ... < 32) hold the same output.
     for (int o = QB; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     part[threadIdx.x] = acc;

@@ -177,7 +177,7 @@ struct lloid_ctx {
     unsigned long long* d_coinc_red = nullptr;
     // split path job tables: FIR over all slices, levels per depth below the top
     FirTcJob* d_firtc = nullptr; FirMaps* d_firmaps = nullptr; TileInfo* d_firtc_base = nullptr;   // per tile
-    int n_firtc = 0, firtc_tiles = 0, firtc_smem = 0, firtc_strip = 0, firtc_stages = 0;
+    int n_firtc = 0, firtc_tiles = 0, firtc_smem = 0, firtc_strip = 0, firtc_stages = 0, firtc_ctas = 1;
     static constexpr int kMaxDepth = 8;
     // one table per (depth, F slot): F = 0 (lowest level), 2, 4, ..., 64 -> slot 0..6
     static constexpr int kFSlots = 7;
@@ -452,8 +452,9 @@ std::vector<int> build_sched(const std::vector<double>& cost, int nd, int n_sm, 
     *grid_out = grid;
     return h;
 }
-lloid_status upload_sched(lloid_ctx* ctx, const std::vector<double>& cost, int nd, int** d_out, int* grid_out) {
-    return upload_vec(ctx, d_out, build_sched(cost, nd, ctx->n_sm, grid_out));
+lloid_status upload_sched(lloid_ctx* ctx, const std::vector<double>& cost, int nd, int** d_out, int* grid_out,
+                          int ctas_per_sm = 1) {
+    return upload_vec(ctx, d_out, build_sched(cost, nd, ctx->n_sm * ctas_per_sm, grid_out));
 }
 
 bool split_precision(const lloid_ctx* ctx) { return ctx->cfg.precision != LLOID_FP32; }
@@ -636,6 +637,16 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             (st = upload_vec(ctx, &ctx->d_lev_base[d], lb[d])))
             return st;
     }
+    // FIR shared memory: the strips, the epilogue staging and the barriers, then A' stages.
+    // Two CTAs per SM (each with 256 TMEM columns) when each still gets 2 stages; else one
+    // CTA with as many stages as fit.
+    const int fir_fixed = 4 * strip + FirCfg<false>::EPI_BYTES + 256 + 1024;   // EPI_BYTES is the same for both
+    const int fir_sbytes = bf ? FirCfg<true>::STAGE_BYTES : FirCfg<false>::STAGE_BYTES;
+    {
+        const int st2 = std::min(FirCfg<false>::MAX_STAGES, (113 * 1024 - fir_fixed) / fir_sbytes);
+        if (st2 >= 2) { ctx->firtc_ctas = 2; ctx->firtc_stages = st2; }
+        else { ctx->firtc_ctas = 1; ctx->firtc_stages = std::min(FirCfg<false>::MAX_STAGES, (227 * 1024 - fir_fixed) / fir_sbytes); }
+    }
     {   // schedules: cost ~ MMAs of a tile plus a fixed epilogue share
         const int mk = bf ? 3 : 2;
         std::vector<double> fc;
@@ -643,7 +654,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             for (int k = 0; k < f.Mtiles * f.ctiles; ++k) fc.push_back(mk * f.Kp / 16.0 + 16.0);
         for (int v = 0; v < 2; ++v) {
             const int ndv = v ? nd : 1;
-            if ((st = upload_sched(ctx, fc, ndv, &ctx->d_fir_sched[v], &ctx->fir_grid[v]))) return st;
+            if ((st = upload_sched(ctx, fc, ndv, &ctx->d_fir_sched[v], &ctx->fir_grid[v], ctx->firtc_ctas))) return st;
         }
         for (int d = 0; d < lloid_ctx::kLevTables; ++d) {
             if (lj[d].empty()) continue;
@@ -661,12 +672,8 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     ctx->firtc_tiles = ft;
     ctx->firtc_strip = strip;
     ctx->max_depth = max_depth;
-    // as many A' stages as fit next to the strips, the epilogue staging and the barriers
-    const int fixed = 4 * strip + FirCfg<false>::EPI_BYTES + 256 + 1024;   // EPI_BYTES is the same for both
-    const int sbytes = bf ? FirCfg<true>::STAGE_BYTES : FirCfg<false>::STAGE_BYTES;
-    ctx->firtc_stages = std::min(FirCfg<false>::MAX_STAGES, (227 * 1024 - fixed) / sbytes);
     if (ctx->firtc_stages < 2) return fail(ctx, LLOID_EINVAL, "FIR strips of %d bytes leave no room for 2 stages", strip);
-    const int fsmem = ctx->firtc_stages * sbytes + fixed;
+    const int fsmem = ctx->firtc_stages * fir_sbytes + fir_fixed;
     ctx->firtc_smem = fsmem;
     if (fsmem > 227 * 1024) return fail(ctx, LLOID_EINVAL, "FIR shared memory %d exceeds the limit", fsmem);
     if (bf) CK(cudaFuncSetAttribute(k_fir_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem));
