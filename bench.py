@@ -257,8 +257,8 @@ def algorithmic_work(slices, M, f0=F0, n_up=8):
 # capture summarised in profiles/k_level_tc_k_fir_tc_bank1000.md; valid only
 # while the tensor-core kernel sources hash to the prefix it was taken with.
 TRAFFIC_SOURCES = ("kernels_tc.cuh", "kernels_tc2.cuh", "lloid_common.cuh")
-TRAFFIC_SHA = "5ac558c712c55d4f"
-TRAFFIC = {("bank1000", "fp16_split", 8, 2): {"upsample": 76.6e6, "recon": 157.5e6, "fir": 127.1e6}}
+TRAFFIC_SHA = "822f4761ed7fedee"
+TRAFFIC = {("bank1000", "fp16_split", 8, 2): {"upsample": 76.5e6, "recon": 156.9e6, "fir": 118.7e6}}
 
 
 def measured_traffic(workload, precision, block_seconds, n_det, stage):
