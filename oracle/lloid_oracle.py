@@ -44,7 +44,7 @@ What it computes (every array is float64, every step written out plainly):
       xi2 = sum_{t=-d}^{d} |z[k+t] - z[k] R(t)|^2 / sum_{t=-d}^{d} (2 - 2 |R(t)|^2),
     R the template's complex autocorrelation with R(0) = 1.
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open:
 * discrete unit-variance form of Eq. 1 (no factor 2): E|z|^2 = 2 in white
   noise and an injection at amplitude A gives |z| = A;
 * downsampling is zero-phase (centred) with unit DC gain, w = g / sum(g), and
