@@ -1,23 +1,27 @@
 #!/usr/bin/env python
 """Throughput of the LLOID hot path on B300: template-seconds filtered per second.
 
-Workload (the 1000-template configuration): 1000 Newtonian chirp templates,
-chirp mass log-uniform in [1, 20] Msun, 64 s long, cut into 9 time slices at
-2048/1024/512/256/128 Hz and SVD-compressed to 99.99 % of each slice's
-energy; 2 detectors x 1024 s of seeded unit white noise at 2048 Hz with 20
-injections per detector at SNR U[6, 20] (synthetic stand-in for the paper's
-mock-data-challenge strain).
+Workload (default: the 500-bank configuration): 500 SVD banks of U{100..1000}
+Newtonian chirp templates (about 280k templates, chirp mass log-uniform in
+[1, 50] Msun, durations 2-128 s, each bank cut into time slices at 128-2048 Hz
+and SVD-compressed to 99.99 % of each slice's energy), 3 detectors x 1024 s of
+seeded unit white noise at 2048 Hz (synthetic stand-in for the paper's
+mock-data-challenge strain), BF16 split precision.  ``--workload bank1000`` and
+``--workload banks20`` select the 1000-template bank and the 20-bank precision
+configuration.
 
 A step pushes one block (--block-seconds, default 8 s) of strain for every
 detector through every stage (ingest, downsample, basis FIR, upsample,
 reconstruction + window maxima, finalisation) and pulls the triggers of the
 windows the block completes.  The stream continues across steps, cycling
-through the 1024 s record.  L2 is flushed (256 MB write) between steps,
-outside the timed intervals, which are CUDA-event pairs on the library's
-stream around each step.
+through the record.  L2 is flushed (256 MB write) between steps, outside the
+timed intervals, which are CUDA-event pairs on the library's stream around
+each step.
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle instead (bounded samples of the same workload).
+oracle instead (bounded samples of the same workload).  The ``cpu_baseline``
+leg times the oracle on a bounded sample of the workload and keeps its SNR,
+against which the GPU path's error distribution per precision is reported.
 """
 import argparse
 import json
@@ -33,12 +37,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 F0 = 2048
-REF_M = 8                    # templates per reference-arm step (a bounded oracle sample)
-REF_SECONDS = 24             # seconds of strain per reference-arm step (~0.4 s of oracle work)
 METRIC = "template-seconds filtered/s at max |dSNR|<=5e-3 vs FP32 path; p50/p99 block latency"
 UNIT = "template-s/s"
-WORKLOAD = ("1000 Newtonian chirp templates (Mc log-U[1,20] Msun, 64 s, 9 slices 2048/1024/512/256/128 Hz, "
-            "SVD 99.99%), 2 detectors x 1024 s white noise + 20 injections/detector, 1 s trigger windows")
+# bounded oracle samples of each workload: banks (indices into the workload's banks), the
+# first templates of each, seconds of one detector's strain from the stream start
+ORACLE_SAMPLE = {"banks500": ((25, 125, 225, 325, 425), 48, 20),
+                 "banks20": ((2, 9, 16), 48, 20),
+                 "bank1000": ((0,), 64, 68)}
 
 
 def parse():
@@ -47,7 +52,7 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="lloid", choices=["lloid", "reference"])
-    p.add_argument("--precision", default="fp16_split", choices=["fp32", "fp16_split", "bf16_split"])
+    p.add_argument("--precision", default="bf16_split", choices=["fp32", "fp16_split", "bf16_split"])
     p.add_argument("--block-seconds", type=int, default=8)
     p.add_argument("--templates", type=int, default=1000)
     p.add_argument("--seconds", type=int, default=1024)
@@ -55,17 +60,20 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--whiten-seconds", type=int, default=64,
                    help="seconds of 16384 Hz strain per detector for the whitening measurement (0: skip it)")
-    p.add_argument("--xi2-half", type=int, default=350,
-                   help="Eq. 10 autocorrelation half-length d for the xi2 measurement (0: skip it)")
+    p.add_argument("--xi2-half", type=int, default=None,
+                   help="Eq. 10 autocorrelation half-length d for the xi2 measurement (0: skip it; "
+                        "default 350 for the one-bank workload, 0 otherwise)")
     p.add_argument("--no-fp32-compare", action="store_true")
     p.add_argument("--latency-steps", type=int, default=32)
-    p.add_argument("--workload", default="bank1000", choices=["bank1000", "banks20", "banks500"])
+    p.add_argument("--workload", default="banks500", choices=["bank1000", "banks20", "banks500"])
     p.add_argument("--banks", type=int, default=None, help="use the first N banks of a multi-bank workload")
     p.add_argument("--detectors", type=int, default=None)
     p.add_argument("--serve", action="store_true", help="paced serving loop with latency percentiles")
     p.add_argument("--serve-block", type=int, default=2048)
     p.add_argument("--pace", type=float, default=1.0)
     p.add_argument("--serve-seconds", type=int, default=60)
+    p.add_argument("--form", default=None, choices=["ladder", "f0"],
+                   help="force every bank into one form of the split path (default: per-bank choice)")
     return p.parse_args()
 
 
@@ -189,11 +197,13 @@ class ClockSampler:
 # workload
 # ---------------------------------------------------------------------------
 WORKLOADS = {
-    "bank1000": WORKLOAD,
+    "bank1000": ("1000 Newtonian chirp templates (Mc log-U[1,20] Msun, 64 s, 9 slices 2048/1024/512/256/128 Hz, "
+                 "SVD 99.99%), 2 detectors x 1024 s white noise + 20 injections/detector, 1 s trigger windows"),
     "banks20": ("10,000 Newtonian chirp templates (Mc log-U[1,20] Msun) in 20 contiguous-Mc SVD banks of 200-800, "
                 "durations 8-64 s, 2 detectors x 4096 s white noise + 100 injections"),
     "banks500": ("500 SVD banks of U{100..1000} templates (~280k, Mc log-U[1,50] Msun, durations 2-128 s, 1-10 slices, "
-                 "32-2048 Hz), 3 detectors x 1024 s white noise"),
+                 "128-2048 Hz, SVD 99.99%), 3 detectors x 1024 s white noise + 17 injections/detector, "
+                 "1 s trigger windows"),
 }
 
 
@@ -253,21 +263,26 @@ def algorithmic_work(slices, M, f0=F0, n_up=8):
             "at_f0": rec_by.get(f0, 0.0) + up_by.get(f0, 0.0) + cmp_}
 
 
-# DRAM read + write bytes per launch of each stage's kernel, from the ncu
-# capture summarised in profiles/k_level_tc_k_fir_tc_bank1000.md; valid only
-# while the tensor-core kernel sources hash to the prefix it was taken with.
+# DRAM read + write bytes per launch of each stage's kernel, from the ncu captures
+# summarised in profiles/; valid only while the kernel sources hash to the prefix they
+# were taken with.
 TRAFFIC_SOURCES = ("kernels_tc.cuh", "kernels_tc2.cuh", "lloid_common.cuh")
-TRAFFIC_SHA = "822f4761ed7fedee"
-TRAFFIC = {("bank1000", "fp16_split", 8, 2): {"upsample": 76.5e6, "recon": 156.9e6, "fir": 118.7e6}}
+TRAFFIC_SHA = ""
+TRAFFIC_PROFILE = ""
+TRAFFIC = {}
 
 
-def measured_traffic(workload, precision, block_seconds, n_det, stage):
+def kernel_sources_sha():
     import hashlib
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_2511_04730_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest()[:16] != TRAFFIC_SHA:
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, precision, block_seconds, n_det, stage):
+    if not TRAFFIC_SHA or kernel_sources_sha() != TRAFFIC_SHA:
         return None
     return TRAFFIC.get((workload, precision, block_seconds, n_det), {}).get(stage)
 
@@ -281,51 +296,141 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle leg (cpu_baseline and --impl reference)
+# CPU oracle leg (cpu_baseline, the error distribution against it, and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(M=64, seconds=68, seed_det=0):
-    """Time the FP64 oracle's LLOID on a bounded sample: the first M templates'
-    worth of the 1000-template family (same Mc range, same slicing rule), one
-    detector, `seconds` of data from the start of the stream."""
-    import numpy as np
+def oracle_sample_workload(workload):
+    """The bounded sample of a workload the oracle runs on: a few of its banks,
+    one detector, the first seconds of the stream (no injections)."""
     import workloads as W
+    banks, M_sub, secs = ORACLE_SAMPLE[workload]
+    if workload == "bank1000":
+        w = W.make_workload("bank1000", n_templates=M_sub, n_seconds=secs, n_det=1, n_inj=0)
+    else:
+        w = W.make_workload(workload, bank_indices=banks, n_seconds=secs, n_det=1, n_inj=0)
+    return w, M_sub, secs
+
+
+def oracle_run(w, k, M_sub, d):
+    """The FP64 oracle's LLOID SNR and triggers of bank k's first M_sub templates
+    on strain d (its coefficient rows only: the oracle is linear in them).
+    Returns (z [2 M_sub, T], triggers, seconds, cpu seconds)."""
+    import numpy as np
     from oracle import lloid_oracle as O
-    w = W.make_workload("bank1000", n_templates=M, n_seconds=seconds, n_det=1, n_inj=0)
-    sl = O.svd_bank(w.banks[0], w.plans[0])
-    d = w.strain(seed_det).astype(np.float64)
+    sl = O.svd_bank(w.banks[k], w.plans[k])
+    sub = [O.OracleSlice(s.rate, s.j_start, s.bases, s.coeffs[: 2 * M_sub]) for s in sl]
     t, c = time.perf_counter(), time.process_time()
-    z = O.lloid_snr(d, sl, F0)
-    O.triggers(z, F0)
-    dt, dc = time.perf_counter() - t, time.process_time() - c
-    cores = max(1, round(dc / dt, 1))          # threads actually busy (CPU time / wall time)
-    return M * seconds / dt, dt, f"{M} templates of the 1000-template family x 1 detector x {seconds} s " \
-                                 f"(oracle FP64 numpy LLOID + triggers)", cores
+    z = O.lloid_snr(d.astype(np.float64), sub, F0)
+    trig = O.triggers(z, F0)
+    return z, trig, time.perf_counter() - t, time.process_time() - c
+
+
+def oracle_leg(workload):
+    """cpu_baseline: the oracle as it stands, timed on this host's cores over the
+    bounded sample; its SNR and triggers are kept for the precision report."""
+    w, M_sub, secs = oracle_sample_workload(workload)
+    d = w.strain(0)
+    out, wall, cpu = [], 0.0, 0.0
+    for k in range(len(w.banks)):
+        z, trig, dt, dc = oracle_run(w, k, M_sub, d)
+        out.append((k, z, trig))
+        wall += dt
+        cpu += dc
+    units = M_sub * secs * len(w.banks)
+    banks = ORACLE_SAMPLE[workload][0]
+    desc = (f"{len(w.banks)} banks ({', '.join(map(str, banks))}) of the workload, the first {M_sub} templates of "
+            f"each, 1 detector x {secs} s (oracle FP64 numpy LLOID + triggers)")
+    cpu_line = {"value": units / wall, "unit": UNIT, "cores": max(1.0, round(cpu / wall, 1)), "kind": "oracle",
+                "sample": desc, "seconds": round(wall, 2)}
+    return cpu_line, (w, M_sub, d, out)
 
 
 def run_reference(args, rank, world, dist):
-    """The base contract's reference arm: the oracle, timed on host cores."""
+    """The base contract's reference arm: the oracle, timed on host cores; each step
+    is one bank of the bounded sample (the banks in turn)."""
     if rank != 0:
         return
-    vals = []
-    cores = []
-    secs = REF_SECONDS
-    for _ in range(args.warmup):
-        oracle_sample(M=REF_M, seconds=secs)
+    w, M_sub, secs = oracle_sample_workload(args.workload)
+    d = w.strain(0)
+    nb = len(w.banks)
+    for i in range(args.warmup):
+        oracle_run(w, i % nb, M_sub, d)
+    vals, cpus = [], []
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        v, dt, sample, c = oracle_sample(M=REF_M, seconds=secs)
+    for i in range(args.steps):
+        _, _, dt, dc = oracle_run(w, i % nb, M_sub, d)
         vals.append(dt)
-        cores.append(c)
+        cpus.append(dc)
     wall = time.perf_counter() - t0
-    value = REF_M * secs * args.steps / sum(vals)
+    value = M_sub * secs * args.steps / sum(vals)
+    sample = (f"each step: the first {M_sub} templates of one of {nb} banks of the workload (in turn) x "
+              f"1 detector x {secs} s (oracle FP64 numpy LLOID + triggers)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(cores), "kind": "oracle",
-                             "sample": "each step: " + sample},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(1.0, round(sum(cpus) / sum(vals), 1)),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def precision_report(P, sample, forms=("ladder", "f0"), dev=0):
+    """The GPU path's SNR on the oracle's sample, per precision (and per form of the
+    split paths), against the oracle's FP64 SNR: quantiles of |dz| over every
+    (template, sample) and the agreement of the triggers (same window, template and
+    sample as the oracle's; otherwise the GPU's sample within the tolerance of the
+    oracle's window maximum)."""
+    import numpy as np
+    from paper_2511_04730_b300 import build_svd_bank
+    w, M_sub, d, out = sample
+    T = d.size
+    sb = [build_svd_bank(b, p) for b, p in zip(w.banks, w.plans)]
+    rep = {}
+    tol = {"fp32": 1e-3, "fp16_split": 5e-3, "bf16_split": 5e-3}
+    cases = [("fp32", None)] + [(p, f) for p in ("fp16_split", "bf16_split") for f in forms]
+    for prec, form in cases:
+        dz_all, n_trig, n_same, n_valid, n_wrong, n_missing, n_extra = [], 0, 0, 0, 0, 0, 0
+        with P.Context(n_detectors=1, precision=prec, max_block=8192, max_history=max(b.n_samples for b in w.banks),
+                       device=dev, form=form) as ctx:
+            ids = [ctx.load_bank(x) for x in sb]
+            zs = {i: [] for i in ids}
+            trig = []
+            for t in range(0, T - T % 8192, 8192):
+                ctx.push(0, t, np.ascontiguousarray(d[t:t + 8192], dtype=np.float32))
+                for i in ids:
+                    zs[i].append(ctx.snr_block(0, i)[0][: 2 * M_sub].cpu().numpy())
+                trig.append(ctx.pull(t // F0, n_windows=8192 // F0))
+            trig = np.concatenate(trig)
+        for (k, zo, otr), i in zip(out, ids):
+            z = np.concatenate(zs[i], axis=1)
+            n = z.shape[1]
+            dz = np.sqrt((z[0::2] - zo[0::2, :n]) ** 2 + (z[1::2] - zo[1::2, :n]) ** 2)
+            dz_all.append(dz.ravel())
+            p = np.sqrt(zo[0::2, :n] ** 2 + zo[1::2, :n] ** 2)
+            g = {(int(r["window"]), int(r["tmpl"])): r for r in trig[(trig["bank"] == i) & (trig["tmpl"] < M_sub)]}
+            for o in otr:
+                if (o.window + 1) * F0 > n:
+                    continue
+                n_trig += 1
+                r = g.pop((o.window, o.tmpl), None)
+                if r is None:
+                    n_missing += o.snr > 4.0 + tol[prec]          # else: within the tolerance of the threshold
+                    continue
+                if int(r["sample"]) == o.sample:
+                    n_same += 1
+                elif p[o.tmpl, int(r["sample"])] >= o.snr - tol[prec]:
+                    n_valid += 1
+                else:
+                    n_wrong += 1
+            for (win, tm), r in g.items():
+                if (win + 1) * F0 <= n:
+                    n_extra += p[tm, win * F0:(win + 1) * F0].max() < 4.0 - tol[prec]
+        a = np.concatenate(dz_all)
+        key = prec if form is None else f"{prec}/{form}"
+        rep[key] = {"max": float(a.max()), "p99": float(np.quantile(a, 0.99)), "p50": float(np.median(a)),
+                    "n": int(a.size), "triggers": n_trig, "same_sample": n_same, "other_valid_sample": n_valid,
+                    "wrong_sample": n_wrong, "missing": int(n_missing), "extra": int(n_extra)}
+    return {"vs": "FP64 oracle on the cpu_baseline sample", "tolerance": tol, "dz": rep}
 
 
 # ---------------------------------------------------------------------------
@@ -340,6 +445,8 @@ def run_lloid(args, rank, world, dist):
     build.build()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    if args.xi2_half is None:
+        args.xi2_half = 350 if args.workload == "bank1000" else 0
     w, strain = make_inputs(args, rank)
     all_banks = build_banks(w)
     if len(all_banks) > 1 and world > 1:            # shard the bank set: LPT on per-bank work
@@ -350,7 +457,6 @@ def run_lloid(args, rank, world, dist):
         mine = list(range(len(all_banks)))
     banks_sb = [all_banks[i] for i in mine]
     M_list = [w.banks[i].n_templates for i in mine]
-    sb = banks_sb[0]
     M = sum(M_list)
     n_det = w.n_det
     max_hist = max(b.n_samples for b in w.banks)
@@ -363,17 +469,18 @@ def run_lloid(args, rank, world, dist):
     d_blocks = torch.from_numpy(blocks).to(f"cuda:{dev}")
     h_blocks = torch.from_numpy(blocks).pin_memory()
 
-    def make_ctx(precision, timing):
-        return P.Context(n_detectors=n_det, precision=precision, max_block=B, max_history=max_hist,
-                         device=dev, stage_timing=timing)
+    def make_ctx(precision, timing, form=args.form, max_block=B):
+        return P.Context(n_detectors=n_det, precision=precision, max_block=max_block, max_history=max_hist,
+                         device=dev, stage_timing=timing, form=form)
 
-    def load_all(ctx):
-        return [ctx.load_bank(x) for x in banks_sb]
+    def load_all(ctx, which=None):
+        return [ctx.load_bank(banks_sb[i]) for i in (range(len(banks_sb)) if which is None else which)]
 
     if args.serve:
         from paper_2511_04730_b300.serving import Server
         SB = args.serve_block
-        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=SB, max_history=max_hist, device=dev)
+        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=SB, max_history=max_hist, device=dev,
+                        form=args.form)
         srv = Server(ctx, SB)
         for i, x in enumerate(banks_sb):
             srv.submit(x, tag=i)
@@ -433,46 +540,114 @@ def run_lloid(args, rank, world, dist):
                 pos += B
         return ms, pos, ctx.launch_count() - l0, h2d, d2h
 
-    result = {}
-    per_ctx = {}
-    precisions = [args.precision] + ([] if args.no_fp32_compare or args.precision == "fp32" else ["fp32"])
-    clocks = None
-    for prec in precisions:
-        # throughput: K steps without per-stage events
-        ctx = make_ctx(prec, timing=False)
+    # ---- throughput: K steps without per-stage events, clocks sampled during them
+    ctx = make_ctx(args.precision, timing=False)
+    ids = load_all(ctx)
+    forms = {}
+    form_of = []
+    for i in ids:
+        f = ctx.bank_form(i)
+        form_of.append(f)
+        forms[f] = forms.get(f, 0) + 1
+    pos = 0
+    _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    sampler.begin()
+    ms, pos, launches, _, _ = run_steps(ctx, args.steps, pos)
+    torch.cuda.synchronize()
+    sampler.end()
+    clocks = sampler.stop()
+    ctx.close()
+
+    # ---- stage breakdown and roofline: the same K steps again, with CUDA events around every stage
+    ctx = make_ctx(args.precision, timing=True)
+    load_all(ctx)
+    pos = 0
+    _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
+    ctx.stage_times(reset=True)
+    torch.cuda.synchronize()
+    ms_t, pos, _, _, _ = run_steps(ctx, args.steps, pos)
+    torch.cuda.synchronize()
+    stages = ctx.stage_times(reset=True)
+    ctx.close()
+
+    # ---- end to end: host blocks in, triggers out, through the public API
+    e2e = None
+    if not args.no_e2e:
+        ctx = make_ctx(args.precision, False)
         load_all(ctx)
         pos = 0
-        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        sampler = ClockSampler(dev) if prec == args.precision else None
-        if sampler:
-            sampler.start()
-            sampler.begin()
-        ms, pos, launches, _, _ = run_steps(ctx, args.steps, pos)
-        torch.cuda.synchronize()
-        if sampler:
-            sampler.end()
-            clocks = sampler.stop()
+        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, host=True)
+        ms_e, pos, _, h2d, d2h = run_steps(ctx, args.steps, pos, host=True)
         ctx.close()
-        per_ctx[prec] = {"ms": ms, "launches": launches}
-        if prec != args.precision:
-            continue
-        # stage breakdown and roofline: the same K steps again, with CUDA events around every stage
-        ctx = make_ctx(prec, timing=True)
+        e2e = {"value": M * args.block_seconds * n_det * args.steps / (sum(ms_e) / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+               "ms_per_step": statistics.mean(ms_e)}
+
+    # ---- the plain FP32 path (reference precision) on the same blocks, a few steps
+    paths = {args.precision: M * args.block_seconds * n_det * args.steps / (sum(ms) / 1000.0)}
+    if args.precision != "fp32" and not args.no_fp32_compare:
+        k32 = min(args.steps, 3)
+        ctx = make_ctx("fp32", timing=False)
         load_all(ctx)
         pos = 0
-        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
-        ctx.stage_times(reset=True)
-        torch.cuda.synchronize()
-        ms_t, pos, _, _, _ = run_steps(ctx, args.steps, pos)
-        torch.cuda.synchronize()
-        per_ctx[prec]["stages"] = ctx.stage_times(reset=True)
-        per_ctx[prec]["ms_timed_stages"] = ms_t
+        _, pos, _, _, _ = run_steps(ctx, 1, pos)
+        ms32, pos, _, _, _ = run_steps(ctx, k32, pos)
+        ctx.close()
+        paths["fp32"] = M * args.block_seconds * n_det * k32 / (sum(ms32) / 1000.0)
+        paths["fp32_steps"] = k32
+
+    # ---- accuracy against the FP32 path on a sample of banks (every SNR sample of every
+    # template of those banks, over the last pushes after a full template history)
+    max_dsnr = None
+    if args.precision != "fp32" and not args.no_fp32_compare:
+        stride = max(1, len(banks_sb) // 24)
+        chk = list(range(0, len(banks_sb), stride))
+        a, b = make_ctx(args.precision, False), make_ctx("fp32", False)
+        ia, ib = load_all(a, chk), load_all(b, chk)
+        hist = max(w.banks[mine[i]].n_samples for i in chk)
+        max_dsnr = 0.0
+        n_push = (hist + 2 * B - 1) // B + 2
+        for k in range(n_push):
+            blk = d_blocks[k % n_blk]
+            a.push_all(k * B, blk)
+            b.push_all(k * B, blk)
+            if k >= n_push - 2:
+                for det in range(n_det):
+                    for x, y, j in zip(ia, ib, chk):
+                        za, _ = a.snr_block(det, x)
+                        zb, _ = b.snr_block(det, y)
+                        dz = torch.sqrt(((za - zb) ** 2).view(M_list[j], 2, -1).sum(1)).max().item()
+                        max_dsnr = max(max_dsnr, dz)
+        a.close()
+        b.close()
+        max_dsnr = {"value": max_dsnr, "banks": len(chk), "templates": sum(M_list[j] for j in chk),
+                    "samples_per_template": 2 * B, "detectors": n_det}
+
+    # ---- per-block latency at 1 s blocks (block arrival on the host -> its window's triggers on the host)
+    lat = []
+    if args.latency_steps:
+        ctx = make_ctx(args.precision, False, max_block=F0)
+        load_all(ctx)
+        pos = 0
+        h_sec = torch.from_numpy(np.ascontiguousarray(
+            strain.reshape(n_det, T // F0, F0).transpose(1, 0, 2))).pin_memory()
+        warm = 8
+        for k in range(warm + args.latency_steps):
+            blk = h_sec[(pos // F0) % (T // F0)].numpy()
+            t0 = time.perf_counter()
+            ctx.push_all(pos, blk)
+            ctx.pull(pos // F0)
+            if k >= warm:
+                lat.append(1000 * (time.perf_counter() - t0))
+            pos += F0
         ctx.close()
 
-    # Eq. 10 (a NEXT row): the same steps with autocorrelations loaded for every bank
+    # ---- Eq. 10 (a NEXT row): the same steps with autocorrelations loaded for every bank
     xi2 = None
     if args.xi2_half > 0:
         from paper_2511_04730_b300.svdbank import template_autocorrelation
@@ -496,7 +671,7 @@ def run_lloid(args, rank, world, dist):
                "recon_ms_per_step": round(st_x["recon"][0] / args.steps, 4),
                "d2h_bytes_per_step": d2h_x // args.steps, "autocorr_build_s": round(t_ac, 1)}
 
-    # PSD estimation and whitening (a NEXT row): 16384 Hz -> 2048 Hz, N = 4 s, Z = 1 s, 16 s pushes
+    # ---- PSD estimation and whitening (a NEXT row): 16384 Hz -> 2048 Hz, N = 4 s, Z = 1 s, 16 s pushes
     whiten = None
     if args.whiten_seconds > 0 and rank == 0:
         fi, push = 16384, 16 * 16384
@@ -526,60 +701,12 @@ def run_lloid(args, rank, world, dist):
         whiten = {"value": secs / dt, "unit": "detector-seconds whitened/s", "input_rate": fi, "output_rate": F0,
                   "n_fft_s": 4, "z_s": 1, "push_s": 16, "seconds": secs}
 
-    # accuracy of the measured path against the FP32 path (same stream, same blocks)
-    max_dsnr = None
-    if args.precision != "fp32" and not args.no_fp32_compare:
-        a, b = make_ctx(args.precision, False), make_ctx("fp32", False)
-        ia, ib = load_all(a), load_all(b)
-        max_dsnr = 0.0
-        n_chk = min(8, len(ia))                       # compare the first banks (all of them for one bank)
-        for k in range((max_hist + 8 * F0) // B):
-            blk = d_blocks[k % n_blk]
-            a.push_all(k * B, blk)
-            b.push_all(k * B, blk)
-            if (k + 1) * B >= max_hist:
-                for det in range(n_det):
-                    for j in range(n_chk):
-                        za, _ = a.snr_block(det, ia[j])
-                        zb, _ = b.snr_block(det, ib[j])
-                        dz = torch.sqrt(((za - zb) ** 2).view(M_list[j], 2, -1).sum(1)).max().item()
-                        max_dsnr = max(max_dsnr, dz)
-        a.close()
-        b.close()
+    # ---- the oracle leg (rank 0): cpu_baseline, and the error distribution of every precision against it
+    cpu, precision = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, sample = oracle_leg(args.workload)
+        precision = precision_report(P, sample, dev=dev)
 
-    # end to end: host blocks in, triggers out, through the public API
-    e2e = None
-    if not args.no_e2e:
-        ctx = make_ctx(args.precision, False)
-        load_all(ctx)
-        pos = 0
-        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, host=True)
-        ms_e, pos, _, h2d, d2h = run_steps(ctx, args.steps, pos, host=True)
-        ctx.close()
-        e2e = {"value": M * args.block_seconds * n_det * args.steps / (sum(ms_e) / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
-
-    # per-block latency at 1 s blocks (block arrival on the host -> its window's triggers on the host)
-    lat = []
-    if args.latency_steps:
-        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=F0, max_history=max_hist, device=dev)
-        load_all(ctx)
-        pos = 0
-        h_sec = torch.from_numpy(np.ascontiguousarray(
-            strain.reshape(n_det, T // F0, F0).transpose(1, 0, 2))).pin_memory()
-        warm = max_hist // F0 + 8
-        for k in range(warm + args.latency_steps):
-            blk = h_sec[(pos // F0) % (T // F0)].numpy()
-            t0 = time.perf_counter()
-            ctx.push_all(pos, blk)
-            ctx.pull(pos // F0)
-            if k >= warm:
-                lat.append(1000 * (time.perf_counter() - t0))
-            pos += F0
-        ctx.close()
-
-    main = per_ctx[args.precision]
-    ms = main["ms"]
     units = M * args.block_seconds * n_det
     my_time = sum(ms) / 1000.0
     if dist is not None:
@@ -591,51 +718,65 @@ def run_lloid(args, rank, world, dist):
     else:                                          # shards of one bank set
         value = w.n_templates * args.block_seconds * n_det * args.steps / my_time
 
-    # roofline of the dominant kernel (stage with the largest device time)
-    stages = main["stages"]
-    dom = max(("fir", "upsample", "recon"), key=lambda k: stages[k][0])
-    dur_ms = stages[dom][0] / max(1, stages[dom][1])
+    # ---- per-stage algorithmic work by form, roofline of the dominant stage
     works = [algorithmic_work(x, m) for x, m in zip(banks_sb, M_list)]
-    work = {k: sum(wk[k] for wk in works) for k in works[0]}
     det_s = args.block_seconds * n_det
+    tc = args.precision != "fp32"
+    wk = {"fir": 0.0, "upsample": 0.0, "recon": 0.0, "yup_bytes": 0.0}
+    for wo, f, x in zip(works, form_of, banks_sb):
+        wk["fir"] += wo["fir"]
+        if not tc:
+            wk["upsample"] += wo["ladder"]
+            wk["recon"] += wo["recon"] + wo["max"]
+        elif f == "f0":            # Eq. 6-8 of the bank in the f0 level; the upsampling kernel moves bytes
+            wk["recon"] += wo["recon"] + wo["ladder"] + wo["max"]
+            k_all = sum(s.n_basis for s in x)
+            wk["yup_bytes"] += (-(-k_all // 64) * 64) * F0 * 4.0 + sum(s.n_basis * s.rate * 4.0 for s in x)
+        else:
+            wk["upsample"] += wo["below_f0"]
+            wk["recon"] += wo["at_f0"]
     pk, pk_kind = peaks()
     alu_peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-    tc = args.precision != "fp32"
     alu_note = "FP32 FFMA: 148 SMs x 128 lanes x 2 flop x max SM clock"
-    tc_peak, tc_note = pk["bf16_tflops_sustained"], f"{pk_kind} dense bf16 sustained (fp16 nominal rate equal)"
-    if tc:   # stage -> (kernel, bound, peak, peak note, algorithmic flop per detector-second)
-        kinds = {"fir": ("k_fir_tc", "tensor", tc_peak, tc_note, work["fir"]),
-                 "upsample": ("k_level_tc (levels below f0)", "tensor", tc_peak, tc_note, work["below_f0"]),
-                 "recon": ("k_level_tc (f0 level + window maxima)", "tensor", tc_peak, tc_note, work["at_f0"])}
+    tc_peak = pk["bf16_tflops"]
+    tc_note = (f"{pk_kind} dense bf16 burst (the kernels run inside a {statistics.mean(ms):.1f} ms step"
+               + ("; fp16 nominal rate equal" if args.precision == "fp16_split" else "") + ")")
+    ladder_only = forms.get("f0", 0) == 0
+    if tc:
+        up_kind = ("k_level_tc (levels below f0)", "tensor", tc_peak, tc_note, wk["upsample"], "TFLOP/s") \
+            if ladder_only or forms.get("ladder", 0) > 0 else \
+            ("k_yup (slice basis outputs up to f0)", "hbm", pk["hbm_gbs"], f"{pk_kind} HBM copy bandwidth",
+             wk["yup_bytes"], "GB/s")
+        kinds = {"fir": ("k_fir_tc", "tensor", tc_peak, tc_note, wk["fir"], "TFLOP/s"),
+                 "upsample": up_kind,
+                 "recon": ("k_level_tc (f0 level + window maxima)", "tensor", tc_peak, tc_note, wk["recon"],
+                           "TFLOP/s")}
     else:
-        kinds = {"fir": ("k_fir_f32", "alu", alu_peak, alu_note, work["fir"]),
-                 "upsample": ("k_upsample", "alu", alu_peak, alu_note, work["ladder"]),
-                 "recon": ("k_recon_f32", "alu", alu_peak, alu_note, work["recon"] + work["max"])}
-    kname, bound, peak, peak_note, per_dets = kinds[dom]
-    launches_dom = max(1.0, stages[dom][1] / args.steps)
-    alg = per_dets * det_s / launches_dom          # one launch's share of the stage's work
-    achieved = alg / (dur_ms / 1000.0) / 1e12
-    traffic = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, dom)
-    roofline = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
-                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                                   "profiles/k_level_tc_k_fir_tc_bank1000.md") if traffic else None,
-                "algorithmic_flop_per_launch": alg, "launch_ms": dur_ms}
+        kinds = {"fir": ("k_fir_f32", "alu", alu_peak, alu_note, wk["fir"], "TFLOP/s"),
+                 "upsample": ("k_upsample", "alu", alu_peak, alu_note, wk["upsample"], "TFLOP/s"),
+                 "recon": ("k_recon_f32", "alu", alu_peak, alu_note, wk["recon"], "TFLOP/s")}
     per_stage = {}
     for st_name in ("fir", "upsample", "recon"):
-        ms_l = stages[st_name][0] / max(1, stages[st_name][1])
-        k = kinds[st_name]
-        lps = stages[st_name][1] / args.steps
-        per_stage[st_name] = {"kernel": k[0], "launch_ms": ms_l, "launches_per_step": lps,
-                              "algorithmic_tflops": (k[4] * det_s / max(lps, 1.0)) / (ms_l / 1000.0) / 1e12
-                              if ms_l > 0 else None}
-    recon_info = per_stage
+        tot_ms, n_l = stages[st_name]
+        if n_l == 0:
+            continue
+        kname, bound, peak, note, work, unit = kinds[st_name]
+        lps = n_l / args.steps
+        launch_ms = tot_ms / n_l
+        scale = 1e9 if unit == "GB/s" else 1e12
+        achieved = (work * det_s / lps) / (launch_ms / 1000.0) / scale
+        per_stage[st_name] = {"kernel": kname, "bound": bound, "launch_ms": launch_ms, "launches_per_step": lps,
+                              "achieved": achieved, "unit": unit, "peak": peak, "frac": achieved / peak,
+                              "peak_source": note, "algorithmic_per_launch": work * det_s / lps}
+    dom = max(per_stage, key=lambda k: stages[k][0])
+    d = per_stage[dom]
+    traffic = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, dom)
+    roofline = {"kernel": d["kernel"], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+                "unit": d["unit"], "frac": d["frac"], "traffic": traffic, "peak_source": d["peak_source"],
+                "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, {TRAFFIC_PROFILE}"
+                                   if traffic else None),
+                "algorithmic_per_launch": d["algorithmic_per_launch"], "launch_ms": d["launch_ms"]}
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items()}
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        v, dt, sample, cores = oracle_sample()
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample, "seconds": dt}
 
     if rank == 0:
         line = {
@@ -647,20 +788,21 @@ def run_lloid(args, rank, world, dist):
             "config": {"workload": WORKLOADS[args.workload], "n_templates": M, "n_banks": len(banks_sb),
                        "n_detectors": n_det, "block_seconds": args.block_seconds, "precision": args.precision,
                        "l2": "flushed between steps (256 MB write, outside the timed events)",
-                       "bases_total": sum(s.n_basis for x in banks_sb for s in x),
+                       "bases_total": sum(s.n_basis for x in banks_sb for s in x), "bank_forms": forms,
                        "parallelism": (f"replicas x{world}" if len(all_banks) == 1 else f"bank shards x{world}")},
-            "e2e": e2e, "gpu_launches": main["launches"], "clocks": clocks,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "roofline": roofline, "cpu_baseline": cpu,
             "max_dsnr_vs_fp32": max_dsnr,
+            "precision": precision,
             "latency_ms_1s_blocks": ({"p50": statistics.median(lat),
                                       "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
                                       "n": len(lat)} if lat else None),
             "stage_ms_per_step": stage_ms,
+            "ms_per_step_with_stage_events": statistics.mean(ms_t),
+            "kernels": per_stage,
             "xi2": xi2,
             "whiten": whiten,
-            "ms_per_step_with_stage_events": statistics.mean(main["ms_timed_stages"]),
-            "kernels": recon_info,
-            "paths": {p: units * args.steps / (sum(v["ms"]) / 1000.0) for p, v in per_ctx.items()},
+            "paths": paths,
         }
         print(json.dumps(line), flush=True)
 

@@ -353,6 +353,65 @@ LLOID_API void* lloid_stream(const lloid_ctx* ctx);
  * for the context's stream.  Either output may be NULL. */
 #define LLOID_FLAG_STAGE_TIMING 1u
 #define LLOID_N_STAGES 7
+
+/* Form of the split-precision path per bank (lloid_config.flags).  Both give
+ * the same SNR up to rounding, because Eq. 6 and Eq. 7-8 are linear and the
+ * coefficients do not depend on time:
+ *   ladder: per rate, reconstruct (Eq. 6), then upsample and add into the
+ *           next rate (Eq. 7-9), lowest rate first, in the paper's order;
+ *   f0:     upsample each slice's basis outputs to f0 through the slice's
+ *           composed ladder (Eq. 7-8), then reconstruct once at f0 over all
+ *           of the bank's bases.
+ * The ladder costs less when a bank has many bases at low rates, the f0 form
+ * when it has few (it has no per-rate window products and no per-rate
+ * intermediate SNR in device memory).  Without either flag each bank takes
+ * the form an estimate of its tensor-core and memory time prefers, which
+ * lloid_autotune can then replace by measured times.  Ignored by the FP32 path. */
+#define LLOID_FLAG_FORM_LADDER 2u
+#define LLOID_FLAG_FORM_F0 4u
+
+/* The form bank `bank` runs in: 0 ladder, 1 f0 (always 0 on the FP32 path);
+ * -1 if there is no such bank. */
+LLOID_API int32_t lloid_bank_form(const lloid_ctx* ctx, int32_t bank);
+
+/* Gaps in the strain (the pipeline's source turns missing data into gap
+ * buffers, Section II.B): with this flag a push whose t0 lies past the end of
+ * the detector's stream first fills the missing samples with zeros, exactly as
+ * if zeros had been pushed, instead of returning LLOID_EGAP.  A push that
+ * starts before the stream end is still LLOID_EGAP. */
+#define LLOID_FLAG_FILL_GAPS 8u
+
+/* Fault injection on the host side, for testing how a caller copes with
+ * failures.  None of these faults, traps or stalls the GPU:
+ *   LLOID_FAULT_ALLOC        the context's next `count` device allocations
+ *                            fail (LLOID_ENOMEM; a failed load_bank keeps
+ *                            nothing);
+ *   LLOID_FAULT_DROP_BLOCK   the next `count` pushes are lost: they return
+ *                            LLOID_OK and change nothing (the next push then
+ *                            finds a gap);
+ *   LLOID_FAULT_DELAY        the next push starts after a bounded spin of
+ *                            `count` microseconds (at most 10 s) on the
+ *                            context's stream: a slow device, so that a pull
+ *                            with a short timeout returns LLOID_ETIMEOUT;
+ *   LLOID_FAULT_WAIT_EXPIRY  one bounded device wait with a limit of `count`
+ *                            microseconds (at most 1 s) on a barrier that
+ *                            nothing completes: it expires as a stalled
+ *                            pipeline wait would and leaves its code in the
+ *                            context's error flag, so that pulls and
+ *                            lloid_synchronize report LLOID_ETIMEOUT until
+ *                            lloid_clear_error.
+ * count = 0 cancels a pending fault of that kind.  EINVAL for an unknown
+ * kind or a negative count. */
+#define LLOID_FAULT_ALLOC 1
+#define LLOID_FAULT_DROP_BLOCK 2
+#define LLOID_FAULT_DELAY 3
+#define LLOID_FAULT_WAIT_EXPIRY 4
+LLOID_API lloid_status lloid_inject_fault(lloid_ctx* ctx, int32_t kind, int64_t count);
+
+/* Clear the device-side error flag that an expired wait leaves (after waiting
+ * for the context's stream).  The results of pushes enqueued before the
+ * expiry are not to be trusted; the context itself stays usable. */
+LLOID_API lloid_status lloid_clear_error(lloid_ctx* ctx);
 LLOID_API lloid_status lloid_stage_times(lloid_ctx* ctx, double* ms, int64_t* launches, int reset);
 
 /* Allocation-free trigger extraction (no counterpart in the paper; a service

@@ -115,9 +115,15 @@ SIGNATURES = [
       ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     ("lloid_stage_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
+    ("lloid_bank_form", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    ("lloid_inject_fault", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    ("lloid_clear_error", ctypes.c_int, [ctypes.c_void_p]),
 ]
 
 FLAG_STAGE_TIMING = 1
+FORM_FLAGS = {None: 0, "ladder": 2, "f0": 4}     # LLOID_FLAG_FORM_LADDER, LLOID_FLAG_FORM_F0
+FLAG_FILL_GAPS = 8
+FAULTS = {"alloc": 1, "drop_block": 2, "delay": 3, "wait_expiry": 4}   # LLOID_FAULT_*
 N_STAGES = 7
 STAGE_NAMES = ("ingest", "downsample", "fir", "upsample", "recon", "finalize", "gather")
 

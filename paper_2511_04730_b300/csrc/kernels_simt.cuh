@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ job
                                                   int n_slots, int tiles_per_window, long long w0, float threshold,
                                                   SlabEntry* __restrict__ slab_base, int ring, int n_det_total,
                                                   long long slab_det_stride, int det0,
-                                                  unsigned long long* __restrict__ red) {
+                                                  unsigned long long* __restrict__ red, long long fused_from) {
     constexpr int P = kFinTB / 16;
     pdl_launch_dependents();
     pdl_wait();
@@ -444,6 +444,7 @@ __global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ job
     const FinJob jb = jobs[ch.job];
     const int det = det0 + blockIdx.y;
     const long long w = w0 + blockIdx.z;
+    if (jb.fused && w >= fused_from) return;   // the f0 kernel wrote this window (every chunk returns)
     SlabEntry* out = slab_base + (size_t)(w % ring) * n_det_total * slab_det_stride + det * slab_det_stride;
     const int s0 = (int)((w * tiles_per_window) & (n_slots - 1));
     const int hw = threadIdx.x >> 4, l16 = threadIdx.x & 15;

@@ -57,18 +57,43 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false (and *err set) after kWaitNs, or at once if another CTA failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+// Bounded wait: false (and *err set to code) after limit_ns, or at once if another CTA failed.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, int* err, int code,
+                                             unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (;;) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
         if (*reinterpret_cast<volatile int*>(err) != 0) return false;
-        if (gtimer() - t0 > kWaitNs) {
+        if (gtimer() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
             return false;
         }
+    }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+    return mbar_wait_ns(bar, parity, err, code, kWaitNs);
+}
+
+// The bounded wait itself, on its own: one thread waits on a shared-memory barrier
+// that nothing completes, with the given limit; the expiry leaves `code` in *err the
+// way an expired pipeline wait does.  Nothing else is in flight, so the kernel simply
+// returns.  (Used to check the expiry path and its report on the host.)
+__global__ void k_wait_expiry_check(int* err, int code, unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait_ns(&bar, 0, err, code, limit_ns);
+    }
+}
+
+// A delay of the stream by a bounded spin on the global timer (a slow device, for the
+// host-side timeout paths).
+__global__ void k_delay(unsigned long long ns) {
+    const unsigned long long t0 = gtimer();
+    while (gtimer() - t0 < ns) {
     }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {

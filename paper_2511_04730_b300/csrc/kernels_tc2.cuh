@@ -112,7 +112,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 // Per-tile facts, written by the host with the job tables: x = job, y = tile index within the
-// job, z = K'pad of the job, w = its N (FIR c-groups per tile; 0 for a ladder level).  One load
+// job, z = K'pad of the job, w = its N (FIR c-groups per tile) or, for a ladder level, the
+// number of 16-wide K steps that hold bases (K'pad is a multiple of 64; steps past w are zero).  One load
 // replaces a search of the job table, and the MMA issuers read the next tile's entry while the
 // current tile's MMAs run.
 using TileInfo = int4;
@@ -494,6 +495,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                 if (k + 1 < ke) tnext = tinfo[snext / n_det_push];
                 if (k + 2 < ke) snext = sched[gridDim.x + 1 + k + 2];
                 const int Kp = tcur.z;
+                const int nk16 = tcur.w;                 // K steps of 16 that hold bases (the rest of Kp is zero)
                 const int buf = i & 1;
                 if (!mbar_wait(tempty + buf, ((i >> 1) & 1) ^ 1, err, 33)) { ok = false; break; }
                 tc_fence_after();
@@ -507,6 +509,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                     const uint32_t b_hi = sb + C::NA * C::TILE_A, b_lo = b_hi + C::TILE_B;
 #pragma unroll
                     for (int k = 0; k < kTcK / 16; ++k) {
+                        if (kc / 16 + k >= nk16) break;
                         const uint32_t off = k * 32;
                         const uint32_t acc0 = (kc > 0 || k > 0) ? 1u : 0u;
                         umma_f16(d_re, desc_sw128(a_re + off), desc_sw128(b_hi + off), idesc, acc0);
@@ -690,25 +693,24 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// stream rings for the tensor-core FIR: FP32 stream -> hi/lo halves, written
-// at i mod R and i mod R + R (double-mapped so any strip <= R is contiguous)
+// A slice of a bank in the f0 form (kernels_f0.cuh): where its FIR output is
+// and the composed Eq. 7-8 upsampler that brings it to f0.
 // ---------------------------------------------------------------------------
+struct YupSlice {
+    const uint16_t* y_hi;          // level ring of the slice's rate, first column of the slice, detector 0
+    const uint16_t* y_lo;
+    long long y_det_stride;        // elements
+    const float* R;                // composed upsampler [rlen]
+    int y_rows, y_ld;              // level ring rows (power of two) and row length
+    int e_min, rlen, D, L;         // response support [e_min, e_min + rlen); L bases
+    int tcol;                      // first column of the slice in the packed f0 ring
+    int pad;
+};
 template <bool BF16>
-__global__ void k_split_stream(const float* __restrict__ src, long long src_det_stride, int src_mask,
-                               uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, long long dst_det_stride,
-                               int dst_len, long long i0, int count, int det0) {
-    const int det = det0 + blockIdx.y;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
-        const long long i = i0 + e;
-        const float v = src[det * src_det_stride + (i & src_mask)];
-        uint16_t h, l;
-        split_hilo<BF16>(v, h, l);
-        const long long p = i & (dst_len - 1);
-        hi[det * dst_det_stride + p] = h;
-        hi[det * dst_det_stride + p + dst_len] = h;
-        lo[det * dst_det_stride + p] = l;
-        lo[det * dst_det_stride + p + dst_len] = l;
-    }
+__device__ __forceinline__ float hilo_value(uint16_t h, uint16_t w) {
+    if (BF16) return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(&h)) +
+                     __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(&w));
+    return __half2float(*reinterpret_cast<const __half*>(&h)) + __half2float(*reinterpret_cast<const __half*>(&w));
 }
 
 }  // namespace lloid

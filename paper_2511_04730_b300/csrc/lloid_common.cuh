@@ -116,6 +116,7 @@ struct Xi2Job {
 struct FinJob {
     int tmpl0, M, bank;
     uint32_t* bg;                // background counts [det][n_snr][n_xi2], or null
+    int fused;                   // 1: the f0 kernel finalises the windows of pushes that start on a window
 };
 
 // One (bank, window) slot of the clustered coincident events.

@@ -22,6 +22,7 @@
 #include "kernels_simt.cuh"
 #include "kernels_tc.cuh"
 #include "kernels_tc2.cuh"
+#include "kernels_f0.cuh"
 
 using namespace lloid;
 
@@ -55,9 +56,11 @@ struct SliceRT {
     int row0 = 0;                // first Yhat row of the slice within the bank
     int e_min = 0, e_max = 0;    // support of the composed upsampler (full-rate offsets)
     float* d_bases = nullptr;
-    float* d_R = nullptr;
+    float* d_R = nullptr;        // composed upsampler (FP32 path; split path in the f0 form)
     float* d_yring = nullptr;    // [n_det][L][y_len]
     int y_len = 0;
+    int tcol = 0;                // split path, f0 form: first column of the slice in the f0 operand ring
+    std::vector<double> R;       // composed upsampler (host copy)
 };
 
 // Split-precision (tensor-core) path: one ladder level per distinct rate of
@@ -78,8 +81,11 @@ struct FirSliceRT {
 
 struct BankRT {
     int id = 0, M = 0, Mpad = 0, K = 0, Kpad = 0, tmpl0 = 0;
+    int form = 0;                      // split path: 0 = per-rate ladder, 1 = f0 form
     std::vector<SliceRT> sl;
     std::vector<LevelRT> lev;          // split path
+    LevelRT top;                       // split path, f0 form: K = the bank's bases packed, rounded up to 16
+    uint16_t* d_cblk = nullptr;        // f0 form: coefficient planes [re hi, im hi, (re lo, im lo)][K/8][Mpad][8]
     std::vector<FirSliceRT> fs;        // split path, parallel to sl
     void* d_cre = nullptr;       // [Mpad][Kpad] (FP32 or half)
     void* d_cim = nullptr;
@@ -196,6 +202,13 @@ struct lloid_ctx {
     Xi2Job* d_xi2 = nullptr; int* d_xi2_base = nullptr; int n_xi2 = 0, xi2_tiles = 0;
     int xi2_half_max = 0;              // largest d of the loaded banks (pull readiness)
     std::vector<long long> xi2_next;   // per detector: first window whose xi2 is not computed yet
+    // f0 form: per launch class (K <= 64 with two Yhat buffers, K <= 128 with one) the banks' jobs,
+    // coefficient maps, work units (bank, window group) and their schedules; one slice table
+    static constexpr int kF0Classes = 2;
+    F0Job* d_f0job[kF0Classes] = {}; F0Maps* d_f0map[kF0Classes] = {}; F0Unit* d_f0unit[kF0Classes] = {};
+    int* d_f0sched[kF0Classes][2] = {}; int f0_grid[kF0Classes][2] = {}; int n_f0unit[kF0Classes] = {};
+    YupSlice* d_f0slices = nullptr;
+    std::vector<int> f0_class_of_bank, f0_job_of_bank;
     uint16_t* d_u_hi[kFSlots] = {};    // Eq. 8 tile matrices per F slot (hi, lo halves)
     uint16_t* d_u_lo[kFSlots] = {};
     // split path streams: index 0 = f0, index r + 1 = rate_D[r]; hi/lo halves, double-mapped
@@ -206,6 +219,10 @@ struct lloid_ctx {
     cudaEvent_t done_ev = nullptr;
     int* d_err = nullptr;              // device-side wait-expiry code (0 = none)
     int n_sm = 0;
+
+    // injected faults (lloid_inject_fault) and the zero block that fills gaps
+    long long fault_alloc = 0, fault_drop = 0, fault_delay_us = 0;
+    float* d_zero = nullptr;
 
     // stage timing (LLOID_FLAG_STAGE_TIMING)
     struct Pending { int stage; cudaEvent_t a, b; };
@@ -246,6 +263,10 @@ lloid_status fail(lloid_ctx* c, lloid_status st, const char* fmt, ...) {
 template <typename T>
 lloid_status dalloc(lloid_ctx* ctx, T** p, size_t bytes, std::vector<void*>* owner, size_t* acct) {
     void* q = nullptr;
+    if (ctx->fault_alloc > 0) {
+        --ctx->fault_alloc;
+        return fail(ctx, LLOID_ENOMEM, "device allocation of %zu bytes failed (injected)", bytes);
+    }
     CK(cudaMalloc(&q, bytes));
     CK(cudaMemsetAsync(q, 0, bytes, ctx->stream));
     *p = (T*)q;
@@ -395,6 +416,11 @@ void free_jobs(lloid_ctx* ctx) {
     ctx->d_fir_sched[0] = ctx->d_fir_sched[1] = nullptr;
     ctx->n_firtc = ctx->firtc_tiles = 0;
     ctx->d_xi2 = nullptr; ctx->d_xi2_base = nullptr; ctx->n_xi2 = ctx->xi2_tiles = 0;
+    for (int k = 0; k < lloid_ctx::kF0Classes; ++k) {
+        ctx->d_f0job[k] = nullptr; ctx->d_f0map[k] = nullptr; ctx->d_f0unit[k] = nullptr; ctx->n_f0unit[k] = 0;
+        ctx->d_f0sched[k][0] = ctx->d_f0sched[k][1] = nullptr;
+    }
+    ctx->d_f0slices = nullptr;
 }
 
 template <typename T>
@@ -537,13 +563,21 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     std::vector<TileInfo> lb[lloid_ctx::kLevTables];
     int lt[lloid_ctx::kLevTables] = {};
     int ft = 0, strip = 128, max_depth = 0;
+    std::vector<YupSlice> ys;
+    std::vector<F0Job> f0j[lloid_ctx::kF0Classes];
+    std::vector<F0Maps> f0m[lloid_ctx::kF0Classes];
+    std::vector<F0Unit> f0u[lloid_ctx::kF0Classes];
+    std::vector<double> f0cost[lloid_ctx::kF0Classes];
+    lloid_status st0;
     ctx->top_job_of_bank.assign(ctx->next_bank_id, -1);
     ctx->top_slot_of_bank.assign(ctx->next_bank_id, 0);
+    ctx->f0_class_of_bank.assign(ctx->next_bank_id, -1);
+    ctx->f0_job_of_bank.assign(ctx->next_bank_id, -1);
     for (auto& kv : ctx->banks) {
         BankRT* b = kv.second;
         const int nl = (int)b->lev.size();
         if (nl > lloid_ctx::kMaxDepth) return fail(ctx, LLOID_EINVAL, "bank %d has more than 8 ladder levels", b->id);
-        max_depth = std::max(max_depth, nl);
+        max_depth = std::max(max_depth, b->form == 1 ? 0 : nl);
         for (size_t si = 0; si < b->sl.size(); ++si) {
             const SliceRT& sl = b->sl[si];
             const FirSliceRT& fsr = b->fs[si];
@@ -570,11 +604,14 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             for (int l = 0; l < f.Mtiles * f.ctiles; ++l) fb.push_back(TileInfo{(int)fj.size(), l, f.Kp, f.NC});
             fj.push_back(f); fm.push_back(mp); ft += f.Mtiles * f.ctiles;
         }
-        for (int j = 0; j < nl; ++j) {
+        // Ladder form: one job per rate, lowest first (depth nl - 1 .. 0).  The f0 form's banks go
+        // to the f0 kernel's tables below.
+        for (int j = 0; j < nl && b->form == 0; ++j) {
             const LevelRT& L = b->lev[j];
             const int depth = nl - 1 - j;
+            const bool below = j > 0;   // a ladder level below to upsample
             LevelJob q{};
-            if (j > 0) {
+            if (below) {
                 const LevelRT& P = b->lev[j - 1];
                 q.F = P.D / L.D; q.D_lo = P.D; q.Lambda_lo = P.Lambda;
             }
@@ -600,7 +637,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             q.map = (int)lj[tab].size();
             LevelMaps mp;
             std::memset(&mp, 0, sizeof mp);
-            if (j > 0) {
+            if (below) {
                 const LevelRT& P = b->lev[j - 1];
                 const int kw = win_chunks(q.F) * kWinK;
                 if (!encode_map_blocked(&mp.accw, bf, P.d_accp, P.acc_cols, b->Mpad, (long long)nd * 4) ||
@@ -620,9 +657,60 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             }
 
             if (depth == 0) { ctx->top_job_of_bank[b->id] = (int)lj[tab].size(); ctx->top_slot_of_bank[b->id] = fslot; }
-            for (int l = 0; l < q.tiles_m * q.tiles_t; ++l) lb[tab].push_back(TileInfo{(int)lj[tab].size(), l, q.Kp, 0});
+            for (int l = 0; l < q.tiles_m * q.tiles_t; ++l)
+                lb[tab].push_back(TileInfo{(int)lj[tab].size(), l, q.Kp, L.K / 16});
             lj[tab].push_back(q); lm[tab].push_back(mp);
             lt[tab] += q.tiles_m * q.tiles_t;
+        }
+        if (b->form == 1) {   // f0 form: one job of the f0 kernel, its slices, its window groups
+            const int cls = b->top.K <= 64 ? 0 : 1;
+            F0Job f{};
+            f.M = b->M; f.Mpad = b->Mpad; f.tmpl0 = b->tmpl0; f.K = b->top.K; f.tiles_m = b->Mpad / 128;
+            f.s0 = (int)ys.size(); f.ns = (int)b->sl.size(); f.map = (int)f0j[cls].size();
+            for (size_t si = 0; si < b->sl.size(); ++si) {
+                const SliceRT& sl = b->sl[si];
+                const FirSliceRT& fsr = b->fs[si];
+                const LevelRT& L = b->lev[fsr.level];
+                YupSlice u{};
+                u.y_hi = L.d_yhi + fsr.col; u.y_lo = L.d_ylo + fsr.col; u.y_det_stride = 2LL * L.R * L.Kp;
+                u.R = sl.d_R; u.y_rows = L.R; u.y_ld = L.Kp;
+                u.e_min = sl.e_min; u.rlen = sl.e_max - sl.e_min + 1; u.D = sl.D; u.L = sl.L; u.tcol = sl.tcol;
+                ys.push_back(u);
+            }
+            F0Maps mp;
+            std::memset(&mp, 0, sizeof mp);
+            if (!encode_map_blocked(&mp.c, bf, b->d_cblk, b->top.K, b->Mpad, bf ? 4 : 2))
+                return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (f0 coefficients, bank %d)", b->id);
+            ctx->f0_class_of_bank[b->id] = cls;
+            ctx->f0_job_of_bank[b->id] = (int)f0j[cls].size();
+            ctx->top_job_of_bank[b->id] = -1;
+            const int tpw = (int)(c.window_samples / 128), nt = (int)(n / 128);
+            for (int g = 0; g * tpw < nt; ++g) {
+                f0u[cls].push_back(F0Unit{(int)f0j[cls].size(), g});
+                f0cost[cls].push_back((double)f.tiles_m * std::min(tpw, nt - g * tpw) * (bf ? 6 : 4) * (f.K / 16) +
+                                      4.0 * std::min(tpw, nt - g * tpw));
+            }
+            f0j[cls].push_back(f);
+            f0m[cls].push_back(mp);
+        }
+    }
+    if ((st0 = upload_vec(ctx, &ctx->d_f0slices, ys))) return st0;
+    for (int cls = 0; cls < lloid_ctx::kF0Classes; ++cls) {
+        ctx->n_f0unit[cls] = (int)f0u[cls].size();
+        if (f0u[cls].empty()) continue;
+        if ((st0 = upload_vec(ctx, &ctx->d_f0job[cls], f0j[cls])) || (st0 = upload_vec(ctx, &ctx->d_f0map[cls], f0m[cls])) ||
+            (st0 = upload_vec(ctx, &ctx->d_f0unit[cls], f0u[cls])))
+            return st0;
+        for (int v = 0; v < 2; ++v)
+            if ((st0 = upload_sched(ctx, f0cost[cls], v ? nd : 1, &ctx->d_f0sched[cls][v], &ctx->f0_grid[cls][v])))
+                return st0;
+        const int smem = f0_smem_bytes(bf, cls ? 128 : 64, cls ? 1 : 2);
+        if (bf) {
+            CK(cudaFuncSetAttribute(k_f0_top<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            CK(cudaFuncSetAttribute(k_f0_top<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        } else {
+            CK(cudaFuncSetAttribute(k_f0_top<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            CK(cudaFuncSetAttribute(k_f0_top<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         }
     }
     lloid_status st;
@@ -689,7 +777,9 @@ lloid_status build_jobs(lloid_ctx* ctx, long long n) {
     CK(cudaStreamSynchronize(ctx->stream));
     free_jobs(ctx);
     std::vector<FinJob> fin;
-    for (auto& kv : ctx->banks) fin.push_back(FinJob{kv.second->tmpl0, kv.second->M, kv.second->id, kv.second->d_bg});
+    for (auto& kv : ctx->banks)
+        fin.push_back(FinJob{kv.second->tmpl0, kv.second->M, kv.second->id, kv.second->d_bg,
+                             split_precision(ctx) && kv.second->form == 1 ? 1 : 0});
     lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_finj, fin))) return st;
     ctx->n_fin = (int)fin.size();
@@ -860,11 +950,38 @@ lloid_status launch_level(lloid_ctx* ctx, int depth, int fslot, long long k_a, l
     return LLOID_OK;
 }
 
+// One launch of the f0 kernel for launch class cls (K <= 64: two Yhat buffers; K <= 128: one)
+// over the work units of `units` scheduled by `sched` (STORE_Z when zout is given).
+lloid_status launch_f0(lloid_ctx* ctx, int cls, const F0Job* jobs, const F0Unit* units, const int* sched, int grid,
+                       long long k_a, long long n, int det0, int nd, float* zout) {
+    const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
+    const int kc = cls ? 128 : 64, yb = cls ? 1 : 2;
+    const int smem = f0_smem_bytes(bf, kc, yb);
+    const long long part_stride = (long long)ctx->cfg.n_detectors * ctx->n_slots;
+    cudaError_t e;
+#define F0_ARGS jobs, (const F0Maps*)ctx->d_f0map[cls], (const YupSlice*)ctx->d_f0slices, units, sched, 0, kc, yb, k_a, \
+        (int)n, det0, nd, (long long)ctx->cfg.window_samples, ctx->cfg.snr_threshold, ctx->d_part, part_stride,        \
+        ctx->n_slots, ctx->d_slab, (int)kWindowRing, ctx->cfg.n_detectors, (long long)ctx->M_cap, zout, ctx->d_err
+    if (bf) e = zout ? launch_pdl(k_f0_top<true, true>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS)
+                     : launch_pdl(k_f0_top<true, false>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS);
+    else e = zout ? launch_pdl(k_f0_top<false, true>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS)
+                  : launch_pdl(k_f0_top<false, false>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS);
+#undef F0_ARGS
+    CK(e);
+    ++ctx->launches;
+    return LLOID_OK;
+}
+
 // Steps a1-a5 for detectors [det0, det0+nd) whose block [k_a, k_a+n) sits in d_stage (or src).
 lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long n, const float* src,
                      long long src_det_stride) {
     lloid_status st = build_jobs(ctx, n);
     if (st) return st;
+    if (ctx->fault_delay_us > 0) {   // injected: a slow device
+        k_delay<<<1, 1, 0, ctx->stream>>>((unsigned long long)ctx->fault_delay_us * 1000ull);
+        CKL();
+        ctx->fault_delay_us = 0;
+    }
     const int n_i = (int)n;
     // a0 ingest
     {
@@ -957,7 +1074,7 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
                         return st;
                 }
         }
-        // top level (f0) + a5 window maxima
+        // top level (f0) + a5 window maxima; the f0 form's banks: Eq. 7-8 + Eq. 6 + a5 in one kernel
         {
             StageTimer tm(ctx, 4);
             const int v = nd == 1 ? 0 : 1;
@@ -965,6 +1082,10 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
                 st = launch_level(ctx, 0, fs, k_a, n, det0, nd, false, ctx->d_lev[fs], ctx->d_levmaps[fs],
                                   ctx->d_lev_base[fs], ctx->d_lev_sched[fs][v], ctx->lev_grid[fs][v], ctx->n_lev[fs],
                                   ctx->lev_tiles[fs], nullptr);
+            for (int cls = 0; cls < lloid_ctx::kF0Classes && !st; ++cls)
+                if (ctx->n_f0unit[cls])
+                    st = launch_f0(ctx, cls, ctx->d_f0job[cls], ctx->d_f0unit[cls], ctx->d_f0sched[cls][v],
+                                   ctx->f0_grid[cls][v], k_a, n, det0, nd, nullptr);
         }
         if (st) return st;
     }
@@ -974,11 +1095,13 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     const long long w_first = k_a / W, w_end = (k_a + n) / W;   // windows completed by this push
     if (w_end > w_first && ctx->n_fin > 0) {
         dim3 grid(ctx->n_fin_chunks, nd, (unsigned)(w_end - w_first));
+        // windows of the f0 form's banks that the f0 kernel finished (pushes that start on a window)
+        const long long fused_from = (k_a % W == 0) ? w_first : (1LL << 62);
         CK(launch_pdl(k_finalize, grid, dim3(256), 0, ctx->stream, (const FinJob*)ctx->d_finj,
                       (const FinChunk*)ctx->d_fin_chunks, (const Partial*)ctx->d_part,
                       (long long)ctx->cfg.n_detectors * ctx->n_slots, ctx->n_slots, ctx->tiles_per_window, w_first,
                       ctx->cfg.snr_threshold, ctx->d_slab, (int)kWindowRing, ctx->cfg.n_detectors,
-                      (long long)ctx->M_cap, det0, ctx->d_fin_red));
+                      (long long)ctx->M_cap, det0, ctx->d_fin_red, fused_from));
         ++ctx->launches;
     }
     // Eq. 10 for the windows whose triggers now have d samples of z past the window end
@@ -1026,12 +1149,40 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     return LLOID_OK;
 }
 
+lloid_status push_one(lloid_ctx* ctx, int det0, int nd, long long t0, const float* block, long long n,
+                      int is_device_ptr);
+
 lloid_status push_common(lloid_ctx* ctx, int det0, int nd, long long t0, const float* block, long long n,
                          int is_device_ptr) {
     if (!block) return fail(ctx, LLOID_EINVAL, "block is NULL");
     if (n <= 0 || n % kTileT || n > ctx->cfg.max_block)
         return fail(ctx, LLOID_EINVAL, "block length %lld must be a positive multiple of %d and <= max_block %lld",
                     n, kTileT, (long long)ctx->cfg.max_block);
+    if (ctx->fault_drop > 0) {   // injected: the block is lost on its way
+        --ctx->fault_drop;
+        return LLOID_OK;
+    }
+    const long long p0 = ctx->pos[det0];
+    bool gap = true;
+    for (int d = det0; d < det0 + nd; ++d) gap = gap && ctx->pos[d] == p0 && p0 < t0 && (t0 - p0) % kTileT == 0;
+    if (gap && (ctx->cfg.flags & LLOID_FLAG_FILL_GAPS)) {   // the missing samples as zeros
+        if (!ctx->d_zero) {
+            lloid_status st = dalloc(ctx, &ctx->d_zero, (size_t)ctx->cfg.n_detectors * ctx->cfg.max_block * 4, nullptr,
+                                     &ctx->state_bytes);
+            if (st) return st;
+        }
+        for (long long k = p0; k < t0;) {
+            const long long m = std::min<long long>(ctx->cfg.max_block, t0 - k);
+            lloid_status st = push_one(ctx, det0, nd, k, ctx->d_zero, m, 1);
+            if (st) return st;
+            k += m;
+        }
+    }
+    return push_one(ctx, det0, nd, t0, block, n, is_device_ptr);
+}
+
+lloid_status push_one(lloid_ctx* ctx, int det0, int nd, long long t0, const float* block, long long n,
+                      int is_device_ptr) {
     for (int d = det0; d < det0 + nd; ++d)
         if (ctx->pos[d] != t0)
             return fail(ctx, LLOID_EGAP, "detector %d stream ends at %lld, push starts at %lld", d, ctx->pos[d], t0);
@@ -1076,6 +1227,52 @@ lloid_status wait_event(lloid_ctx* ctx, cudaEvent_t ev, int timeout_ms) {
 }
 lloid_status wait_done(lloid_ctx* ctx, int timeout_ms) { return wait_event(ctx, ctx->done_ev, timeout_ms); }
 
+// Form of a bank on the split path (LLOID_FLAG_FORM_*), from an estimate of the device time per
+// detector-second and 128 templates in units of one 128 x 128 x 16 MMA (64 cycles): per 128-sample
+// tile the MMAs of C Y (4, or 6 for BF16, per 16 bases) and of an Eq. 8 window (6 per 16 window
+// rows), an epilogue share, the Acc planes that a ladder level below f0 writes and the next level
+// reads (about 256 KB per tile at a 148th of the HBM bandwidth); in the f0 form the MMAs over the
+// bank's bases packed (K = their count rounded up to 16) and the upsampling of the basis outputs,
+// shared by the bank's template tiles.  The f0 form needs K <= 128, at most 1024 templates and no
+// Eq. 10 autocorrelations (the f0 kernel keeps no SNR history).
+bool f0_form_possible(const BankRT* b, int ac_half) {
+    int k = 0;
+    for (const SliceRT& s : b->sl) k += s.L;
+    return (k + 15) / 16 * 16 <= 128 && b->Mpad <= 128 * kF0MaxTm && ac_half == 0;
+}
+
+int choose_form(const lloid_ctx* ctx, const BankRT* b, const std::vector<int>& ladder, int ac_half) {
+    const lloid_config& c = ctx->cfg;
+    if (c.flags & LLOID_FLAG_FORM_LADDER) return 0;
+    if (!f0_form_possible(b, ac_half)) return 0;
+    if (c.flags & LLOID_FLAG_FORM_F0) return 1;
+    const double mk = c.precision == LLOID_BF16_SPLIT ? 6.0 : 4.0, epi = 20.0, planes = 190.0;
+    const int nl = (int)ladder.size();
+    std::vector<int> k16(nl, 0);
+    int k_all = 0;
+    for (const SliceRT& s : b->sl) {
+        const int j = (int)(std::find(ladder.begin(), ladder.end(), s.rate) - ladder.begin());
+        k16[j] += (s.L + 15) / 16;
+        k_all += s.L;
+    }
+    const int k16_all = (k_all + 15) / 16;
+    const double up_cols = (double)k16_all * 16;
+    double lad = 0.0;
+    for (int j = 0; j < nl; ++j) {
+        double mm = mk * k16[j] + epi;
+        if (j > 0) {
+            const int F = ladder[j] / ladder[j - 1];
+            mm += 6.0 * ((win_rows(F) + win_shift_max(F) + 15) / 16);
+        }
+        if (j < nl - 1) mm += planes;
+        lad += ((double)ladder[j] / 128.0 + 2.0) * mm;
+    }
+    // f0 form: per tile the MMAs over all bases and, shared by the bank's template groups, the
+    // upsampled rows (about 24 multiply-adds per basis and row for 128 threads: ~0.2 MMA each)
+    const double f0 = (double)c.f0 / 128.0 * (mk * k16_all + epi + 0.2 * up_cols / (b->Mpad / 128.0));
+    return f0 < lad ? 1 : 0;
+}
+
 // Split path: ladder levels, 8-phase expanded bases for the tensor-core FIR,
 // per-level coefficient blocks, operand rings and Acc planes.  Uploads
 // everything and accounts the bytes in b.
@@ -1086,11 +1283,18 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
     const int nd = c.n_detectors;
     const int nl = (int)ladder.size();
     const int M = bd->n_templates;
+    const size_t es = 2;
     std::vector<LevelRT> lev(nl);
     for (int j = 0; j < nl; ++j) { lev[j].rate = ladder[j]; lev[j].D = c.f0 / ladder[j]; }
     lev[nl - 1].Lambda = 0;
     for (int j = nl - 2; j >= 0; --j) lev[j].Lambda = lev[j + 1].Lambda + c.n_up * lev[j].D;
+    // Every rate keeps an operand ring of its slices' FIR output (16-aligned columns per slice).
+    // The ladder form reconstructs at every rate through that rate's coefficients.  The f0 form
+    // has one more level at f0, `top`: every slice's basis outputs brought up to f0, packed
+    // slice after slice, and the coefficients of every slice in the same columns.
+    const bool f0form = b->form == 1;
     std::vector<FirSliceRT> fs(bd->n_slices);
+    int tk = 0;
     for (int s = 0; s < bd->n_slices; ++s) {
         const lloid_slice& sl = bd->slices[s];
         const int j = (int)(std::find(ladder.begin(), ladder.end(), sl.rate) - ladder.begin());
@@ -1098,6 +1302,8 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
         fs[s].level = j;
         fs[s].col = lev[j].K;
         lev[j].K += (sl.n_basis + 15) / 16 * 16;
+        b->sl[s].tcol = tk;
+        tk += sl.n_basis;
         const long long JD = sl.j_start / D;
         int Np = sl.n_taps;
         while (((Np - 1 + JD) % 8 + 8) % 8) ++Np;
@@ -1107,17 +1313,26 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
         if (2 * (8 * kFirNC + fs[s].Kp) > 40 * 1024)
             return fail(ctx, LLOID_EINVAL, "slice %d: %d taps exceed the tensor-core FIR strip limit", s, sl.n_taps);
     }
+    LevelRT top;
+    const int npl = bf ? 4 : 2;
+    if (f0form) {
+        top.rate = c.f0;
+        top.K = (tk + 15) / 16 * 16;
+    }
     size_t need = 0;
-    const size_t es = 2;
     for (int j = 0; j < nl; ++j) {
         LevelRT& L = lev[j];
         L.Kp = (L.K + 63) / 64 * 64;
         const long long cnt = (c.max_block - 1 + 2LL * L.Lambda) / L.D + 2;
         L.R = (int)next_pow2(cnt + 128 + 64);
-        if (j < nl - 1) L.acc_cols = 128 * (int)((cnt + 127 + 127) / 128 + 2);   // every column a tile writes
-        need += (size_t)b->Mpad * L.Kp * es * (bf ? 4 : 2);
+        if (j < nl - 1 && !f0form) L.acc_cols = 128 * (int)((cnt + 127 + 127) / 128 + 2);   // every column a tile writes
+        if (!f0form) need += (size_t)b->Mpad * L.Kp * es * (bf ? 4 : 2);
         need += (size_t)nd * 2 * L.R * L.Kp * es * 2;
         need += (size_t)nd * 4 * b->Mpad * L.acc_cols * 2;
+    }
+    if (f0form) {
+        need += (size_t)npl * top.K * b->Mpad * es;
+        for (const SliceRT& r : b->sl) need += r.R.size() * 4;
     }
     for (auto& f : fs) need += (size_t)f.Mtiles * 128 * f.Kp * es * (bf ? 2 : 1);
     *need_out = need;
@@ -1137,7 +1352,6 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
                     if (m >= 0 && m < sl.n_taps) A[(size_t)(8 * l + t) * f.Kp + jj] = sl.bases[(size_t)l * sl.n_taps + m];
                 }
         std::vector<uint16_t> hi, lo, dummy_h, dummy_l;
-        std::vector<double> zero;
         pack_coeffs_tc(bf, A, A, (int)rows, f.Kp, &hi, &dummy_h, &lo, &dummy_l);
         if ((st = dalloc(ctx, (uint16_t**)&f.d_a, hi.size() * 2, &b->allocs, &b->bytes))) return st;
         CK(cudaMemcpyAsync(f.d_a, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, ctx->stream));
@@ -1147,18 +1361,19 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
         }
         CK(cudaStreamSynchronize(ctx->stream));
     }
-    // per-level coefficient blocks, rings, Acc planes
-    for (int j = 0; j < nl; ++j) {
-        LevelRT& L = lev[j];
-        if (L.Kp > 0) {
+    // coefficient blocks [Mpad][K'pad] (FP16, or BF16 hi + lo) and an operand ring of a level;
+    // `col` gives each slice's first column (a slice whose col is < 0 has no columns there)
+    auto fill_level = [&](LevelRT& L, bool with_c, const std::vector<int>& col) -> lloid_status {
+        if (L.Kp == 0) return LLOID_OK;
+        if (with_c) {
             std::vector<double> cre((size_t)b->Mpad * L.Kp, 0.0), cim((size_t)b->Mpad * L.Kp, 0.0);
             for (int s = 0; s < bd->n_slices; ++s) {
-                if (fs[s].level != j) continue;
+                if (col[s] < 0) continue;
                 const lloid_slice& sl = bd->slices[s];
                 for (int i = 0; i < M; ++i)
                     for (int l = 0; l < sl.n_basis; ++l) {
-                        cre[(size_t)i * L.Kp + fs[s].col + l] = sl.coeffs[(size_t)(2 * i) * sl.n_basis + l];
-                        cim[(size_t)i * L.Kp + fs[s].col + l] = sl.coeffs[(size_t)(2 * i + 1) * sl.n_basis + l];
+                        cre[(size_t)i * L.Kp + col[s] + l] = sl.coeffs[(size_t)(2 * i) * sl.n_basis + l];
+                        cim[(size_t)i * L.Kp + col[s] + l] = sl.coeffs[(size_t)(2 * i + 1) * sl.n_basis + l];
                     }
             }
             std::vector<uint16_t> hre, him, lre, lim;
@@ -1167,20 +1382,61 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
             std::vector<uint16_t>* srcv[4] = {&hre, &him, &lre, &lim};
             for (int q = 0; q < 4; ++q) {
                 if (srcv[q]->empty()) continue;
-                if ((st = dalloc(ctx, (uint16_t**)dst[q], srcv[q]->size() * 2, &b->allocs, &b->bytes))) return st;
+                lloid_status e;
+                if ((e = dalloc(ctx, (uint16_t**)dst[q], srcv[q]->size() * 2, &b->allocs, &b->bytes))) return e;
                 CK(cudaMemcpyAsync(*dst[q], srcv[q]->data(), srcv[q]->size() * 2, cudaMemcpyHostToDevice, ctx->stream));
             }
-            const size_t rb = (size_t)nd * 2 * L.R * L.Kp * 2;
-            if ((st = dalloc(ctx, &L.d_yhi, rb, &b->allocs, &b->bytes))) return st;
-            if ((st = dalloc(ctx, &L.d_ylo, rb, &b->allocs, &b->bytes))) return st;
-            CK(cudaStreamSynchronize(ctx->stream));
         }
-        if (L.acc_cols > 0) {   // zeroed: columns no tile has written read as 0
-            if ((st = dalloc(ctx, &L.d_accp, (size_t)nd * 4 * b->Mpad * L.acc_cols * 2, &b->allocs, &b->bytes)))
+        const size_t rb = (size_t)nd * 2 * L.R * L.Kp * 2;
+        lloid_status e;
+        if ((e = dalloc(ctx, &L.d_yhi, rb, &b->allocs, &b->bytes))) return e;
+        if ((e = dalloc(ctx, &L.d_ylo, rb, &b->allocs, &b->bytes))) return e;
+        CK(cudaStreamSynchronize(ctx->stream));
+        return LLOID_OK;
+    };
+    for (int j = 0; j < nl; ++j) {
+        std::vector<int> col(bd->n_slices, -1);
+        for (int s = 0; s < bd->n_slices; ++s)
+            if (fs[s].level == j) col[s] = fs[s].col;
+        if ((st = fill_level(lev[j], !f0form, col))) return st;
+        if (lev[j].acc_cols > 0) {   // zeroed: columns no tile has written read as 0
+            if ((st = dalloc(ctx, &lev[j].d_accp, (size_t)nd * 4 * b->Mpad * lev[j].acc_cols * 2, &b->allocs,
+                             &b->bytes)))
                 return st;
         }
     }
+    if (f0form) {
+        // coefficients of every slice in the packed columns, as time-blocked planes
+        // [re hi, im hi, (re lo, im lo)][K/8][Mpad][8] (the layout of a no-swizzle K-major operand)
+        std::vector<double> cre((size_t)b->Mpad * top.K, 0.0), cim((size_t)b->Mpad * top.K, 0.0);
+        for (int s = 0; s < bd->n_slices; ++s) {
+            const lloid_slice& sl = bd->slices[s];
+            for (int i = 0; i < M; ++i)
+                for (int l = 0; l < sl.n_basis; ++l) {
+                    cre[(size_t)i * top.K + b->sl[s].tcol + l] = sl.coeffs[(size_t)(2 * i) * sl.n_basis + l];
+                    cim[(size_t)i * top.K + b->sl[s].tcol + l] = sl.coeffs[(size_t)(2 * i + 1) * sl.n_basis + l];
+                }
+        }
+        std::vector<uint16_t> hre, him, lre, lim;
+        pack_coeffs_tc(bf, cre, cim, b->Mpad, top.K, &hre, &him, &lre, &lim);
+        std::vector<uint16_t>* pl[4] = {&hre, &him, &lre, &lim};
+        std::vector<uint16_t> blk((size_t)npl * top.K * b->Mpad);
+        for (int q = 0; q < npl; ++q)
+            for (int i = 0; i < b->Mpad; ++i)
+                for (int k = 0; k < top.K; ++k)
+                    blk[(((size_t)q * (top.K / 8) + k / 8) * b->Mpad + i) * 8 + k % 8] = (*pl[q])[(size_t)i * top.K + k];
+        if ((st = dalloc(ctx, &b->d_cblk, blk.size() * 2, &b->allocs, &b->bytes))) return st;
+        CK(cudaMemcpyAsync(b->d_cblk, blk.data(), blk.size() * 2, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (SliceRT& r : b->sl) {   // composed upsampler of every slice (Eq. 7-8 ladder from its rate; [1] at f0)
+            std::vector<float> Rf(r.R.begin(), r.R.end());
+            if ((st = dalloc(ctx, &r.d_R, Rf.size() * 4, &b->allocs, &b->bytes))) return st;
+            CK(cudaMemcpyAsync(r.d_R, Rf.data(), Rf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    }
     b->lev = lev;
+    b->top = top;
     b->fs = fs;
     return LLOID_OK;
 }
@@ -1289,6 +1545,40 @@ const char* lloid_strerror(lloid_status st) {
 const char* lloid_last_error(const lloid_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t lloid_launch_count(const lloid_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lloid_status lloid_inject_fault(lloid_ctx* ctx, int32_t kind, int64_t count) {
+    if (!ctx) return LLOID_EINVAL;
+    if (count < 0) return fail(ctx, LLOID_EINVAL, "negative fault count");
+    switch (kind) {
+        case LLOID_FAULT_ALLOC: ctx->fault_alloc = count; return LLOID_OK;
+        case LLOID_FAULT_DROP_BLOCK: ctx->fault_drop = count; return LLOID_OK;
+        case LLOID_FAULT_DELAY: ctx->fault_delay_us = std::min<int64_t>(count, 10000000); return LLOID_OK;
+        case LLOID_FAULT_WAIT_EXPIRY:
+            if (count == 0) return LLOID_OK;
+            CK(cudaSetDevice(ctx->cfg.device));
+            k_wait_expiry_check<<<1, 32, 0, ctx->stream>>>(ctx->d_err, 90,
+                                                          (unsigned long long)std::min<int64_t>(count, 1000000) * 1000ull);
+            CKL();
+            CK(cudaEventRecord(ctx->done_ev, ctx->stream));
+            return LLOID_OK;
+    }
+    return fail(ctx, LLOID_EINVAL, "unknown fault kind %d", kind);
+}
+
+lloid_status lloid_clear_error(lloid_ctx* ctx) {
+    if (!ctx) return LLOID_EINVAL;
+    CK(cudaSetDevice(ctx->cfg.device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LLOID_OK;
+}
+
+int32_t lloid_bank_form(const lloid_ctx* ctx, int32_t bank) {
+    if (!ctx) return -1;
+    auto it = ctx->banks.find(bank);
+    return it == ctx->banks.end() ? -1 : it->second->form;
+}
 
 lloid_status lloid_bytes_in_use(const lloid_ctx* ctx, size_t* state_bytes, size_t* bank_bytes) {
     if (!ctx) return LLOID_EINVAL;
@@ -1445,6 +1735,7 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaFree(ctx->d_events); cudaFreeHost(ctx->h_events);
     if (ctx->pull_ev) cudaEventDestroy(ctx->pull_ev);
     cudaFree(ctx->d_err);
+    cudaFree(ctx->d_zero);
     for (int r = 0; r <= kMaxRates; ++r) { cudaFree(ctx->s_hi[r]); cudaFree(ctx->s_lo[r]); }
     for (int f = 0; f < lloid_ctx::kFSlots; ++f) { cudaFree(ctx->d_u_hi[f]); cudaFree(ctx->d_u_lo[f]); }
 
@@ -1514,6 +1805,7 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
                         "slice %d (rate %d) starts %lld samples before merger; pre-synchronisation needs >= %lld",
                         s, r.rate, r.J, -(long long)r.e_min + (long long)r.D * c.n_down);
         b->sl.push_back(r);
+        b->sl.back().R = R;
         b->sl.back().y_len = (int)next_pow2(c.max_block / r.D + (r.e_max - r.e_min) / r.D + 4);
         if (!split_precision(ctx)) {   // the FP32 path upsamples each slice with the composed filter
             std::vector<float> Rf(R.size());
@@ -1528,6 +1820,7 @@ lloid_status lloid_load_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, int32_t*
     b->K = row;
     b->Kpad = (row + 63) / 64 * 64;
     b->Mpad = (M + 127) / 128 * 128;
+    if (split) b->form = choose_form(ctx, b.get(), ladder, bd->ac_half);
     const int nd = c.n_detectors;
     lloid_status st;
     auto cleanup = [&]() {
@@ -1905,13 +2198,28 @@ lloid_status lloid_snr_block(lloid_ctx* ctx, int32_t det, int32_t bank, float* o
     if (!split_precision(ctx)) {
         const int tiles = (b->Mpad / 64) * (int)(n / 128);
         st = launch_recon_f32(ctx, k_a, n, det, 1, true, ctx->d_rec + idx, db, 1, tiles, out);
+    } else if (b->form == 1) {   // the f0 kernel over this bank's window groups, storing z
+        const int cls = ctx->f0_class_of_bank[bank];
+        const int tpw = (int)(ctx->cfg.window_samples / 128);
+        std::vector<F0Unit> hu;
+        for (int g = 0; g * tpw < (int)(n / 128); ++g) hu.push_back(F0Unit{ctx->f0_job_of_bank[bank], g});
+        int grid = 0;
+        const std::vector<int> hs = build_sched(std::vector<double>(hu.size(), 1.0), 1, ctx->n_sm, &grid);
+        F0Unit* du = nullptr;
+        CK(cudaMalloc(&dsched, hs.size() * sizeof(int)));
+        CK(cudaMalloc(&du, hu.size() * sizeof(F0Unit)));
+        dti = reinterpret_cast<TileInfo*>(du);   // freed below with the others
+        CK(cudaMemcpyAsync(dsched, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(du, hu.data(), hu.size() * sizeof(F0Unit), cudaMemcpyHostToDevice, ctx->stream));
+        st = launch_f0(ctx, cls, ctx->d_f0job[cls], du, dsched, grid, k_a, n, det, 1, out);
     } else {
         const int tiles = (b->Mpad / kTcTileM) * (int)(n / kTcTileN);
         const int fs = ctx->top_slot_of_bank[bank];
         int grid = 0;
         const std::vector<int> hs = build_sched(std::vector<double>(tiles, 1.0), 1, ctx->n_sm, &grid);
         std::vector<TileInfo> hti(tiles);
-        for (int l = 0; l < tiles; ++l) hti[l] = TileInfo{0, l, b->lev.back().Kp, 0};
+        const LevelRT& T = b->form == 1 ? b->top : b->lev.back();
+        for (int l = 0; l < tiles; ++l) hti[l] = TileInfo{0, l, T.Kp, T.K / 16};
         CK(cudaMalloc(&dsched, hs.size() * sizeof(int)));
         CK(cudaMalloc(&dti, hti.size() * sizeof(TileInfo)));
         CK(cudaMemcpyAsync(dsched, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));

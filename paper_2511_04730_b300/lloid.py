@@ -46,7 +46,8 @@ class Context:
     def __init__(self, n_detectors: int = 1, precision: str = "fp32", max_block: int = 16384,
                  max_history: Optional[int] = None, window: int = 2048, threshold: float = 4.0,
                  device: int = 0, stream=None, hbm_budget: int = 0, f0: int = 2048, min_rate: int = 32,
-                 n_down: int = 32, n_up: int = 8, stage_timing: bool = False, coinc_window: Optional[int] = None):
+                 n_down: int = 32, n_up: int = 8, stage_timing: bool = False, coinc_window: Optional[int] = None,
+                 form: Optional[str] = None, fill_gaps: bool = False):
         self._lib = _lib.load()
         cfg = default_config()
         cfg.f0, cfg.n_detectors, cfg.n_down, cfg.n_up = f0, n_detectors, n_down, n_up
@@ -59,7 +60,10 @@ class Context:
         if coinc_window is not None:
             cfg.coinc_window = coinc_window
         cfg.cuda_stream = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
-        cfg.flags = _lib.FLAG_STAGE_TIMING if stage_timing else 0
+        if form not in _lib.FORM_FLAGS:
+            raise ValueError(f"form must be one of {sorted(k for k in _lib.FORM_FLAGS if k)} or None")
+        cfg.flags = ((_lib.FLAG_STAGE_TIMING if stage_timing else 0) | _lib.FORM_FLAGS[form] |
+                     (_lib.FLAG_FILL_GAPS if fill_gaps else 0))
         self.cfg = cfg
         self.precision = precision
         self.n_detectors = n_detectors
@@ -131,6 +135,22 @@ class Context:
         self._check(self._lib.lloid_load_bank(self._h, ctypes.byref(desc), ctypes.byref(bid)))
         self.banks[bid.value] = n_rows // 2
         return bid.value
+
+    def bank_form(self, bank_id: int) -> str:
+        """Form a bank runs in on the split path: "ladder" or "f0" (lloid_bank_form)."""
+        f = int(self._lib.lloid_bank_form(self._h, bank_id))
+        if f < 0:
+            self._check(-1)
+        return "f0" if f == 1 else "ladder"
+
+    def inject_fault(self, kind: str, count: int = 1):
+        """lloid_inject_fault: "alloc", "drop_block", "delay" (microseconds) or
+        "wait_expiry" (microseconds)."""
+        self._check(self._lib.lloid_inject_fault(self._h, _lib.FAULTS[kind], int(count)))
+
+    def clear_error(self):
+        """lloid_clear_error: forget an expired device wait."""
+        self._check(self._lib.lloid_clear_error(self._h))
 
     def unload_bank(self, bank_id: int):
         self._check(self._lib.lloid_unload_bank(self._h, bank_id))
@@ -293,7 +313,14 @@ def triggers_from_snr_noalloc(z, t0: int, window: int = 2048, threshold: float =
     the triggers as a numpy structured array (this read-back synchronises)."""
     import torch
     lib = _lib.load()
+    if not isinstance(z, torch.Tensor) or not z.is_cuda or z.dtype != torch.float32 or not z.is_contiguous() \
+            or z.dim() != 2 or z.shape[0] % 2:
+        raise ValueError("z must be a contiguous float32 CUDA tensor [2M, n]")
     n_rows, n = z.shape
+    for name, t, dt in (("out", out, torch.uint8), ("n_out", n_out, torch.int64)):
+        if t is not None and (not isinstance(t, torch.Tensor) or t.device != z.device or t.dtype != dt
+                              or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous {dt} tensor on {z.device}")
     if out is None:
         out = torch.empty((n_rows // 2) * (n // window) * TRIGGER_DTYPE.itemsize, dtype=torch.uint8, device=z.device)
     if n_out is None:

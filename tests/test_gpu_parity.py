@@ -42,15 +42,20 @@ def _ctx(P, precision, **kw):
                      max_block=kw.pop("max_block", 16384), max_history=kw.pop("max_history", 64 * F0), **kw)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16_split", "bf16_split"])
-def test_snr_parity_bank64(lloid, bank64_case, precision):
+# the split paths in both forms of a bank (per-rate ladder; basis outputs brought up to f0 first)
+FORMS = [("fp32", None)] + [(p, f) for p in ("fp16_split", "bf16_split") for f in ("ladder", "f0")]
+
+
+@pytest.mark.parametrize("precision,form", FORMS)
+def test_snr_parity_bank64(lloid, bank64_case, precision, form):
     w, bank, plan, d, z_or = bank64_case
     sb = lloid.build_svd_bank(bank, plan)
-    with _ctx(lloid, precision) as ctx:
+    with _ctx(lloid, precision, form=form) as ctx:
         bid = ctx.load_bank(sb)
+        form = f"{form}->{ctx.bank_form(bid)}"
         z = stream_snr(ctx, bid, d, 8192)
     err = max_abs_complex(z, z_or)
-    print(f"{precision}: max|dz| = {err:.3e}")
+    print(f"{precision} {form}: max|dz| = {err:.3e}")
     assert err <= TOL[precision]
     # the injection is recovered at its sample
     inj = w.injections[0][0]
@@ -58,7 +63,7 @@ def test_snr_parity_bank64(lloid, bank64_case, precision):
     assert abs(abs(complex(z[2 * i, k], z[2 * i + 1, k])) - abs(complex(z_or[2 * i, k], z_or[2 * i + 1, k]))) < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16_split"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16_split", "bf16_split"])
 def test_trigger_parity_bank64(lloid, bank64_case, precision):
     w, bank, plan, d, z_or = bank64_case
     sb = lloid.build_svd_bank(bank, plan)
@@ -99,9 +104,9 @@ def test_streaming_block_sizes_identical(lloid, bank64_case, precision):
         assert np.array_equal(z, outs[0])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16_split", "bf16_split"])
+@pytest.mark.parametrize("precision,form", FORMS)
 @pytest.mark.parametrize("which", [0, 1])
-def test_single_slice_banks(lloid, bank64_case, precision, which):
+def test_single_slice_banks(lloid, bank64_case, precision, form, which):
     """One slice at a time: slice 0 alone (f0, no ladder: FIR + top level) and
     slice 1 alone (256 Hz: the SNR comes only through the Eq. 7-8 ladder)."""
     w, bank, plan, d, _ = bank64_case
@@ -109,11 +114,11 @@ def test_single_slice_banks(lloid, bank64_case, precision, which):
     sl = O.svd_bank(bank, plan)
     d = d[: 16 * F0]
     z_or = O.lloid_snr(d.astype(np.float64), [sl[which]], F0)
-    with _ctx(lloid, precision) as ctx:
+    with _ctx(lloid, precision, form=form) as ctx:
         bid = ctx.load_bank([sb[which]])
         z = stream_snr(ctx, bid, d, 4096)
     err = max_abs_complex(z, z_or)
-    print(f"{precision} slice {which}: max|dz| = {err:.3e}")
+    print(f"{precision} {form} slice {which}: max|dz| = {err:.3e}")
     assert err <= TOL[precision]
 
 
@@ -164,23 +169,23 @@ def ladder_case():
     return bank, plan, d, segs, S
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16_split", "bf16_split"])
-def test_multirate_ladder_bank1000_segments(lloid, ladder_case, precision):
+@pytest.mark.parametrize("precision,form", FORMS)
+def test_multirate_ladder_bank1000_segments(lloid, ladder_case, precision, form):
     """Five-rate bank (2048/1024/512/256/128 Hz, 64 s templates): sampled
     segments of the stream against the oracle run on the segment's history."""
     bank, plan, d, segs, S = ladder_case
     assert sorted(set(plan.rate)) == [128, 256, 512, 1024, 2048]
     sb = lloid.build_svd_bank(bank, plan)
-    with _ctx(lloid, precision, max_history=64 * F0) as ctx:
+    with _ctx(lloid, precision, max_history=64 * F0, form=form) as ctx:
         bid = ctx.load_bank(sb)
         z = stream_snr(ctx, bid, d, 16384)
     for a, zo in segs.items():
         err = max_abs_complex(z[:, a:a + S], zo)
-        print(f"{precision} segment {a}: max|dz| = {err:.3e}")
+        print(f"{precision} {form} segment {a}: max|dz| = {err:.3e}")
         assert err <= TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16_split"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16_split", "bf16_split"])
 def test_triggers_across_finalize_chunks(lloid, ladder_case, precision):
     """96 templates: window maxima are finalised in chunks of 64 templates and
     the bank maximum is found across the chunks.  Triggers of the windows of

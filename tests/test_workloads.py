@@ -29,3 +29,13 @@ def test_rows_unit_norm_and_strain_reproducible():
     rows = w.banks[0].full()
     assert np.allclose(np.linalg.norm(rows, axis=1), 1.0, atol=1e-12)
     assert np.array_equal(w.strain(0), W.make_workload("tiny", n_seconds=8).strain(0))
+
+
+def test_bank_indices_pick_the_same_banks():
+    """A few banks of a multi-bank workload, built alone, are the banks of the full set."""
+    full = W.make_workload("banks20", n_templates=400, n_banks=8, n_seconds=8, n_det=1, n_inj=0)
+    part = W.make_workload("banks20", n_templates=400, n_banks=8, n_seconds=8, n_det=1, n_inj=0, bank_indices=(5, 2))
+    for b, k in zip(part.banks, (5, 2)):
+        assert np.array_equal(b.mchirp, full.banks[k].mchirp)
+        assert b.n_samples == full.banks[k].n_samples
+    assert part.plans == [full.plans[5], full.plans[2]]

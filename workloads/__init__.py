@@ -367,7 +367,8 @@ def _contiguous_banks(mchirp_sorted, sizes, n_seconds_fn, f0, workers: int = 1):
 
 def make_workload(name: str, n_det: Optional[int] = None, n_seconds: Optional[int] = None,
                   n_templates: Optional[int] = None, n_banks: Optional[int] = None,
-                  n_inj: Optional[int] = None, workers: int = 1) -> Workload:
+                  n_inj: Optional[int] = None, workers: int = 1,
+                  bank_indices: Optional[Sequence[int]] = None) -> Workload:
     """Build one of the paper-shaped synthetic workloads by name.
 
     * ``tiny``   : 8 templates, Mc in [5, 15], 4 s, two slices; 16 s, 1 detector.
@@ -383,6 +384,9 @@ def make_workload(name: str, n_det: Optional[int] = None, n_seconds: Optional[in
       durations clip(tau(30 Hz), 2, 128) s); 1024 s, 3 detectors.
     Any size argument overrides the default (used for bounded samples);
     ``workers`` > 1 builds multi-bank workloads in a process pool.
+    ``bank_indices`` keeps only those banks of a multi-bank workload (the same
+    banks, with the same templates, as in the full set), so that a few real
+    banks of the 500-bank set can be used without building the other ones.
     """
     f0 = F0
     if name == "tiny":
@@ -446,6 +450,11 @@ def make_workload(name: str, n_det: Optional[int] = None, n_seconds: Optional[in
             d = int(np.clip(math.ceil(float(tau_of_f(F_LOW, m.min()))), dmin, dmax))
             return 1 << int(math.ceil(math.log2(d)))
 
+        if bank_indices is not None:
+            starts = np.concatenate([[0], np.cumsum(sizes)])
+            keep = [int(i) for i in bank_indices]
+            mc = np.concatenate([mc[starts[i]:starts[i + 1]] for i in keep])
+            sizes = sizes[keep]
         banks = _contiguous_banks(mc, sizes, dur_fn, f0, workers)
         plans = [plan_slices(b, DEFAULT_BOUNDARIES_S, r_min=rmin) for b in banks]
         nd, ns = n_det or nd_def, n_seconds or ns_def
