@@ -74,6 +74,9 @@ def parse():
     p.add_argument("--serve-seconds", type=int, default=60)
     p.add_argument("--form", default=None, choices=["ladder", "f0"],
                    help="force every bank into one form of the split path (default: per-bank choice)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="skip the autotuner (default: tune the form ratio and FIR occupancy on a bank sample)")
+    p.add_argument("--autotune-banks", type=int, default=100, help="banks of the sample the autotuner times")
     return p.parse_args()
 
 
@@ -469,9 +472,23 @@ def run_lloid(args, rank, world, dist):
     d_blocks = torch.from_numpy(blocks).to(f"cuda:{dev}")
     h_blocks = torch.from_numpy(blocks).pin_memory()
 
+    # the autotuner: candidate forms and FIR occupancies timed on a sample of the banks
+    tuning, tune_info = None, None
+    if args.precision != "fp32" and not args.no_autotune and args.form is None:
+        stride = max(1, len(banks_sb) // max(1, args.autotune_banks))
+        sample = banks_sb[::stride]
+        t_tune = time.perf_counter()
+        tuning = P.autotune(sample, B, reps=3, n_detectors=n_det, precision=args.precision,
+                            max_history=max_hist, device=dev)
+        c_def = next(c for c in tuning["candidates"] if c["form"] == "by ratio" and c["form_ratio"] == 1.0)
+        tune_info = {"sample_banks": len(sample), "seconds": round(time.perf_counter() - t_tune, 1),
+                     "chosen": tuning["candidates"][tuning["best"]], "candidates": tuning["candidates"],
+                     "gain_over_default": c_def["ms_per_push"] / tuning["candidates"][tuning["best"]]["ms_per_push"]}
+
     def make_ctx(precision, timing, form=args.form, max_block=B):
         return P.Context(n_detectors=n_det, precision=precision, max_block=max_block, max_history=max_hist,
-                         device=dev, stage_timing=timing, form=form)
+                         device=dev, stage_timing=timing, form=form,
+                         tuning=tuning if precision == args.precision else None)
 
     def load_all(ctx, which=None):
         return [ctx.load_bank(banks_sb[i]) for i in (range(len(banks_sb)) if which is None else which)]
@@ -800,6 +817,7 @@ def run_lloid(args, rank, world, dist):
             "stage_ms_per_step": stage_ms,
             "ms_per_step_with_stage_events": statistics.mean(ms_t),
             "kernels": per_stage,
+            "autotune": tune_info,
             "xi2": xi2,
             "whiten": whiten,
             "paths": paths,

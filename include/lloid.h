@@ -85,8 +85,12 @@ typedef struct {
     int32_t n_down;            /* downsampling half length at the target rate */
     int32_t n_up;              /* upsampling half length at the lower rate */
     int64_t window_samples;    /* trigger window W (multiple of 128) */
-    int64_t window_overlap;    /* window w covers [max(0, wW - overlap), (w+1)W);
-                                  only 0 is implemented (EINVAL otherwise) */
+    int64_t window_overlap;    /* window w covers [max(0, wW - overlap), (w+1)W), so that
+                                  a signal near a window's start is seen in both windows
+                                  (Section II.D.1: light travel time plus a buffer, about
+                                  66 samples at 2048 Hz); 0 <= overlap < 128 (EINVAL
+                                  otherwise).  A window's trigger can then lie before its
+                                  start (sample < wW). */
     float snr_threshold;       /* a trigger needs |z| > snr_threshold */
     int32_t precision;         /* lloid_precision */
     int64_t max_block;         /* largest push, full-rate samples (multiple of 128) */
@@ -98,6 +102,11 @@ typedef struct {
     uint32_t flags;            /* LLOID_FLAG_* bits */
     int32_t coinc_window;      /* coincidence window in samples (Section II.D.3): maximum light
                                   travel time plus buffer, default 66 = (0.0273 + 0.005) s x 2048 */
+    float form_ratio;          /* split path: a bank runs in the f0 form when its estimated time
+                                  in that form is below form_ratio x its estimate in the ladder
+                                  form (<= 0: 1); see LLOID_FLAG_FORM_* and lloid_autotune */
+    int32_t fir_ctas;          /* basis-filter CTAs per SM: 1, 2, or 0 = two when each still gets
+                                  two operand stages, else one */
 } lloid_config;
 
 /* One time slice of a bank (Eq. 3): the leading L bases and their
@@ -373,6 +382,31 @@ LLOID_API void* lloid_stream(const lloid_ctx* ctx);
 /* The form bank `bank` runs in: 0 ladder, 1 f0 (always 0 on the FP32 path);
  * -1 if there is no such bank. */
 LLOID_API int32_t lloid_bank_form(const lloid_ctx* ctx, int32_t bank);
+
+/* The autotuner of the batched path: for pushes of n samples of every
+ * detector with the banks banks[0 .. n_banks - 1] loaded, times candidate
+ * settings on scratch contexts made from *cfg (its stream and stage timing
+ * are not used): every bank in the ladder form, form_ratio 0.5, 1 and 2, every
+ * bank that can in the f0 form, then 1 and 2 basis-filter CTAs per SM with the
+ * fastest of those.  Each candidate gets two warm-up pushes of zeros and then
+ * `reps` timed pushes (CUDA events).  out->form_ratio, out->flags_form (0,
+ * LLOID_FLAG_FORM_LADDER or LLOID_FLAG_FORM_F0) and out->fir_ctas are the
+ * fastest setting, to copy into the lloid_config of the context that
+ * streams; ms[i] is candidate i's device time per push.  EINVAL for bad
+ * arguments; any error of a candidate context is returned. */
+typedef struct {
+    float form_ratio;
+    uint32_t flags_form;
+    int32_t fir_ctas;
+    int32_t n_tried;
+    int32_t best;              /* index of the chosen candidate */
+    float ms[16];
+    float cand_ratio[16];
+    uint32_t cand_flags[16];
+    int32_t cand_ctas[16];
+} lloid_tuning;
+LLOID_API lloid_status lloid_autotune(const lloid_config* cfg, const lloid_bank_desc* banks, int32_t n_banks,
+                                      int64_t n, int32_t reps, lloid_tuning* out);
 
 /* Gaps in the strain (the pipeline's source turns missing data into gap
  * buffers, Section II.B): with this flag a push whose t0 lies past the end of

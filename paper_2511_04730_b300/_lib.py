@@ -26,7 +26,15 @@ class LloidConfig(ctypes.Structure):
         ("snr_threshold", ctypes.c_float), ("precision", ctypes.c_int32), ("max_block", ctypes.c_int64),
         ("max_history", ctypes.c_int64), ("min_rate", ctypes.c_int32), ("device", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_uint32),
-        ("coinc_window", ctypes.c_int32),
+        ("coinc_window", ctypes.c_int32), ("form_ratio", ctypes.c_float), ("fir_ctas", ctypes.c_int32),
+    ]
+
+
+class LloidTuning(ctypes.Structure):
+    _fields_ = [
+        ("form_ratio", ctypes.c_float), ("flags_form", ctypes.c_uint32), ("fir_ctas", ctypes.c_int32),
+        ("n_tried", ctypes.c_int32), ("best", ctypes.c_int32), ("ms", ctypes.c_float * 16),
+        ("cand_ratio", ctypes.c_float * 16), ("cand_flags", ctypes.c_uint32 * 16), ("cand_ctas", ctypes.c_int32 * 16),
     ]
 
 
@@ -117,6 +125,8 @@ SIGNATURES = [
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     ("lloid_bank_form", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     ("lloid_inject_fault", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    ("lloid_autotune", ctypes.c_int, [ctypes.POINTER(LloidConfig), ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                      ctypes.c_int32, ctypes.POINTER(LloidTuning)]),
     ("lloid_clear_error", ctypes.c_int, [ctypes.c_void_p]),
 ]
 

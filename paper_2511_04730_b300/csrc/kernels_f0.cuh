@@ -12,16 +12,18 @@
 // A work unit is (bank, detector, a group of tpw consecutive 128-sample tiles
 // of the push, tpw = window / 128).  Per tile of the group:
 //   builder warps (4): Yhat rows of the tile, computed in FP32 from the FIR's
-//     hi/lo output at each slice's rate, split into hi/lo halves and stored in
-//     shared memory in the no-swizzle K-major layout ([K/8][128 rows][8]);
+//     hi/lo output at each slice's rate (staged in shared memory with the
+//     slice's composed taps), split into hi/lo halves and stored in shared
+//     memory in the no-swizzle K-major layout ([K/8][128 rows][8]);
 //   producer (1 thread): the coefficient tiles of the bank's 128-template
 //     groups, 32 bases per TMA stage, from time-blocked planes
 //     [re hi, im hi, (re lo, im lo)][K/8][Mpad][8];
 //   MMA issuer (1 thread): for every template group, C Yhat into a TMEM
 //     accumulator (re and im, 128 columns each, two buffers), hi/lo products
 //     (FP16: C_hi Y_hi + C_hi Y_lo; BF16: + C_lo Y_hi);
-//   epilogue warps (8): |z|^2 and its argmax over the tile (earliest sample on
-//     ties), kept per template across the group.
+//   epilogue warps (2 x 4): |z|^2 and its argmax over the tile (earliest sample
+//     on ties), kept per template across the group of tiles; one group of four
+//     warps per TMEM buffer, the buffer being the template group's parity.
 // When the push starts on a window boundary every group is one whole trigger
 // window: its end writes each template's window maximum to the trigger slab
 // (threshold, phase) and flags the bank's loudest template, as the window
@@ -45,18 +47,36 @@ constexpr int kF0MaxTm = 8;        // template groups per bank (M <= 1024)
 constexpr int kF0Builders = 4;     // builder warps 2..5
 constexpr int kF0EpiWarps = 8;     // epilogue warps 6..13
 constexpr int kF0Threads = 32 * (2 + kF0Builders + kF0EpiWarps);
-constexpr int kF0CStages = 4;
+constexpr int kF0MaxCStages = 3;
+constexpr int kF0Kc = 96;          // largest K of a bank in the f0 form (two Yhat buffers of this width)
+constexpr int kF0StageRows = 132;  // rows of Y one slice reaches per tile: (127 + rlen - 1) / D + 2 at most
+constexpr int kF0StageFloats = 4096;   // builders' staging of Y rows for one batch of slice pieces (16 KB)
+constexpr int kF0RAll = 4096;      // every slice's composed upsampler, staged once per work unit (16 KB)
+constexpr int kF0MaxSlices = 16;
+constexpr int kF0MaxPieces = 64;   // (slice, column chunk) pieces of a bank: at most 16 + 128 / 8
+
+// Builders' tables in shared memory: the unit's slices, and per tile the pieces of
+// slices (up to 32 columns each) in column order, grouped in batches that fit the staging.
+struct F0SliceS {
+    const uint16_t* y_hi;          // the slice's FIR output ring, detector applied
+    const uint16_t* y_lo;
+    long long q_lo;                // first staged row for the current tile
+    int y_rows, y_ld, D, e_min, rlen, L, roff, nq;
+};
+struct F0Piece { int s, c0, nc, nv, off, pitch, items, item0; };
 
 template <bool BF16>
 struct F0Cfg {
     static constexpr int NPL = BF16 ? 4 : 2;               // coefficient planes
     static constexpr int CPLANE = 128 * 32 * 2;            // one plane of a 32-basis stage (8 KB)
     static constexpr int CSTAGE = NPL * CPLANE;
+    static constexpr int CSTAGES = BF16 ? 2 : 3;           // coefficient stages (what shared memory allows)
 };
-// Shared memory of one launch class: K <= kc (64 or 128) with ybufs Yhat buffers.
+// Shared memory of the kernel: K <= kc with ybufs Yhat buffers.
 __host__ __device__ constexpr int f0_smem_bytes(bool bf16, int kc, int ybufs) {
-    return kF0CStages * (bf16 ? 4 : 2) * 8192 + ybufs * 2 * 128 * kc * 2 + kF0MaxTm * 128 * 16 + 2 * 128 * 16 +
-           4 * 16 + 1024 + 512;
+    return (bf16 ? 2 : 3) * (bf16 ? 4 : 2) * 8192 + ybufs * 2 * 128 * kc * 2 + kF0MaxTm * 128 * 16 +
+           kF0EpiWarps * 16 + (kF0StageFloats + kF0RAll) * 4 + kF0MaxSlices * (int)sizeof(F0SliceS) +
+           kF0MaxPieces * (int)sizeof(F0Piece) + (kF0MaxPieces + 4) * 4 + 1024 + 512;
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -66,25 +86,32 @@ __global__ void __launch_bounds__(kF0Threads, 1)
     k_f0_top(const F0Job* __restrict__ jobs, const F0Maps* __restrict__ maps, const YupSlice* __restrict__ slices,
              const F0Unit* __restrict__ units, const int* __restrict__ sched, int n_units, int kc, int ybufs,
              long long k_a, int n, int det0, int n_det_push, long long window, float threshold,
-             Partial* __restrict__ part, long long part_tmpl_stride, int n_slots, SlabEntry* __restrict__ slab_base,
-             int ring, int n_det_total, long long slab_det_stride, float* __restrict__ zout, int* __restrict__ err) {
+             Partial* __restrict__ part, long long part_tmpl_stride, int n_slots, TailRing tail,
+             SlabEntry* __restrict__ slab_base, int ring, int n_det_total, long long slab_det_stride,
+             float* __restrict__ zout, int* __restrict__ err) {
     using C = F0Cfg<BF16>;
     pdl_launch_dependents();
     const int tpw = (int)(window / 128);
     const int n_tiles = n / 128;
-    const bool aligned = (k_a % window) == 0;              // every group is one whole window
+    // every group is one whole window, which the kernel finalises itself (with a window
+    // overlap the window also needs the tail of the tile before it: the partial ring then)
+    const bool aligned = (k_a % window) == 0 && tail.ov == 0;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* cst = smem;                                   // kF0CStages x CSTAGE
-    uint8_t* ybuf = cst + kF0CStages * C::CSTAGE;          // ybufs x [hi, lo][kc / 8][128][8]
+    uint8_t* cst = smem;                                   // CSTAGES x CSTAGE
+    uint8_t* ybuf = cst + C::CSTAGES * C::CSTAGE;          // ybufs x [hi, lo][kc / 8][128][8]
     const int yplane = 128 * kc * 2;
     float4* rs = reinterpret_cast<float4*>(ybuf + ybufs * 2 * yplane);   // [kF0MaxTm][128] running window maxima
-    float4* xchg = rs + kF0MaxTm * 128;                    // [2][128]
-    float4* red = xchg + 2 * 128;                          // [4] bank-max partials of the half-0 warps
-    uint64_t* bars = reinterpret_cast<uint64_t*>(red + 4);
+    float4* red = rs + kF0MaxTm * 128;                     // [8] bank-max partials of the epilogue warps
+    float* ys = reinterpret_cast<float*>(red + kF0EpiWarps);   // builders: staged Y rows of a batch
+    float* rsm = ys + kF0StageFloats;                       // builders: the unit's composed upsamplers
+    F0SliceS* stab = reinterpret_cast<F0SliceS*>(rsm + kF0RAll);
+    F0Piece* ptab = reinterpret_cast<F0Piece*>(stab + kF0MaxSlices);
+    int* bends = reinterpret_cast<int*>(ptab + kF0MaxPieces);   // [0] batches, [1..] end piece of each
+    uint64_t* bars = reinterpret_cast<uint64_t*>(bends + kF0MaxPieces + 4);   // 2 x 3 + 2 x 2 + 2 x 2 + 1
     uint64_t* cfull = bars;
-    uint64_t* cempty = cfull + kF0CStages;
-    uint64_t* yfull = cempty + kF0CStages;
+    uint64_t* cempty = cfull + kF0MaxCStages;
+    uint64_t* yfull = cempty + kF0MaxCStages;
     uint64_t* yempty = yfull + 2;
     uint64_t* tfull = yempty + 2;
     uint64_t* tempty = tfull + 2;
@@ -93,10 +120,10 @@ __global__ void __launch_bounds__(kF0Threads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kF0CStages; ++s) { mbar_init(cfull + s, 1); mbar_init(cempty + s, 1); }
+        for (int s = 0; s < C::CSTAGES; ++s) { mbar_init(cfull + s, 1); mbar_init(cempty + s, 1); }
         for (int b = 0; b < 2; ++b) {
             mbar_init(yfull + b, 32 * kF0Builders); mbar_init(yempty + b, 1);
-            mbar_init(tfull + b, 1); mbar_init(tempty + b, 32 * kF0EpiWarps);
+            mbar_init(tfull + b, 1); mbar_init(tempty + b, 32 * kF0EpiWarps / 2);
         }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -133,19 +160,19 @@ __global__ void __launch_bounds__(kF0Threads, 1)
 #pragma unroll
                             for (int pl = 0; pl < C::NPL; ++pl)
                                 tma_load_4d(sb + pl * C::CPLANE, &mp->c, cfull + stage, 0, tm * 4, kc0 >> 3, pl);
-                            if (++stage == kF0CStages) { stage = 0; phase ^= 1; }
+                            if (++stage == C::CSTAGES) { stage = 0; phase ^= 1; }
                         }
             }
-            for (int s = 0; s < kF0CStages; ++s) {
+            for (int s = 0; s < C::CSTAGES; ++s) {
                 if (!mbar_wait(cempty + stage, phase ^ 1, err, 62)) break;
-                if (++stage == kF0CStages) { stage = 0; phase ^= 1; }
+                if (++stage == C::CSTAGES) { stage = 0; phase ^= 1; }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {   // ------------------------------------------------ MMA issuer
             constexpr uint32_t idesc = idesc_f16(BF16, 128, 128);
             int stage = 0, i = 0, yi = 0;
-            uint32_t phase = 0;
+            uint32_t phase = 0, nb[2] = {0u, 0u};         // uses of each TMEM buffer (buffer = tm & 1)
             bool ok = true;
             for (int u = ub; u < ue && ok; ++u) {
                 const int it = sched[gridDim.x + 1 + u];
@@ -160,8 +187,9 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                     tc_fence_after();
                     const uint32_t y_hi = smem_u32(ybuf + yb * 2 * yplane), y_lo = y_hi + yplane;
                     for (int tm = 0; tm < jb.tiles_m && ok; ++tm, ++i) {
-                        const int buf = i & 1;
-                        if (!mbar_wait(tempty + buf, ((i >> 1) & 1) ^ 1, err, 64)) { ok = false; break; }
+                        const int buf = tm & 1;
+                        const uint32_t use = nb[buf]++;
+                        if (!mbar_wait(tempty + buf, (use & 1) ^ 1, err, 64)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t d_re = tmem + buf * 256, d_im = d_re + 128;
                         for (int kc0 = 0; kc0 < jb.K; kc0 += 32) {
@@ -184,7 +212,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                                 }
                             }
                             umma_commit(cempty + stage);
-                            if (++stage == kF0CStages) { stage = 0; phase ^= 1; }
+                            if (++stage == C::CSTAGES) { stage = 0; phase ^= 1; }
                         }
                         if (!ok) break;
                         umma_commit(tfull + buf);
@@ -198,23 +226,82 @@ __global__ void __launch_bounds__(kF0Threads, 1)
         }
     } else if (warp < 2 + kF0Builders) {
         // ---------------------------------------------------------------- Yhat builders
+        // Per unit: the slices' composed upsamplers are staged once.  Per tile: the rows of Y
+        // each slice reaches are staged in FP32 for a batch of (slice, 32-column) pieces at a
+        // time (all loads of a batch in flight together), then each thread forms its time
+        // row's outputs from shared memory and emits them in column order.
         const int row = threadIdx.x - 64;                  // 0..127: time row of the tile
+        constexpr int NB = 32 * kF0Builders;
         int yi = 0;
         bool ok = true;
+        auto bsync = [] { asm volatile("bar.sync 3, %0;" ::"n"(32 * kF0Builders) : "memory"); };
         for (int u = ub; u < ue && ok; ++u) {
             const int it = sched[gridDim.x + 1 + u];
             const int det = det0 + it % n_det_push;
             const F0Unit un = units[it / n_det_push];
             const F0Job jb = jobs[un.job];
             const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
+            bsync();                                        // the previous unit's tables are free
+            if (row == 0) {
+                int roff = 0;
+                for (int q = 0; q < jb.ns; ++q) {
+                    const YupSlice sl = slices[jb.s0 + q];
+                    F0SliceS& t = stab[q];
+                    t.y_hi = sl.y_hi + det * sl.y_det_stride;
+                    t.y_lo = sl.y_lo + det * sl.y_det_stride;
+                    t.y_rows = sl.y_rows; t.y_ld = sl.y_ld; t.D = sl.D; t.e_min = sl.e_min; t.rlen = sl.rlen;
+                    t.L = sl.L; t.roff = roff;
+                    roff += sl.rlen;
+                }
+            }
+            bsync();
+            for (int q = 0; q < jb.ns; ++q) {
+                const YupSlice& sl = slices[jb.s0 + q];
+                for (int e = row; e < sl.rlen; e += NB) rsm[stab[q].roff + e] = __ldg(sl.R + e);
+            }
             for (int tt = t0; tt < t1; ++tt, ++yi) {
                 const int yb = ybufs == 2 ? (yi & 1) : 0;
                 const uint32_t ypar = ybufs == 2 ? ((yi >> 1) & 1) : (yi & 1);
                 const bool got = mbar_wait(yempty + yb, ypar ^ 1, err, 67);
-                if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+                uint32_t all_got;                           // go on together, or stop together
+                asm volatile(
+                    "{\n\t.reg .pred p, q;\n\t setp.ne.u32 p, %1, 0;\n\t"
+                    "bar.red.and.pred q, 3, %2, p;\n\t selp.u32 %0, 1, 0, q;\n\t}\n"
+                    : "=r"(all_got)
+                    : "r"((uint32_t)got), "n"(32 * kF0Builders)
+                    : "memory");
+                if (!all_got) { ok = false; break; }
                 uint8_t* yh = ybuf + yb * 2 * yplane;
                 uint8_t* yl = yh + yplane;
-                const long long k = k_a + 128LL * tt + row;
+                const long long k0 = k_a + 128LL * tt;
+                if (row < jb.ns) {                          // each slice's first row and row count
+                    F0SliceS& t = stab[row];
+                    const long long e_max = (long long)t.e_min + t.rlen - 1;
+                    t.q_lo = fdiv(k0 - e_max + t.D - 1, t.D);
+                    t.nq = (int)(fdiv(k0 + 127 - t.e_min, t.D) - t.q_lo + 1);
+                }
+                bsync();
+                if (row == 0) {                             // this tile's pieces, in batches
+                    int np = 0, nbat = 0, off = 0, items = 0;
+                    for (int q = 0; q < jb.ns; ++q) {
+                        F0SliceS& t = stab[q];
+                        // pieces of up to 32 columns, narrower when many rows must fit the staging
+                        const int cw = 8 * min(4, (kF0StageFloats / t.nq - 4) / 8);
+                        for (int c0 = 0; c0 < t.L; c0 += cw) {
+                            F0Piece pc;
+                            pc.s = q; pc.c0 = c0; pc.nc = min(cw, t.L - c0); pc.nv = (pc.nc + 7) >> 3;
+                            pc.pitch = 8 * pc.nv + 4;
+                            if (off + t.nq * pc.pitch > kF0StageFloats) { bends[1 + nbat++] = np; off = 0; items = 0; }
+                            pc.off = off; pc.items = t.nq * pc.nv; pc.item0 = items;
+                            off += t.nq * pc.pitch;
+                            items += pc.items;
+                            ptab[np++] = pc;
+                        }
+                    }
+                    bends[1 + nbat++] = np;
+                    bends[0] = nbat;
+                }
+                bsync();
                 float v[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) v[j] = 0.f;
@@ -233,29 +320,76 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                     }
                     ++col;
                 };
-                for (int s = jb.s0; s < jb.s0 + jb.ns; ++s) {
-                    const YupSlice sl = slices[s];
-                    const long long e_max = (long long)sl.e_min + sl.rlen - 1;
-                    const long long qa = fdiv(k - e_max + sl.D - 1, sl.D), qb = fdiv(k - sl.e_min, sl.D);
-                    const int r_a = (int)(k - sl.D * qa - sl.e_min);          // R index of qa
-                    const uint16_t* yhs = sl.y_hi + det * sl.y_det_stride;
-                    const uint16_t* yls = sl.y_lo + det * sl.y_det_stride;
-                    for (int l0 = 0; l0 < sl.L; l0 += 8) {
-                        float acc[8];
+                const int nbat = bends[0];
+                for (int bt = 0, p0 = 0; bt < nbat; ++bt) {
+                    const int p1 = bends[1 + bt];
+                    const int n_items = ptab[p1 - 1].item0 + ptab[p1 - 1].items;
+                    // stage: four items per thread in flight at a time
+                    for (int e0 = row; e0 < n_items; e0 += 4 * NB) {
+                        uint4 hv[4], lv[4];
+                        int dst[4];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[j] = 0.f;
-                        int r = r_a;
-                        for (long long q = qa; q <= qb; ++q, r -= sl.D) {
-                            const float wq = __ldg(sl.R + r);
-                            const long long ro = (q & (sl.y_rows - 1)) * sl.y_ld + l0;
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                if (l0 + j < sl.L) acc[j] = fmaf(hilo_value<BF16>(yhs[ro + j], yls[ro + j]), wq, acc[j]);
+                        for (int uu = 0; uu < 4; ++uu) {
+                            const int e = e0 + uu * NB;
+                            dst[uu] = -1;
+                            if (e < n_items) {
+                                int pi = p0;
+                                while (pi + 1 < p1 && ptab[pi + 1].item0 <= e) ++pi;
+                                const F0Piece pc = ptab[pi];
+                                const F0SliceS& t = stab[pc.s];
+                                const int ie = e - pc.item0, qi = ie / pc.nv, c8 = ie - qi * pc.nv;
+                                const long long o = ((t.q_lo + qi) & (t.y_rows - 1)) * t.y_ld + pc.c0 + 8 * c8;
+                                hv[uu] = *reinterpret_cast<const uint4*>(t.y_hi + o);
+                                lv[uu] = *reinterpret_cast<const uint4*>(t.y_lo + o);
+                                dst[uu] = pc.off + qi * pc.pitch + 8 * c8;
+                            }
                         }
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if (l0 + j < sl.L) emit(acc[j]);
+                        for (int uu = 0; uu < 4; ++uu) {
+                            if (dst[uu] < 0) continue;
+                            const uint16_t* hp = reinterpret_cast<const uint16_t*>(&hv[uu]);
+                            const uint16_t* lp = reinterpret_cast<const uint16_t*>(&lv[uu]);
+                            float x[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) x[j] = hilo_value<BF16>(hp[j], lp[j]);
+                            float4* d4 = reinterpret_cast<float4*>(ys + dst[uu]);
+                            d4[0] = make_float4(x[0], x[1], x[2], x[3]);
+                            d4[1] = make_float4(x[4], x[5], x[6], x[7]);
+                        }
                     }
+                    bsync();
+                    for (int pi = p0; pi < p1; ++pi) {
+                        const F0Piece pc = ptab[pi];
+                        // the slice's fields in registers (the stores below must not make them reload)
+                        const int D = stab[pc.s].D, rlen = stab[pc.s].rlen, nq = stab[pc.s].nq;
+                        const int e_min = stab[pc.s].e_min, roff = stab[pc.s].roff;
+                        const long long q_lo = stab[pc.s].q_lo;
+                        const int r0 = (int)(k0 + row - D * q_lo - e_min);   // R index of (row, q_lo)
+                        const int qa = max(0, (r0 - rlen + D) / D), qb = min(nq - 1, r0 / D);
+                        const float* rr = rsm + roff + r0;
+                        const float* yp = ys + pc.off;
+                        const int pitch = pc.pitch, nv = pc.nv, nc = pc.nc;
+                        for (int c8 = 0; c8 < nv; ++c8) {
+                            float acc[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+#pragma unroll 4
+                            for (int qi = qa; qi <= qb; ++qi) {
+                                const float wq = rr[-D * qi];
+                                const float4 a = *reinterpret_cast<const float4*>(yp + qi * pitch + 8 * c8);
+                                const float4 b4 = *reinterpret_cast<const float4*>(yp + qi * pitch + 8 * c8 + 4);
+                                acc[0] = fmaf(a.x, wq, acc[0]); acc[1] = fmaf(a.y, wq, acc[1]);
+                                acc[2] = fmaf(a.z, wq, acc[2]); acc[3] = fmaf(a.w, wq, acc[3]);
+                                acc[4] = fmaf(b4.x, wq, acc[4]); acc[5] = fmaf(b4.y, wq, acc[5]);
+                                acc[6] = fmaf(b4.z, wq, acc[6]); acc[7] = fmaf(b4.w, wq, acc[7]);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                if (8 * c8 + j < nc) emit(acc[j]);
+                        }
+                    }
+                    bsync();                                // the staging is free for the next batch
+                    p0 = p1;
                 }
                 while (col < jb.K) emit(0.f);
                 fence_proxy_async_smem();                   // generic-proxy stores -> tensor-core reads
@@ -264,64 +398,89 @@ __global__ void __launch_bounds__(kF0Threads, 1)
         }
     } else {
         // ---------------------------------------------------------------- epilogue
-        // warp & 3: the TMEM lane quarter (rows); half: which 64 columns of the tile
+        // Two groups of four warps, one per TMEM buffer: group g takes the template groups
+        // tm with tm & 1 == g, all 128 samples of each tile; warp & 3 is the TMEM lane quarter.
+        // No barrier inside a unit: each group runs at its own pace.
         const int qd = warp & 3;
-        const int half = (warp - 2 - kF0Builders) >> 2;
+        const int grp = (warp - 2 - kF0Builders) >> 2;
         const int rowm = qd * 32 + lane;
-        int i = 0;
+        uint32_t nuse = 0;                                  // uses of this group's buffer
         for (int u = ub; u < ue; ++u) {
             const int it = sched[gridDim.x + 1 + u];
             const int det = det0 + it % n_det_push;
             const F0Unit un = units[it / n_det_push];
             const F0Job& jb = jobs[un.job];
             const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
-            float gbest = -1.f;                             // bank maximum of this thread's rows (half 0)
+            float gbest = -1.f;                             // bank maximum of this thread's rows
             int gm = 0x7fffffff;
             bool fail = false;
             for (int tt = t0; tt < t1 && !fail; ++tt) {
-                for (int tm = 0; tm < jb.tiles_m; ++tm, ++i) {
-                    const int buf = i & 1;
-                    const bool got = __all_sync(0xffffffffu, mbar_wait(tfull + buf, (i >> 1) & 1, err, 68));
+                for (int tm = grp; tm < jb.tiles_m; tm += 2) {
+                    const bool got = __all_sync(0xffffffffu, mbar_wait(tfull + grp, nuse & 1, err, 68));
+                    ++nuse;
+                    if (!got) { fail = true; break; }
                     tc_fence_after();
-                    const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + buf * 256;
+                    const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + grp * 256;
                     const int m = tm * 128 + rowm;
-                    float best = -1.f, bre = 0.f, bim = 0.f;
-                    int bk = 0x7fffffff;
+                    const long long k0 = k_a + 128LL * tt;
+                    const bool pre = tail.ov > 0 && (k0 + 128) % window == 0;   // the next window's overlap
+                    const int tail_from = pre ? 128 - tail.ov : 128;
+                    float best = -1.f, bre = 0.f, bim = 0.f, tbest = -1.f, tre = 0.f, tim = 0.f;
+                    int bk = 0x7fffffff, tk = 0x7fffffff;
 #pragma unroll 1
-                    for (int c = half * 64; got && c < half * 64 + 64; c += 16) {
-                        float re[16], im[16];
-                        tmem_ld16(base + c, re);
-                        tmem_ld16(base + 128 + c, im);
+                    for (int c = 0; c < 128; c += 32) {
+                        uint32_t ru[32], iu[32];            // re and im of 32 samples: both loads, one wait
+                        tmem_ld32_nw(base + c, ru);
+                        tmem_ld32_nw(base + 128 + c, iu);
+                        tmem_wait_ld();
+                        // |z|^2 and its maximum first; the sample (the first that reaches it) and its
+                        // re, im only when the chunk beats what came before (earlier samples win ties)
+                        float pz[32], t16[16];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float p = re[j] * re[j] + im[j] * im[j];
-                            if (p > best) { best = p; bk = c + j; bre = re[j]; bim = im[j]; }
+                        for (int j = 0; j < 32; ++j) {
+                            const float re = __uint_as_float(ru[j]), im = __uint_as_float(iu[j]);
+                            pz[j] = re * re + im * im;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) t16[j] = fmaxf(pz[j], pz[j + 16]);
+#pragma unroll
+                        for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+                            for (int j = 0; j < h; ++j) t16[j] = fmaxf(t16[j], t16[j + h]);
+                        const float mx = t16[0];
+                        if (mx > best) {
+                            uint32_t eq = 0;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) eq |= (pz[j] == mx ? 1u : 0u) << j;
+                            const int jj = __ffs(eq) - 1;
+                            float sr = 0.f, si = 0.f;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                sr = j == jj ? __uint_as_float(ru[j]) : sr;
+                                si = j == jj ? __uint_as_float(iu[j]) : si;
+                            }
+                            best = mx;
+                            bk = c + jj;
+                            bre = sr;
+                            bim = si;
+                        }
+                        if (pre) {                           // the tail of a tile before a window start
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (c + j >= tail_from && pz[j] > tbest) {
+                                    tbest = pz[j]; tk = c + j; tre = __uint_as_float(ru[j]); tim = __uint_as_float(iu[j]);
+                                }
                         }
                         if (STORE_Z && m < jb.M) {
                             float* zr = zout + (long long)(2 * m) * n + 128LL * tt + c;
                             float* zi = zr + n;
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) { zr[j] = re[j]; zi[j] = im[j]; }
+                            for (int j = 0; j < 32; ++j) { zr[j] = __uint_as_float(ru[j]); zi[j] = __uint_as_float(iu[j]); }
                         }
                     }
                     tc_fence_before();
-                    mbar_arrive(tempty + buf);
-                    float4* xb = xchg + buf * 128;
-                    if (!STORE_Z && half == 1) xb[rowm] = make_float4(best, __int_as_float(bk), bre, bim);
-                    // every epilogue thread goes on only if every one of them got its tile (a wait that
-                    // ran out stops them all here, together); this also orders the exchange above
-                    uint32_t all_got;
-                    asm volatile(
-                        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-                        "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
-                        : "=r"(all_got)
-                        : "r"((uint32_t)got), "n"(32 * kF0EpiWarps)
-                        : "memory");
-                    if (!all_got) { fail = true; break; }
-                    if (STORE_Z || half == 1) continue;
-                    const float4 o = xb[rowm];
-                    if (o.x > best) { best = o.x; bk = __float_as_int(o.y); bre = o.z; bim = o.w; }
-                    const long long k0 = k_a + 128LL * tt;
+                    mbar_arrive(tempty + grp);
+                    if (STORE_Z) continue;
                     const long long kwin0 = (k0 / window) * window;
                     const int koff = (int)(k0 - kwin0) + bk;
                     if (!aligned) {
@@ -329,6 +488,12 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                             const int slot = (int)((k0 / 128) & (n_slots - 1));
                             part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots + slot] =
                                 make_float4(best, __int_as_float(koff), bre, bim);
+                            if (pre) {
+                                const long long w1 = (k0 + 128) / window;
+                                tail.p[(long long)(jb.tmpl0 + m) * tail.tmpl_stride + (long long)det * tail.n +
+                                       (w1 & (tail.n - 1))] =
+                                    make_float4(tbest, __int_as_float((int)(k0 - w1 * window) + tk), tre, tim);
+                            }
                         }
                         continue;
                     }
@@ -356,35 +521,46 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                     }
                 }
             }
-            if (fail) break;
-            if (STORE_Z || !aligned || t1 - t0 != tpw) continue;
-            // the bank's loudest template of the window (lowest index on ties), among the
-            // 128 half-0 threads; its slot gets the bank-maximum flag if it triggered
-            if (half == 0) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float ob = __shfl_xor_sync(0xffffffffu, gbest, o);
-                    const int om = __shfl_xor_sync(0xffffffffu, gm, o);
-                    if (ob > gbest || (ob == gbest && om < gm)) { gbest = ob; gm = om; }
-                }
-                if (lane == 0) red[qd] = make_float4(gbest, __int_as_float(gm), 0.f, 0.f);
-                asm volatile("bar.sync 2, %0;" ::"n"(128) : "memory");
-                float vb = red[0].x;
-                int vm = __float_as_int(red[0].y);
-#pragma unroll
-                for (int q = 1; q < 4; ++q) {
-                    const float x = red[q].x;
-                    const int mm = __float_as_int(red[q].y);
-                    if (x > vb || (x == vb && mm < vm)) { vb = x; vm = mm; }
-                }
-                if (vm < jb.M && (vm & 127) == rowm) {        // this thread wrote that template's slot
-                    const long long w = (k_a + 128LL * t0) / window;
-                    SlabEntry* out = slab_base + (size_t)(w % ring) * n_det_total * slab_det_stride +
-                                     (size_t)det * slab_det_stride + jb.tmpl0 + vm;
-                    if (out->flags & 1) out->flags |= 2;
-                }
-                asm volatile("bar.sync 2, %0;" ::"n"(128) : "memory");   // red[] is reused by the next unit
+            if (STORE_Z) {
+                if (fail) break;
+                continue;
             }
+            // both groups agree that the unit went through (a wait that ran out stops them together)
+            uint32_t all_ok;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+                : "=r"(all_ok)
+                : "r"((uint32_t)!fail), "n"(32 * kF0EpiWarps)
+                : "memory");
+            if (!all_ok) break;
+            if (!aligned || t1 - t0 != tpw) continue;
+            // the bank's loudest template of the window (lowest index on ties), over both groups;
+            // its slot gets the bank-maximum flag if it triggered
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, gbest, o);
+                const int om = __shfl_xor_sync(0xffffffffu, gm, o);
+                if (ob > gbest || (ob == gbest && om < gm)) { gbest = ob; gm = om; }
+            }
+            const int ew = warp - 2 - kF0Builders;
+            if (lane == 0) red[ew] = make_float4(gbest, __int_as_float(gm), 0.f, 0.f);
+            asm volatile("bar.sync 2, %0;" ::"n"(32 * kF0EpiWarps) : "memory");
+            float vb = red[0].x;
+            int vm = __float_as_int(red[0].y);
+#pragma unroll
+            for (int q = 1; q < kF0EpiWarps; ++q) {
+                const float x = red[q].x;
+                const int mm = __float_as_int(red[q].y);
+                if (x > vb || (x == vb && mm < vm)) { vb = x; vm = mm; }
+            }
+            if (vm < jb.M && (vm & 127) == rowm && ((vm >> 7) & 1) == grp) {   // the thread that wrote that slot
+                const long long w = (k_a + 128LL * t0) / window;
+                SlabEntry* out = slab_base + (size_t)(w % ring) * n_det_total * slab_det_stride +
+                                 (size_t)det * slab_det_stride + jb.tmpl0 + vm;
+                if (out->flags & 1) out->flags |= 2;
+            }
+            asm volatile("bar.sync 2, %0;" ::"n"(32 * kF0EpiWarps) : "memory");   // red[] is reused by the next unit
         }
     }
     tc_fence_before();

@@ -281,7 +281,7 @@ template <bool STORE_Z>
 __global__ void __launch_bounds__(256) k_recon_f32(const ReconJob* __restrict__ jobs, const int* __restrict__ tile_base,
                                                    int n_jobs, long long k_a, int n, int det0, long long window,
                                                    Partial* __restrict__ part, long long part_tmpl_stride,
-                                                   int n_slots, float* __restrict__ zout) {
+                                                   int n_slots, TailRing tail, float* __restrict__ zout) {
     const int t = blockIdx.x;
     const int j = find_job(tile_base, n_jobs, t);
     const ReconJob& jb = jobs[j];
@@ -342,16 +342,22 @@ __global__ void __launch_bounds__(256) k_recon_f32(const ReconJob* __restrict__ 
     const long long tile_abs = (k_a + t0) / kTileT;
     const long long kwin0 = ((k_a + t0) / window) * window;
     const int slot = (int)(tile_abs & (n_slots - 1));
+    // window overlap: a tile that ends where a window starts also keeps its last ov samples
+    const long long w1 = (k_a + t0 + 128) / window;
+    const bool pre = tail.ov > 0 && (k_a + t0 + 128) % window == 0;
+    const int tail_from = pre ? 128 - tail.ov : 128;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int m = m0 + w * 8 + i;
-        float best = -1.f, bre = 0.f, bim = 0.f;
-        int bk = 0x7fffffff;
+        float best = -1.f, bre = 0.f, bim = 0.f, tbest = -1.f, tre = 0.f, tim = 0.f;
+        int bk = 0x7fffffff, tk = 0x7fffffff;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float p = are[i][q] * are[i][q] + aim[i][q] * aim[i][q];
             int k = (int)(k_a + t0 + lane * 4 + q - kwin0);
             if (better(p, k, best, bk)) { best = p; bk = k; bre = are[i][q]; bim = aim[i][q]; }
+            const int kt = (int)(k_a + t0 + lane * 4 + q - w1 * window);
+            if (lane * 4 + q >= tail_from && better(p, kt, tbest, tk)) { tbest = p; tk = kt; tre = are[i][q]; tim = aim[i][q]; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -360,11 +366,22 @@ __global__ void __launch_bounds__(256) k_recon_f32(const ReconJob* __restrict__ 
             float ore = __shfl_xor_sync(0xffffffffu, bre, o);
             float oim = __shfl_xor_sync(0xffffffffu, bim, o);
             if (better(ob, ok, best, bk)) { best = ob; bk = ok; bre = ore; bim = oim; }
+            if (pre) {
+                ob = __shfl_xor_sync(0xffffffffu, tbest, o);
+                ok = __shfl_xor_sync(0xffffffffu, tk, o);
+                ore = __shfl_xor_sync(0xffffffffu, tre, o);
+                oim = __shfl_xor_sync(0xffffffffu, tim, o);
+                if (better(ob, ok, tbest, tk)) { tbest = ob; tk = ok; tre = ore; tim = oim; }
+            }
         }
         if (m < jb.M) {
-            if (lane == 0 && part != nullptr)
+            if (lane == 0 && part != nullptr) {
                 part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots + slot] =
                     make_float4(best, __int_as_float(bk), bre, bim);
+                if (pre)
+                    tail.p[(long long)(jb.tmpl0 + m) * tail.tmpl_stride + (long long)det * tail.n + (w1 & (tail.n - 1))] =
+                        make_float4(tbest, __int_as_float(tk), tre, tim);
+            }
             if (STORE_Z) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -436,7 +453,8 @@ __global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ job
                                                   int n_slots, int tiles_per_window, long long w0, float threshold,
                                                   SlabEntry* __restrict__ slab_base, int ring, int n_det_total,
                                                   long long slab_det_stride, int det0,
-                                                  unsigned long long* __restrict__ red, long long fused_from) {
+                                                  unsigned long long* __restrict__ red, long long fused_from,
+                                                  TailRing tail) {
     constexpr int P = kFinTB / 16;
     pdl_launch_dependents();
     pdl_wait();
@@ -469,6 +487,12 @@ __global__ void __launch_bounds__(256) k_finalize(const FinJob* __restrict__ job
             const Partial* pt = part + (long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots;
             for (int s = l16 + 16; s < tiles_per_window; s += 16) {
                 const float4 u = pt[(s0 + s) & (n_slots - 1)];
+                const int k = __float_as_int(u.y);
+                if (better(u.x, k, best, bk)) { best = u.x; bk = k; bre = u.z; bim = u.w; }
+            }
+            if (l16 == 0 && tail.ov > 0 && w > 0) {   // the overlap: samples before the window's start
+                const float4 u = tail.p[(long long)(jb.tmpl0 + m) * tail.tmpl_stride + (long long)det * tail.n +
+                                        (w & (tail.n - 1))];
                 const int k = __float_as_int(u.y);
                 if (better(u.x, k, best, bk)) { best = u.x; bk = k; bre = u.z; bim = u.w; }
             }

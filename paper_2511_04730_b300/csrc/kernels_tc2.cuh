@@ -378,7 +378,7 @@ struct LevCfg {
     static constexpr int STG_PITCH = 80;               // 32 samples x 2 B + 16 B pad: conflict-free rows
     static constexpr int STG_BUF = 32 * STG_PITCH;     // one warp's 32 templates x 32 samples
     static constexpr int STG = EPI_WARPS * STG_BUF;    // per-warp transpose buffers (planes; the top's SNR history)
-    static constexpr int XCHG = TOP ? 2 * 128 * 16 : 0;   // top: tile-argmax exchange between the column halves
+    static constexpr int XCHG = TOP ? 4 * 128 * 16 : 0;   // top: tile and tail argmax exchange between the column halves
     static constexpr int SMEM = STAGES * STAGE_BYTES + STG + XCHG + 1024 + 256;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
 };
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
     k_level_tc(const LevelJob* __restrict__ jobs, const LevelMaps* __restrict__ maps,
                const TileInfo* __restrict__ tinfo, const int* __restrict__ sched, int n_jobs, int tiles_per_det, long long k_a, long long k_b,
                int det0, int n_det_push, long long window, Partial* __restrict__ part, long long part_tmpl_stride,
-               int n_slots, float* __restrict__ zout, int* __restrict__ err) {
+               int n_slots, TailRing tail, float* __restrict__ zout, int* __restrict__ err) {
     using C = LevCfg<BF16, TOP>;
     pdl_launch_dependents();
     constexpr int EPI = 32 * C::EPI_WARPS;
@@ -578,6 +578,12 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
             const bool has_acc = jb.Kp > 0 || F != 0;
             float best = -1.f, bre = 0.f, bim = 0.f;
             int bk = 0x7fffffff;
+            // window overlap: the last ov samples of a tile that ends where a window starts
+            const long long ktile = Q0 + 128LL * tt;
+            const bool pre = tail.ov > 0 && (ktile + 128) % window == 0;
+            const int tail_from = pre ? 128 - tail.ov : 128;
+            float tbest = -1.f, tre = 0.f, tim = 0.f;
+            int tk = 0x7fffffff;
             if (TOP) {
 #pragma unroll 1
                 for (int c = half * 64; c < half * 64 + 64; c += 16) {
@@ -593,6 +599,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                     for (int j = 0; j < 16; ++j) {
                         const float p = re[j] * re[j] + im[j] * im[j];
                         if (p > best) { best = p; bk = c + j; bre = re[j]; bim = im[j]; }
+                        if (c + j >= tail_from && p > tbest) { tbest = p; tk = c + j; tre = re[j]; tim = im[j]; }
                     }
                     if (STORE_Z && m < jb.M) {
                         const int n = (int)(k_b - k_a);
@@ -669,7 +676,11 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
             if (TOP && !STORE_Z) {
                 // the later half hands its tile argmax to the earlier half (which wins ties)
                 float4* xb = xchg + buf * 128;
-                if (half == 1) xb[rowm] = make_float4(best, __int_as_float(bk), bre, bim);
+                float4* xt = xchg + (2 + buf) * 128;
+                if (half == 1) {
+                    xb[rowm] = make_float4(best, __int_as_float(bk), bre, bim);
+                    xt[rowm] = make_float4(tbest, __int_as_float(tk), tre, tim);
+                }
                 asm volatile("bar.sync 1, %0;" ::"n"(EPI) : "memory");
                 if (half == 0 && m < jb.M) {
                     const float4 o = xb[rowm];
@@ -679,6 +690,13 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                     const int slot = (int)((k0 / kTcTileN) & (n_slots - 1));
                     part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots + slot] =
                         make_float4(best, __int_as_float((int)(k0 - kwin0) + bk), bre, bim);
+                    if (pre) {
+                        const float4 ot = xt[rowm];
+                        if (ot.x > tbest) { tbest = ot.x; tk = __float_as_int(ot.y); tre = ot.z; tim = ot.w; }
+                        const long long w1 = (k0 + 128) / window;
+                        tail.p[(long long)(jb.tmpl0 + m) * tail.tmpl_stride + (long long)det * tail.n + (w1 & (tail.n - 1))] =
+                            make_float4(tbest, __int_as_float((int)(k0 - w1 * window) + tk), tre, tim);
+                    }
                 }
             }
         }

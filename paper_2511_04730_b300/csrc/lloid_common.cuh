@@ -93,6 +93,17 @@ struct ReconJob {
 // x = |z|^2, y = sample offset inside its window (int bits), z = Re, w = Im.
 using Partial = float4;
 
+// Window overlap (Section II.D.1): window w also covers the `ov` samples before its
+// start.  A 128-sample tile that ends where a window starts keeps the maximum over its
+// last ov samples (sample offsets relative to that window's start, so negative) in
+// p[tmpl * tmpl_stride + det * n + (w mod n)], w the window it precedes.  ov = 0: none.
+struct TailRing {
+    Partial* p;
+    long long tmpl_stride;
+    int n;                       // windows in the ring (power of two)
+    int ov;                      // 0 .. 127
+};
+
 // Dense per-window trigger slot for one (detector, template).
 struct SlabEntry {
     float snr, phase, re, im;

@@ -155,6 +155,8 @@ struct lloid_ctx {
     int tiles_per_window = 0;
     int n_slots = 0;                   // partial ring slots per (template, detector)
     Partial* d_part = nullptr;         // [M_cap][n_det][n_slots]
+    Partial* d_tail = nullptr;         // window overlap: [M_cap][n_det][n_tail] (TailRing)
+    int n_tail = 0;
     SlabEntry* d_slab = nullptr;       // [kWindowRing][n_det][M_cap]
     int* d_counts = nullptr;
     int counts_cap = 0;
@@ -202,9 +204,9 @@ struct lloid_ctx {
     Xi2Job* d_xi2 = nullptr; int* d_xi2_base = nullptr; int n_xi2 = 0, xi2_tiles = 0;
     int xi2_half_max = 0;              // largest d of the loaded banks (pull readiness)
     std::vector<long long> xi2_next;   // per detector: first window whose xi2 is not computed yet
-    // f0 form: per launch class (K <= 64 with two Yhat buffers, K <= 128 with one) the banks' jobs,
-    // coefficient maps, work units (bank, window group) and their schedules; one slice table
-    static constexpr int kF0Classes = 2;
+    // f0 form: the banks' jobs, coefficient maps, work units (bank, detector, window group) and
+    // their schedules, and one slice table
+    static constexpr int kF0Classes = 1;
     F0Job* d_f0job[kF0Classes] = {}; F0Maps* d_f0map[kF0Classes] = {}; F0Unit* d_f0unit[kF0Classes] = {};
     int* d_f0sched[kF0Classes][2] = {}; int f0_grid[kF0Classes][2] = {}; int n_f0unit[kF0Classes] = {};
     YupSlice* d_f0slices = nullptr;
@@ -219,6 +221,7 @@ struct lloid_ctx {
     cudaEvent_t done_ev = nullptr;
     int* d_err = nullptr;              // device-side wait-expiry code (0 = none)
     int n_sm = 0;
+    int smem_optin = 0;                // largest dynamic shared memory a block may opt into
 
     // injected faults (lloid_inject_fault) and the zero block that fills gaps
     long long fault_alloc = 0, fault_drop = 0, fault_delay_us = 0;
@@ -368,6 +371,16 @@ lloid_status ensure_template_capacity(lloid_ctx* ctx, long long need) {
         CK(cudaMemcpyAsync(np, ctx->d_part, (size_t)ctx->M_cap * nd * ctx->n_slots * sizeof(Partial),
                            cudaMemcpyDeviceToDevice, ctx->stream));
     }
+    // overlap tails: [M][det][n_tail] -> prefix copy
+    Partial* ntl = nullptr;
+    const size_t tbytes = (size_t)cap * nd * ctx->n_tail * sizeof(Partial);
+    CK(cudaMalloc(&ntl, tbytes));
+    const long long tfill = cap * nd * ctx->n_tail;
+    k_fill_partials<<<(unsigned)((tfill + 255) / 256), 256, 0, ctx->stream>>>(ntl, tfill);
+    CKL();
+    if (ctx->d_tail)
+        CK(cudaMemcpyAsync(ntl, ctx->d_tail, (size_t)ctx->M_cap * nd * ctx->n_tail * sizeof(Partial),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
     // slab: [ring][det][M] -> pitched copy
     SlabEntry* ns = nullptr;
     size_t sbytes = (size_t)kWindowRing * nd * cap * sizeof(SlabEntry);
@@ -388,14 +401,16 @@ lloid_status ensure_template_capacity(lloid_ctx* ctx, long long need) {
     CK(cudaMalloc(&nt, (size_t)nd * cap * sizeof(TriggerOut)));
     CK(cudaStreamSynchronize(ctx->stream));
     size_t old = ctx->M_cap ? ((size_t)ctx->M_cap * nd * ctx->n_slots * sizeof(Partial) +
+                               (size_t)ctx->M_cap * nd * ctx->n_tail * sizeof(Partial) +
                                (size_t)kWindowRing * nd * ctx->M_cap * sizeof(SlabEntry) +
                                ctx->M_cap * sizeof(int) + (size_t)nd * ctx->M_cap * sizeof(TriggerOut))
                             : 0;
     cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_counts); cudaFree(ctx->d_trig);
-    ctx->d_part = np; ctx->d_slab = ns; ctx->d_bank_of = nb; ctx->d_counts = nc; ctx->d_trig = nt;
+    cudaFree(ctx->d_tail);
+    ctx->d_part = np; ctx->d_slab = ns; ctx->d_bank_of = nb; ctx->d_counts = nc; ctx->d_trig = nt; ctx->d_tail = ntl;
     ctx->counts_cap = nchunks;
     ctx->trig_cap = (long long)nd * cap;
-    ctx->state_bytes += pbytes + sbytes + cap * sizeof(int) + (size_t)nd * cap * sizeof(TriggerOut) - old;
+    ctx->state_bytes += pbytes + tbytes + sbytes + cap * sizeof(int) + (size_t)nd * cap * sizeof(TriggerOut) - old;
     ctx->M_cap = cap;
     ctx->h_bank_of.resize(cap, -1);
     return LLOID_OK;
@@ -484,6 +499,11 @@ lloid_status upload_sched(lloid_ctx* ctx, const std::vector<double>& cost, int n
 }
 
 bool split_precision(const lloid_ctx* ctx) { return ctx->cfg.precision != LLOID_FP32; }
+
+TailRing tail_ring(const lloid_ctx* ctx) {
+    return TailRing{ctx->d_tail, (long long)ctx->cfg.n_detectors * ctx->n_tail, ctx->n_tail,
+                    (int)ctx->cfg.window_overlap};
+}
 
 bool timing(const lloid_ctx* ctx) { return (ctx->cfg.flags & LLOID_FLAG_STAGE_TIMING) != 0; }
 
@@ -663,7 +683,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             lt[tab] += q.tiles_m * q.tiles_t;
         }
         if (b->form == 1) {   // f0 form: one job of the f0 kernel, its slices, its window groups
-            const int cls = b->top.K <= 64 ? 0 : 1;
+            const int cls = 0;   // one launch for every bank in the f0 form
             F0Job f{};
             f.M = b->M; f.Mpad = b->Mpad; f.tmpl0 = b->tmpl0; f.K = b->top.K; f.tiles_m = b->Mpad / 128;
             f.s0 = (int)ys.size(); f.ns = (int)b->sl.size(); f.map = (int)f0j[cls].size();
@@ -704,7 +724,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
         for (int v = 0; v < 2; ++v)
             if ((st0 = upload_sched(ctx, f0cost[cls], v ? nd : 1, &ctx->d_f0sched[cls][v], &ctx->f0_grid[cls][v])))
                 return st0;
-        const int smem = f0_smem_bytes(bf, cls ? 128 : 64, cls ? 1 : 2);
+        const int smem = f0_smem_bytes(bf, kF0Kc, 2);
         if (bf) {
             CK(cudaFuncSetAttribute(k_f0_top<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             CK(cudaFuncSetAttribute(k_f0_top<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -732,7 +752,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     const int fir_sbytes = bf ? FirCfg<true>::STAGE_BYTES : FirCfg<false>::STAGE_BYTES;
     {
         const int st2 = std::min(FirCfg<false>::MAX_STAGES, (113 * 1024 - fir_fixed) / fir_sbytes);
-        if (st2 >= 2) { ctx->firtc_ctas = 2; ctx->firtc_stages = st2; }
+        if (st2 >= 2 && c.fir_ctas != 1) { ctx->firtc_ctas = 2; ctx->firtc_stages = st2; }
         else { ctx->firtc_ctas = 1; ctx->firtc_stages = std::min(FirCfg<false>::MAX_STAGES, (227 * 1024 - fir_fixed) / fir_sbytes); }
     }
     {   // schedules: cost ~ MMAs of a tile plus a fixed epilogue share
@@ -890,11 +910,11 @@ lloid_status launch_recon_f32(lloid_ctx* ctx, long long k_a, long long n, int de
     dim3 grid(tiles, n_det_push);
     if (store_z)
         k_recon_f32<true><<<grid, 256, 0, ctx->stream>>>(jobs, base, n_jobs, k_a, (int)n, det0, ctx->cfg.window_samples,
-                                                        nullptr, part_stride, ctx->n_slots, zout);
+                                                        nullptr, part_stride, ctx->n_slots, tail_ring(ctx), zout);
     else
         k_recon_f32<false><<<grid, 256, 0, ctx->stream>>>(jobs, base, n_jobs, k_a, (int)n, det0,
                                                          ctx->cfg.window_samples, ctx->d_part, part_stride,
-                                                         ctx->n_slots, nullptr);
+                                                         ctx->n_slots, tail_ring(ctx), nullptr);
     CKL();
     return LLOID_OK;
 }
@@ -902,17 +922,18 @@ lloid_status launch_recon_f32(lloid_ctx* ctx, long long k_a, long long n, int de
 template <bool BF16, bool TOP, bool SZ, int F>
 cudaError_t launch_lv1(dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps, const TileInfo* base,
                 const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0, int nd, long long W,
-                Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
-    return launch_pdl(k_level_tc<BF16, TOP, SZ, F>, g, dim3(LevCfg<BF16, TOP>::THREADS), LevCfg<BF16, TOP>::SMEM, st, jobs, maps, base, sched, n_jobs, tiles, k_a, k_b,
-                                                                      det0, nd, W, part, part_stride, n_slots, zout,
-                                                                      err);
+                Partial* part, long long part_stride, int n_slots, TailRing tail, float* zout, int* err) {
+    return launch_pdl(k_level_tc<BF16, TOP, SZ, F>, g, dim3(LevCfg<BF16, TOP>::THREADS), LevCfg<BF16, TOP>::SMEM, st,
+                      jobs, maps, base, sched, n_jobs, tiles, k_a, k_b, det0, nd, W, part, part_stride, n_slots, tail,
+                      zout, err);
 }
 template <bool BF16, bool TOP, bool SZ>
 cudaError_t launch_lv_f(int F, dim3 g, int smem, cudaStream_t st, const LevelJob* jobs, const LevelMaps* maps,
                  const TileInfo* base, const int* sched, int n_jobs, int tiles, long long k_a, long long k_b, int det0,
-                 int nd, long long W, Partial* part, long long part_stride, int n_slots, float* zout, int* err) {
+                 int nd, long long W, Partial* part, long long part_stride, int n_slots, TailRing tail, float* zout,
+                 int* err) {
 #define LV_F(FV) launch_lv1<BF16, TOP, SZ, FV>(g, smem, st, jobs, maps, base, sched, n_jobs, tiles, k_a, k_b, det0, nd, W, \
-                                               part, part_stride, n_slots, zout, err)
+                                               part, part_stride, n_slots, tail, zout, err)
     switch (F) {
         case 0: return LV_F(0);
         case 2: return LV_F(2);
@@ -940,7 +961,8 @@ lloid_status launch_level(lloid_ctx* ctx, int depth, int fslot, long long k_a, l
     cudaError_t le = cudaSuccess;
 #define LAUNCH_LV(BFV, TOPV, SZ)                                                                                     \
     le = launch_lv_f<BFV, TOPV, SZ>(F, g, smem, ctx->stream, jobs, maps, base, sched, n_jobs, tiles, k_a, k_a + n, det0,   \
-                               n_det_push, ctx->cfg.window_samples, part, part_stride, ctx->n_slots, zout, ctx->d_err)
+                               n_det_push, ctx->cfg.window_samples, part, part_stride, ctx->n_slots, tail_ring(ctx), zout, \
+                               ctx->d_err)
     if (depth > 0) { if (bf) LAUNCH_LV(true, false, false); else LAUNCH_LV(false, false, false); }
     else if (store_z) { if (bf) LAUNCH_LV(true, true, true); else LAUNCH_LV(false, true, true); }
     else { if (bf) LAUNCH_LV(true, true, false); else LAUNCH_LV(false, true, false); }
@@ -950,18 +972,19 @@ lloid_status launch_level(lloid_ctx* ctx, int depth, int fslot, long long k_a, l
     return LLOID_OK;
 }
 
-// One launch of the f0 kernel for launch class cls (K <= 64: two Yhat buffers; K <= 128: one)
+// One launch of the f0 kernel (every bank in the f0 form; K <= kF0Kc, two Yhat buffers)
 // over the work units of `units` scheduled by `sched` (STORE_Z when zout is given).
 lloid_status launch_f0(lloid_ctx* ctx, int cls, const F0Job* jobs, const F0Unit* units, const int* sched, int grid,
                        long long k_a, long long n, int det0, int nd, float* zout) {
     const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
-    const int kc = cls ? 128 : 64, yb = cls ? 1 : 2;
+    const int kc = kF0Kc, yb = 2;
     const int smem = f0_smem_bytes(bf, kc, yb);
     const long long part_stride = (long long)ctx->cfg.n_detectors * ctx->n_slots;
     cudaError_t e;
 #define F0_ARGS jobs, (const F0Maps*)ctx->d_f0map[cls], (const YupSlice*)ctx->d_f0slices, units, sched, 0, kc, yb, k_a, \
         (int)n, det0, nd, (long long)ctx->cfg.window_samples, ctx->cfg.snr_threshold, ctx->d_part, part_stride,        \
-        ctx->n_slots, ctx->d_slab, (int)kWindowRing, ctx->cfg.n_detectors, (long long)ctx->M_cap, zout, ctx->d_err
+        ctx->n_slots, tail_ring(ctx), ctx->d_slab, (int)kWindowRing, ctx->cfg.n_detectors, (long long)ctx->M_cap, zout,   \
+        ctx->d_err
     if (bf) e = zout ? launch_pdl(k_f0_top<true, true>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS)
                      : launch_pdl(k_f0_top<true, false>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS);
     else e = zout ? launch_pdl(k_f0_top<false, true>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS)
@@ -1096,12 +1119,12 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
     if (w_end > w_first && ctx->n_fin > 0) {
         dim3 grid(ctx->n_fin_chunks, nd, (unsigned)(w_end - w_first));
         // windows of the f0 form's banks that the f0 kernel finished (pushes that start on a window)
-        const long long fused_from = (k_a % W == 0) ? w_first : (1LL << 62);
+        const long long fused_from = (k_a % W == 0 && ctx->cfg.window_overlap == 0) ? w_first : (1LL << 62);
         CK(launch_pdl(k_finalize, grid, dim3(256), 0, ctx->stream, (const FinJob*)ctx->d_finj,
                       (const FinChunk*)ctx->d_fin_chunks, (const Partial*)ctx->d_part,
                       (long long)ctx->cfg.n_detectors * ctx->n_slots, ctx->n_slots, ctx->tiles_per_window, w_first,
                       ctx->cfg.snr_threshold, ctx->d_slab, (int)kWindowRing, ctx->cfg.n_detectors,
-                      (long long)ctx->M_cap, det0, ctx->d_fin_red, fused_from));
+                      (long long)ctx->M_cap, det0, ctx->d_fin_red, fused_from, tail_ring(ctx)));
         ++ctx->launches;
     }
     // Eq. 10 for the windows whose triggers now have d samples of z past the window end
@@ -1233,18 +1256,26 @@ lloid_status wait_done(lloid_ctx* ctx, int timeout_ms) { return wait_event(ctx, 
 // rows), an epilogue share, the Acc planes that a ladder level below f0 writes and the next level
 // reads (about 256 KB per tile at a 148th of the HBM bandwidth); in the f0 form the MMAs over the
 // bank's bases packed (K = their count rounded up to 16) and the upsampling of the basis outputs,
-// shared by the bank's template tiles.  The f0 form needs K <= 128, at most 1024 templates and no
+// shared by the bank's template tiles.  The f0 form needs K <= 96, at most 1024 templates and no
 // Eq. 10 autocorrelations (the f0 kernel keeps no SNR history).
-bool f0_form_possible(const BankRT* b, int ac_half) {
-    int k = 0;
-    for (const SliceRT& s : b->sl) k += s.L;
-    return (k + 15) / 16 * 16 <= 128 && b->Mpad <= 128 * kF0MaxTm && ac_half == 0;
+bool f0_form_possible(const lloid_ctx* ctx, const BankRT* b, int ac_half) {
+    const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
+    if (f0_smem_bytes(bf, kF0Kc, 2) > ctx->smem_optin) return false;
+    int k = 0, rall = 0;
+    for (const SliceRT& s : b->sl) {
+        k += s.L;
+        const int rlen = s.e_max - s.e_min + 1;
+        rall += rlen;
+        if ((127 + rlen - 1) / s.D + 2 > kF0StageRows) return false;
+    }
+    return (k + 15) / 16 * 16 <= kF0Kc && b->Mpad <= 128 * kF0MaxTm && ac_half == 0 && rall <= kF0RAll &&
+           (int)b->sl.size() <= kF0MaxSlices;
 }
 
 int choose_form(const lloid_ctx* ctx, const BankRT* b, const std::vector<int>& ladder, int ac_half) {
     const lloid_config& c = ctx->cfg;
     if (c.flags & LLOID_FLAG_FORM_LADDER) return 0;
-    if (!f0_form_possible(b, ac_half)) return 0;
+    if (!f0_form_possible(ctx, b, ac_half)) return 0;
     if (c.flags & LLOID_FLAG_FORM_F0) return 1;
     const double mk = c.precision == LLOID_BF16_SPLIT ? 6.0 : 4.0, epi = 20.0, planes = 190.0;
     const int nl = (int)ladder.size();
@@ -1270,7 +1301,8 @@ int choose_form(const lloid_ctx* ctx, const BankRT* b, const std::vector<int>& l
     // f0 form: per tile the MMAs over all bases and, shared by the bank's template groups, the
     // upsampled rows (about 24 multiply-adds per basis and row for 128 threads: ~0.2 MMA each)
     const double f0 = (double)c.f0 / 128.0 * (mk * k16_all + epi + 0.2 * up_cols / (b->Mpad / 128.0));
-    return f0 < lad ? 1 : 0;
+    const double ratio = c.form_ratio > 0.f ? c.form_ratio : 1.0;
+    return f0 < ratio * lad ? 1 : 0;
 }
 
 // Split path: ladder levels, 8-phase expanded bases for the tensor-core FIR,
@@ -1450,7 +1482,7 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
     const int nd = c.n_detectors;
     hdr->clear();
     seg->clear();
-    long long h[] = {0x4C4C4F4944535431LL, 4, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
+    long long h[] = {0x4C4C4F4944535431LL, 5, c.f0, nd, c.n_down, c.n_up, c.window_samples, c.precision,
                      c.max_block, c.max_history, c.min_rate, (long long)ctx->banks.size(), ctx->M_used,
                      ctx->M_cap, ctx->n_slots};
     hdr->assign(h, h + sizeof h / sizeof h[0]);
@@ -1467,6 +1499,7 @@ void state_layout(lloid_ctx* ctx, std::vector<long long>* hdr, std::vector<Segme
             seg->push_back({ctx->s_lo[r], (size_t)nd * 2 * ctx->s_len[r] * 2});
         }
     seg->push_back({ctx->d_part, (size_t)ctx->M_cap * nd * ctx->n_slots * sizeof(Partial)});
+    seg->push_back({ctx->d_tail, (size_t)ctx->M_cap * nd * ctx->n_tail * sizeof(Partial)});
     seg->push_back({ctx->d_slab, (size_t)kWindowRing * nd * ctx->M_cap * sizeof(SlabEntry)});
     if (ctx->d_events) seg->push_back({ctx->d_events, (size_t)kWindowRing * ctx->bank_cap * sizeof(EventEntry)});
     for (auto& kv : ctx->banks) {
@@ -1524,6 +1557,8 @@ void lloid_config_default(lloid_config* c) {
     c->cuda_stream = nullptr;
     c->flags = 0;
     c->coinc_window = 66;   // (0.0273 + 0.005) s at 2048 Hz
+    c->form_ratio = 1.0f;
+    c->fir_ctas = 0;
 }
 
 const char* lloid_strerror(lloid_status st) {
@@ -1563,6 +1598,73 @@ lloid_status lloid_inject_fault(lloid_ctx* ctx, int32_t kind, int64_t count) {
             return LLOID_OK;
     }
     return fail(ctx, LLOID_EINVAL, "unknown fault kind %d", kind);
+}
+
+lloid_status lloid_autotune(const lloid_config* cfg, const lloid_bank_desc* banks, int32_t n_banks, int64_t n,
+                            int32_t reps, lloid_tuning* out) {
+    if (!cfg || !banks || n_banks < 1 || !out || reps < 1 || n <= 0 || n > cfg->max_block || n % kTileT)
+        return LLOID_EINVAL;
+    std::memset(out, 0, sizeof *out);
+    const int nd = cfg->n_detectors;
+    float* zeros = nullptr;
+    {
+        cudaError_t e = cudaSetDevice(cfg->device);
+        if (e == cudaSuccess) e = cudaMalloc(&zeros, (size_t)nd * n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(zeros, 0, (size_t)nd * n * sizeof(float));
+        if (e != cudaSuccess) { cudaFree(zeros); return e == cudaErrorMemoryAllocation ? LLOID_ENOMEM : LLOID_ECUDA; }
+    }
+    // time one candidate: a scratch context, every bank, two warm-up pushes, `reps` timed pushes
+    auto trial = [&](float ratio, uint32_t form_flags, int ctas, float* ms) -> lloid_status {
+        lloid_config c = *cfg;
+        c.cuda_stream = nullptr;
+        c.flags = (c.flags & ~(LLOID_FLAG_STAGE_TIMING | LLOID_FLAG_FORM_LADDER | LLOID_FLAG_FORM_F0)) | form_flags;
+        c.form_ratio = ratio;
+        c.fir_ctas = ctas;
+        c.hbm_budget_bytes = 0;
+        lloid_ctx* ctx = nullptr;
+        lloid_status st = lloid_create(&c, &ctx);
+        if (st) return st;
+        int32_t id;
+        for (int b = 0; b < n_banks && !st; ++b) st = lloid_load_bank(ctx, banks + b, &id);
+        cudaEvent_t a = nullptr, z = nullptr;
+        if (!st && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess)) st = LLOID_ECUDA;
+        long long t = 0;
+        for (int k = 0; k < 2 && !st; ++k, t += n) st = lloid_push_strain_all(ctx, t, zeros, n, 1);
+        if (!st && cudaEventRecord(a, ctx->stream) != cudaSuccess) st = LLOID_ECUDA;
+        for (int k = 0; k < reps && !st; ++k, t += n) st = lloid_push_strain_all(ctx, t, zeros, n, 1);
+        if (!st && (cudaEventRecord(z, ctx->stream) != cudaSuccess || cudaEventSynchronize(z) != cudaSuccess ||
+                    cudaEventElapsedTime(ms, a, z) != cudaSuccess))
+            st = LLOID_ECUDA;
+        if (!st) st = lloid_synchronize(ctx);
+        *ms /= reps;
+        if (a) cudaEventDestroy(a);
+        if (z) cudaEventDestroy(z);
+        lloid_destroy(ctx);
+        return st;
+    };
+    lloid_status st = LLOID_OK;
+    const float ratios[5] = {1.f, 1.f, 0.5f, 2.f, 1.f};
+    const uint32_t forms[5] = {LLOID_FLAG_FORM_LADDER, 0u, 0u, 0u, LLOID_FLAG_FORM_F0};
+    int best = -1;
+    for (int i = 0; i < 5 && !st; ++i) {
+        const int k = out->n_tried++;
+        out->cand_ratio[k] = ratios[i]; out->cand_flags[k] = forms[i]; out->cand_ctas[k] = cfg->fir_ctas;
+        st = trial(ratios[i], forms[i], cfg->fir_ctas, &out->ms[k]);
+        if (!st && (best < 0 || out->ms[k] < out->ms[best])) best = k;
+    }
+    for (int ctas = 1; ctas <= 2 && !st; ++ctas) {
+        const int k = out->n_tried++;
+        out->cand_ratio[k] = out->cand_ratio[best]; out->cand_flags[k] = out->cand_flags[best]; out->cand_ctas[k] = ctas;
+        st = trial(out->cand_ratio[k], out->cand_flags[k], ctas, &out->ms[k]);
+        if (!st && out->ms[k] < out->ms[best]) best = k;
+    }
+    cudaFree(zeros);
+    if (st) return st;
+    out->best = best;
+    out->form_ratio = out->cand_ratio[best];
+    out->flags_form = out->cand_flags[best];
+    out->fir_ctas = out->cand_ctas[best];
+    return LLOID_OK;
 }
 
 lloid_status lloid_clear_error(lloid_ctx* ctx) {
@@ -1614,13 +1716,15 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         c.max_history < 0 || !is_pow2(c.min_rate) || c.min_rate > c.f0 || c.f0 / c.min_rate > 256 ||
         c.precision < 0 || c.precision > 2 || !(c.snr_threshold >= 0.f) || c.coinc_window < 0)
         return fail(nullptr, LLOID_EINVAL, "bad configuration");
-    if (c.window_overlap != 0) return LLOID_EINVAL;
+    if (c.window_overlap < 0 || c.window_overlap >= 128 || c.window_overlap >= c.window_samples)
+        return fail(nullptr, LLOID_EINVAL, "window_overlap must be in [0, 128)");
     if (c.max_block / c.window_samples + 1 > kWindowRing)
         return fail(nullptr, LLOID_EINVAL, "a push may complete at most %d trigger windows", kWindowRing);
     if (c.precision != LLOID_FP32 && (c.max_block % kTcTileN || c.n_up != 8 || c.f0 / c.min_rate > 64))
         return fail(nullptr, LLOID_EINVAL, "tensor-core paths need max_block % 128 == 0 and n_up == 8");
     CK(cudaSetDevice(c.device));
     CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, c.device));
+    CK(cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
     if (c.cuda_stream) {
         ctx->stream = (cudaStream_t)c.cuda_stream;
     } else {
@@ -1703,6 +1807,7 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
     CK(cudaEventRecord(ctx->done_ev, ctx->stream));
     ctx->tiles_per_window = (int)(c.window_samples / kTileT);
     ctx->n_slots = (int)next_pow2(((c.max_block + c.window_samples - 1) / c.window_samples + 2) * ctx->tiles_per_window);
+    ctx->n_tail = (int)next_pow2((c.max_block + c.window_samples - 1) / c.window_samples + 3);
     CK(cudaHostAlloc((void**)&ctx->h_total, sizeof(long long), cudaHostAllocDefault));
     CK(cudaHostAlloc((void**)&ctx->h_err, sizeof(int), cudaHostAllocDefault));
     CK(cudaEventCreateWithFlags(&ctx->pull_ev, cudaEventDisableTiming));
@@ -1729,7 +1834,7 @@ void lloid_destroy(lloid_ctx* ctx) {
     for (int r = 0; r < ctx->n_rates; ++r) { cudaFree(ctx->rate_ring[r]); cudaFree(ctx->w_down[r]); }
     cudaFree(ctx->d_stage);
     for (int i = 0; i < 2; ++i) { cudaFreeHost(ctx->h_stage[i]); if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]); }
-    cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_tmpl0_of);
+    cudaFree(ctx->d_part); cudaFree(ctx->d_tail); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_tmpl0_of);
     cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
     cudaFreeHost(ctx->h_err); cudaFreeHost(ctx->h_trig);
     cudaFree(ctx->d_events); cudaFreeHost(ctx->h_events);

@@ -40,6 +40,70 @@ def default_config() -> _lib.LloidConfig:
     return cfg
 
 
+def _bank_desc(slices: Iterable, autocorr=None):
+    """lloid_bank_desc of a bank (and the arrays it points to, to keep alive)."""
+    slices = list(slices)
+    keep = []
+    arr = (_lib.LloidSlice * len(slices))()
+    n_rows = None
+    for i, s in enumerate(slices):
+        b = np.ascontiguousarray(s.bases, dtype=np.float64)
+        c = np.ascontiguousarray(s.coeffs, dtype=np.float64)
+        keep += [b, c]
+        if n_rows is None:
+            n_rows = c.shape[0]
+        arr[i].rate, arr[i].n_taps, arr[i].j_start = int(s.rate), int(b.shape[1]), int(s.j_start)
+        arr[i].n_basis = int(b.shape[0])
+        arr[i].bases = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr[i].coeffs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if c.shape != (n_rows, b.shape[0]):
+            raise ValueError("coeffs must be [2M, L] with one 2M for the bank")
+    keep.append(arr)
+    desc = _lib.LloidBankDesc(n_rows // 2, len(slices), arr)
+    if autocorr is not None:
+        ac = np.asarray(autocorr, dtype=np.complex128)
+        if ac.ndim != 2 or ac.shape[0] != n_rows // 2 or ac.shape[1] % 2 != 1:
+            raise ValueError("autocorr must be [M, 2d + 1] complex")
+        acf = np.ascontiguousarray(ac.view(np.float64).reshape(ac.shape[0], ac.shape[1], 2))
+        keep.append(acf)
+        desc.ac_half = (ac.shape[1] - 1) // 2
+        desc.autocorr = acf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return desc, keep, n_rows
+
+
+def autotune(banks, n: int, reps: int = 4, n_detectors: int = 1, precision: str = "bf16_split",
+             max_block: Optional[int] = None, max_history: Optional[int] = None, device: int = 0,
+             f0: int = 2048, window: int = 2048) -> dict:
+    """lloid_autotune: time the candidate forms and basis-filter occupancies on
+    scratch contexts with these banks and pushes of n samples; returns the
+    chosen setting (pass it as Context(tuning=...)) with every candidate's
+    device time per push."""
+    lib = _lib.load()
+    cfg = default_config()
+    cfg.f0, cfg.n_detectors, cfg.window_samples = f0, n_detectors, window
+    cfg.precision = _lib.PRECISIONS[precision]
+    cfg.max_block = n if max_block is None else max_block
+    if max_history is not None:
+        cfg.max_history = max_history
+    cfg.device = device
+    descs = (_lib.LloidBankDesc * len(banks))()
+    keep = []
+    for i, b in enumerate(banks):
+        d, k, _ = _bank_desc(b)
+        descs[i] = d
+        keep.append(k)
+    out = _lib.LloidTuning()
+    st = lib.lloid_autotune(ctypes.byref(cfg), ctypes.cast(descs, ctypes.c_void_p), len(banks), n, reps,
+                            ctypes.byref(out))
+    if st != 0:
+        raise LloidError(st, "lloid_autotune failed")
+    names = {0: "by ratio", 2: "all ladder", 4: "all f0"}
+    cands = [{"form": names.get(out.cand_flags[i], "?"), "form_ratio": out.cand_ratio[i],
+              "fir_ctas": out.cand_ctas[i], "ms_per_push": out.ms[i]} for i in range(out.n_tried)]
+    return {"form_ratio": out.form_ratio, "flags_form": out.flags_form, "fir_ctas": out.fir_ctas,
+            "best": out.best, "candidates": cands}
+
+
 class Context:
     """One LLOID streaming context on one GPU (``lloid_create``)."""
 
@@ -47,11 +111,13 @@ class Context:
                  max_history: Optional[int] = None, window: int = 2048, threshold: float = 4.0,
                  device: int = 0, stream=None, hbm_budget: int = 0, f0: int = 2048, min_rate: int = 32,
                  n_down: int = 32, n_up: int = 8, stage_timing: bool = False, coinc_window: Optional[int] = None,
-                 form: Optional[str] = None, fill_gaps: bool = False):
+                 form: Optional[str] = None, fill_gaps: bool = False, overlap: int = 0,
+                 tuning: Optional[dict] = None):
         self._lib = _lib.load()
         cfg = default_config()
         cfg.f0, cfg.n_detectors, cfg.n_down, cfg.n_up = f0, n_detectors, n_down, n_up
         cfg.window_samples, cfg.snr_threshold = window, threshold
+        cfg.window_overlap = overlap
         cfg.precision = _lib.PRECISIONS[precision]
         cfg.max_block = max_block
         if max_history is not None:
@@ -64,6 +130,10 @@ class Context:
             raise ValueError(f"form must be one of {sorted(k for k in _lib.FORM_FLAGS if k)} or None")
         cfg.flags = ((_lib.FLAG_STAGE_TIMING if stage_timing else 0) | _lib.FORM_FLAGS[form] |
                      (_lib.FLAG_FILL_GAPS if fill_gaps else 0))
+        if tuning is not None:          # the result of autotune()
+            if form is None:
+                cfg.flags |= tuning["flags_form"]
+            cfg.form_ratio, cfg.fir_ctas = tuning["form_ratio"], tuning["fir_ctas"]
         self.cfg = cfg
         self.precision = precision
         self.n_detectors = n_detectors
@@ -106,31 +176,7 @@ class Context:
         and coeffs [2M, L] (float64); optional autocorr [M, 2d + 1] complex
         (R_i(t), t = -d .. d) enables the Eq. 10 statistic for its triggers.
         Returns the bank id."""
-        slices = list(slices)
-        keep = []
-        arr = (_lib.LloidSlice * len(slices))()
-        n_rows = None
-        for i, s in enumerate(slices):
-            b = np.ascontiguousarray(s.bases, dtype=np.float64)
-            c = np.ascontiguousarray(s.coeffs, dtype=np.float64)
-            keep += [b, c]
-            if n_rows is None:
-                n_rows = c.shape[0]
-            arr[i].rate, arr[i].n_taps, arr[i].j_start = int(s.rate), int(b.shape[1]), int(s.j_start)
-            arr[i].n_basis = int(b.shape[0])
-            arr[i].bases = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-            arr[i].coeffs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-            if c.shape != (n_rows, b.shape[0]):
-                raise ValueError("coeffs must be [2M, L] with one 2M for the bank")
-        desc = _lib.LloidBankDesc(n_rows // 2, len(slices), arr)
-        if autocorr is not None:
-            ac = np.asarray(autocorr, dtype=np.complex128)
-            if ac.ndim != 2 or ac.shape[0] != n_rows // 2 or ac.shape[1] % 2 != 1:
-                raise ValueError("autocorr must be [M, 2d + 1] complex")
-            acf = np.ascontiguousarray(ac.view(np.float64).reshape(ac.shape[0], ac.shape[1], 2))
-            keep.append(acf)
-            desc.ac_half = (ac.shape[1] - 1) // 2
-            desc.autocorr = acf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        desc, keep, n_rows = _bank_desc(slices, autocorr)
         bid = ctypes.c_int32()
         self._check(self._lib.lloid_load_bank(self._h, ctypes.byref(desc), ctypes.byref(bid)))
         self.banks[bid.value] = n_rows // 2

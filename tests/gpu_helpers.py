@@ -30,7 +30,7 @@ def max_abs_complex(za, zb):
     return float(np.sqrt(d.max()))
 
 
-def compare_triggers(gpu, oracle_trigs, z_oracle, tol, window, threshold=4.0, t_offset=0):
+def compare_triggers(gpu, oracle_trigs, z_oracle, tol, window, threshold=4.0, t_offset=0, overlap=0):
     """Check GPU triggers against the oracle's.
 
     Unique parts are compared exactly: the set of (window, template) pairs
@@ -45,7 +45,7 @@ def compare_triggers(gpu, oracle_trigs, z_oracle, tol, window, threshold=4.0, t_
     problems = []
     for key in set(o) | set(g):
         w, i = key
-        a = max(0, w * window) - t_offset
+        a = max(0, w * window - overlap) - t_offset
         b = (w + 1) * window - t_offset
         seg = p[i, a:b]
         best = float(seg.max())

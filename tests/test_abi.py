@@ -51,7 +51,9 @@ int main(void) {
          sizeof(lloid_config), sizeof(lloid_slice), sizeof(lloid_bank_desc), sizeof(lloid_trigger),
          sizeof(lloid_event));
   P(lloid_config, max_block) P(lloid_config, hbm_budget_bytes) P(lloid_config, cuda_stream) P(lloid_config, flags)
-  P(lloid_config, coinc_window)
+  P(lloid_config, coinc_window) P(lloid_config, form_ratio) P(lloid_config, fir_ctas)
+  printf("lloid_tuning %zu\n", sizeof(lloid_tuning));
+  P(lloid_tuning, ms) P(lloid_tuning, cand_ratio) P(lloid_tuning, cand_ctas)
   P(lloid_slice, j_start) P(lloid_slice, bases) P(lloid_slice, coeffs)
   P(lloid_bank_desc, ac_half) P(lloid_bank_desc, autocorr)
   P(lloid_trigger, window) P(lloid_trigger, sample) P(lloid_trigger, snr) P(lloid_trigger, im) P(lloid_trigger, xi2)
@@ -66,7 +68,7 @@ int main(void) {
         subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
     got = dict(line.rsplit(" ", 1) for line in out if line)
-    m = {"lloid_config": _lib.LloidConfig, "lloid_slice": _lib.LloidSlice,
+    m = {"lloid_config": _lib.LloidConfig, "lloid_slice": _lib.LloidSlice, "lloid_tuning": _lib.LloidTuning,
          "lloid_bank_desc": _lib.LloidBankDesc, "lloid_trigger": _lib.LloidTrigger, "lloid_event": _lib.LloidEvent}
     for k, v in got.items():
         if "." in k:
@@ -85,6 +87,7 @@ def test_host_only_calls(lib):
     # coincidence window: maximum light travel time plus buffer (Section II.D.3), at 2048 Hz
     assert cfg.coinc_window == int((0.0273 + 0.005) * 2048)
     assert cfg.snr_threshold == 4.0 and cfg.window_overlap == 0
+    assert cfg.form_ratio == 1.0 and cfg.fir_ctas == 0
     assert lib.lloid_strerror(-4) == b"discontinuous push (t0 is not the stream end)"
     assert lib.lloid_strerror(0) == b"ok"
     assert lib.lloid_last_error(None) == b"null context"

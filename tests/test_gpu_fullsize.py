@@ -175,10 +175,10 @@ ZOO = [
     (12, (0.0, 1.0, 8.0), (2048, 128)),                                       # F = 16
     (300, (0.0, 0.5, 2.0, 8.0), (2048, 512, 32)),                             # F = 16 then 4, three tiles
     (300, (0.0, 1.0, 8.0), (2048, 64)),                                       # F = 32, three tiles
-    (8, (0.0, 0.25, 0.5, 1.0, 1.5, 2.0, 3.0, 8.0), (2048, 1024, 512, 256, 128, 64, 32)),    # F = 2 x 6
+    (6, (0.0, 0.25, 0.5, 1.0, 1.5, 2.0, 3.0, 8.0), (2048, 1024, 512, 256, 128, 64, 32)),    # F = 2 x 6
 ]
-# the small banks have at most 128 bases, so they can run in the f0 form; the 300-template
-# banks (more than 128 bases) stay in the ladder form whatever the context asks
+# the small banks have at most 96 bases, so they can run in the f0 form; the 300-template
+# banks (more than 96 bases) stay in the ladder form whatever the context asks
 
 
 @pytest.fixture(scope="module")
