@@ -62,6 +62,7 @@ struct F0SliceS {
     const uint16_t* y_lo;
     long long q_lo;                // first staged row for the current tile
     int y_rows, y_ld, D, e_min, rlen, L, roff, nq;
+    int col0;                      // first column of the slice in Yhat
 };
 struct F0Piece { int s, c0, nc, nv, off, pitch, items, item0; };
 
@@ -81,6 +82,95 @@ __host__ __device__ constexpr int f0_smem_bytes(bool bf16, int kc, int ybufs) {
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Two packed hi/lo 16-bit pairs (element 0 in the low half) back to FP32 sums.
+template <bool BF16>
+__device__ __forceinline__ float2 hilo_pair(uint32_t h, uint32_t l) {
+    if (BF16)
+        return make_float2(__uint_as_float(h << 16) + __uint_as_float(l << 16),
+                           __uint_as_float(h & 0xffff0000u) + __uint_as_float(l & 0xffff0000u));
+    return make_float2(__half2float(__ushort_as_half((unsigned short)(h & 0xffffu))) +
+                           __half2float(__ushort_as_half((unsigned short)(l & 0xffffu))),
+                       __half2float(__ushort_as_half((unsigned short)(h >> 16))) +
+                           __half2float(__ushort_as_half((unsigned short)(l >> 16))));
+}
+
+// One Yhat element split into its hi and lo halves, stored at byte offset o of the two planes.
+template <bool BF16>
+__device__ __forceinline__ void put_hilo(uint8_t* yh, uint8_t* yl, int o, float x) {
+    if (BF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        *reinterpret_cast<__nv_bfloat16*>(yh + o) = h;
+        *reinterpret_cast<__nv_bfloat16*>(yl + o) = __float2bfloat16_rn(x - __bfloat162float(h));
+    } else {
+        const __half h = __float2half_rn(x);
+        *reinterpret_cast<__half*>(yh + o) = h;
+        *reinterpret_cast<__half*>(yl + o) = __float2half_rn(x - __half2float(h));
+    }
+}
+
+// |z|^2 of two samples with the packed FP32 pipe: re^2 rounded, then + im^2 fused.
+__device__ __forceinline__ void zsq2(uint32_t re0, uint32_t re1, uint32_t im0, uint32_t im1, float& p0, float& p1) {
+    asm("{\n\t.reg .b64 r, i, p;\n\t"
+        "mov.b64 r, {%2, %3};\n\tmov.b64 i, {%4, %5};\n\t"
+        "mul.rn.f32x2 p, r, r;\n\tfma.rn.f32x2 p, i, i, p;\n\t"
+        "mov.b64 {%0, %1}, p;\n\t}"
+        : "=f"(p0), "=f"(p1)
+        : "r"(re0), "r"(re1), "r"(im0), "r"(im1));
+}
+// The same, as a volatile statement: recomputed where needed instead of kept live in registers.
+__device__ __forceinline__ void zsq2_again(uint32_t re0, uint32_t re1, uint32_t im0, uint32_t im1, float& p0, float& p1) {
+    asm volatile("{\n\t.reg .b64 r, i, p;\n\t"
+                 "mov.b64 r, {%2, %3};\n\tmov.b64 i, {%4, %5};\n\t"
+                 "mul.rn.f32x2 p, r, r;\n\tfma.rn.f32x2 p, i, i, p;\n\t"
+                 "mov.b64 {%0, %1}, p;\n\t}"
+                 : "=f"(p0), "=f"(p1)
+                 : "r"(re0), "r"(re1), "r"(im0), "r"(im1));
+}
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+// Eq. 7-8 composed into one polyphase filter, for one time row and NV chunks of 8
+// columns of a slice piece: acc[8c + j] = sum_q R[r0 - D q] Y[q][8c + j] over the
+// staged rows q in [qa, qb] (rr = R + r0, yp = the piece's staged rows).  The tap is
+// loaded once for all chunks.
+template <int NV>
+__device__ __forceinline__ void f0_taps(const float* yp, int pitch, const float* rr, int D, int qa, int qb,
+                                        float (&acc)[8 * NV]) {
+#pragma unroll
+    for (int j = 0; j < 8 * NV; ++j) acc[j] = 0.f;
+#pragma unroll 2
+    for (int qi = qa; qi <= qb; ++qi) {
+        const float wq = rr[-D * qi];
+        const float* y = yp + qi * pitch;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            const float4 a = *reinterpret_cast<const float4*>(y + 8 * c);
+            const float4 b = *reinterpret_cast<const float4*>(y + 8 * c + 4);
+            acc[8 * c + 0] = fmaf(a.x, wq, acc[8 * c + 0]); acc[8 * c + 1] = fmaf(a.y, wq, acc[8 * c + 1]);
+            acc[8 * c + 2] = fmaf(a.z, wq, acc[8 * c + 2]); acc[8 * c + 3] = fmaf(a.w, wq, acc[8 * c + 3]);
+            acc[8 * c + 4] = fmaf(b.x, wq, acc[8 * c + 4]); acc[8 * c + 5] = fmaf(b.y, wq, acc[8 * c + 5]);
+            acc[8 * c + 6] = fmaf(b.z, wq, acc[8 * c + 6]); acc[8 * c + 7] = fmaf(b.w, wq, acc[8 * c + 7]);
+        }
+    }
+}
+
+// A piece's outputs for this thread's row: nc columns from packed column col0 on.
+template <bool BF16, int NV>
+__device__ __forceinline__ void f0_piece(const float* yp, int pitch, const float* rr, int D, int qa, int qb, int nc,
+                                         int col0, int row, uint8_t* yh, uint8_t* yl) {
+    float acc[8 * NV];
+    f0_taps<NV>(yp, pitch, rr, D, qa, qb, acc);
+#pragma unroll
+    for (int j = 0; j < 8 * NV; ++j) {
+        if (j < nc) {
+            const int col = col0 + j;
+            put_hilo<BF16>(yh, yl, (col >> 3) * 2048 + row * 16 + (col & 7) * 2, acc[j]);
+        }
+    }
+}
+
 template <bool BF16, bool STORE_Z>
 __global__ void __launch_bounds__(kF0Threads, 1)
     k_f0_top(const F0Job* __restrict__ jobs, const F0Maps* __restrict__ maps, const YupSlice* __restrict__ slices,
@@ -97,7 +187,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
     // overlap the window also needs the tail of the tile before it: the partial ring then)
     const bool aligned = (k_a % window) == 0 && tail.ov == 0;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // 1 KB aligned, still a shared pointer
     uint8_t* cst = smem;                                   // CSTAGES x CSTAGE
     uint8_t* ybuf = cst + C::CSTAGES * C::CSTAGE;          // ybufs x [hi, lo][kc / 8][128][8]
     const int yplane = 128 * kc * 2;
@@ -142,17 +232,21 @@ __global__ void __launch_bounds__(kF0Threads, 1)
 
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
+            // A stage is free again once the MMAs that read it are done: the issuer commits to
+            // cempty after every chunk but a template group's last, whose stage the epilogue
+            // group frees when it sees the group's accumulator (a commit costs the tensor pipe
+            // about as much as a few MMAs).  Either way one arrival per use of the stage.
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
             for (int u = ub; u < ue && ok; ++u) {
                 const int it = sched[gridDim.x + 1 + u];
                 const F0Unit un = units[it / n_det_push];
-                const F0Job& jb = jobs[un.job];
+                const F0Job jb = jobs[un.job];                 // a copy: the asm "memory" clobbers would reload it
                 const F0Maps* mp = maps + jb.map;
                 const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
                 for (int tt = t0; tt < t1 && ok; ++tt)
-                    for (int tm = 0; tm < jb.tiles_m && ok; ++tm)
+                    for (int tm = 0; tm < jb.tiles_m && ok; ++tm) {
                         for (int kc0 = 0; kc0 < jb.K; kc0 += 32) {
                             if (!mbar_wait(cempty + stage, phase ^ 1, err, 61)) { ok = false; break; }
                             uint8_t* sb = cst + stage * C::CSTAGE;
@@ -162,8 +256,9 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                                 tma_load_4d(sb + pl * C::CPLANE, &mp->c, cfull + stage, 0, tm * 4, kc0 >> 3, pl);
                             if (++stage == C::CSTAGES) { stage = 0; phase ^= 1; }
                         }
+                    }
             }
-            for (int s = 0; s < C::CSTAGES; ++s) {
+            for (int s2 = 0; s2 < C::CSTAGES && ok; ++s2) {
                 if (!mbar_wait(cempty + stage, phase ^ 1, err, 62)) break;
                 if (++stage == C::CSTAGES) { stage = 0; phase ^= 1; }
             }
@@ -177,7 +272,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
             for (int u = ub; u < ue && ok; ++u) {
                 const int it = sched[gridDim.x + 1 + u];
                 const F0Unit un = units[it / n_det_push];
-                const F0Job& jb = jobs[un.job];
+                const F0Job jb = jobs[un.job];                 // a copy: the asm "memory" clobbers would reload it
                 const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
                 const int k16 = jb.K / 16;
                 for (int tt = t0; tt < t1 && ok; ++tt, ++yi) {
@@ -211,7 +306,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                                     umma_f16(d_im, desc_win(sb + 3 * C::CPLANE + ao), desc_win(y_hi + bo), idesc, 1u);
                                 }
                             }
-                            umma_commit(cempty + stage);
+                            if (kc0 + 32 < jb.K) umma_commit(cempty + stage);   // the last: the epilogue frees it
                             if (++stage == C::CSTAGES) { stage = 0; phase ^= 1; }
                         }
                         if (!ok) break;
@@ -229,7 +324,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
         // Per unit: the slices' composed upsamplers are staged once.  Per tile: the rows of Y
         // each slice reaches are staged in FP32 for a batch of (slice, 32-column) pieces at a
         // time (all loads of a batch in flight together), then each thread forms its time
-        // row's outputs from shared memory and emits them in column order.
+        // row's outputs from shared memory, a piece at a time, and stores their hi/lo halves.
         const int row = threadIdx.x - 64;                  // 0..127: time row of the tile
         constexpr int NB = 32 * kF0Builders;
         int yi = 0;
@@ -243,16 +338,18 @@ __global__ void __launch_bounds__(kF0Threads, 1)
             const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
             bsync();                                        // the previous unit's tables are free
             if (row == 0) {
-                int roff = 0;
+                int roff = 0, col = 0;
                 for (int q = 0; q < jb.ns; ++q) {
                     const YupSlice sl = slices[jb.s0 + q];
                     F0SliceS& t = stab[q];
                     t.y_hi = sl.y_hi + det * sl.y_det_stride;
                     t.y_lo = sl.y_lo + det * sl.y_det_stride;
                     t.y_rows = sl.y_rows; t.y_ld = sl.y_ld; t.D = sl.D; t.e_min = sl.e_min; t.rlen = sl.rlen;
-                    t.L = sl.L; t.roff = roff;
+                    t.L = sl.L; t.roff = roff; t.col0 = col;
                     roff += sl.rlen;
+                    col += sl.L;
                 }
+                bends[kF0MaxPieces + 3] = col;              // the bank's basis count; columns up to K are zero
             }
             bsync();
             for (int q = 0; q < jb.ns; ++q) {
@@ -302,24 +399,10 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                     bends[0] = nbat;
                 }
                 bsync();
-                float v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = 0.f;
-                int col = 0;
-                auto emit = [&](float x) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (j == (col & 7)) v[j] = x;
-                    if ((col & 7) == 7) {
-                        uint32_t h[4], w[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) split_hilo2<BF16>(v[2 * j], v[2 * j + 1], h[j], w[j]);
-                        const int o = (col >> 3) * 2048 + row * 16;
-                        *reinterpret_cast<uint4*>(yh + o) = make_uint4(h[0], h[1], h[2], h[3]);
-                        *reinterpret_cast<uint4*>(yl + o) = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
-                    ++col;
-                };
+                if (tt - t0 < ybufs) {                      // first use of this buffer in the unit: zero the padding
+                    for (int col = bends[kF0MaxPieces + 3]; col < jb.K; ++col)
+                        put_hilo<BF16>(yh, yl, (col >> 3) * 2048 + row * 16 + (col & 7) * 2, 0.f);
+                }
                 const int nbat = bends[0];
                 for (int bt = 0, p0 = 0; bt < nbat; ++bt) {
                     const int p1 = bends[1 + bt];
@@ -347,51 +430,35 @@ __global__ void __launch_bounds__(kF0Threads, 1)
 #pragma unroll
                         for (int uu = 0; uu < 4; ++uu) {
                             if (dst[uu] < 0) continue;
-                            const uint16_t* hp = reinterpret_cast<const uint16_t*>(&hv[uu]);
-                            const uint16_t* lp = reinterpret_cast<const uint16_t*>(&lv[uu]);
-                            float x[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) x[j] = hilo_value<BF16>(hp[j], lp[j]);
+                            const float2 x0 = hilo_pair<BF16>(hv[uu].x, lv[uu].x);
+                            const float2 x1 = hilo_pair<BF16>(hv[uu].y, lv[uu].y);
+                            const float2 x2 = hilo_pair<BF16>(hv[uu].z, lv[uu].z);
+                            const float2 x3 = hilo_pair<BF16>(hv[uu].w, lv[uu].w);
                             float4* d4 = reinterpret_cast<float4*>(ys + dst[uu]);
-                            d4[0] = make_float4(x[0], x[1], x[2], x[3]);
-                            d4[1] = make_float4(x[4], x[5], x[6], x[7]);
+                            d4[0] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                            d4[1] = make_float4(x2.x, x2.y, x3.x, x3.y);
                         }
                     }
                     bsync();
                     for (int pi = p0; pi < p1; ++pi) {
                         const F0Piece pc = ptab[pi];
-                        // the slice's fields in registers (the stores below must not make them reload)
-                        const int D = stab[pc.s].D, rlen = stab[pc.s].rlen, nq = stab[pc.s].nq;
-                        const int e_min = stab[pc.s].e_min, roff = stab[pc.s].roff;
-                        const long long q_lo = stab[pc.s].q_lo;
-                        const int r0 = (int)(k0 + row - D * q_lo - e_min);   // R index of (row, q_lo)
-                        const int qa = max(0, (r0 - rlen + D) / D), qb = min(nq - 1, r0 / D);
-                        const float* rr = rsm + roff + r0;
+                        const F0SliceS& t = stab[pc.s];
+                        const int D = t.D;
+                        const int r0 = (int)(k0 + row - D * t.q_lo - t.e_min);   // R index of (row, q_lo)
+                        const int qa = max(0, (r0 - t.rlen + D) / D), qb = min(t.nq - 1, r0 / D);
+                        const float* rr = rsm + t.roff + r0;
                         const float* yp = ys + pc.off;
-                        const int pitch = pc.pitch, nv = pc.nv, nc = pc.nc;
-                        for (int c8 = 0; c8 < nv; ++c8) {
-                            float acc[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) acc[j] = 0.f;
-#pragma unroll 4
-                            for (int qi = qa; qi <= qb; ++qi) {
-                                const float wq = rr[-D * qi];
-                                const float4 a = *reinterpret_cast<const float4*>(yp + qi * pitch + 8 * c8);
-                                const float4 b4 = *reinterpret_cast<const float4*>(yp + qi * pitch + 8 * c8 + 4);
-                                acc[0] = fmaf(a.x, wq, acc[0]); acc[1] = fmaf(a.y, wq, acc[1]);
-                                acc[2] = fmaf(a.z, wq, acc[2]); acc[3] = fmaf(a.w, wq, acc[3]);
-                                acc[4] = fmaf(b4.x, wq, acc[4]); acc[5] = fmaf(b4.y, wq, acc[5]);
-                                acc[6] = fmaf(b4.z, wq, acc[6]); acc[7] = fmaf(b4.w, wq, acc[7]);
-                            }
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                if (8 * c8 + j < nc) emit(acc[j]);
+                        const int c0 = t.col0 + pc.c0;
+                        switch (pc.nv) {
+                            case 1: f0_piece<BF16, 1>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
+                            case 2: f0_piece<BF16, 2>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
+                            case 3: f0_piece<BF16, 3>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
+                            default: f0_piece<BF16, 4>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
                         }
                     }
                     bsync();                                // the staging is free for the next batch
                     p0 = p1;
                 }
-                while (col < jb.K) emit(0.f);
                 fence_proxy_async_smem();                   // generic-proxy stores -> tensor-core reads
                 mbar_arrive(yfull + yb);
             }
@@ -405,12 +472,14 @@ __global__ void __launch_bounds__(kF0Threads, 1)
         const int grp = (warp - 2 - kF0Builders) >> 2;
         const int rowm = qd * 32 + lane;
         uint32_t nuse = 0;                                  // uses of this group's buffer
+        long long chunks = 0;                               // coefficient chunks of the CTA's earlier units
         for (int u = ub; u < ue; ++u) {
             const int it = sched[gridDim.x + 1 + u];
             const int det = det0 + it % n_det_push;
             const F0Unit un = units[it / n_det_push];
-            const F0Job& jb = jobs[un.job];
+            const F0Job jb = jobs[un.job];                 // a copy: the asm "memory" clobbers would reload it
             const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
+            const int nch = (jb.K + 31) / 32;                // coefficient chunks per template group
             float gbest = -1.f;                             // bank maximum of this thread's rows
             int gm = 0x7fffffff;
             bool fail = false;
@@ -420,13 +489,25 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                     ++nuse;
                     if (!got) { fail = true; break; }
                     tc_fence_after();
+                    if (qd == 0 && lane == 0) {             // the MMAs have read the group's last chunk
+                        const long long last = chunks + ((long long)(tt - t0) * jb.tiles_m + tm + 1) * nch - 1;
+                        mbar_arrive(cempty + (int)(last % C::CSTAGES));
+                    }
                     const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + grp * 256;
                     const int m = tm * 128 + rowm;
                     const long long k0 = k_a + 128LL * tt;
                     const bool pre = tail.ov > 0 && (k0 + 128) % window == 0;   // the next window's overlap
                     const int tail_from = pre ? 128 - tail.ov : 128;
+                    const long long kwin0 = (k0 / window) * window;
+                    const int kb = (int)(k0 - kwin0);          // the tile's first sample in its window
+                    // best: the tile's maximum, or with whole windows the window's so far (then a
+                    // chunk is searched for its sample only when it beats the window, not the tile)
                     float best = -1.f, bre = 0.f, bim = 0.f, tbest = -1.f, tre = 0.f, tim = 0.f;
-                    int bk = 0x7fffffff, tk = 0x7fffffff;
+                    int bk = 0x7fffffff, tk = 0x7fffffff;      // bk: offset in the window
+                    if (aligned && tt > t0) {
+                        const float4 prev = rs[tm * 128 + rowm];
+                        best = prev.x; bk = __float_as_int(prev.y); bre = prev.z; bim = prev.w;
+                    }
 #pragma unroll 1
                     for (int c = 0; c < 128; c += 32) {
                         uint32_t ru[32], iu[32];            // re and im of 32 samples: both loads, one wait
@@ -435,23 +516,24 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                         tmem_wait_ld();
                         // |z|^2 and its maximum first; the sample (the first that reaches it) and its
                         // re, im only when the chunk beats what came before (earlier samples win ties)
-                        float pz[32], t16[16];
+                        float ma = -1.f, mb = -1.f;          // two chains of three-way maxima
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float re = __uint_as_float(ru[j]), im = __uint_as_float(iu[j]);
-                            pz[j] = re * re + im * im;
+                        for (int j = 0; j < 32; j += 4) {
+                            float p0, p1, p2, p3;
+                            zsq2(ru[j], ru[j + 1], iu[j], iu[j + 1], p0, p1);
+                            zsq2(ru[j + 2], ru[j + 3], iu[j + 2], iu[j + 3], p2, p3);
+                            ma = fmax3f(ma, p0, p1);
+                            mb = fmax3f(mb, p2, p3);
                         }
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) t16[j] = fmaxf(pz[j], pz[j + 16]);
-#pragma unroll
-                        for (int h = 8; h > 0; h >>= 1)
-#pragma unroll
-                            for (int j = 0; j < h; ++j) t16[j] = fmaxf(t16[j], t16[j + h]);
-                        const float mx = t16[0];
-                        if (mx > best) {
+                        const float mx = fmaxf(ma, mb);
+                        if (mx > best) {                     // |z|^2 again (same bits) to find the sample
                             uint32_t eq = 0;
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) eq |= (pz[j] == mx ? 1u : 0u) << j;
+                            for (int j = 0; j < 32; j += 2) {
+                                float p0, p1;
+                                zsq2_again(ru[j], ru[j + 1], iu[j], iu[j + 1], p0, p1);
+                                eq |= ((p0 == mx ? 1u : 0u) | (p1 == mx ? 2u : 0u)) << j;
+                            }
                             const int jj = __ffs(eq) - 1;
                             float sr = 0.f, si = 0.f;
 #pragma unroll
@@ -460,16 +542,22 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                                 si = j == jj ? __uint_as_float(iu[j]) : si;
                             }
                             best = mx;
-                            bk = c + jj;
+                            bk = kb + c + jj;
                             bre = sr;
                             bim = si;
                         }
                         if (pre) {                           // the tail of a tile before a window start
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (c + j >= tail_from && pz[j] > tbest) {
-                                    tbest = pz[j]; tk = c + j; tre = __uint_as_float(ru[j]); tim = __uint_as_float(iu[j]);
-                                }
+                            for (int j = 0; j < 32; j += 2) {
+                                float pp[2];
+                                zsq2_again(ru[j], ru[j + 1], iu[j], iu[j + 1], pp[0], pp[1]);
+#pragma unroll
+                                for (int h = 0; h < 2; ++h)
+                                    if (c + j + h >= tail_from && pp[h] > tbest) {
+                                        tbest = pp[h]; tk = c + j + h;
+                                        tre = __uint_as_float(ru[j + h]); tim = __uint_as_float(iu[j + h]);
+                                    }
+                            }
                         }
                         if (STORE_Z && m < jb.M) {
                             float* zr = zout + (long long)(2 * m) * n + 128LL * tt + c;
@@ -481,13 +569,11 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                     tc_fence_before();
                     mbar_arrive(tempty + grp);
                     if (STORE_Z) continue;
-                    const long long kwin0 = (k0 / window) * window;
-                    const int koff = (int)(k0 - kwin0) + bk;
                     if (!aligned) {
                         if (m < jb.M) {
                             const int slot = (int)((k0 / 128) & (n_slots - 1));
                             part[(long long)(jb.tmpl0 + m) * part_tmpl_stride + (long long)det * n_slots + slot] =
-                                make_float4(best, __int_as_float(koff), bre, bim);
+                                make_float4(best, __int_as_float(bk), bre, bim);
                             if (pre) {
                                 const long long w1 = (k0 + 128) / window;
                                 tail.p[(long long)(jb.tmpl0 + m) * tail.tmpl_stride + (long long)det * tail.n +
@@ -497,11 +583,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                         }
                         continue;
                     }
-                    float4 r = make_float4(best, __int_as_float(koff), bre, bim);
-                    if (tt > t0) {                           // earlier tiles win ties
-                        const float4 prev = rs[tm * 128 + rowm];
-                        if (!(best > prev.x)) r = prev;
-                    }
+                    const float4 r = make_float4(best, __int_as_float(bk), bre, bim);   // earlier tiles won ties
                     rs[tm * 128 + rowm] = r;
                     if (tt == t1 - 1 && t1 - t0 == tpw && m < jb.M) {   // the window is complete: its trigger slot
                         const long long w = kwin0 / window;
@@ -521,6 +603,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                     }
                 }
             }
+            chunks += (long long)(t1 - t0) * jb.tiles_m * nch;
             if (STORE_Z) {
                 if (fail) break;
                 continue;

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(192, 1)
     using C = FirCfg<BF16>;
     pdl_launch_dependents();
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // 1 KB aligned, still a shared pointer
     uint8_t* stage_area = smem;
     uint8_t* strip_area = smem + n_stages * C::STAGE_BYTES;                // 2 buffers x (hi, lo) x strip_bytes
     uint16_t* epi = reinterpret_cast<uint16_t*>(strip_area + 4 * strip_bytes);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(192, 1)
                 const int it = sched[gridDim.x + 1 + k];
                 const int det = det0 + it % n_det_push;
                 const TileInfo ti = tinfo[it / n_det_push];
-                const FirTcJob& jb = jobs[ti.x];
+                const FirTcJob jb = jobs[ti.x];   // a copy: the asm "memory" clobbers would reload it
                 const int local = ti.y;
                 const int mt = local % jb.Mtiles, ct = local / jb.Mtiles;
                 const long long qa = fdiv(k_a - 1 + jb.Lambda, jb.D) + 1;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(192, 1)
             const int it = sched[gridDim.x + 1 + k];
             const int det = det0 + it % n_det_push;
             const TileInfo ti = tinfo[it / n_det_push];
-            const FirTcJob& jb = jobs[ti.x];
+            const FirTcJob jb = jobs[ti.x];   // a copy: the asm "memory" clobbers would reload it
             const int local = ti.y;
             const int mt = local % jb.Mtiles, ct = local / jb.Mtiles;
             const long long qa = fdiv(k_a - 1 + jb.Lambda, jb.D) + 1;
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
     constexpr int NWC = win_chunks(F);
     constexpr int NK16 = (win_rows(F) + win_shift_max(F) + 15) / 16;   // K steps of 16 rows that U can reach
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // 1 KB aligned, still a shared pointer
     uint8_t* stg = smem + C::STAGES * C::STAGE_BYTES;
     float4* xchg = reinterpret_cast<float4*>(stg + C::STG);
     uint64_t* full = reinterpret_cast<uint64_t*>(stg + C::STG + C::XCHG);
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
                 const int it = sched[gridDim.x + 1 + k];
                 const int det = det0 + it % n_det_push;
                 const TileInfo ti = tinfo[it / n_det_push];
-                const LevelJob& jb = jobs[ti.x];
+                const LevelJob jb = jobs[ti.x];   // a copy: the asm "memory" clobbers would reload it
                 const LevelMaps* mp = maps + jb.map;
                 const int local = ti.y;
                 const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(LevCfg<BF16, TOP>::THREADS, 1)
             const int it = sched[gridDim.x + 1 + k];
             const int det = det0 + it % n_det_push;
             const TileInfo ti = tinfo[it / n_det_push];
-            const LevelJob& jb = jobs[ti.x];
+            const LevelJob jb = jobs[ti.x];   // a copy: the asm "memory" clobbers would reload it
             const int local = ti.y;
             const int tm = local % jb.tiles_m, tt = local / jb.tiles_m;
             const int buf = i & 1;
@@ -724,11 +724,5 @@ struct YupSlice {
     int tcol;                      // first column of the slice in the packed f0 ring
     int pad;
 };
-template <bool BF16>
-__device__ __forceinline__ float hilo_value(uint16_t h, uint16_t w) {
-    if (BF16) return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(&h)) +
-                     __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(&w));
-    return __half2float(*reinterpret_cast<const __half*>(&h)) + __half2float(*reinterpret_cast<const __half*>(&w));
-}
 
 }  // namespace lloid

@@ -732,6 +732,11 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             CK(cudaFuncSetAttribute(k_f0_top<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             CK(cudaFuncSetAttribute(k_f0_top<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         }
+        int fit = 0;   // registers (the kernel's cap) and shared memory of one CTA on one SM
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, bf ? k_f0_top<true, false> : k_f0_top<false, false>,
+                                                         kF0Threads, smem));
+        if (fit < 1) return fail(ctx, LLOID_ECUDA, "the f0-form kernel (%d threads, %d B shared) does not fit an SM",
+                                 kF0Threads, smem);
     }
     lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_firtc, fj)) || (st = upload_vec(ctx, &ctx->d_firmaps, fm)) ||
