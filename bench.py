@@ -72,6 +72,9 @@ def parse():
     p.add_argument("--serve-block", type=int, default=2048)
     p.add_argument("--pace", type=float, default=1.0)
     p.add_argument("--serve-seconds", type=int, default=60)
+    p.add_argument("--serve-blocks", type=int, default=None, help="blocks to stream (overrides --serve-seconds)")
+    p.add_argument("--no-serve-summary", action="store_true",
+                   help="skip the short 10x-pace serving run of the default bench line")
     p.add_argument("--form", default=None, choices=["ladder", "f0"],
                    help="force every bank into one form of the split path (default: per-bank choice)")
     p.add_argument("--no-autotune", action="store_true",
@@ -493,46 +496,80 @@ def run_lloid(args, rank, world, dist):
     def load_all(ctx, which=None):
         return [ctx.load_bank(banks_sb[i]) for i in (range(len(banks_sb)) if which is None else which)]
 
-    if args.serve:
+    def serve_measure(block, pace, n_serve):
+        """The streaming loop (serving.Server) over the bank set: every bank is submitted,
+        admitted under the HBM budget, the FIR history filled at full speed, then n_serve
+        blocks of `block` samples from every detector arrive at `pace` times real time.
+        Latency: block arrival -> the triggers of the windows it completes on the host."""
         from paper_2511_04730_b300.serving import Server
-        SB = args.serve_block
-        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=SB, max_history=max_hist, device=dev,
-                        form=args.form)
-        srv = Server(ctx, SB)
+        ctx = P.Context(n_detectors=n_det, precision=args.precision, max_block=block, max_history=max_hist,
+                        device=dev, form=args.form)
+        srv = Server(ctx, block)
         for i, x in enumerate(banks_sb):
             srv.submit(x, tag=i)
-        nb = T // SB
-        blocks_s = np.ascontiguousarray(strain.reshape(n_det, nb, SB).transpose(1, 0, 2))
+        nb = T // block
+        blocks_s = np.ascontiguousarray(strain.reshape(n_det, nb, block).transpose(1, 0, 2))
         src = lambda k: blocks_s[k % nb]
-        warm = max_hist // SB + 4
+        warm = max_hist // block + 4
         for k in range(warm):                          # admit every bank and fill the history
             srv.step(src(k))
         srv.latency_ms.clear()
-        n_serve = args.serve_seconds * F0 // SB
         t0 = time.perf_counter()
-        srv.run_paced(lambda k: src(warm + k), n_serve, pace=args.pace)
+        srv.run_paced(lambda k: src(warm + k), n_serve, pace=pace)
         wall = time.perf_counter() - t0
         ctx.close()
+        return {"block_seconds": block / F0, "pace": pace, "blocks": n_serve, "latency_ms": srv.latency_summary(),
+                "seconds_streamed": n_serve * block / F0, "wall_s": round(wall, 2),
+                "template_s_per_s": M * n_det * n_serve * block / F0 / wall,
+                "data": f"the workload's {T // F0} s of strain per detector, cycled"}
+
+    if args.serve:
+        res = serve_measure(args.serve_block, args.pace, args.serve_blocks or args.serve_seconds * F0 // args.serve_block)
         if rank == 0:
-            lat = srv.latency_summary()
             print(json.dumps({
                 "mode": "serve", "metric": "per-block latency (block arrival -> its windows' triggers on the host)",
-                "latency_ms": lat, "block_seconds": SB / F0, "pace": args.pace, "seconds_streamed": n_serve * SB / F0,
-                "wall_s": wall, "template_s_per_s": M * n_det * n_serve * SB / F0 / wall,
-                "n_templates": M, "n_banks": len(banks_sb), "n_detectors": n_det, "precision": args.precision,
+                **res, "n_templates": M, "n_banks": len(banks_sb), "n_detectors": n_det, "precision": args.precision,
                 "workload": WORKLOADS[args.workload]}), flush=True)
         return
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
 
-    def run_steps(ctx, k_steps, pos, host=False, lat=None, lag=0):
+    def run_steps(ctx, k_steps, pos, host=False, lat=None, lag=0, pipelined=False):
         """k_steps timed steps; returns (ms per step list, pos, launches, h2d, d2h).
         lag = 1: pull the windows that became ready (xi2 needs d samples of the
-        next block), i.e. the previous block's last window and this block's others."""
+        next block), i.e. the previous block's last window and this block's others.
+        pipelined: each step's pull is submitted behind its push and collected after
+        the next push (the host reads a block's triggers while the GPU filters the
+        next); the K steps are timed as one region and every pull is collected in it."""
         ext = torch.cuda.ExternalStream(ctx.stream_ptr, device=f"cuda:{dev}")
         ms, h2d, d2h = [], 0, 0
         l0 = ctx.launch_count()
         with torch.cuda.stream(ext):
+            if pipelined:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                tickets = []
+                a.record(ext)
+                for _ in range(k_steps):
+                    flush.fill_(pos & 0xFF)                   # L2 flush, inside the region
+                    k = (pos // B) % n_blk
+                    if host:
+                        blk = h_blocks[k].numpy()
+                        ctx.push_all(pos, blk)
+                        h2d += blk.nbytes
+                    else:
+                        ctx.push_all(pos, d_blocks[k])
+                    w_lo = max(0, pos // F0 - lag)
+                    tickets.append(ctx.pull_submit(w_lo, n_windows=(pos + B) // F0 - lag - w_lo))
+                    if len(tickets) > 1:
+                        d2h += 8 + ctx.pull_collect(tickets.pop(0)).nbytes
+                    pos += B
+                for t in tickets:
+                    d2h += 8 + ctx.pull_collect(t).nbytes
+                b.record(ext)
+                b.synchronize()
+                ms = [a.elapsed_time(b) / k_steps] * k_steps
+                return ms, pos, ctx.launch_count() - l0, h2d, d2h
             for _ in range(k_steps):
                 flush.fill_(pos & 0xFF)                       # L2 flush, outside the events
                 a = torch.cuda.Event(enable_timing=True)
@@ -567,14 +604,14 @@ def run_lloid(args, rank, world, dist):
         form_of.append(f)
         forms[f] = forms.get(f, 0) + 1
     pos = 0
-    _, pos, _, _, _ = run_steps(ctx, args.warmup, pos)
+    _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, pipelined=True)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(dev)
     sampler.start()
     sampler.begin()
-    ms, pos, launches, _, _ = run_steps(ctx, args.steps, pos)
+    ms, pos, launches, _, _ = run_steps(ctx, args.steps, pos, pipelined=True)
     torch.cuda.synchronize()
     sampler.end()
     clocks = sampler.stop()
@@ -598,8 +635,8 @@ def run_lloid(args, rank, world, dist):
         ctx = make_ctx(args.precision, False)
         load_all(ctx)
         pos = 0
-        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, host=True)
-        ms_e, pos, _, h2d, d2h = run_steps(ctx, args.steps, pos, host=True)
+        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, host=True, pipelined=True)
+        ms_e, pos, _, h2d, d2h = run_steps(ctx, args.steps, pos, host=True, pipelined=True)
         ctx.close()
         e2e = {"value": M * args.block_seconds * n_det * args.steps / (sum(ms_e) / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
@@ -612,8 +649,8 @@ def run_lloid(args, rank, world, dist):
         ctx = make_ctx("fp32", timing=False)
         load_all(ctx)
         pos = 0
-        _, pos, _, _, _ = run_steps(ctx, 1, pos)
-        ms32, pos, _, _, _ = run_steps(ctx, k32, pos)
+        _, pos, _, _, _ = run_steps(ctx, 1, pos, pipelined=True)
+        ms32, pos, _, _, _ = run_steps(ctx, k32, pos, pipelined=True)
         ctx.close()
         paths["fp32"] = M * args.block_seconds * n_det * k32 / (sum(ms32) / 1000.0)
         paths["fp32_steps"] = k32
@@ -675,10 +712,10 @@ def run_lloid(args, rank, world, dist):
         for x, ac in zip(banks_sb, acs):
             ctx.load_bank(x, autocorr=ac)
         pos = 0
-        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, lag=1)
+        _, pos, _, _, _ = run_steps(ctx, args.warmup, pos, lag=1, pipelined=True)
         ctx.stage_times(reset=True)
         torch.cuda.synchronize()
-        ms_x, pos, _, _, d2h_x = run_steps(ctx, args.steps, pos, lag=1)
+        ms_x, pos, _, _, d2h_x = run_steps(ctx, args.steps, pos, lag=1, pipelined=True)
         st_x = ctx.stage_times(reset=True)
         ctx.close()
         units_x = M * args.block_seconds * n_det
@@ -795,6 +832,12 @@ def run_lloid(args, rank, world, dist):
                 "algorithmic_per_launch": d["algorithmic_per_launch"], "launch_ms": d["launch_ms"]}
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items()}
 
+    # a short run of the streaming loop at 10x real time (the full serving measurement is --serve)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve_summary:
+        serving = {"0.25s_blocks_10x": serve_measure(F0 // 4, 10.0, 800),
+                   "1s_blocks_10x": serve_measure(F0, 10.0, 200)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -804,7 +847,8 @@ def run_lloid(args, rank, world, dist):
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "n_templates": M, "n_banks": len(banks_sb),
                        "n_detectors": n_det, "block_seconds": args.block_seconds, "precision": args.precision,
-                       "l2": "flushed between steps (256 MB write, outside the timed events)",
+                       "l2": "flushed between steps (256 MB write on the stream, inside the timed region)",
+                       "pulls": "each step's triggers submitted behind its push, collected after the next push",
                        "bases_total": sum(s.n_basis for x in banks_sb for s in x), "bank_forms": forms,
                        "parallelism": (f"replicas x{world}" if len(all_banks) == 1 else f"bank shards x{world}")},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
@@ -817,6 +861,7 @@ def run_lloid(args, rank, world, dist):
             "stage_ms_per_step": stage_ms,
             "ms_per_step_with_stage_events": statistics.mean(ms_t),
             "kernels": per_stage,
+            "serving": serving,
             "autotune": tune_info,
             "xi2": xi2,
             "whiten": whiten,

@@ -243,6 +243,27 @@ LLOID_API lloid_status lloid_pull_triggers(lloid_ctx* ctx, int64_t window, lloid
 LLOID_API lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_trigger* out,
                                                  int64_t cap, int64_t* n_out, int32_t timeout_ms);
 
+/* A pull in two halves, so that the host can read one block's triggers while the
+ * GPU filters the next.  lloid_pull_submit checks windows w0 .. w0 + n_windows - 1
+ * as lloid_pull_triggers_range does (EINVAL, ENOTREADY, EEXPIRED), enqueues their
+ * compaction and the copy to pinned host memory behind the pushes already
+ * enqueued, and returns at once with *ticket (0..7).  At most 8 pulls are
+ * submitted and not yet collected: EINVAL for a ninth.  The list is the one the
+ * blocking pull would return at the time of the submit: later pushes do not
+ * change it. */
+LLOID_API lloid_status lloid_pull_submit(lloid_ctx* ctx, int64_t w0, int64_t n_windows, int32_t* ticket);
+
+/* Waits up to timeout_ms (< 0: forever) for a submitted pull and copies its
+ * triggers into the host array out[cap], ordered as lloid_pull_triggers_range
+ * orders them.  ETIMEOUT if the copy has not landed (the ticket stays valid) or
+ * a kernel wait expired; ERANGE if cap is too small (*n_out = the number needed,
+ * nothing copied, the ticket stays valid).  Otherwise the ticket is released.  A
+ * list longer than the part copied at submit time is read from the device; if
+ * another pull has compacted since, its windows are compacted again, which
+ * needs them still retained (EEXPIRED otherwise). */
+LLOID_API lloid_status lloid_pull_collect(lloid_ctx* ctx, int32_t ticket, lloid_trigger* out, int64_t cap,
+                                          int64_t* n_out, int32_t timeout_ms);
+
 /* Coincident events of windows w0 .. w0 + n_windows - 1 (1 <= n_windows <=
  * 16), ordered by window then bank: at most one per (bank, window), formed on
  * the GPU from the windows' triggers of all detectors (Sections II.D.3-4).

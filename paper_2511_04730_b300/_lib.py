@@ -109,6 +109,10 @@ SIGNATURES = [
     ("lloid_pull_triggers_range", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                  ctypes.POINTER(LloidTrigger), ctypes.c_int64,
                                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("lloid_pull_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int32)]),
+    ("lloid_pull_collect", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(LloidTrigger),
+                                          ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     ("lloid_snr_block", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("lloid_synchronize", ctypes.c_int, [ctypes.c_void_p]),

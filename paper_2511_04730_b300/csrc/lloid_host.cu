@@ -163,11 +163,23 @@ struct lloid_ctx {
     TriggerOut* d_trig = nullptr;
     long long trig_cap = 0;
     long long* d_total = nullptr;
-    long long* h_total = nullptr;
-    int* h_err = nullptr;                  // pinned copy of d_err taken by a pull
-    TriggerOut* h_trig = nullptr;          // pinned first part of a pulled list
-    long long h_trig_cap = 0, last_pull = 0;
-    cudaEvent_t pull_ev = nullptr;
+    // Pulls: slot 0 serves the blocking pulls, slots 1..kPullSlots the submitted ones.
+    // A slot holds, in pinned memory, the error flag, the count and the first `want`
+    // triggers of its compacted list, copied behind the pushes on the stream.
+    struct PullSlot {
+        TriggerOut* h = nullptr;           // first part of the list
+        long long cap = 0, want = 0;
+        long long* h_total = nullptr;
+        int* h_err = nullptr;
+        cudaEvent_t ev = nullptr;
+        long long w0 = 0, n_windows = 0;
+        unsigned long long seq = 0;        // gather number: d_trig still holds the list while it is the last
+        bool busy = false;
+    };
+    static constexpr int kPullSlots = 8;
+    PullSlot pull[kPullSlots + 1];
+    unsigned long long gather_seq = 0;
+    long long last_pull = 0;
 
     // job tables for the current push length
     bool jobs_dirty = true;
@@ -1813,9 +1825,11 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
     ctx->tiles_per_window = (int)(c.window_samples / kTileT);
     ctx->n_slots = (int)next_pow2(((c.max_block + c.window_samples - 1) / c.window_samples + 2) * ctx->tiles_per_window);
     ctx->n_tail = (int)next_pow2((c.max_block + c.window_samples - 1) / c.window_samples + 3);
-    CK(cudaHostAlloc((void**)&ctx->h_total, sizeof(long long), cudaHostAllocDefault));
-    CK(cudaHostAlloc((void**)&ctx->h_err, sizeof(int), cudaHostAllocDefault));
-    CK(cudaEventCreateWithFlags(&ctx->pull_ev, cudaEventDisableTiming));
+    for (auto& ps : ctx->pull) {
+        CK(cudaHostAlloc((void**)&ps.h_total, sizeof(long long), cudaHostAllocDefault));
+        CK(cudaHostAlloc((void**)&ps.h_err, sizeof(int), cudaHostAllocDefault));
+        CK(cudaEventCreateWithFlags(&ps.ev, cudaEventDisableTiming));
+    }
     if ((st = dalloc(ctx, &ctx->d_err, sizeof(int), nullptr, &ctx->state_bytes))) return st;
     if ((st = dalloc(ctx, &ctx->d_total, sizeof(long long), nullptr, &ctx->state_bytes))) return st;
     if ((st = ensure_template_capacity(ctx, 1024))) return st;
@@ -1840,10 +1854,12 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaFree(ctx->d_stage);
     for (int i = 0; i < 2; ++i) { cudaFreeHost(ctx->h_stage[i]); if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]); }
     cudaFree(ctx->d_part); cudaFree(ctx->d_tail); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_tmpl0_of);
-    cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total); cudaFreeHost(ctx->h_total);
-    cudaFreeHost(ctx->h_err); cudaFreeHost(ctx->h_trig);
+    cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total);
+    for (auto& ps : ctx->pull) {
+        cudaFreeHost(ps.h); cudaFreeHost(ps.h_total); cudaFreeHost(ps.h_err);
+        if (ps.ev) cudaEventDestroy(ps.ev);
+    }
     cudaFree(ctx->d_events); cudaFreeHost(ctx->h_events);
-    if (ctx->pull_ev) cudaEventDestroy(ctx->pull_ev);
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_zero);
     for (int r = 0; r <= kMaxRates; ++r) { cudaFree(ctx->s_hi[r]); cudaFree(ctx->s_lo[r]); }
@@ -2112,12 +2128,12 @@ lloid_status lloid_push_strain_all(lloid_ctx* ctx, int64_t t0, const float* bloc
     return push_common(ctx, 0, ctx->cfg.n_detectors, t0, blocks, n, is_device_ptr);
 }
 
-lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_trigger* out,
-                                       int64_t cap, int64_t* n_out, int32_t timeout_ms) {
-    if (!ctx) return LLOID_EINVAL;
-    if (!n_out || (cap > 0 && !out) || w0 < 0 || n_windows < 1 || n_windows > kWindowRing)
-        return fail(ctx, LLOID_EINVAL, "bad output arguments");
-    *n_out = 0;
+// Checks that windows w0 .. w0 + n_windows - 1 can be pulled now, then enqueues their
+// compaction (k_gather_count / k_gather_scatter into d_trig) and the copy of the error
+// flag, the count and the first `want` triggers into slot ps, and records the slot's event.
+static lloid_status pull_enqueue(lloid_ctx* ctx, long long w0, long long n_windows, lloid_ctx::PullSlot* ps,
+                                 long long want_at_least) {
+    if (w0 < 0 || n_windows < 1 || n_windows > kWindowRing) return fail(ctx, LLOID_EINVAL, "bad window range");
     const long long W = ctx->cfg.window_samples;
     const long long w1 = w0 + n_windows - 1;
     long long fin_min = ctx->fin[0], fin_max = ctx->fin[0];
@@ -2132,10 +2148,14 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
     if (w0 + kWindowRing <= fin_max) return fail(ctx, LLOID_EEXPIRED, "window %lld is no longer retained", (long long)w0);
     const int nd = ctx->cfg.n_detectors;
     const int M_used = ctx->M_used;
-    lloid_status st;
-    if (M_used == 0) {
-        if ((st = wait_done(ctx, timeout_ms))) return st;
-        return check_kernel_err(ctx);
+    ps->w0 = w0;
+    ps->n_windows = n_windows;
+    ps->want = 0;
+    if (M_used == 0) {   // nothing to compact: the error flag alone
+        *ps->h_total = 0;
+        CK(cudaMemcpyAsync(ps->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaEventRecord(ps->ev, ctx->stream));
+        return LLOID_OK;
     }
     const long long total = n_windows * nd * M_used;
     const int chunks = (int)((total + 1023) / 1024);
@@ -2151,17 +2171,16 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
         CK(cudaMalloc(&ctx->d_trig, total * sizeof(TriggerOut)));
         ctx->trig_cap = total;
     }
-    // Everything below is enqueued behind the pushes; the host waits once, for the
-    // error flag, the count and a first part of the list (sized from the last pull)
-    // in pinned memory, and copies the rest only when the list is longer.
-    const long long want = std::min<long long>(total, std::max<long long>(256, 2 * ctx->last_pull + 64));
-    if (want > ctx->h_trig_cap) {
-        CK(cudaStreamSynchronize(ctx->stream));
-        cudaFreeHost(ctx->h_trig);
-        ctx->h_trig = nullptr;
-        const long long cap2 = std::max<long long>(want, 2 * ctx->h_trig_cap);
-        CK(cudaHostAlloc((void**)&ctx->h_trig, cap2 * sizeof(TriggerOut), cudaHostAllocDefault));
-        ctx->h_trig_cap = cap2;
+    // the first part of the list, sized from the last pull (the rest is copied when needed)
+    const long long want = std::min<long long>(total, std::max<long long>({256, 2 * ctx->last_pull + 64, want_at_least}));
+    if (want > ps->cap) {
+        CK(cudaEventSynchronize(ps->ev));   // the slot's earlier copy is done with the buffer
+        const long long cap2 = std::max<long long>(want, 2 * ps->cap);
+        cudaFreeHost(ps->h);
+        ps->h = nullptr;
+        ps->cap = 0;
+        CK(cudaHostAlloc((void**)&ps->h, cap2 * sizeof(TriggerOut), cudaHostAllocDefault));
+        ps->cap = cap2;
     }
     {
         StageTimer tmg(ctx, 6);
@@ -2174,27 +2193,87 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
                       W, ctx->d_trig, ctx->trig_cap, ctx->d_total));
         ctx->launches += 2;
     }
-    CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_trig, ctx->d_trig, want * sizeof(TriggerOut), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaEventRecord(ctx->pull_ev, ctx->stream));
-    if ((st = wait_event(ctx, ctx->pull_ev, timeout_ms))) return st;
-    if (*ctx->h_err)
+    ps->want = want;
+    ps->seq = ++ctx->gather_seq;
+    CK(cudaMemcpyAsync(ps->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ps->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ps->h, ctx->d_trig, want * sizeof(TriggerOut), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ps->ev, ctx->stream));
+    return LLOID_OK;
+}
+
+// Waits for slot ps, then copies its list into out[cap].  A list longer than the slot's
+// first part takes the rest from d_trig when no later compaction has replaced it, or is
+// compacted again from the trigger slab (blocking) when one has.
+static lloid_status pull_finish(lloid_ctx* ctx, lloid_ctx::PullSlot* ps, lloid_trigger* out, int64_t cap,
+                                int64_t* n_out, int32_t timeout_ms) {
+    lloid_status st;
+    if ((st = wait_event(ctx, ps->ev, timeout_ms))) return st;
+    if (*ps->h_err)
         return fail(ctx, LLOID_ETIMEOUT, "a kernel wait expired (code %d); results of the last pushes are invalid",
-                    *ctx->h_err);
-    const long long cnt = *ctx->h_total;
+                    *ps->h_err);
+    const long long cnt = *ps->h_total;
     *n_out = cnt;
     ctx->last_pull = cnt;
     if (cnt > cap) return fail(ctx, LLOID_ERANGE, "%lld triggers, capacity %lld", cnt, (long long)cap);
     static_assert(sizeof(TriggerOut) == sizeof(lloid_trigger), "trigger layout");
-    const long long head = std::min(cnt, want);
-    if (head > 0) std::memcpy(out, ctx->h_trig, head * sizeof(lloid_trigger));
+    const long long head = std::min(cnt, ps->want);
+    if (head > 0) std::memcpy(out, ps->h, head * sizeof(lloid_trigger));
     if (cnt > head) {
+        if (ps->seq != ctx->gather_seq) {   // d_trig holds a later list: compact these windows again
+            lloid_ctx::PullSlot& s0 = ctx->pull[0];
+            if ((st = pull_enqueue(ctx, ps->w0, ps->n_windows, &s0, cnt))) return st;
+            return pull_finish(ctx, &s0, out, cap, n_out, timeout_ms);
+        }
         CK(cudaMemcpyAsync(out + head, ctx->d_trig + head, (cnt - head) * sizeof(lloid_trigger),
                            cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
     return LLOID_OK;
+}
+
+lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_windows, lloid_trigger* out,
+                                       int64_t cap, int64_t* n_out, int32_t timeout_ms) {
+    if (!ctx) return LLOID_EINVAL;
+    if (!n_out || (cap > 0 && !out) || w0 < 0 || n_windows < 1 || n_windows > kWindowRing)
+        return fail(ctx, LLOID_EINVAL, "bad output arguments");
+    *n_out = 0;
+    lloid_status st;
+    if (ctx->M_used == 0) {
+        if ((st = wait_done(ctx, timeout_ms))) return st;
+        return check_kernel_err(ctx);
+    }
+    lloid_ctx::PullSlot* ps = &ctx->pull[0];
+    if ((st = pull_enqueue(ctx, w0, n_windows, ps, 0))) return st;
+    return pull_finish(ctx, ps, out, cap, n_out, timeout_ms);
+}
+
+lloid_status lloid_pull_submit(lloid_ctx* ctx, int64_t w0, int64_t n_windows, int32_t* ticket) {
+    if (!ctx) return LLOID_EINVAL;
+    if (!ticket) return fail(ctx, LLOID_EINVAL, "null ticket");
+    *ticket = -1;
+    int k = 1;
+    while (k <= lloid_ctx::kPullSlots && ctx->pull[k].busy) ++k;
+    if (k > lloid_ctx::kPullSlots) return fail(ctx, LLOID_EINVAL, "%d pulls already submitted", lloid_ctx::kPullSlots);
+    lloid_status st;
+    if ((st = pull_enqueue(ctx, w0, n_windows, &ctx->pull[k], 0))) return st;
+    ctx->pull[k].busy = true;
+    *ticket = k - 1;
+    return LLOID_OK;
+}
+
+lloid_status lloid_pull_collect(lloid_ctx* ctx, int32_t ticket, lloid_trigger* out, int64_t cap, int64_t* n_out,
+                                int32_t timeout_ms) {
+    if (!ctx) return LLOID_EINVAL;
+    if (!n_out || (cap > 0 && !out)) return fail(ctx, LLOID_EINVAL, "bad output arguments");
+    *n_out = 0;
+    if (ticket < 0 || ticket >= lloid_ctx::kPullSlots || !ctx->pull[ticket + 1].busy)
+        return fail(ctx, LLOID_EINVAL, "no submitted pull with ticket %d", ticket);
+    lloid_ctx::PullSlot* ps = &ctx->pull[ticket + 1];
+    const lloid_status st = pull_finish(ctx, ps, out, cap, n_out, timeout_ms);
+    // a list too long for out, or a wait that ran out before the copy landed: kept for a retry
+    if (st != LLOID_ERANGE && cudaEventQuery(ps->ev) != cudaErrorNotReady) ps->busy = false;
+    return st;
 }
 
 lloid_status lloid_set_background_bins(lloid_ctx* ctx, const float* snr_edges, int32_t n_snr, const float* xi2_edges,
@@ -2256,13 +2335,14 @@ lloid_status lloid_pull_events(lloid_ctx* ctx, int64_t w0, int64_t n_windows, ll
     for (long long w = w0; w <= w1; ++w)
         CK(cudaMemcpyAsync(ctx->h_events + (w - w0) * ctx->bank_cap, ctx->d_events + (w % kWindowRing) * ctx->bank_cap,
                            row, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaEventRecord(ctx->pull_ev, ctx->stream));
+    lloid_ctx::PullSlot& s0 = ctx->pull[0];
+    CK(cudaMemcpyAsync(s0.h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(s0.ev, ctx->stream));
     lloid_status st;
-    if ((st = wait_event(ctx, ctx->pull_ev, timeout_ms))) return st;
-    if (*ctx->h_err)
+    if ((st = wait_event(ctx, s0.ev, timeout_ms))) return st;
+    if (*s0.h_err)
         return fail(ctx, LLOID_ETIMEOUT, "a kernel wait expired (code %d); results of the last pushes are invalid",
-                    *ctx->h_err);
+                    *s0.h_err);
     long long cnt = 0;
     for (long long w = w0; w <= w1; ++w)
         for (int bk = 0; bk < ctx->bank_cap; ++bk) {

@@ -266,6 +266,26 @@ class Context:
             self._check(st)
             return out[: n_out.value].copy()
 
+    def pull_submit(self, window: int, n_windows: int = 1) -> int:
+        """Start a pull of windows window .. window + n_windows - 1 behind the
+        pushes already enqueued; returns a ticket for pull_collect."""
+        t = ctypes.c_int32()
+        self._check(self._lib.lloid_pull_submit(self._h, window, n_windows, ctypes.byref(t)))
+        return int(t.value)
+
+    def pull_collect(self, ticket: int, timeout_ms: int = -1) -> np.ndarray:
+        """Triggers of a submitted pull (TRIGGER_DTYPE), once its copy has landed."""
+        n_out = ctypes.c_int64()
+        st = self._lib.lloid_pull_collect(self._h, ticket, None, 0, ctypes.byref(n_out), timeout_ms)
+        if st == 0:
+            return np.zeros(0, dtype=TRIGGER_DTYPE)
+        if st != -8:
+            self._check(st)
+        out = np.empty(int(n_out.value), dtype=TRIGGER_DTYPE)
+        self._check(self._lib.lloid_pull_collect(self._h, ticket, out.ctypes.data_as(ctypes.POINTER(_lib.LloidTrigger)),
+                                                 out.size, ctypes.byref(n_out), timeout_ms))
+        return out[: n_out.value]
+
     def set_background_bins(self, snr_edges, xi2_edges):
         """Start background collection (Section II.D.5) on these ascending edges."""
         se = np.ascontiguousarray(snr_edges, dtype=np.float32)

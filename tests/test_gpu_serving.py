@@ -1,8 +1,9 @@
 """Serving: admission by HBM budget and continuous batching.
 
 A bank admitted while the stream runs must give, from its second push on,
-exactly the triggers it gives when it runs from the start; a bank that does
-not fit the budget waits until a running bank finishes."""
+exactly the triggers it gives when it runs from the start (banks of 200
+templates, two template tiles, in both forms of the split path); a bank that
+does not fit the budget waits until a running bank finishes."""
 import numpy as np
 import pytest
 
@@ -25,22 +26,25 @@ def P():
 
 @pytest.fixture(scope="module")
 def case(P):
-    w = W.make_workload("banks20", n_templates=240, n_banks=3, n_seconds=24, n_det=2, n_inj=0)
+    w = W.make_workload("banks20", n_templates=600, n_banks=3, n_seconds=24, n_det=2, n_inj=0)
     banks = [P.build_svd_bank(b, p) for b, p in zip(w.banks, w.plans)]
     strain = np.stack([w.strain(d) for d in range(2)]).astype(np.float32)
     return banks, strain
 
 
 def _ctx(P, **kw):
-    return P.Context(n_detectors=2, precision="fp16_split", max_block=F0, max_history=64 * F0, **kw)
+    kw.setdefault("precision", "fp16_split")
+    return P.Context(n_detectors=2, max_block=F0, max_history=64 * F0, **kw)
 
 
-def test_midstream_admission_matches_from_start(P, case):
+@pytest.mark.parametrize("precision,form", [("fp16_split", "ladder"), ("bf16_split", "f0"), ("fp32", None)])
+def test_midstream_admission_matches_from_start(P, case, precision, form):
     from paper_2511_04730_b300.serving import Server
     banks, strain = case
+    assert min(len(b[0].coeffs) // 2 for b in banks) > 128       # coefficient rows: re and im per template
     n_blocks = strain.shape[1] // F0
     blk = lambda k: np.ascontiguousarray(strain[:, k * F0:(k + 1) * F0])
-    with _ctx(P) as a, _ctx(P) as b:
+    with _ctx(P, precision=precision, form=form) as a, _ctx(P, precision=precision, form=form) as b:
         sa, sb = Server(a, F0), Server(b, F0)
         for i, bank in enumerate(banks):
             sa.submit(bank, tag=i)
