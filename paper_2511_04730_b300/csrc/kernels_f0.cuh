@@ -280,7 +280,11 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                     const uint32_t ypar = ybufs == 2 ? ((yi >> 1) & 1) : (yi & 1);
                     if (!mbar_wait(yfull + yb, ypar, err, 63)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t y_hi = smem_u32(ybuf + yb * 2 * yplane), y_lo = y_hi + yplane;
+                    // descriptors of the tile's Yhat planes; those of a stage and of each 16-wide K step
+                    // follow by adding (byte offset >> 4) to the start-address field (addresses < 256 KB:
+                    // no carry out of it).  Issuing an MMA takes the issuing thread about as long as the
+                    // MMA runs, so the descriptors are formed before the chunk's MMAs, not between them.
+                    const uint64_t byh = desc_win(smem_u32(ybuf + yb * 2 * yplane)), byl = byh + (uint64_t)(yplane >> 4);
                     for (int tm = 0; tm < jb.tiles_m && ok; ++tm, ++i) {
                         const int buf = tm & 1;
                         const uint32_t use = nb[buf]++;
@@ -290,20 +294,28 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                         for (int kc0 = 0; kc0 < jb.K; kc0 += 32) {
                             if (!mbar_wait(cfull + stage, phase, err, 65)) { ok = false; break; }
                             tc_fence_after();
-                            const uint32_t sb = smem_u32(cst + stage * C::CSTAGE);
+                            const uint64_t ba = desc_win(smem_u32(cst + stage * C::CSTAGE));
+                            const int nk = min(2, k16 - kc0 / 16);    // 16-wide K steps in this chunk
+                            uint64_t a[2][4], bh[2], bl[2];
 #pragma unroll
                             for (int j = 0; j < 2; ++j) {
-                                const int kk = kc0 / 16 + j;
-                                if (kk >= k16) break;
-                                const uint32_t ao = j * 4096, bo = kk * 4096;
-                                const uint32_t acc0 = kk > 0 ? 1u : 0u;
-                                umma_f16(d_re, desc_win(sb + ao), desc_win(y_hi + bo), idesc, acc0);
-                                umma_f16(d_re, desc_win(sb + ao), desc_win(y_lo + bo), idesc, 1u);
-                                umma_f16(d_im, desc_win(sb + C::CPLANE + ao), desc_win(y_hi + bo), idesc, acc0);
-                                umma_f16(d_im, desc_win(sb + C::CPLANE + ao), desc_win(y_lo + bo), idesc, 1u);
+#pragma unroll
+                                for (int pl = 0; pl < 4; ++pl) a[j][pl] = ba + (uint64_t)((pl * C::CPLANE + j * 4096) >> 4);
+                                bh[j] = byh + (uint64_t)((kc0 / 16 + j) * 256);
+                                bl[j] = byl + (uint64_t)((kc0 / 16 + j) * 256);
+                            }
+                            const uint32_t acc0 = kc0 > 0 ? 1u : 0u;
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                if (j >= nk) break;
+                                const uint32_t aj = j > 0 ? 1u : acc0;
+                                umma_f16(d_re, a[j][0], bh[j], idesc, aj);
+                                umma_f16(d_re, a[j][0], bl[j], idesc, 1u);
+                                umma_f16(d_im, a[j][1], bh[j], idesc, aj);
+                                umma_f16(d_im, a[j][1], bl[j], idesc, 1u);
                                 if (BF16) {
-                                    umma_f16(d_re, desc_win(sb + 2 * C::CPLANE + ao), desc_win(y_hi + bo), idesc, 1u);
-                                    umma_f16(d_im, desc_win(sb + 3 * C::CPLANE + ao), desc_win(y_hi + bo), idesc, 1u);
+                                    umma_f16(d_re, a[j][2], bh[j], idesc, 1u);
+                                    umma_f16(d_im, a[j][3], bh[j], idesc, 1u);
                                 }
                             }
                             if (kc0 + 32 < jb.K) umma_commit(cempty + stage);   // the last: the epilogue frees it
@@ -508,17 +520,14 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                         const float4 prev = rs[tm * 128 + rowm];
                         best = prev.x; bk = __float_as_int(prev.y); bre = prev.z; bim = prev.w;
                     }
-#pragma unroll 1
-                    for (int c = 0; c < 128; c += 32) {
-                        uint32_t ru[32], iu[32];            // re and im of 32 samples: both loads, one wait
-                        tmem_ld32_nw(base + c, ru);
-                        tmem_ld32_nw(base + 128 + c, iu);
-                        tmem_wait_ld();
+                    // 16-sample chunks of re and im; the next chunk's loads are in flight while
+                    // this one is reduced (two register sets, one wait per chunk)
+                    auto chunk = [&](const uint32_t (&ru)[16], const uint32_t (&iu)[16], int c) {
                         // |z|^2 and its maximum first; the sample (the first that reaches it) and its
                         // re, im only when the chunk beats what came before (earlier samples win ties)
                         float ma = -1.f, mb = -1.f;          // two chains of three-way maxima
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4) {
+                        for (int j = 0; j < 16; j += 4) {
                             float p0, p1, p2, p3;
                             zsq2(ru[j], ru[j + 1], iu[j], iu[j + 1], p0, p1);
                             zsq2(ru[j + 2], ru[j + 3], iu[j + 2], iu[j + 3], p2, p3);
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                         if (mx > best) {                     // |z|^2 again (same bits) to find the sample
                             uint32_t eq = 0;
 #pragma unroll
-                            for (int j = 0; j < 32; j += 2) {
+                            for (int j = 0; j < 16; j += 2) {
                                 float p0, p1;
                                 zsq2_again(ru[j], ru[j + 1], iu[j], iu[j + 1], p0, p1);
                                 eq |= ((p0 == mx ? 1u : 0u) | (p1 == mx ? 2u : 0u)) << j;
@@ -537,7 +546,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                             const int jj = __ffs(eq) - 1;
                             float sr = 0.f, si = 0.f;
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
+                            for (int j = 0; j < 16; ++j) {
                                 sr = j == jj ? __uint_as_float(ru[j]) : sr;
                                 si = j == jj ? __uint_as_float(iu[j]) : si;
                             }
@@ -546,9 +555,9 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                             bre = sr;
                             bim = si;
                         }
-                        if (pre) {                           // the tail of a tile before a window start
+                        if (pre && c + 16 > tail_from) {    // the tail of a tile before a window start
 #pragma unroll
-                            for (int j = 0; j < 32; j += 2) {
+                            for (int j = 0; j < 16; j += 2) {
                                 float pp[2];
                                 zsq2_again(ru[j], ru[j + 1], iu[j], iu[j + 1], pp[0], pp[1]);
 #pragma unroll
@@ -563,8 +572,25 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                             float* zr = zout + (long long)(2 * m) * n + 128LL * tt + c;
                             float* zi = zr + n;
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) { zr[j] = __uint_as_float(ru[j]); zi[j] = __uint_as_float(iu[j]); }
+                            for (int j = 0; j < 16; ++j) { zr[j] = __uint_as_float(ru[j]); zi[j] = __uint_as_float(iu[j]); }
                         }
+                    };
+                    uint32_t ra[16], ia[16], rb[16], ib[16];
+                    tmem_ld16_nw(base, ra);
+                    tmem_ld16_nw(base + 128, ia);
+                    tmem_wait_ld16(ra, ia);
+#pragma unroll 1
+                    for (int c = 0; c < 128; c += 32) {
+                        tmem_ld16_nw(base + c + 16, rb);
+                        tmem_ld16_nw(base + 128 + c + 16, ib);
+                        chunk(ra, ia, c);
+                        tmem_wait_ld16(rb, ib);
+                        if (c + 32 < 128) {
+                            tmem_ld16_nw(base + c + 32, ra);
+                            tmem_ld16_nw(base + 128 + c + 32, ia);
+                        }
+                        chunk(rb, ib, c + 16);
+                        if (c + 32 < 128) tmem_wait_ld16(ra, ia);
                     }
                     tc_fence_before();
                     mbar_arrive(tempty + grp);
