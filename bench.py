@@ -776,16 +776,19 @@ def run_lloid(args, rank, world, dist):
     works = [algorithmic_work(x, m) for x, m in zip(banks_sb, M_list)]
     det_s = args.block_seconds * n_det
     tc = args.precision != "fp32"
-    wk = {"fir": 0.0, "upsample": 0.0, "recon": 0.0, "yup_bytes": 0.0}
-    for wo, f, x in zip(works, form_of, banks_sb):
+    wk = {"fir": 0.0, "upsample": 0.0, "recon": 0.0, "f0_executed": 0.0}
+    products = 3 if args.precision == "bf16_split" else 2
+    for wo, f, x, m in zip(works, form_of, banks_sb, M_list):
         wk["fir"] += wo["fir"]
         if not tc:
             wk["upsample"] += wo["ladder"]
             wk["recon"] += wo["recon"] + wo["max"]
-        elif f == "f0":            # Eq. 6-8 of the bank in the f0 level; the upsampling kernel moves bytes
+        elif f == "f0":            # Eq. 6-8 of the bank, all in the f0 kernel
             wk["recon"] += wo["recon"] + wo["ladder"] + wo["max"]
             k_all = sum(s.n_basis for s in x)
-            wk["yup_bytes"] += (-(-k_all // 64) * 64) * F0 * 4.0 + sum(s.n_basis * s.rate * 4.0 for s in x)
+            # tensor work the f0 kernel executes: re and im of C Yhat at f0 over the padded bases and
+            # template tiles, one MMA per hi/lo product
+            wk["f0_executed"] += 2 * 2.0 * (-(-m // 128) * 128) * (-(-k_all // 16) * 16) * F0 * products
         else:
             wk["upsample"] += wo["below_f0"]
             wk["recon"] += wo["at_f0"]
@@ -795,16 +798,13 @@ def run_lloid(args, rank, world, dist):
     tc_peak = pk["bf16_tflops"]
     tc_note = (f"{pk_kind} dense bf16 burst (the kernels run inside a {statistics.mean(ms):.1f} ms step"
                + ("; fp16 nominal rate equal" if args.precision == "fp16_split" else "") + ")")
-    ladder_only = forms.get("f0", 0) == 0
     if tc:
-        up_kind = ("k_level_tc (levels below f0)", "tensor", tc_peak, tc_note, wk["upsample"], "TFLOP/s") \
-            if ladder_only or forms.get("ladder", 0) > 0 else \
-            ("k_yup (slice basis outputs up to f0)", "hbm", pk["hbm_gbs"], f"{pk_kind} HBM copy bandwidth",
-             wk["yup_bytes"], "GB/s")
+        rec_name = ("k_level_tc (f0 level + window maxima)" if forms.get("f0", 0) == 0 else
+                    "k_f0_top (f0 form: upsampling + reconstruction + window maxima)" if forms.get("ladder", 0) == 0
+                    else "k_f0_top (f0-form banks) + k_level_tc (f0 level of ladder-form banks)")
         kinds = {"fir": ("k_fir_tc", "tensor", tc_peak, tc_note, wk["fir"], "TFLOP/s"),
-                 "upsample": up_kind,
-                 "recon": ("k_level_tc (f0 level + window maxima)", "tensor", tc_peak, tc_note, wk["recon"],
-                           "TFLOP/s")}
+                 "upsample": ("k_level_tc (levels below f0)", "tensor", tc_peak, tc_note, wk["upsample"], "TFLOP/s"),
+                 "recon": (rec_name, "tensor", tc_peak, tc_note, wk["recon"], "TFLOP/s")}
     else:
         kinds = {"fir": ("k_fir_f32", "alu", alu_peak, alu_note, wk["fir"], "TFLOP/s"),
                  "upsample": ("k_upsample", "alu", alu_peak, alu_note, wk["upsample"], "TFLOP/s"),
@@ -822,6 +822,8 @@ def run_lloid(args, rank, world, dist):
         per_stage[st_name] = {"kernel": kname, "bound": bound, "launch_ms": launch_ms, "launches_per_step": lps,
                               "achieved": achieved, "unit": unit, "peak": peak, "frac": achieved / peak,
                               "peak_source": note, "algorithmic_per_launch": work * det_s / lps}
+        if st_name == "recon" and wk["f0_executed"] > 0:   # context: what the tensor pipe actually runs
+            per_stage[st_name]["f0_kernel_executed_tflop_per_step"] = wk["f0_executed"] * det_s / 1e12
     dom = max(per_stage, key=lambda k: stages[k][0])
     d = per_stage[dom]
     traffic = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, dom)

@@ -1,6 +1,5 @@
-// The f0 form of a bank on the tensor cores: slice upsampling (Eq. 7-8),
-// reconstruction (Eq. 6) and the trigger window maxima (Section II.D.1) in
-// one kernel.
+// The f0 form of a bank: slice upsampling (Eq. 7-8), then reconstruction
+// (Eq. 6) and the trigger window maxima (Section II.D.1) on the tensor cores.
 //
 // Eq. 6 and Eq. 7-8 are linear and the coefficients do not depend on time, so
 // the bank's SNR is z = C Yhat with Yhat_l[k] = sum_q Y_l[q] R[k - D q - e_min]:
@@ -9,15 +8,19 @@
 // The columns of Yhat are the bank's bases packed slice after slice, so K is
 // the bank's basis count rounded up to 16.
 //
-// A work unit is (bank, detector, a group of tpw consecutive 128-sample tiles
-// of the push, tpw = window / 128).  Per tile of the group:
-//   builder warps (4): Yhat rows of the tile, computed in FP32 from the FIR's
-//     hi/lo output at each slice's rate (staged in shared memory with the
-//     slice's composed taps), split into hi/lo halves and stored in shared
-//     memory in the no-swizzle K-major layout ([K/8][128 rows][8]);
-//   producer (1 thread): the coefficient tiles of the bank's 128-template
-//     groups, 32 bases per TMA stage, from time-blocked planes
-//     [re hi, im hi, (re lo, im lo)][K/8][Mpad][8];
+// k_yhat: a CTA per (bank, detector, group of tpw consecutive 128-sample tiles
+// of the push, tpw = window / 128) forms Yhat tile by tile in FP32 from the
+// FIR's hi/lo output at each slice's rate (staged in shared memory with the
+// slice's composed taps; a thread per time row and half of the slice pieces),
+// splits it into hi/lo halves and writes them to HBM as time-blocked planes
+// [det][hi, lo][K/8][rows][8]: a tile is then one TMA box per plane that lands
+// in the no-swizzle K-major operand layout ([K/8][128 rows][8]).  Several of
+// these CTAs share an SM, which the upsampling's dependent loads need.
+//
+// k_f0_top: per work unit of the same shape, per tile of the group:
+//   producer (1 thread): the tile's Yhat planes (one box each) and the
+//     coefficient tiles of the bank's 128-template groups, 32 bases per TMA
+//     stage, from time-blocked planes [re hi, im hi, (re lo, im lo)][K/8][Mpad][8];
 //   MMA issuer (1 thread): for every template group, C Yhat into a TMEM
 //     accumulator (re and im, 128 columns each, two buffers), hi/lo products
 //     (FP16: C_hi Y_hi + C_hi Y_lo; BF16: + C_lo Y_hi);
@@ -38,16 +41,25 @@ struct F0Job {
     int M, Mpad, tmpl0, K;         // templates, padded, first global template, packed K (multiple of 16)
     int tiles_m;                   // Mpad / 128 (at most kF0MaxTm)
     int s0, ns;                    // the bank's slices in the slice table (YupSlice)
-    int map;                       // index into the coefficient maps
+    int map;                       // index into the maps
+    int pc0, np;                   // the bank's pieces in the piece table (F0Piece)
+    int bt0, nbat;                 // and the ends of its staging batches
+    uint16_t* yh;                  // Yhat planes [det][hi, lo][K/8][yrows][8] of the current push
+    int yrows;                     // rows (samples) of a plane: the largest push
+    int pad;
 };
-struct F0Maps { CUtensorMap c; };  // [planes][K/8][Mpad][8], box 128 rows x 32 bases of one plane
+struct F0Maps {
+    CUtensorMap c;                 // [planes][K/8][Mpad][8], box 128 rows x 32 bases of one plane
+    CUtensorMap y;                 // [det * 2 + plane][K/8][yrows][8], box 128 rows x K bases of one plane
+};
 struct F0Unit { int job, g; };     // group g: tiles [g tpw, min((g + 1) tpw, n / 128)) of the push
 
 constexpr int kF0MaxTm = 8;        // template groups per bank (M <= 1024)
-constexpr int kF0Builders = 4;     // builder warps 2..5
-constexpr int kF0EpiWarps = 8;     // epilogue warps 6..13
-constexpr int kF0Threads = 32 * (2 + kF0Builders + kF0EpiWarps);
-constexpr int kF0MaxCStages = 3;
+constexpr int kF0EpiWarps = 8;     // epilogue warps 2..9
+constexpr int kF0Threads = 32 * (2 + kF0EpiWarps);
+constexpr int kF0MaxCStages = 4;
+constexpr int kYhThreads = 128;    // k_yhat: a thread per time row
+constexpr int kYhRing = 8;         // k_yhat: 8-column groups of a row held until complete
 constexpr int kF0Kc = 96;          // largest K of a bank in the f0 form (two Yhat buffers of this width)
 constexpr int kF0StageRows = 132;  // rows of Y one slice reaches per tile: (127 + rlen - 1) / D + 2 at most
 constexpr int kF0StageFloats = 4096;   // builders' staging of Y rows for one batch of slice pieces (16 KB)
@@ -55,13 +67,15 @@ constexpr int kF0RAll = 4096;      // every slice's composed upsampler, staged o
 constexpr int kF0MaxSlices = 16;
 constexpr int kF0MaxPieces = 64;   // (slice, column chunk) pieces of a bank: at most 16 + 128 / 8
 
-// Builders' tables in shared memory: the unit's slices, and per tile the pieces of
-// slices (up to 32 columns each) in column order, grouped in batches that fit the staging.
+// k_yhat's tables in shared memory: the unit's slices, and the pieces of slices (up to 32
+// columns each) in column order, grouped in batches that fit the staging.  A push starts on a
+// multiple of 128 samples and every D divides 128, so a slice reaches the same number of Y rows
+// from every tile: the pieces and batches are fixed per bank (built with the job tables).
 struct F0SliceS {
     const uint16_t* y_hi;          // the slice's FIR output ring, detector applied
     const uint16_t* y_lo;
-    long long q_lo;                // first staged row for the current tile
     int y_rows, y_ld, D, e_min, rlen, L, roff, nq;
+    int qoff;                      // first staged row of a tile: tile start / D + qoff
     int col0;                      // first column of the slice in Yhat
 };
 struct F0Piece { int s, c0, nc, nv, off, pitch, items, item0; };
@@ -71,13 +85,17 @@ struct F0Cfg {
     static constexpr int NPL = BF16 ? 4 : 2;               // coefficient planes
     static constexpr int CPLANE = 128 * 32 * 2;            // one plane of a 32-basis stage (8 KB)
     static constexpr int CSTAGE = NPL * CPLANE;
-    static constexpr int CSTAGES = BF16 ? 2 : 3;           // coefficient stages (what shared memory allows)
+    static constexpr int CSTAGES = BF16 ? 3 : 4;           // coefficient stages (what shared memory allows)
 };
-// Shared memory of the kernel: K <= kc with ybufs Yhat buffers.
+// Shared memory of k_f0_top: K <= kc with ybufs Yhat buffers.
 __host__ __device__ constexpr int f0_smem_bytes(bool bf16, int kc, int ybufs) {
-    return (bf16 ? 2 : 3) * (bf16 ? 4 : 2) * 8192 + ybufs * 2 * 128 * kc * 2 + kF0MaxTm * 128 * 16 +
-           kF0EpiWarps * 16 + (kF0StageFloats + kF0RAll) * 4 + kF0MaxSlices * (int)sizeof(F0SliceS) +
-           kF0MaxPieces * (int)sizeof(F0Piece) + (kF0MaxPieces + 4) * 4 + 1024 + 512;
+    return (bf16 ? 3 : 4) * (bf16 ? 4 : 2) * 8192 + ybufs * 2 * 128 * kc * 2 + kF0MaxTm * 128 * 16 +
+           kF0EpiWarps * 16 + 1024 + 512;
+}
+// Shared memory of k_yhat: staging, composed upsamplers, tables and the rows' group rings.
+__host__ __device__ constexpr int yhat_smem_bytes() {
+    return (kF0StageFloats + kF0RAll) * 4 + kF0MaxSlices * (int)sizeof(F0SliceS) + kF0MaxPieces * (int)sizeof(F0Piece) +
+           (kF0MaxPieces + 4) * 4 + 2 * kYhRing * 128 * 16 + 1024;
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -166,15 +184,144 @@ __device__ __forceinline__ void f0_piece(const float* yp, int pitch, const float
     for (int j = 0; j < 8 * NV; ++j) {
         if (j < nc) {
             const int col = col0 + j;
-            put_hilo<BF16>(yh, yl, (col >> 3) * 2048 + row * 16 + (col & 7) * 2, acc[j]);
+            put_hilo<BF16>(yh, yl, ((col >> 3) & (kYhRing - 1)) * 2048 + row * 16 + (col & 7) * 2, acc[j]);
         }
     }
 }
 
+// Yhat of one work unit (bank, detector, group of tiles) into HBM (see the file comment).
+// Per unit the slices' composed upsamplers are staged once.  Per tile the rows of Y each
+// slice reaches are staged in FP32 for a batch of (slice, up to 32-column) pieces at a
+// time (four loads per thread in flight), then each thread forms its time row's outputs
+// piece by piece in column order, stores their hi/lo halves into its row of a ring of
+// 8-column groups, and sends every group it has completed to HBM as one 16-byte store
+// per plane (a warp: 512 contiguous bytes), zeroing the slot for its next use.
+template <bool BF16>
+__global__ void __launch_bounds__(kYhThreads)
+    k_yhat(const F0Job* __restrict__ jobs, const YupSlice* __restrict__ slices, const F0Piece* __restrict__ pieces,
+           const int* __restrict__ batch_end, const F0Unit* __restrict__ units, long long k_a, int n, int det0,
+           long long window) {
+    constexpr int NB = kYhThreads;
+    const int tpw = (int)(window / 128);
+    const int n_tiles = n / 128;
+    const int row = threadIdx.x;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    constexpr int yplane = kYhRing * 128 * 16;
+    uint8_t* yh = smem;                                    // the rows' group rings: [hi, lo][kYhRing][128][8]
+    uint8_t* yl = yh + yplane;
+    float* ys = reinterpret_cast<float*>(yh + 2 * yplane); // staged Y rows of a batch
+    float* rsm = ys + kF0StageFloats;                      // the unit's composed upsamplers
+    F0SliceS* stab = reinterpret_cast<F0SliceS*>(rsm + kF0RAll);
+    F0Piece* ptab = reinterpret_cast<F0Piece*>(stab + kF0MaxSlices);
+    int* bends = reinterpret_cast<int*>(ptab + kF0MaxPieces);   // end piece of each batch
+
+    const F0Unit un = units[blockIdx.x];
+    const F0Job jb = jobs[un.job];
+    const int det = det0 + (int)blockIdx.y;
+    const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
+    pdl_wait();   // the FIR's output is written by an earlier kernel of the stream
+    for (int q = threadIdx.x; q < jb.ns; q += NB) {
+        const YupSlice sl = slices[jb.s0 + q];
+        F0SliceS& t = stab[q];
+        t.y_hi = sl.y_hi + det * sl.y_det_stride;
+        t.y_lo = sl.y_lo + det * sl.y_det_stride;
+        t.y_rows = sl.y_rows; t.y_ld = sl.y_ld; t.D = sl.D; t.e_min = sl.e_min; t.rlen = sl.rlen;
+        t.L = sl.L; t.roff = sl.roff; t.nq = sl.nq; t.qoff = sl.qoff; t.col0 = sl.tcol;
+    }
+    for (int i = threadIdx.x; i < jb.np; i += NB) ptab[i] = pieces[jb.pc0 + i];
+    for (int i = threadIdx.x; i < jb.nbat; i += NB) bends[i] = batch_end[jb.bt0 + i];
+    for (int q = 0; q < jb.ns; ++q) {
+        const YupSlice& sl = slices[jb.s0 + q];
+        for (int e = threadIdx.x; e < sl.rlen; e += NB) rsm[sl.roff + e] = __ldg(sl.R + e);
+    }
+    __syncthreads();
+    uint4* ghi = reinterpret_cast<uint4*>(jb.yh + (long long)det * 2 * jb.K * jb.yrows) + row;
+    uint4* glo = ghi + (long long)jb.K * jb.yrows / 8;
+    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int g = 0; g < kYhRing; ++g) {                     // empty slots read as zero (the padding columns)
+        *reinterpret_cast<uint4*>(yh + g * 2048 + row * 16) = z4;
+        *reinterpret_cast<uint4*>(yl + g * 2048 + row * 16) = z4;
+    }
+    // group g of this row's tile tt to HBM, its slot zeroed
+    auto flush = [&](int g, int tt) {
+        uint4* sh = reinterpret_cast<uint4*>(yh + (g & (kYhRing - 1)) * 2048 + row * 16);
+        uint4* sl = reinterpret_cast<uint4*>(yl + (g & (kYhRing - 1)) * 2048 + row * 16);
+        const long long o = (long long)g * jb.yrows + 128LL * tt;
+        ghi[o] = *sh;
+        glo[o] = *sl;
+        *sh = z4;
+        *sl = z4;
+    };
+    for (int tt = t0; tt < t1; ++tt) {
+        const long long k0 = k_a + 128LL * tt;
+        int flushed = 0;                                    // groups of this tile already sent
+        for (int bt = 0, p0 = 0; bt < jb.nbat; ++bt) {
+            const int p1 = bends[bt];
+            const int n_items = ptab[p1 - 1].item0 + ptab[p1 - 1].items;
+            // stage: four items per thread in flight at a time
+            for (int e0 = threadIdx.x; e0 < n_items; e0 += 4 * NB) {
+                uint4 hv[4], lv[4];
+                int dst[4];
+#pragma unroll
+                for (int uu = 0; uu < 4; ++uu) {
+                    const int e = e0 + uu * NB;
+                    dst[uu] = -1;
+                    if (e < n_items) {
+                        int pi = p0;
+                        while (pi + 1 < p1 && ptab[pi + 1].item0 <= e) ++pi;
+                        const F0Piece pc = ptab[pi];
+                        const F0SliceS& t = stab[pc.s];
+                        const int ie = e - pc.item0, qi = ie / pc.nv, c8 = ie - qi * pc.nv;
+                        const long long q_lo = k0 / t.D + t.qoff;
+                        const long long o = ((q_lo + qi) & (t.y_rows - 1)) * t.y_ld + pc.c0 + 8 * c8;
+                        hv[uu] = *reinterpret_cast<const uint4*>(t.y_hi + o);
+                        lv[uu] = *reinterpret_cast<const uint4*>(t.y_lo + o);
+                        dst[uu] = pc.off + qi * pc.pitch + 8 * c8;
+                    }
+                }
+#pragma unroll
+                for (int uu = 0; uu < 4; ++uu) {
+                    if (dst[uu] < 0) continue;
+                    const float2 x0 = hilo_pair<BF16>(hv[uu].x, lv[uu].x);
+                    const float2 x1 = hilo_pair<BF16>(hv[uu].y, lv[uu].y);
+                    const float2 x2 = hilo_pair<BF16>(hv[uu].z, lv[uu].z);
+                    const float2 x3 = hilo_pair<BF16>(hv[uu].w, lv[uu].w);
+                    float4* d4 = reinterpret_cast<float4*>(ys + dst[uu]);
+                    d4[0] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                    d4[1] = make_float4(x2.x, x2.y, x3.x, x3.y);
+                }
+            }
+            __syncthreads();
+            for (int pi = p0; pi < p1; ++pi) {
+                const F0Piece pc = ptab[pi];
+                const F0SliceS& t = stab[pc.s];
+                const int D = t.D;
+                const int r0 = row - D * t.qoff - t.e_min;       // R index of (row, the tile's first row)
+                const int qa = max(0, (r0 - t.rlen + D) / D), qb = min(t.nq - 1, r0 / D);
+                const float* rr = rsm + t.roff + r0;
+                const float* yp = ys + pc.off;
+                const int c0 = t.col0 + pc.c0;
+                switch (pc.nv) {
+                    case 1: f0_piece<BF16, 1>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
+                    case 2: f0_piece<BF16, 2>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
+                    case 3: f0_piece<BF16, 3>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
+                    default: f0_piece<BF16, 4>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
+                }
+                for (const int done = (c0 + pc.nc) >> 3; flushed < done; ++flushed) flush(flushed, tt);
+            }
+            __syncthreads();                                // the staging is free for the next batch
+            p0 = p1;
+        }
+        for (; flushed < jb.K / 8; ++flushed) flush(flushed, tt);   // the last group and the padding
+    }
+    pdl_launch_dependents();
+}
+
 template <bool BF16, bool STORE_Z>
 __global__ void __launch_bounds__(kF0Threads, 1)
-    k_f0_top(const F0Job* __restrict__ jobs, const F0Maps* __restrict__ maps, const YupSlice* __restrict__ slices,
-             const F0Unit* __restrict__ units, const int* __restrict__ sched, int n_units, int kc, int ybufs,
+    k_f0_top(const F0Job* __restrict__ jobs, const F0Maps* __restrict__ maps, const F0Unit* __restrict__ units, const int* __restrict__ sched, int n_units, int kc, int ybufs,
              long long k_a, int n, int det0, int n_det_push, long long window, float threshold,
              Partial* __restrict__ part, long long part_tmpl_stride, int n_slots, TailRing tail,
              SlabEntry* __restrict__ slab_base, int ring, int n_det_total, long long slab_det_stride,
@@ -193,12 +340,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
     const int yplane = 128 * kc * 2;
     float4* rs = reinterpret_cast<float4*>(ybuf + ybufs * 2 * yplane);   // [kF0MaxTm][128] running window maxima
     float4* red = rs + kF0MaxTm * 128;                     // [8] bank-max partials of the epilogue warps
-    float* ys = reinterpret_cast<float*>(red + kF0EpiWarps);   // builders: staged Y rows of a batch
-    float* rsm = ys + kF0StageFloats;                       // builders: the unit's composed upsamplers
-    F0SliceS* stab = reinterpret_cast<F0SliceS*>(rsm + kF0RAll);
-    F0Piece* ptab = reinterpret_cast<F0Piece*>(stab + kF0MaxSlices);
-    int* bends = reinterpret_cast<int*>(ptab + kF0MaxPieces);   // [0] batches, [1..] end piece of each
-    uint64_t* bars = reinterpret_cast<uint64_t*>(bends + kF0MaxPieces + 4);   // 2 x 3 + 2 x 2 + 2 x 2 + 1
+    uint64_t* bars = reinterpret_cast<uint64_t*>(red + kF0EpiWarps);   // 2 x 4 + 2 x 2 + 2 x 2 + 1
     uint64_t* cfull = bars;
     uint64_t* cempty = cfull + kF0MaxCStages;
     uint64_t* yfull = cempty + kF0MaxCStages;
@@ -212,7 +354,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::CSTAGES; ++s) { mbar_init(cfull + s, 1); mbar_init(cempty + s, 1); }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(yfull + b, 32 * kF0Builders); mbar_init(yempty + b, 1);
+            mbar_init(yfull + b, 1); mbar_init(yempty + b, 1);
             mbar_init(tfull + b, 1); mbar_init(tempty + b, 32 * kF0EpiWarps / 2);
         }
         mbar_init(drain, 1);
@@ -236,16 +378,25 @@ __global__ void __launch_bounds__(kF0Threads, 1)
             // cempty after every chunk but a template group's last, whose stage the epilogue
             // group frees when it sees the group's accumulator (a commit costs the tensor pipe
             // about as much as a few MMAs).  Either way one arrival per use of the stage.
-            int stage = 0;
+            int stage = 0, yi = 0;
             uint32_t phase = 0;
             bool ok = true;
             for (int u = ub; u < ue && ok; ++u) {
                 const int it = sched[gridDim.x + 1 + u];
+                const int det = det0 + it % n_det_push;
                 const F0Unit un = units[it / n_det_push];
                 const F0Job jb = jobs[un.job];                 // a copy: the asm "memory" clobbers would reload it
                 const F0Maps* mp = maps + jb.map;
                 const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
-                for (int tt = t0; tt < t1 && ok; ++tt)
+                for (int tt = t0; tt < t1 && ok; ++tt, ++yi) {
+                    // the tile's Yhat: one box per plane, once the MMAs of the buffer's last tile are done
+                    const int yb = ybufs == 2 ? (yi & 1) : 0;
+                    const uint32_t ypar = ybufs == 2 ? ((yi >> 1) & 1) : (yi & 1);
+                    if (!mbar_wait(yempty + yb, ypar ^ 1, err, 67)) { ok = false; break; }
+                    mbar_expect_tx(yfull + yb, (uint32_t)(2 * jb.K * 256));
+                    uint8_t* yh = ybuf + yb * 2 * yplane;
+                    tma_load_4d(yh, &mp->y, yfull + yb, 0, 4 * tt, 0, det * 2);
+                    tma_load_4d(yh + yplane, &mp->y, yfull + yb, 0, 4 * tt, 0, det * 2 + 1);
                     for (int tm = 0; tm < jb.tiles_m && ok; ++tm) {
                         for (int kc0 = 0; kc0 < jb.K; kc0 += 32) {
                             if (!mbar_wait(cempty + stage, phase ^ 1, err, 61)) { ok = false; break; }
@@ -257,6 +408,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                             if (++stage == C::CSTAGES) { stage = 0; phase ^= 1; }
                         }
                     }
+                }
             }
             for (int s2 = 0; s2 < C::CSTAGES && ok; ++s2) {
                 if (!mbar_wait(cempty + stage, phase ^ 1, err, 62)) break;
@@ -331,157 +483,13 @@ __global__ void __launch_bounds__(kF0Threads, 1)
             umma_commit(drain);
             mbar_wait(drain, 0, err, 66);
         }
-    } else if (warp < 2 + kF0Builders) {
-        // ---------------------------------------------------------------- Yhat builders
-        // Per unit: the slices' composed upsamplers are staged once.  Per tile: the rows of Y
-        // each slice reaches are staged in FP32 for a batch of (slice, 32-column) pieces at a
-        // time (all loads of a batch in flight together), then each thread forms its time
-        // row's outputs from shared memory, a piece at a time, and stores their hi/lo halves.
-        const int row = threadIdx.x - 64;                  // 0..127: time row of the tile
-        constexpr int NB = 32 * kF0Builders;
-        int yi = 0;
-        bool ok = true;
-        auto bsync = [] { asm volatile("bar.sync 3, %0;" ::"n"(32 * kF0Builders) : "memory"); };
-        for (int u = ub; u < ue && ok; ++u) {
-            const int it = sched[gridDim.x + 1 + u];
-            const int det = det0 + it % n_det_push;
-            const F0Unit un = units[it / n_det_push];
-            const F0Job jb = jobs[un.job];
-            const int t0 = un.g * tpw, t1 = min(t0 + tpw, n_tiles);
-            bsync();                                        // the previous unit's tables are free
-            if (row == 0) {
-                int roff = 0, col = 0;
-                for (int q = 0; q < jb.ns; ++q) {
-                    const YupSlice sl = slices[jb.s0 + q];
-                    F0SliceS& t = stab[q];
-                    t.y_hi = sl.y_hi + det * sl.y_det_stride;
-                    t.y_lo = sl.y_lo + det * sl.y_det_stride;
-                    t.y_rows = sl.y_rows; t.y_ld = sl.y_ld; t.D = sl.D; t.e_min = sl.e_min; t.rlen = sl.rlen;
-                    t.L = sl.L; t.roff = roff; t.col0 = col;
-                    roff += sl.rlen;
-                    col += sl.L;
-                }
-                bends[kF0MaxPieces + 3] = col;              // the bank's basis count; columns up to K are zero
-            }
-            bsync();
-            for (int q = 0; q < jb.ns; ++q) {
-                const YupSlice& sl = slices[jb.s0 + q];
-                for (int e = row; e < sl.rlen; e += NB) rsm[stab[q].roff + e] = __ldg(sl.R + e);
-            }
-            for (int tt = t0; tt < t1; ++tt, ++yi) {
-                const int yb = ybufs == 2 ? (yi & 1) : 0;
-                const uint32_t ypar = ybufs == 2 ? ((yi >> 1) & 1) : (yi & 1);
-                const bool got = mbar_wait(yempty + yb, ypar ^ 1, err, 67);
-                uint32_t all_got;                           // go on together, or stop together
-                asm volatile(
-                    "{\n\t.reg .pred p, q;\n\t setp.ne.u32 p, %1, 0;\n\t"
-                    "bar.red.and.pred q, 3, %2, p;\n\t selp.u32 %0, 1, 0, q;\n\t}\n"
-                    : "=r"(all_got)
-                    : "r"((uint32_t)got), "n"(32 * kF0Builders)
-                    : "memory");
-                if (!all_got) { ok = false; break; }
-                uint8_t* yh = ybuf + yb * 2 * yplane;
-                uint8_t* yl = yh + yplane;
-                const long long k0 = k_a + 128LL * tt;
-                if (row < jb.ns) {                          // each slice's first row and row count
-                    F0SliceS& t = stab[row];
-                    const long long e_max = (long long)t.e_min + t.rlen - 1;
-                    t.q_lo = fdiv(k0 - e_max + t.D - 1, t.D);
-                    t.nq = (int)(fdiv(k0 + 127 - t.e_min, t.D) - t.q_lo + 1);
-                }
-                bsync();
-                if (row == 0) {                             // this tile's pieces, in batches
-                    int np = 0, nbat = 0, off = 0, items = 0;
-                    for (int q = 0; q < jb.ns; ++q) {
-                        F0SliceS& t = stab[q];
-                        // pieces of up to 32 columns, narrower when many rows must fit the staging
-                        const int cw = 8 * min(4, (kF0StageFloats / t.nq - 4) / 8);
-                        for (int c0 = 0; c0 < t.L; c0 += cw) {
-                            F0Piece pc;
-                            pc.s = q; pc.c0 = c0; pc.nc = min(cw, t.L - c0); pc.nv = (pc.nc + 7) >> 3;
-                            pc.pitch = 8 * pc.nv + 4;
-                            if (off + t.nq * pc.pitch > kF0StageFloats) { bends[1 + nbat++] = np; off = 0; items = 0; }
-                            pc.off = off; pc.items = t.nq * pc.nv; pc.item0 = items;
-                            off += t.nq * pc.pitch;
-                            items += pc.items;
-                            ptab[np++] = pc;
-                        }
-                    }
-                    bends[1 + nbat++] = np;
-                    bends[0] = nbat;
-                }
-                bsync();
-                if (tt - t0 < ybufs) {                      // first use of this buffer in the unit: zero the padding
-                    for (int col = bends[kF0MaxPieces + 3]; col < jb.K; ++col)
-                        put_hilo<BF16>(yh, yl, (col >> 3) * 2048 + row * 16 + (col & 7) * 2, 0.f);
-                }
-                const int nbat = bends[0];
-                for (int bt = 0, p0 = 0; bt < nbat; ++bt) {
-                    const int p1 = bends[1 + bt];
-                    const int n_items = ptab[p1 - 1].item0 + ptab[p1 - 1].items;
-                    // stage: four items per thread in flight at a time
-                    for (int e0 = row; e0 < n_items; e0 += 4 * NB) {
-                        uint4 hv[4], lv[4];
-                        int dst[4];
-#pragma unroll
-                        for (int uu = 0; uu < 4; ++uu) {
-                            const int e = e0 + uu * NB;
-                            dst[uu] = -1;
-                            if (e < n_items) {
-                                int pi = p0;
-                                while (pi + 1 < p1 && ptab[pi + 1].item0 <= e) ++pi;
-                                const F0Piece pc = ptab[pi];
-                                const F0SliceS& t = stab[pc.s];
-                                const int ie = e - pc.item0, qi = ie / pc.nv, c8 = ie - qi * pc.nv;
-                                const long long o = ((t.q_lo + qi) & (t.y_rows - 1)) * t.y_ld + pc.c0 + 8 * c8;
-                                hv[uu] = *reinterpret_cast<const uint4*>(t.y_hi + o);
-                                lv[uu] = *reinterpret_cast<const uint4*>(t.y_lo + o);
-                                dst[uu] = pc.off + qi * pc.pitch + 8 * c8;
-                            }
-                        }
-#pragma unroll
-                        for (int uu = 0; uu < 4; ++uu) {
-                            if (dst[uu] < 0) continue;
-                            const float2 x0 = hilo_pair<BF16>(hv[uu].x, lv[uu].x);
-                            const float2 x1 = hilo_pair<BF16>(hv[uu].y, lv[uu].y);
-                            const float2 x2 = hilo_pair<BF16>(hv[uu].z, lv[uu].z);
-                            const float2 x3 = hilo_pair<BF16>(hv[uu].w, lv[uu].w);
-                            float4* d4 = reinterpret_cast<float4*>(ys + dst[uu]);
-                            d4[0] = make_float4(x0.x, x0.y, x1.x, x1.y);
-                            d4[1] = make_float4(x2.x, x2.y, x3.x, x3.y);
-                        }
-                    }
-                    bsync();
-                    for (int pi = p0; pi < p1; ++pi) {
-                        const F0Piece pc = ptab[pi];
-                        const F0SliceS& t = stab[pc.s];
-                        const int D = t.D;
-                        const int r0 = (int)(k0 + row - D * t.q_lo - t.e_min);   // R index of (row, q_lo)
-                        const int qa = max(0, (r0 - t.rlen + D) / D), qb = min(t.nq - 1, r0 / D);
-                        const float* rr = rsm + t.roff + r0;
-                        const float* yp = ys + pc.off;
-                        const int c0 = t.col0 + pc.c0;
-                        switch (pc.nv) {
-                            case 1: f0_piece<BF16, 1>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
-                            case 2: f0_piece<BF16, 2>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
-                            case 3: f0_piece<BF16, 3>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
-                            default: f0_piece<BF16, 4>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
-                        }
-                    }
-                    bsync();                                // the staging is free for the next batch
-                    p0 = p1;
-                }
-                fence_proxy_async_smem();                   // generic-proxy stores -> tensor-core reads
-                mbar_arrive(yfull + yb);
-            }
-        }
     } else {
         // ---------------------------------------------------------------- epilogue
         // Two groups of four warps, one per TMEM buffer: group g takes the template groups
         // tm with tm & 1 == g, all 128 samples of each tile; warp & 3 is the TMEM lane quarter.
         // No barrier inside a unit: each group runs at its own pace.
         const int qd = warp & 3;
-        const int grp = (warp - 2 - kF0Builders) >> 2;
+        const int grp = (warp - 2) >> 2;
         const int rowm = qd * 32 + lane;
         uint32_t nuse = 0;                                  // uses of this group's buffer
         long long chunks = 0;                               // coefficient chunks of the CTA's earlier units
@@ -652,7 +660,7 @@ __global__ void __launch_bounds__(kF0Threads, 1)
                 const int om = __shfl_xor_sync(0xffffffffu, gm, o);
                 if (ob > gbest || (ob == gbest && om < gm)) { gbest = ob; gm = om; }
             }
-            const int ew = warp - 2 - kF0Builders;
+            const int ew = warp - 2;
             if (lane == 0) red[ew] = make_float4(gbest, __int_as_float(gm), 0.f, 0.f);
             asm volatile("bar.sync 2, %0;" ::"n"(32 * kF0EpiWarps) : "memory");
             float vb = red[0].x;

@@ -722,7 +722,9 @@ struct YupSlice {
     int y_rows, y_ld;              // level ring rows (power of two) and row length
     int e_min, rlen, D, L;         // response support [e_min, e_min + rlen); L bases
     int tcol;                      // first column of the slice in the packed f0 ring
-    int pad;
+    int nq;                        // rows of Y a 128-sample tile reaches (the same for every tile)
+    int qoff;                      // first of them: tile start / D + qoff
+    int roff;                      // offset of R in the bank's staged upsamplers
 };
 
 }  // namespace lloid

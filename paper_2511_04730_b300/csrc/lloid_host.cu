@@ -86,6 +86,7 @@ struct BankRT {
     std::vector<LevelRT> lev;          // split path
     LevelRT top;                       // split path, f0 form: K = the bank's bases packed, rounded up to 16
     uint16_t* d_cblk = nullptr;        // f0 form: coefficient planes [re hi, im hi, (re lo, im lo)][K/8][Mpad][8]
+    uint16_t* d_yf0 = nullptr;         // f0 form: Yhat of the current push [det][hi, lo][K/8][max_block][8]
     std::vector<FirSliceRT> fs;        // split path, parallel to sl
     void* d_cre = nullptr;       // [Mpad][Kpad] (FP32 or half)
     void* d_cim = nullptr;
@@ -222,6 +223,8 @@ struct lloid_ctx {
     F0Job* d_f0job[kF0Classes] = {}; F0Maps* d_f0map[kF0Classes] = {}; F0Unit* d_f0unit[kF0Classes] = {};
     int* d_f0sched[kF0Classes][2] = {}; int f0_grid[kF0Classes][2] = {}; int n_f0unit[kF0Classes] = {};
     YupSlice* d_f0slices = nullptr;
+    F0Piece* d_f0pieces = nullptr;     // k_yhat's staging pieces of every bank in the f0 form
+    int* d_f0bends = nullptr;          // and the ends of their batches
     std::vector<int> f0_class_of_bank, f0_job_of_bank;
     uint16_t* d_u_hi[kFSlots] = {};    // Eq. 8 tile matrices per F slot (hi, lo halves)
     uint16_t* d_u_lo[kFSlots] = {};
@@ -367,6 +370,22 @@ bool encode_map_blocked(CUtensorMap* m, bool bf16, const void* base, long long c
     return r == CUDA_SUCCESS;
 }
 
+// The same planes with a box of 128 rows x kb blocks of 8 columns (kb <= 12): a whole Yhat tile
+// of a bank (K = 8 kb bases) in one load.
+bool encode_map_blocked_kb(CUtensorMap* m, bool bf16, const void* base, long long cols, long long rows,
+                           long long planes, int kb) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {256, (cuuint64_t)(rows / 32), (cuuint64_t)(cols / 8), (cuuint64_t)planes};
+    cuuint64_t strides[3] = {512, (cuuint64_t)rows * 16, (cuuint64_t)(cols / 8) * rows * 16};
+    cuuint32_t box[4] = {256, 4, (cuuint32_t)kb, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
+                    const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 lloid_status ensure_template_capacity(lloid_ctx* ctx, long long need) {
     if (need <= ctx->M_cap) return LLOID_OK;
     const int nd = ctx->cfg.n_detectors;
@@ -447,7 +466,7 @@ void free_jobs(lloid_ctx* ctx) {
         ctx->d_f0job[k] = nullptr; ctx->d_f0map[k] = nullptr; ctx->d_f0unit[k] = nullptr; ctx->n_f0unit[k] = 0;
         ctx->d_f0sched[k][0] = ctx->d_f0sched[k][1] = nullptr;
     }
-    ctx->d_f0slices = nullptr;
+    ctx->d_f0slices = nullptr; ctx->d_f0pieces = nullptr; ctx->d_f0bends = nullptr;
 }
 
 template <typename T>
@@ -596,6 +615,8 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     int lt[lloid_ctx::kLevTables] = {};
     int ft = 0, strip = 128, max_depth = 0;
     std::vector<YupSlice> ys;
+    std::vector<F0Piece> f0pc;
+    std::vector<int> f0be;
     std::vector<F0Job> f0j[lloid_ctx::kF0Classes];
     std::vector<F0Maps> f0m[lloid_ctx::kF0Classes];
     std::vector<F0Unit> f0u[lloid_ctx::kF0Classes];
@@ -699,6 +720,11 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             F0Job f{};
             f.M = b->M; f.Mpad = b->Mpad; f.tmpl0 = b->tmpl0; f.K = b->top.K; f.tiles_m = b->Mpad / 128;
             f.s0 = (int)ys.size(); f.ns = (int)b->sl.size(); f.map = (int)f0j[cls].size();
+            f.yh = b->d_yf0; f.yrows = (int)c.max_block;
+            // A tile starts on a multiple of 128 = a multiple of every D: slice s reaches rows
+            // [k0 / D + qoff, + nq) of its Y ring, nq the same for every tile
+            auto floordiv = [](long long a, long long d) { return a >= 0 ? a / d : -((-a + d - 1) / d); };
+            int roff = 0;
             for (size_t si = 0; si < b->sl.size(); ++si) {
                 const SliceRT& sl = b->sl[si];
                 const FirSliceRT& fsr = b->fs[si];
@@ -707,12 +733,41 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                 u.y_hi = L.d_yhi + fsr.col; u.y_lo = L.d_ylo + fsr.col; u.y_det_stride = 2LL * L.R * L.Kp;
                 u.R = sl.d_R; u.y_rows = L.R; u.y_ld = L.Kp;
                 u.e_min = sl.e_min; u.rlen = sl.e_max - sl.e_min + 1; u.D = sl.D; u.L = sl.L; u.tcol = sl.tcol;
+                u.qoff = (int)floordiv(-(long long)sl.e_max + sl.D - 1, sl.D);
+                u.nq = (int)(floordiv(127 - sl.e_min, sl.D) - u.qoff + 1);
+                u.roff = roff;
+                roff += u.rlen;
                 ys.push_back(u);
             }
+            // pieces of up to 32 columns (narrower when many rows must fit the staging), in column
+            // order, in batches of at most kF0StageFloats staged values
+            f.pc0 = (int)f0pc.size();
+            f.bt0 = (int)f0be.size();
+            int off = 0, items = 0, np = 0;
+            for (int q = 0; q < f.ns; ++q) {
+                const YupSlice& u = ys[f.s0 + q];
+                const int cw = 8 * std::min(4, (kF0StageFloats / u.nq - 4) / 8);
+                for (int c0 = 0; c0 < u.L; c0 += cw) {
+                    F0Piece pc{};
+                    pc.s = q; pc.c0 = c0; pc.nc = std::min(cw, u.L - c0); pc.nv = (pc.nc + 7) >> 3;
+                    pc.pitch = 8 * pc.nv + 4;
+                    if (off + u.nq * pc.pitch > kF0StageFloats) { f0be.push_back(np); off = 0; items = 0; }
+                    pc.off = off; pc.items = u.nq * pc.nv; pc.item0 = items;
+                    off += u.nq * pc.pitch;
+                    items += pc.items;
+                    f0pc.push_back(pc);
+                    ++np;
+                }
+            }
+            f0be.push_back(np);
+            f.np = np;
+            f.nbat = (int)f0be.size() - f.bt0;
+            if (np > kF0MaxPieces) return fail(ctx, LLOID_EINVAL, "bank %d: %d staging pieces", b->id, np);
             F0Maps mp;
             std::memset(&mp, 0, sizeof mp);
-            if (!encode_map_blocked(&mp.c, bf, b->d_cblk, b->top.K, b->Mpad, bf ? 4 : 2))
-                return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (f0 coefficients, bank %d)", b->id);
+            if (!encode_map_blocked(&mp.c, bf, b->d_cblk, b->top.K, b->Mpad, bf ? 4 : 2) ||
+                !encode_map_blocked_kb(&mp.y, bf, b->d_yf0, b->top.K, c.max_block, 2LL * nd, b->top.K / 8))
+                return fail(ctx, LLOID_ECUDA, "cuTensorMapEncodeTiled failed (f0 operands, bank %d)", b->id);
             ctx->f0_class_of_bank[b->id] = cls;
             ctx->f0_job_of_bank[b->id] = (int)f0j[cls].size();
             ctx->top_job_of_bank[b->id] = -1;
@@ -726,7 +781,9 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             f0m[cls].push_back(mp);
         }
     }
-    if ((st0 = upload_vec(ctx, &ctx->d_f0slices, ys))) return st0;
+    if ((st0 = upload_vec(ctx, &ctx->d_f0slices, ys)) || (st0 = upload_vec(ctx, &ctx->d_f0pieces, f0pc)) ||
+        (st0 = upload_vec(ctx, &ctx->d_f0bends, f0be)))
+        return st0;
     for (int cls = 0; cls < lloid_ctx::kF0Classes; ++cls) {
         ctx->n_f0unit[cls] = (int)f0u[cls].size();
         if (f0u[cls].empty()) continue;
@@ -749,6 +806,9 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                                                          kF0Threads, smem));
         if (fit < 1) return fail(ctx, LLOID_ECUDA, "the f0-form kernel (%d threads, %d B shared) does not fit an SM",
                                  kF0Threads, smem);
+        const int ysm = yhat_smem_bytes();
+        if (bf) CK(cudaFuncSetAttribute(k_yhat<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ysm));
+        else CK(cudaFuncSetAttribute(k_yhat<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ysm));
     }
     lloid_status st;
     if ((st = upload_vec(ctx, &ctx->d_firtc, fj)) || (st = upload_vec(ctx, &ctx->d_firmaps, fm)) ||
@@ -998,7 +1058,7 @@ lloid_status launch_f0(lloid_ctx* ctx, int cls, const F0Job* jobs, const F0Unit*
     const int smem = f0_smem_bytes(bf, kc, yb);
     const long long part_stride = (long long)ctx->cfg.n_detectors * ctx->n_slots;
     cudaError_t e;
-#define F0_ARGS jobs, (const F0Maps*)ctx->d_f0map[cls], (const YupSlice*)ctx->d_f0slices, units, sched, 0, kc, yb, k_a, \
+#define F0_ARGS jobs, (const F0Maps*)ctx->d_f0map[cls], units, sched, 0, kc, yb, k_a, \
         (int)n, det0, nd, (long long)ctx->cfg.window_samples, ctx->cfg.snr_threshold, ctx->d_part, part_stride,        \
         ctx->n_slots, tail_ring(ctx), ctx->d_slab, (int)kWindowRing, ctx->cfg.n_detectors, (long long)ctx->M_cap, zout,   \
         ctx->d_err
@@ -1007,6 +1067,24 @@ lloid_status launch_f0(lloid_ctx* ctx, int cls, const F0Job* jobs, const F0Unit*
     else e = zout ? launch_pdl(k_f0_top<false, true>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS)
                   : launch_pdl(k_f0_top<false, false>, dim3(grid), dim3(kF0Threads), smem, ctx->stream, F0_ARGS);
 #undef F0_ARGS
+    CK(e);
+    ++ctx->launches;
+    return LLOID_OK;
+}
+
+// Eq. 7-8 of every bank in the f0 form: Yhat of the push into the banks' planes (k_yhat), a CTA
+// per (window group of a bank, detector).
+lloid_status launch_yhat(lloid_ctx* ctx, int cls, long long k_a, long long n, int det0, int nd) {
+    const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
+    const int smem = yhat_smem_bytes();
+    const dim3 grid((unsigned)ctx->n_f0unit[cls], (unsigned)nd);
+    cudaError_t e;
+#define YH_ARGS (const F0Job*)ctx->d_f0job[cls], (const YupSlice*)ctx->d_f0slices, (const F0Piece*)ctx->d_f0pieces, \
+        (const int*)ctx->d_f0bends, (const F0Unit*)ctx->d_f0unit[cls], k_a, (int)n, det0,                         \
+        (long long)ctx->cfg.window_samples
+    if (bf) e = launch_pdl(k_yhat<true>, grid, dim3(kYhThreads), smem, ctx->stream, YH_ARGS);
+    else e = launch_pdl(k_yhat<false>, grid, dim3(kYhThreads), smem, ctx->stream, YH_ARGS);
+#undef YH_ARGS
     CK(e);
     ++ctx->launches;
     return LLOID_OK;
@@ -1113,8 +1191,11 @@ lloid_status process(lloid_ctx* ctx, int det0, int nd, long long k_a, long long 
                                            ctx->n_lev[tb], ctx->lev_tiles[tb], nullptr)))
                         return st;
                 }
+            // the f0 form's banks: every slice's basis outputs brought up to f0 (Eq. 7-8)
+            for (int cls = 0; cls < lloid_ctx::kF0Classes; ++cls)
+                if (ctx->n_f0unit[cls] && (st = launch_yhat(ctx, cls, k_a, n, det0, nd))) return st;
         }
-        // top level (f0) + a5 window maxima; the f0 form's banks: Eq. 7-8 + Eq. 6 + a5 in one kernel
+        // top level (f0) + a5 window maxima; the f0 form's banks: Eq. 6 + a5 in one kernel
         {
             StageTimer tm(ctx, 4);
             const int v = nd == 1 ? 0 : 1;
@@ -1381,6 +1462,7 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
     }
     if (f0form) {
         need += (size_t)npl * top.K * b->Mpad * es;
+        need += (size_t)nd * 2 * top.K * c.max_block * es;   // Yhat planes
         for (const SliceRT& r : b->sl) need += r.R.size() * 4;
     }
     for (auto& f : fs) need += (size_t)f.Mtiles * 128 * f.Kp * es * (bf ? 2 : 1);
@@ -1476,6 +1558,7 @@ lloid_status prepare_split_bank(lloid_ctx* ctx, const lloid_bank_desc* bd, const
                     blk[(((size_t)q * (top.K / 8) + k / 8) * b->Mpad + i) * 8 + k % 8] = (*pl[q])[(size_t)i * top.K + k];
         if ((st = dalloc(ctx, &b->d_cblk, blk.size() * 2, &b->allocs, &b->bytes))) return st;
         CK(cudaMemcpyAsync(b->d_cblk, blk.data(), blk.size() * 2, cudaMemcpyHostToDevice, ctx->stream));
+        if ((st = dalloc(ctx, &b->d_yf0, (size_t)nd * 2 * top.K * c.max_block * 2, &b->allocs, &b->bytes))) return st;
         CK(cudaStreamSynchronize(ctx->stream));
         for (SliceRT& r : b->sl) {   // composed upsampler of every slice (Eq. 7-8 ladder from its rate; [1] at f0)
             std::vector<float> Rf(r.R.begin(), r.R.end());
