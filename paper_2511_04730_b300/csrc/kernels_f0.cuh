@@ -78,7 +78,7 @@ struct F0SliceS {
     int qoff;                      // first staged row of a tile: tile start / D + qoff
     int col0;                      // first column of the slice in Yhat
 };
-struct F0Piece { int s, c0, nc, nv, off, pitch, items, item0; };
+struct F0Piece { int s, c0, nc, nv, off, pitch, items, item0; };   // nv = 0: a slice at f0, read directly
 
 template <bool BF16>
 struct F0Cfg {
@@ -297,6 +297,25 @@ __global__ void __launch_bounds__(kYhThreads)
             for (int pi = p0; pi < p1; ++pi) {
                 const F0Piece pc = ptab[pi];
                 const F0SliceS& t = stab[pc.s];
+                if (pc.nv == 0) {                           // a slice at f0: Yhat = Y, this row of the ring
+                    const long long o = ((k0 + t.qoff + row) & (t.y_rows - 1)) * t.y_ld;
+                    for (int c = 0; c < pc.nc; c += 8) {
+                        const uint4 hv = *reinterpret_cast<const uint4*>(t.y_hi + o + c);
+                        const uint4 lv = *reinterpret_cast<const uint4*>(t.y_lo + o + c);
+                        const float2 x[4] = {hilo_pair<BF16>(hv.x, lv.x), hilo_pair<BF16>(hv.y, lv.y),
+                                             hilo_pair<BF16>(hv.z, lv.z), hilo_pair<BF16>(hv.w, lv.w)};
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int col = t.col0 + c + j;
+                            if (c + j < pc.nc)
+                                put_hilo<BF16>(yh, yl, ((col >> 3) & (kYhRing - 1)) * 2048 + row * 16 + (col & 7) * 2,
+                                               (j & 1) ? x[j >> 1].y : x[j >> 1].x);
+                        }
+                        for (const int done = (t.col0 + c + min(8, pc.nc - c)) >> 3; flushed < done; ++flushed)
+                            flush(flushed, tt);
+                    }
+                    continue;
+                }
                 const int D = t.D;
                 const int r0 = row - D * t.qoff - t.e_min;       // R index of (row, the tile's first row)
                 const int qa = max(0, (r0 - t.rlen + D) / D), qb = min(t.nq - 1, r0 / D);

@@ -112,6 +112,12 @@ struct lloid_ctx {
     lloid_config cfg{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // Trigger lists go to the host on a stream of their own, so that the copy of one push's
+    // list overlaps the next push's kernels: the compaction records `gathered`, the copy
+    // stream waits for it, and the next compaction waits for the copy (`copied`) before it
+    // overwrites the device list.
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t gathered = nullptr, copied = nullptr;
     std::string err;
     long long launches = 0;
     size_t state_bytes = 0, bank_bytes = 0;
@@ -746,6 +752,13 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
             int off = 0, items = 0, np = 0;
             for (int q = 0; q < f.ns; ++q) {
                 const YupSlice& u = ys[f.s0 + q];
+                if (u.D == 1) {   // R = [1]: Yhat is Y, read straight from the ring (no staged rows)
+                    F0Piece pc{};
+                    pc.s = q; pc.c0 = 0; pc.nc = u.L; pc.nv = 0; pc.off = 0; pc.pitch = 0; pc.items = 0; pc.item0 = items;
+                    f0pc.push_back(pc);
+                    ++np;
+                    continue;
+                }
                 const int cw = 8 * std::min(4, (kF0StageFloats / u.nq - 4) / 8);
                 for (int c0 = 0; c0 < u.L; c0 += cw) {
                     F0Piece pc{};
@@ -1831,6 +1844,10 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
         ctx->own_stream = true;
     }
+    CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->gathered, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->copied, cudaEventDisableTiming));
+    CK(cudaEventRecord(ctx->copied, ctx->copy_stream));
     const int nd = c.n_detectors;
     lloid_status st;
     // full-rate ring: history for the D = 1 filters and the widest downsampler
@@ -1951,6 +1968,9 @@ void lloid_destroy(lloid_ctx* ctx) {
     if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
     for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->copy_stream) { cudaStreamSynchronize(ctx->copy_stream); cudaStreamDestroy(ctx->copy_stream); }
+    if (ctx->gathered) cudaEventDestroy(ctx->gathered);
+    if (ctx->copied) cudaEventDestroy(ctx->copied);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -2265,6 +2285,7 @@ static lloid_status pull_enqueue(lloid_ctx* ctx, long long w0, long long n_windo
         CK(cudaHostAlloc((void**)&ps->h, cap2 * sizeof(TriggerOut), cudaHostAllocDefault));
         ps->cap = cap2;
     }
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->copied, 0));   // the last list has left d_trig
     {
         StageTimer tmg(ctx, 6);
         CK(launch_pdl(k_gather_count, dim3(chunks), dim3(1024), 0, ctx->stream, (const SlabEntry*)ctx->d_slab,
@@ -2278,10 +2299,13 @@ static lloid_status pull_enqueue(lloid_ctx* ctx, long long w0, long long n_windo
     }
     ps->want = want;
     ps->seq = ++ctx->gather_seq;
-    CK(cudaMemcpyAsync(ps->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ps->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ps->h, ctx->d_trig, want * sizeof(TriggerOut), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaEventRecord(ps->ev, ctx->stream));
+    CK(cudaEventRecord(ctx->gathered, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->gathered, 0));
+    CK(cudaMemcpyAsync(ps->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->copy_stream));
+    CK(cudaMemcpyAsync(ps->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->copy_stream));
+    CK(cudaMemcpyAsync(ps->h, ctx->d_trig, want * sizeof(TriggerOut), cudaMemcpyDeviceToHost, ctx->copy_stream));
+    CK(cudaEventRecord(ps->ev, ctx->copy_stream));
+    CK(cudaEventRecord(ctx->copied, ctx->copy_stream));
     return LLOID_OK;
 }
 
