@@ -59,7 +59,7 @@ constexpr int kF0EpiWarps = 8;     // epilogue warps 2..9
 constexpr int kF0Threads = 32 * (2 + kF0EpiWarps);
 constexpr int kF0MaxCStages = 4;
 constexpr int kYhThreads = 128;    // k_yhat: a thread per time row
-constexpr int kYhRing = 8;         // k_yhat: 8-column groups of a row held until complete
+constexpr int kYhRing = 4;         // k_yhat: 8-column groups of a row held until complete (pieces <= 16 bases)
 constexpr int kF0Kc = 96;          // largest K of a bank in the f0 form (two Yhat buffers of this width)
 constexpr int kF0StageRows = 132;  // rows of Y one slice reaches per tile: (127 + rlen - 1) / D + 2 at most
 constexpr int kF0StageFloats = 4096;   // builders' staging of Y rows for one batch of slice pieces (16 KB)
@@ -92,9 +92,10 @@ __host__ __device__ constexpr int f0_smem_bytes(bool bf16, int kc, int ybufs) {
     return (bf16 ? 3 : 4) * (bf16 ? 4 : 2) * 8192 + ybufs * 2 * 128 * kc * 2 + kF0MaxTm * 128 * 16 +
            kF0EpiWarps * 16 + 1024 + 512;
 }
-// Shared memory of k_yhat: staging, composed upsamplers, tables and the rows' group rings.
-__host__ __device__ constexpr int yhat_smem_bytes() {
-    return (kF0StageFloats + kF0RAll) * 4 + kF0MaxSlices * (int)sizeof(F0SliceS) + kF0MaxPieces * (int)sizeof(F0Piece) +
+// Shared memory of k_yhat: staging, composed upsamplers (rall floats, a multiple of 4), tables
+// and the rows' group rings.
+__host__ __device__ constexpr int yhat_smem_bytes(int rall) {
+    return (kF0StageFloats + rall) * 4 + kF0MaxSlices * (int)sizeof(F0SliceS) + kF0MaxPieces * (int)sizeof(F0Piece) +
            (kF0MaxPieces + 4) * 4 + 2 * kYhRing * 128 * 16 + 1024;
 }
 
@@ -200,7 +201,7 @@ template <bool BF16>
 __global__ void __launch_bounds__(kYhThreads)
     k_yhat(const F0Job* __restrict__ jobs, const YupSlice* __restrict__ slices, const F0Piece* __restrict__ pieces,
            const int* __restrict__ batch_end, const F0Unit* __restrict__ units, long long k_a, int n, int det0,
-           long long window) {
+           long long window, int rall) {
     constexpr int NB = kYhThreads;
     const int tpw = (int)(window / 128);
     const int n_tiles = n / 128;
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kYhThreads)
     uint8_t* yl = yh + yplane;
     float* ys = reinterpret_cast<float*>(yh + 2 * yplane); // staged Y rows of a batch
     float* rsm = ys + kF0StageFloats;                      // the unit's composed upsamplers
-    F0SliceS* stab = reinterpret_cast<F0SliceS*>(rsm + kF0RAll);
+    F0SliceS* stab = reinterpret_cast<F0SliceS*>(rsm + rall);
     F0Piece* ptab = reinterpret_cast<F0Piece*>(stab + kF0MaxSlices);
     int* bends = reinterpret_cast<int*>(ptab + kF0MaxPieces);   // end piece of each batch
 

@@ -230,6 +230,7 @@ struct lloid_ctx {
     int* d_f0sched[kF0Classes][2] = {}; int f0_grid[kF0Classes][2] = {}; int n_f0unit[kF0Classes] = {};
     YupSlice* d_f0slices = nullptr;
     F0Piece* d_f0pieces = nullptr;     // k_yhat's staging pieces of every bank in the f0 form
+    int f0_rall = 4;                   // the largest bank's staged upsamplers (floats)
     int* d_f0bends = nullptr;          // and the ends of their batches
     std::vector<int> f0_class_of_bank, f0_job_of_bank;
     uint16_t* d_u_hi[kFSlots] = {};    // Eq. 8 tile matrices per F slot (hi, lo halves)
@@ -628,6 +629,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
     std::vector<F0Unit> f0u[lloid_ctx::kF0Classes];
     std::vector<double> f0cost[lloid_ctx::kF0Classes];
     lloid_status st0;
+    ctx->f0_rall = 4;
     ctx->top_job_of_bank.assign(ctx->next_bank_id, -1);
     ctx->top_slot_of_bank.assign(ctx->next_bank_id, 0);
     ctx->f0_class_of_bank.assign(ctx->next_bank_id, -1);
@@ -759,7 +761,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                     ++np;
                     continue;
                 }
-                const int cw = 8 * std::min(4, (kF0StageFloats / u.nq - 4) / 8);
+                const int cw = 8 * std::min(2, (kF0StageFloats / u.nq - 4) / 8);   // pieces <= 16 bases
                 for (int c0 = 0; c0 < u.L; c0 += cw) {
                     F0Piece pc{};
                     pc.s = q; pc.c0 = c0; pc.nc = std::min(cw, u.L - c0); pc.nv = (pc.nc + 7) >> 3;
@@ -773,6 +775,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                 }
             }
             f0be.push_back(np);
+            ctx->f0_rall = std::max(ctx->f0_rall, (roff + 3) / 4 * 4);
             f.np = np;
             f.nbat = (int)f0be.size() - f.bt0;
             if (np > kF0MaxPieces) return fail(ctx, LLOID_EINVAL, "bank %d: %d staging pieces", b->id, np);
@@ -819,7 +822,7 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                                                          kF0Threads, smem));
         if (fit < 1) return fail(ctx, LLOID_ECUDA, "the f0-form kernel (%d threads, %d B shared) does not fit an SM",
                                  kF0Threads, smem);
-        const int ysm = yhat_smem_bytes();
+        const int ysm = yhat_smem_bytes(kF0RAll);
         if (bf) CK(cudaFuncSetAttribute(k_yhat<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ysm));
         else CK(cudaFuncSetAttribute(k_yhat<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ysm));
     }
@@ -1089,12 +1092,12 @@ lloid_status launch_f0(lloid_ctx* ctx, int cls, const F0Job* jobs, const F0Unit*
 // per (window group of a bank, detector).
 lloid_status launch_yhat(lloid_ctx* ctx, int cls, long long k_a, long long n, int det0, int nd) {
     const bool bf = ctx->cfg.precision == LLOID_BF16_SPLIT;
-    const int smem = yhat_smem_bytes();
+    const int smem = yhat_smem_bytes(ctx->f0_rall);
     const dim3 grid((unsigned)ctx->n_f0unit[cls], (unsigned)nd);
     cudaError_t e;
 #define YH_ARGS (const F0Job*)ctx->d_f0job[cls], (const YupSlice*)ctx->d_f0slices, (const F0Piece*)ctx->d_f0pieces, \
         (const int*)ctx->d_f0bends, (const F0Unit*)ctx->d_f0unit[cls], k_a, (int)n, det0,                         \
-        (long long)ctx->cfg.window_samples
+        (long long)ctx->cfg.window_samples, ctx->f0_rall
     if (bf) e = launch_pdl(k_yhat<true>, grid, dim3(kYhThreads), smem, ctx->stream, YH_ARGS);
     else e = launch_pdl(k_yhat<false>, grid, dim3(kYhThreads), smem, ctx->stream, YH_ARGS);
 #undef YH_ARGS
