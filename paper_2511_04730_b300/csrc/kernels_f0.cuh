@@ -93,10 +93,10 @@ __host__ __device__ constexpr int f0_smem_bytes(bool bf16, int kc, int ybufs) {
            kF0EpiWarps * 16 + 1024 + 512;
 }
 // Shared memory of k_yhat: staging, composed upsamplers (rall floats, a multiple of 4), tables
-// and the rows' group rings.
+// and the rows' group rings of two tiles.
 __host__ __device__ constexpr int yhat_smem_bytes(int rall) {
     return (kF0StageFloats + rall) * 4 + kF0MaxSlices * (int)sizeof(F0SliceS) + kF0MaxPieces * (int)sizeof(F0Piece) +
-           (kF0MaxPieces + 4) * 4 + 2 * kYhRing * 128 * 16 + 1024;
+           (kF0MaxPieces + 4) * 4 + 4 * kYhRing * 128 * 16 + 1024;
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -150,15 +150,17 @@ __device__ __forceinline__ float fmax3f(float a, float b, float c) {
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
 }
-// Eq. 7-8 composed into one polyphase filter, for one time row and NV chunks of 8
-// columns of a slice piece: acc[8c + j] = sum_q R[r0 - D q] Y[q][8c + j] over the
-// staged rows q in [qa, qb] (rr = R + r0, yp = the piece's staged rows).  The tap is
-// loaded once for all chunks.
+// Eq. 7-8 composed into one polyphase filter, for one time row of two consecutive tiles
+// and NV chunks of 8 columns of a slice piece: acc0[8c + j] = sum_q R[r0 - D q] Y[q][8c + j]
+// over the staged rows q in [qa, qb] (rr = R + r0, yp = the piece's staged rows), and acc1
+// the same for the row 128 samples later, whose rows are sh = 128 / D further on with the
+// same taps (D divides 128).  A tap is loaded once for both rows and all chunks.
 template <int NV>
-__device__ __forceinline__ void f0_taps(const float* yp, int pitch, const float* rr, int D, int qa, int qb,
-                                        float (&acc)[8 * NV]) {
+__device__ __forceinline__ void f0_taps2(const float* yp, int pitch, const float* rr, int D, int qa, int qb, int sh,
+                                         float (&acc0)[8 * NV], float (&acc1)[8 * NV]) {
 #pragma unroll
-    for (int j = 0; j < 8 * NV; ++j) acc[j] = 0.f;
+    for (int j = 0; j < 8 * NV; ++j) { acc0[j] = 0.f; acc1[j] = 0.f; }
+    const int psh = sh * pitch;
 #pragma unroll 2
     for (int qi = qa; qi <= qb; ++qi) {
         const float wq = rr[-D * qi];
@@ -167,36 +169,47 @@ __device__ __forceinline__ void f0_taps(const float* yp, int pitch, const float*
         for (int c = 0; c < NV; ++c) {
             const float4 a = *reinterpret_cast<const float4*>(y + 8 * c);
             const float4 b = *reinterpret_cast<const float4*>(y + 8 * c + 4);
-            acc[8 * c + 0] = fmaf(a.x, wq, acc[8 * c + 0]); acc[8 * c + 1] = fmaf(a.y, wq, acc[8 * c + 1]);
-            acc[8 * c + 2] = fmaf(a.z, wq, acc[8 * c + 2]); acc[8 * c + 3] = fmaf(a.w, wq, acc[8 * c + 3]);
-            acc[8 * c + 4] = fmaf(b.x, wq, acc[8 * c + 4]); acc[8 * c + 5] = fmaf(b.y, wq, acc[8 * c + 5]);
-            acc[8 * c + 6] = fmaf(b.z, wq, acc[8 * c + 6]); acc[8 * c + 7] = fmaf(b.w, wq, acc[8 * c + 7]);
+            const float4 a1 = *reinterpret_cast<const float4*>(y + psh + 8 * c);
+            const float4 b1 = *reinterpret_cast<const float4*>(y + psh + 8 * c + 4);
+            acc0[8 * c + 0] = fmaf(a.x, wq, acc0[8 * c + 0]); acc0[8 * c + 1] = fmaf(a.y, wq, acc0[8 * c + 1]);
+            acc0[8 * c + 2] = fmaf(a.z, wq, acc0[8 * c + 2]); acc0[8 * c + 3] = fmaf(a.w, wq, acc0[8 * c + 3]);
+            acc0[8 * c + 4] = fmaf(b.x, wq, acc0[8 * c + 4]); acc0[8 * c + 5] = fmaf(b.y, wq, acc0[8 * c + 5]);
+            acc0[8 * c + 6] = fmaf(b.z, wq, acc0[8 * c + 6]); acc0[8 * c + 7] = fmaf(b.w, wq, acc0[8 * c + 7]);
+            acc1[8 * c + 0] = fmaf(a1.x, wq, acc1[8 * c + 0]); acc1[8 * c + 1] = fmaf(a1.y, wq, acc1[8 * c + 1]);
+            acc1[8 * c + 2] = fmaf(a1.z, wq, acc1[8 * c + 2]); acc1[8 * c + 3] = fmaf(a1.w, wq, acc1[8 * c + 3]);
+            acc1[8 * c + 4] = fmaf(b1.x, wq, acc1[8 * c + 4]); acc1[8 * c + 5] = fmaf(b1.y, wq, acc1[8 * c + 5]);
+            acc1[8 * c + 6] = fmaf(b1.z, wq, acc1[8 * c + 6]); acc1[8 * c + 7] = fmaf(b1.w, wq, acc1[8 * c + 7]);
         }
     }
 }
 
-// A piece's outputs for this thread's row: nc columns from packed column col0 on.
+// A piece's outputs for this thread's row in both tiles: nc columns from packed column col0
+// on, into the two tiles' group rings (y0: [hi, lo] of the first tile, y1 of the second).
 template <bool BF16, int NV>
-__device__ __forceinline__ void f0_piece(const float* yp, int pitch, const float* rr, int D, int qa, int qb, int nc,
-                                         int col0, int row, uint8_t* yh, uint8_t* yl) {
-    float acc[8 * NV];
-    f0_taps<NV>(yp, pitch, rr, D, qa, qb, acc);
+__device__ __forceinline__ void f0_piece2(const float* yp, int pitch, const float* rr, int D, int qa, int qb, int sh,
+                                          int nc, int col0, int row, uint8_t* y0, uint8_t* y1) {
+    float acc0[8 * NV], acc1[8 * NV];
+    f0_taps2<NV>(yp, pitch, rr, D, qa, qb, sh, acc0, acc1);
+    constexpr int plane = kYhRing * 128 * 16;
 #pragma unroll
     for (int j = 0; j < 8 * NV; ++j) {
         if (j < nc) {
             const int col = col0 + j;
-            put_hilo<BF16>(yh, yl, ((col >> 3) & (kYhRing - 1)) * 2048 + row * 16 + (col & 7) * 2, acc[j]);
+            const int o = ((col >> 3) & (kYhRing - 1)) * 2048 + row * 16 + (col & 7) * 2;
+            put_hilo<BF16>(y0, y0 + plane, o, acc0[j]);
+            put_hilo<BF16>(y1, y1 + plane, o, acc1[j]);
         }
     }
 }
 
 // Yhat of one work unit (bank, detector, group of tiles) into HBM (see the file comment).
-// Per unit the slices' composed upsamplers are staged once.  Per tile the rows of Y each
-// slice reaches are staged in FP32 for a batch of (slice, up to 32-column) pieces at a
-// time (four loads per thread in flight), then each thread forms its time row's outputs
-// piece by piece in column order, stores their hi/lo halves into its row of a ring of
-// 8-column groups, and sends every group it has completed to HBM as one 16-byte store
-// per plane (a warp: 512 contiguous bytes), zeroing the slot for its next use.
+// Per unit the slices' composed upsamplers are staged once.  Tiles go in pairs: the rows of
+// Y each slice reaches from both tiles are staged in FP32 for a batch of (slice, up to
+// 16-column) pieces at a time (four loads per thread in flight), then each thread forms the
+// outputs of its time row in both tiles piece by piece in column order (a tap serves both),
+// stores their hi/lo halves into its row of each tile's ring of 8-column groups, and sends
+// every group it has completed to HBM as one 16-byte store per plane (a warp: 512
+// contiguous bytes), zeroing the slot for its next use.
 template <bool BF16>
 __global__ void __launch_bounds__(kYhThreads)
     k_yhat(const F0Job* __restrict__ jobs, const YupSlice* __restrict__ slices, const F0Piece* __restrict__ pieces,
@@ -209,9 +222,8 @@ __global__ void __launch_bounds__(kYhThreads)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr int yplane = kYhRing * 128 * 16;
-    uint8_t* yh = smem;                                    // the rows' group rings: [hi, lo][kYhRing][128][8]
-    uint8_t* yl = yh + yplane;
-    float* ys = reinterpret_cast<float*>(yh + 2 * yplane); // staged Y rows of a batch
+    uint8_t* ring = smem;                                  // the rows' group rings: [tile][hi, lo][kYhRing][128][8]
+    float* ys = reinterpret_cast<float*>(ring + 4 * yplane);   // staged Y rows of a batch
     float* rsm = ys + kF0StageFloats;                      // the unit's composed upsamplers
     F0SliceS* stab = reinterpret_cast<F0SliceS*>(rsm + rall);
     F0Piece* ptab = reinterpret_cast<F0Piece*>(stab + kF0MaxSlices);
@@ -241,23 +253,27 @@ __global__ void __launch_bounds__(kYhThreads)
     uint4* glo = ghi + (long long)jb.K * jb.yrows / 8;
     const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-    for (int g = 0; g < kYhRing; ++g) {                     // empty slots read as zero (the padding columns)
-        *reinterpret_cast<uint4*>(yh + g * 2048 + row * 16) = z4;
-        *reinterpret_cast<uint4*>(yl + g * 2048 + row * 16) = z4;
-    }
-    // group g of this row's tile tt to HBM, its slot zeroed
-    auto flush = [&](int g, int tt) {
-        uint4* sh = reinterpret_cast<uint4*>(yh + (g & (kYhRing - 1)) * 2048 + row * 16);
-        uint4* sl = reinterpret_cast<uint4*>(yl + (g & (kYhRing - 1)) * 2048 + row * 16);
-        const long long o = (long long)g * jb.yrows + 128LL * tt;
-        ghi[o] = *sh;
-        glo[o] = *sl;
-        *sh = z4;
-        *sl = z4;
+    for (int g = 0; g < 4 * kYhRing; ++g)                   // empty slots read as zero (the padding columns)
+        *reinterpret_cast<uint4*>(ring + g * 2048 + row * 16) = z4;
+    // group g of this row's tiles tt (and tt + 1 when `both`) to HBM, the slots zeroed
+    auto flush = [&](int g, int tt, bool both) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint4* sh = reinterpret_cast<uint4*>(ring + h * 2 * yplane + (g & (kYhRing - 1)) * 2048 + row * 16);
+            uint4* sl = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(sh) + yplane);
+            if (h == 0 || both) {
+                const long long o = (long long)g * jb.yrows + 128LL * (tt + h);
+                ghi[o] = *sh;
+                glo[o] = *sl;
+            }
+            *sh = z4;
+            *sl = z4;
+        }
     };
-    for (int tt = t0; tt < t1; ++tt) {
+    for (int tt = t0; tt < t1; tt += 2) {
         const long long k0 = k_a + 128LL * tt;
-        int flushed = 0;                                    // groups of this tile already sent
+        const bool both = tt + 1 < t1;                      // the second tile of the pair is in the push
+        int flushed = 0;                                    // groups of these tiles already sent
         for (int bt = 0, p0 = 0; bt < jb.nbat; ++bt) {
             const int p1 = bends[bt];
             const int n_items = ptab[p1 - 1].item0 + ptab[p1 - 1].items;
@@ -299,21 +315,26 @@ __global__ void __launch_bounds__(kYhThreads)
                 const F0Piece pc = ptab[pi];
                 const F0SliceS& t = stab[pc.s];
                 if (pc.nv == 0) {                           // a slice at f0: Yhat = Y, this row of the ring
-                    const long long o = ((k0 + t.qoff + row) & (t.y_rows - 1)) * t.y_ld;
                     for (int c = 0; c < pc.nc; c += 8) {
-                        const uint4 hv = *reinterpret_cast<const uint4*>(t.y_hi + o + c);
-                        const uint4 lv = *reinterpret_cast<const uint4*>(t.y_lo + o + c);
-                        const float2 x[4] = {hilo_pair<BF16>(hv.x, lv.x), hilo_pair<BF16>(hv.y, lv.y),
-                                             hilo_pair<BF16>(hv.z, lv.z), hilo_pair<BF16>(hv.w, lv.w)};
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int col = t.col0 + c + j;
-                            if (c + j < pc.nc)
-                                put_hilo<BF16>(yh, yl, ((col >> 3) & (kYhRing - 1)) * 2048 + row * 16 + (col & 7) * 2,
-                                               (j & 1) ? x[j >> 1].y : x[j >> 1].x);
+                        for (int h = 0; h < 2; ++h) {
+                            const long long o = ((k0 + 128 * h + t.qoff + row) & (t.y_rows - 1)) * t.y_ld;
+                            const uint4 hv = *reinterpret_cast<const uint4*>(t.y_hi + o + c);
+                            const uint4 lv = *reinterpret_cast<const uint4*>(t.y_lo + o + c);
+                            const float2 x[4] = {hilo_pair<BF16>(hv.x, lv.x), hilo_pair<BF16>(hv.y, lv.y),
+                                                 hilo_pair<BF16>(hv.z, lv.z), hilo_pair<BF16>(hv.w, lv.w)};
+                            uint8_t* yh = ring + h * 2 * yplane;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int col = t.col0 + c + j;
+                                if (c + j < pc.nc)
+                                    put_hilo<BF16>(yh, yh + yplane,
+                                                   ((col >> 3) & (kYhRing - 1)) * 2048 + row * 16 + (col & 7) * 2,
+                                                   (j & 1) ? x[j >> 1].y : x[j >> 1].x);
+                            }
                         }
                         for (const int done = (t.col0 + c + min(8, pc.nc - c)) >> 3; flushed < done; ++flushed)
-                            flush(flushed, tt);
+                            flush(flushed, tt, both);
                     }
                     continue;
                 }
@@ -323,18 +344,14 @@ __global__ void __launch_bounds__(kYhThreads)
                 const float* rr = rsm + t.roff + r0;
                 const float* yp = ys + pc.off;
                 const int c0 = t.col0 + pc.c0;
-                switch (pc.nv) {
-                    case 1: f0_piece<BF16, 1>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
-                    case 2: f0_piece<BF16, 2>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
-                    case 3: f0_piece<BF16, 3>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
-                    default: f0_piece<BF16, 4>(yp, pc.pitch, rr, D, qa, qb, pc.nc, c0, row, yh, yl); break;
-                }
-                for (const int done = (c0 + pc.nc) >> 3; flushed < done; ++flushed) flush(flushed, tt);
+                if (pc.nv == 1) f0_piece2<BF16, 1>(yp, pc.pitch, rr, D, qa, qb, 128 / D, pc.nc, c0, row, ring, ring + 2 * yplane);
+                else f0_piece2<BF16, 2>(yp, pc.pitch, rr, D, qa, qb, 128 / D, pc.nc, c0, row, ring, ring + 2 * yplane);
+                for (const int done = (c0 + pc.nc) >> 3; flushed < done; ++flushed) flush(flushed, tt, both);
             }
             __syncthreads();                                // the staging is free for the next batch
             p0 = p1;
         }
-        for (; flushed < jb.K / 8; ++flushed) flush(flushed, tt);   // the last group and the padding
+        for (; flushed < jb.K / 8; ++flushed) flush(flushed, tt, both);   // the last group and the padding
     }
     pdl_launch_dependents();
 }
