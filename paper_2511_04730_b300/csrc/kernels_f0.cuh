@@ -78,7 +78,7 @@ struct F0SliceS {
     int qoff;                      // first staged row of a tile: tile start / D + qoff
     int col0;                      // first column of the slice in Yhat
 };
-struct F0Piece { int s, c0, nc, nv, off, pitch, items, item0; };   // nv = 0: a slice at f0, read directly
+struct F0Piece { int s, c0, nc, nv, off, pitch, items, item0; };   // nv: 4-column chunks (0: a slice at f0, read directly)
 
 template <bool BF16>
 struct F0Cfg {
@@ -151,15 +151,15 @@ __device__ __forceinline__ float fmax3f(float a, float b, float c) {
     return d;
 }
 // Eq. 7-8 composed into one polyphase filter, for one time row of two consecutive tiles
-// and NV chunks of 8 columns of a slice piece: acc0[8c + j] = sum_q R[r0 - D q] Y[q][8c + j]
+// and NV chunks of 4 columns of a slice piece: acc0[4c + j] = sum_q R[r0 - D q] Y[q][4c + j]
 // over the staged rows q in [qa, qb] (rr = R + r0, yp = the piece's staged rows), and acc1
 // the same for the row 128 samples later, whose rows are sh = 128 / D further on with the
 // same taps (D divides 128).  A tap is loaded once for both rows and all chunks.
 template <int NV>
 __device__ __forceinline__ void f0_taps2(const float* yp, int pitch, const float* rr, int D, int qa, int qb, int sh,
-                                         float (&acc0)[8 * NV], float (&acc1)[8 * NV]) {
+                                         float (&acc0)[4 * NV], float (&acc1)[4 * NV]) {
 #pragma unroll
-    for (int j = 0; j < 8 * NV; ++j) { acc0[j] = 0.f; acc1[j] = 0.f; }
+    for (int j = 0; j < 4 * NV; ++j) { acc0[j] = 0.f; acc1[j] = 0.f; }
     const int psh = sh * pitch;
 #pragma unroll 2
     for (int qi = qa; qi <= qb; ++qi) {
@@ -167,18 +167,12 @@ __device__ __forceinline__ void f0_taps2(const float* yp, int pitch, const float
         const float* y = yp + qi * pitch;
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-            const float4 a = *reinterpret_cast<const float4*>(y + 8 * c);
-            const float4 b = *reinterpret_cast<const float4*>(y + 8 * c + 4);
-            const float4 a1 = *reinterpret_cast<const float4*>(y + psh + 8 * c);
-            const float4 b1 = *reinterpret_cast<const float4*>(y + psh + 8 * c + 4);
-            acc0[8 * c + 0] = fmaf(a.x, wq, acc0[8 * c + 0]); acc0[8 * c + 1] = fmaf(a.y, wq, acc0[8 * c + 1]);
-            acc0[8 * c + 2] = fmaf(a.z, wq, acc0[8 * c + 2]); acc0[8 * c + 3] = fmaf(a.w, wq, acc0[8 * c + 3]);
-            acc0[8 * c + 4] = fmaf(b.x, wq, acc0[8 * c + 4]); acc0[8 * c + 5] = fmaf(b.y, wq, acc0[8 * c + 5]);
-            acc0[8 * c + 6] = fmaf(b.z, wq, acc0[8 * c + 6]); acc0[8 * c + 7] = fmaf(b.w, wq, acc0[8 * c + 7]);
-            acc1[8 * c + 0] = fmaf(a1.x, wq, acc1[8 * c + 0]); acc1[8 * c + 1] = fmaf(a1.y, wq, acc1[8 * c + 1]);
-            acc1[8 * c + 2] = fmaf(a1.z, wq, acc1[8 * c + 2]); acc1[8 * c + 3] = fmaf(a1.w, wq, acc1[8 * c + 3]);
-            acc1[8 * c + 4] = fmaf(b1.x, wq, acc1[8 * c + 4]); acc1[8 * c + 5] = fmaf(b1.y, wq, acc1[8 * c + 5]);
-            acc1[8 * c + 6] = fmaf(b1.z, wq, acc1[8 * c + 6]); acc1[8 * c + 7] = fmaf(b1.w, wq, acc1[8 * c + 7]);
+            const float4 a = *reinterpret_cast<const float4*>(y + 4 * c);
+            const float4 a1 = *reinterpret_cast<const float4*>(y + psh + 4 * c);
+            acc0[4 * c + 0] = fmaf(a.x, wq, acc0[4 * c + 0]); acc0[4 * c + 1] = fmaf(a.y, wq, acc0[4 * c + 1]);
+            acc0[4 * c + 2] = fmaf(a.z, wq, acc0[4 * c + 2]); acc0[4 * c + 3] = fmaf(a.w, wq, acc0[4 * c + 3]);
+            acc1[4 * c + 0] = fmaf(a1.x, wq, acc1[4 * c + 0]); acc1[4 * c + 1] = fmaf(a1.y, wq, acc1[4 * c + 1]);
+            acc1[4 * c + 2] = fmaf(a1.z, wq, acc1[4 * c + 2]); acc1[4 * c + 3] = fmaf(a1.w, wq, acc1[4 * c + 3]);
         }
     }
 }
@@ -188,11 +182,11 @@ __device__ __forceinline__ void f0_taps2(const float* yp, int pitch, const float
 template <bool BF16, int NV>
 __device__ __forceinline__ void f0_piece2(const float* yp, int pitch, const float* rr, int D, int qa, int qb, int sh,
                                           int nc, int col0, int row, uint8_t* y0, uint8_t* y1) {
-    float acc0[8 * NV], acc1[8 * NV];
+    float acc0[4 * NV], acc1[4 * NV];
     f0_taps2<NV>(yp, pitch, rr, D, qa, qb, sh, acc0, acc1);
     constexpr int plane = kYhRing * 128 * 16;
 #pragma unroll
-    for (int j = 0; j < 8 * NV; ++j) {
+    for (int j = 0; j < 4 * NV; ++j) {
         if (j < nc) {
             const int col = col0 + j;
             const int o = ((col >> 3) & (kYhRing - 1)) * 2048 + row * 16 + (col & 7) * 2;
@@ -279,7 +273,7 @@ __global__ void __launch_bounds__(kYhThreads)
             const int n_items = ptab[p1 - 1].item0 + ptab[p1 - 1].items;
             // stage: four items per thread in flight at a time
             for (int e0 = threadIdx.x; e0 < n_items; e0 += 4 * NB) {
-                uint4 hv[4], lv[4];
+                uint2 hv[4], lv[4];
                 int dst[4];
 #pragma unroll
                 for (int uu = 0; uu < 4; ++uu) {
@@ -290,12 +284,12 @@ __global__ void __launch_bounds__(kYhThreads)
                         while (pi + 1 < p1 && ptab[pi + 1].item0 <= e) ++pi;
                         const F0Piece pc = ptab[pi];
                         const F0SliceS& t = stab[pc.s];
-                        const int ie = e - pc.item0, qi = ie / pc.nv, c8 = ie - qi * pc.nv;
+                        const int ie = e - pc.item0, qi = ie / pc.nv, c4 = ie - qi * pc.nv;
                         const long long q_lo = k0 / t.D + t.qoff;
-                        const long long o = ((q_lo + qi) & (t.y_rows - 1)) * t.y_ld + pc.c0 + 8 * c8;
-                        hv[uu] = *reinterpret_cast<const uint4*>(t.y_hi + o);
-                        lv[uu] = *reinterpret_cast<const uint4*>(t.y_lo + o);
-                        dst[uu] = pc.off + qi * pc.pitch + 8 * c8;
+                        const long long o = ((q_lo + qi) & (t.y_rows - 1)) * t.y_ld + pc.c0 + 4 * c4;
+                        hv[uu] = *reinterpret_cast<const uint2*>(t.y_hi + o);
+                        lv[uu] = *reinterpret_cast<const uint2*>(t.y_lo + o);
+                        dst[uu] = pc.off + qi * pc.pitch + 4 * c4;
                     }
                 }
 #pragma unroll
@@ -303,11 +297,7 @@ __global__ void __launch_bounds__(kYhThreads)
                     if (dst[uu] < 0) continue;
                     const float2 x0 = hilo_pair<BF16>(hv[uu].x, lv[uu].x);
                     const float2 x1 = hilo_pair<BF16>(hv[uu].y, lv[uu].y);
-                    const float2 x2 = hilo_pair<BF16>(hv[uu].z, lv[uu].z);
-                    const float2 x3 = hilo_pair<BF16>(hv[uu].w, lv[uu].w);
-                    float4* d4 = reinterpret_cast<float4*>(ys + dst[uu]);
-                    d4[0] = make_float4(x0.x, x0.y, x1.x, x1.y);
-                    d4[1] = make_float4(x2.x, x2.y, x3.x, x3.y);
+                    *reinterpret_cast<float4*>(ys + dst[uu]) = make_float4(x0.x, x0.y, x1.x, x1.y);
                 }
             }
             __syncthreads();
@@ -344,8 +334,13 @@ __global__ void __launch_bounds__(kYhThreads)
                 const float* rr = rsm + t.roff + r0;
                 const float* yp = ys + pc.off;
                 const int c0 = t.col0 + pc.c0;
-                if (pc.nv == 1) f0_piece2<BF16, 1>(yp, pc.pitch, rr, D, qa, qb, 128 / D, pc.nc, c0, row, ring, ring + 2 * yplane);
-                else f0_piece2<BF16, 2>(yp, pc.pitch, rr, D, qa, qb, 128 / D, pc.nc, c0, row, ring, ring + 2 * yplane);
+                uint8_t* r1 = ring + 2 * yplane;
+                switch (pc.nv) {
+                    case 1: f0_piece2<BF16, 1>(yp, pc.pitch, rr, D, qa, qb, 128 / D, pc.nc, c0, row, ring, r1); break;
+                    case 2: f0_piece2<BF16, 2>(yp, pc.pitch, rr, D, qa, qb, 128 / D, pc.nc, c0, row, ring, r1); break;
+                    case 3: f0_piece2<BF16, 3>(yp, pc.pitch, rr, D, qa, qb, 128 / D, pc.nc, c0, row, ring, r1); break;
+                    default: f0_piece2<BF16, 4>(yp, pc.pitch, rr, D, qa, qb, 128 / D, pc.nc, c0, row, ring, r1); break;
+                }
                 for (const int done = (c0 + pc.nc) >> 3; flushed < done; ++flushed) flush(flushed, tt, both);
             }
             __syncthreads();                                // the staging is free for the next batch

@@ -762,11 +762,11 @@ lloid_status build_jobs_split(lloid_ctx* ctx, long long n) {
                     continue;
                 }
                 const int nq2 = u.nq + 128 / u.D;            // the rows both tiles of a pair reach
-                const int cw = 8 * std::min(2, (kF0StageFloats / nq2 - 4) / 8);   // pieces <= 16 bases
+                const int cw = 4 * std::min(4, (kF0StageFloats / nq2 - 4) / 4);   // pieces <= 16 bases
                 for (int c0 = 0; c0 < u.L; c0 += cw) {
                     F0Piece pc{};
-                    pc.s = q; pc.c0 = c0; pc.nc = std::min(cw, u.L - c0); pc.nv = (pc.nc + 7) >> 3;
-                    pc.pitch = 8 * pc.nv + 4;
+                    pc.s = q; pc.c0 = c0; pc.nc = std::min(cw, u.L - c0); pc.nv = (pc.nc + 3) >> 2;
+                    pc.pitch = 4 * pc.nv + 4;
                     if (off + nq2 * pc.pitch > kF0StageFloats) { f0be.push_back(np); off = 0; items = 0; }
                     pc.off = off; pc.items = nq2 * pc.nv; pc.item0 = items;
                     off += nq2 * pc.pitch;
