@@ -269,13 +269,34 @@ def algorithmic_work(slices, M, f0=F0, n_up=8):
             "at_f0": rec_by.get(f0, 0.0) + up_by.get(f0, 0.0) + cmp_}
 
 
+def yhat_flops(slices, f0=F0, n_up=8):
+    """Multiply-adds (x2) per detector-second that k_yhat executes for a bank in the f0 form:
+    every basis of a slice below f0 through its composed upsampler (the Eq. 7-8 stages of the
+    bank's ladder from the slice's rate up, c = F N_up each), ceil(length / D) taps per output
+    sample, columns in chunks of 4; slices at f0 are copied."""
+    lad = sorted(set(s.rate for s in slices) | {f0})
+    total = 0.0
+    for s in slices:
+        if s.rate == f0:
+            continue
+        length = 1
+        chain = [r for r in lad if r >= s.rate]
+        for lo, hi in zip(chain[:-1], chain[1:]):
+            F = hi // lo
+            length = F * (length - 1) + 2 * F * n_up + 1
+        D = f0 // s.rate
+        total += 2.0 * (-(-s.n_basis // 4) * 4) * f0 * (-(-length // D))
+    return total
+
+
 # DRAM read + write bytes per launch of each stage's kernel, from the ncu captures
 # summarised in profiles/; valid only while the kernel sources hash to the prefix they
 # were taken with.
-TRAFFIC_SOURCES = ("kernels_tc.cuh", "kernels_tc2.cuh", "lloid_common.cuh")
-TRAFFIC_SHA = ""
-TRAFFIC_PROFILE = ""
-TRAFFIC = {}
+TRAFFIC_SOURCES = ("kernels_f0.cuh", "kernels_tc.cuh", "kernels_tc2.cuh", "lloid_common.cuh")
+TRAFFIC_SHA = "3039a125aadd606d"
+TRAFFIC_PROFILE = "profiles/dram_banks500_bf16split.md (k_f0_top, one pass, all f0-possible banks in the f0 form)"
+TRAFFIC = {("banks500", "bf16_split", 8, 3): {"recon": 3.379e9 + 0.201e9, "upsample": 8.333e9 + 3.261e9,
+                                               "fir": 1.020e9 + 2.412e9}}
 
 
 def kernel_sources_sha():
@@ -776,7 +797,7 @@ def run_lloid(args, rank, world, dist):
     works = [algorithmic_work(x, m) for x, m in zip(banks_sb, M_list)]
     det_s = args.block_seconds * n_det
     tc = args.precision != "fp32"
-    wk = {"fir": 0.0, "upsample": 0.0, "recon": 0.0, "f0_executed": 0.0}
+    wk = {"fir": 0.0, "upsample": 0.0, "recon": 0.0, "f0_executed": 0.0, "yhat_executed": 0.0}
     products = 3 if args.precision == "bf16_split" else 2
     for wo, f, x, m in zip(works, form_of, banks_sb, M_list):
         wk["fir"] += wo["fir"]
@@ -789,6 +810,7 @@ def run_lloid(args, rank, world, dist):
             # tensor work the f0 kernel executes: re and im of C Yhat at f0 over the padded bases and
             # template tiles, one MMA per hi/lo product
             wk["f0_executed"] += 2 * 2.0 * (-(-m // 128) * 128) * (-(-k_all // 16) * 16) * F0 * products
+            wk["yhat_executed"] += yhat_flops(x)
         else:
             wk["upsample"] += wo["below_f0"]
             wk["recon"] += wo["at_f0"]
@@ -798,12 +820,20 @@ def run_lloid(args, rank, world, dist):
     tc_peak = pk["bf16_tflops"]
     tc_note = (f"{pk_kind} dense bf16 burst (the kernels run inside a {statistics.mean(ms):.1f} ms step"
                + ("; fp16 nominal rate equal" if args.precision == "fp16_split" else "") + ")")
+    yhat_stage = tc and forms.get("f0", 0) > 0
     if tc:
         rec_name = ("k_level_tc (f0 level + window maxima)" if forms.get("f0", 0) == 0 else
                     "k_f0_top (f0 form: upsampling + reconstruction + window maxima)" if forms.get("ladder", 0) == 0
                     else "k_f0_top (f0-form banks) + k_level_tc (f0 level of ladder-form banks)")
+        # the upsample stage holds k_yhat (the f0 form's Eq. 7-8, FP32 multiply-adds, counted as
+        # executed: the paper's order does this work on 2M rows, the f0 form on the K bases) and
+        # the ladder levels below f0 of the ladder-form banks
+        up = (("k_yhat (f0 form, executed FP32 work)" + (" + k_level_tc (ladder levels below f0)"
+                                                           if forms.get("ladder", 0) else ""),
+               "alu", alu_peak, alu_note, wk["yhat_executed"] + wk["upsample"], "TFLOP/s") if yhat_stage else
+              ("k_level_tc (levels below f0)", "tensor", tc_peak, tc_note, wk["upsample"], "TFLOP/s"))
         kinds = {"fir": ("k_fir_tc", "tensor", tc_peak, tc_note, wk["fir"], "TFLOP/s"),
-                 "upsample": ("k_level_tc (levels below f0)", "tensor", tc_peak, tc_note, wk["upsample"], "TFLOP/s"),
+                 "upsample": up,
                  "recon": (rec_name, "tensor", tc_peak, tc_note, wk["recon"], "TFLOP/s")}
     else:
         kinds = {"fir": ("k_fir_f32", "alu", alu_peak, alu_note, wk["fir"], "TFLOP/s"),

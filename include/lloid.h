@@ -248,9 +248,10 @@ LLOID_API lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int
  * as lloid_pull_triggers_range does (EINVAL, ENOTREADY, EEXPIRED), enqueues their
  * compaction and the copy to pinned host memory behind the pushes already
  * enqueued, and returns at once with *ticket (0..7).  At most 8 pulls are
- * submitted and not yet collected: EINVAL for a ninth.  The list is the one the
- * blocking pull would return at the time of the submit: later pushes do not
- * change it. */
+ * submitted and not yet collected: EINVAL for a ninth.  Each holds its compacted
+ * list on the device (n_windows x detectors x loaded templates entries of 40
+ * bytes) until it is collected.  The list is the one the blocking pull would
+ * return at the time of the submit: later pushes and pulls do not change it. */
 LLOID_API lloid_status lloid_pull_submit(lloid_ctx* ctx, int64_t w0, int64_t n_windows, int32_t* ticket);
 
 /* Waits up to timeout_ms (< 0: forever) for a submitted pull and copies its
@@ -258,9 +259,8 @@ LLOID_API lloid_status lloid_pull_submit(lloid_ctx* ctx, int64_t w0, int64_t n_w
  * orders them.  ETIMEOUT if the copy has not landed (the ticket stays valid) or
  * a kernel wait expired; ERANGE if cap is too small (*n_out = the number needed,
  * nothing copied, the ticket stays valid).  Otherwise the ticket is released.  A
- * list longer than the part copied at submit time is read from the device; if
- * another pull has compacted since, its windows are compacted again, which
- * needs them still retained (EEXPIRED otherwise). */
+ * list longer than the part copied at submit time is read from the device (a
+ * blocking copy of the rest); the pinned part then grows for later pulls. */
 LLOID_API lloid_status lloid_pull_collect(lloid_ctx* ctx, int32_t ticket, lloid_trigger* out, int64_t cap,
                                           int64_t* n_out, int32_t timeout_ms);
 

@@ -113,11 +113,12 @@ struct lloid_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     // Trigger lists go to the host on a stream of their own, so that the copy of one push's
-    // list overlaps the next push's kernels: the compaction records `gathered`, the copy
-    // stream waits for it, and the next compaction waits for the copy (`copied`) before it
-    // overwrites the device list.
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t gathered = nullptr, copied = nullptr;
+    // list overlaps the next push's kernels: the compaction records `gathered` and the copy
+    // stream waits for it.  Every pull slot compacts into a device list of its own, so a
+    // later compaction never waits for an earlier copy.  The part of a list beyond its
+    // pinned head is read from the slot's device list on rest_stream when it is collected.
+    cudaStream_t copy_stream = nullptr, rest_stream = nullptr;
+    cudaEvent_t gathered = nullptr;
     std::string err;
     long long launches = 0;
     size_t state_bytes = 0, bank_bytes = 0;
@@ -167,25 +168,24 @@ struct lloid_ctx {
     SlabEntry* d_slab = nullptr;       // [kWindowRing][n_det][M_cap]
     int* d_counts = nullptr;
     int counts_cap = 0;
-    TriggerOut* d_trig = nullptr;
-    long long trig_cap = 0;
-    long long* d_total = nullptr;
     // Pulls: slot 0 serves the blocking pulls, slots 1..kPullSlots the submitted ones.
-    // A slot holds, in pinned memory, the error flag, the count and the first `want`
-    // triggers of its compacted list, copied behind the pushes on the stream.
+    // A slot holds its compacted list and its count on the device until the pull is
+    // collected, and, in pinned memory, the error flag, the count and the first `want`
+    // triggers of the list, copied behind the pushes on copy_stream.
     struct PullSlot {
-        TriggerOut* h = nullptr;           // first part of the list
+        TriggerOut* d = nullptr;           // the compacted list [d_cap]
+        long long d_cap = 0;
+        long long* d_total = nullptr;
+        TriggerOut* h = nullptr;           // first part of the list [cap]
         long long cap = 0, want = 0;
         long long* h_total = nullptr;
         int* h_err = nullptr;
         cudaEvent_t ev = nullptr;
         long long w0 = 0, n_windows = 0;
-        unsigned long long seq = 0;        // gather number: d_trig still holds the list while it is the last
         bool busy = false;
     };
     static constexpr int kPullSlots = 8;
     PullSlot pull[kPullSlots + 1];
-    unsigned long long gather_seq = 0;
     long long last_pull = 0;
 
     // job tables for the current push length
@@ -435,20 +435,17 @@ lloid_status ensure_template_capacity(lloid_ctx* ctx, long long need) {
     int nchunks = (int)((nd * cap + 1023) / 1024);
     int* nc = nullptr;
     CK(cudaMalloc(&nc, nchunks * sizeof(int)));
-    TriggerOut* nt = nullptr;
-    CK(cudaMalloc(&nt, (size_t)nd * cap * sizeof(TriggerOut)));
     CK(cudaStreamSynchronize(ctx->stream));
     size_t old = ctx->M_cap ? ((size_t)ctx->M_cap * nd * ctx->n_slots * sizeof(Partial) +
                                (size_t)ctx->M_cap * nd * ctx->n_tail * sizeof(Partial) +
                                (size_t)kWindowRing * nd * ctx->M_cap * sizeof(SlabEntry) +
-                               ctx->M_cap * sizeof(int) + (size_t)nd * ctx->M_cap * sizeof(TriggerOut))
+                               ctx->M_cap * sizeof(int))
                             : 0;
-    cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_counts); cudaFree(ctx->d_trig);
+    cudaFree(ctx->d_part); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_counts);
     cudaFree(ctx->d_tail);
-    ctx->d_part = np; ctx->d_slab = ns; ctx->d_bank_of = nb; ctx->d_counts = nc; ctx->d_trig = nt; ctx->d_tail = ntl;
+    ctx->d_part = np; ctx->d_slab = ns; ctx->d_bank_of = nb; ctx->d_counts = nc; ctx->d_tail = ntl;
     ctx->counts_cap = nchunks;
-    ctx->trig_cap = (long long)nd * cap;
-    ctx->state_bytes += pbytes + tbytes + sbytes + cap * sizeof(int) + (size_t)nd * cap * sizeof(TriggerOut) - old;
+    ctx->state_bytes += pbytes + tbytes + sbytes + cap * sizeof(int) - old;
     ctx->M_cap = cap;
     ctx->h_bank_of.resize(cap, -1);
     return LLOID_OK;
@@ -1849,9 +1846,8 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         ctx->own_stream = true;
     }
     CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->rest_stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ctx->gathered, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ctx->copied, cudaEventDisableTiming));
-    CK(cudaEventRecord(ctx->copied, ctx->copy_stream));
     const int nd = c.n_detectors;
     lloid_status st;
     // full-rate ring: history for the D = 1 filters and the widest downsampler
@@ -1933,9 +1929,9 @@ lloid_status lloid_create(const lloid_config* cfg, lloid_ctx** out) {
         CK(cudaHostAlloc((void**)&ps.h_total, sizeof(long long), cudaHostAllocDefault));
         CK(cudaHostAlloc((void**)&ps.h_err, sizeof(int), cudaHostAllocDefault));
         CK(cudaEventCreateWithFlags(&ps.ev, cudaEventDisableTiming));
+        if ((st = dalloc(ctx, &ps.d_total, sizeof(long long), nullptr, &ctx->state_bytes))) return st;
     }
     if ((st = dalloc(ctx, &ctx->d_err, sizeof(int), nullptr, &ctx->state_bytes))) return st;
-    if ((st = dalloc(ctx, &ctx->d_total, sizeof(long long), nullptr, &ctx->state_bytes))) return st;
     if ((st = ensure_template_capacity(ctx, 1024))) return st;
     CK(cudaStreamSynchronize(ctx->stream));
     *out = h.release();
@@ -1958,8 +1954,9 @@ void lloid_destroy(lloid_ctx* ctx) {
     cudaFree(ctx->d_stage);
     for (int i = 0; i < 2; ++i) { cudaFreeHost(ctx->h_stage[i]); if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]); }
     cudaFree(ctx->d_part); cudaFree(ctx->d_tail); cudaFree(ctx->d_slab); cudaFree(ctx->d_bank_of); cudaFree(ctx->d_tmpl0_of);
-    cudaFree(ctx->d_counts); cudaFree(ctx->d_trig); cudaFree(ctx->d_total);
+    cudaFree(ctx->d_counts);
     for (auto& ps : ctx->pull) {
+        cudaFree(ps.d); cudaFree(ps.d_total);
         cudaFreeHost(ps.h); cudaFreeHost(ps.h_total); cudaFreeHost(ps.h_err);
         if (ps.ev) cudaEventDestroy(ps.ev);
     }
@@ -1973,8 +1970,8 @@ void lloid_destroy(lloid_ctx* ctx) {
     for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->copy_stream) { cudaStreamSynchronize(ctx->copy_stream); cudaStreamDestroy(ctx->copy_stream); }
+    if (ctx->rest_stream) cudaStreamDestroy(ctx->rest_stream);
     if (ctx->gathered) cudaEventDestroy(ctx->gathered);
-    if (ctx->copied) cudaEventDestroy(ctx->copied);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -2236,10 +2233,11 @@ lloid_status lloid_push_strain_all(lloid_ctx* ctx, int64_t t0, const float* bloc
 }
 
 // Checks that windows w0 .. w0 + n_windows - 1 can be pulled now, then enqueues their
-// compaction (k_gather_count / k_gather_scatter into d_trig) and the copy of the error
-// flag, the count and the first `want` triggers into slot ps, and records the slot's event.
-static lloid_status pull_enqueue(lloid_ctx* ctx, long long w0, long long n_windows, lloid_ctx::PullSlot* ps,
-                                 long long want_at_least) {
+// compaction (k_gather_count / k_gather_scatter) into the slot's device list and, on
+// copy_stream, the copy of the error flag, the count and the first `want` triggers into
+// the slot's pinned memory, and records the slot's event.  The slot must be free (its
+// earlier pull collected).
+static lloid_status pull_enqueue(lloid_ctx* ctx, long long w0, long long n_windows, lloid_ctx::PullSlot* ps) {
     if (w0 < 0 || n_windows < 1 || n_windows > kWindowRing) return fail(ctx, LLOID_EINVAL, "bad window range");
     const long long W = ctx->cfg.window_samples;
     const long long w1 = w0 + n_windows - 1;
@@ -2269,27 +2267,26 @@ static lloid_status pull_enqueue(lloid_ctx* ctx, long long w0, long long n_windo
     if (chunks > ctx->counts_cap) {
         CK(cudaStreamSynchronize(ctx->stream));
         cudaFree(ctx->d_counts);
+        ctx->d_counts = nullptr;
+        ctx->counts_cap = 0;
         CK(cudaMalloc(&ctx->d_counts, chunks * sizeof(int)));
         ctx->counts_cap = chunks;
     }
-    if (total > ctx->trig_cap) {
+    if (total > ps->d_cap) {   // the slot's list: every (window, detector, template) at most once
         CK(cudaStreamSynchronize(ctx->stream));
-        cudaFree(ctx->d_trig);
-        CK(cudaMalloc(&ctx->d_trig, total * sizeof(TriggerOut)));
-        ctx->trig_cap = total;
+        cudaFree(ps->d);
+        ps->d = nullptr;
+        ctx->state_bytes -= (size_t)ps->d_cap * sizeof(TriggerOut);
+        ps->d_cap = 0;
+        CK(cudaMalloc(&ps->d, total * sizeof(TriggerOut)));
+        ps->d_cap = total;
+        ctx->state_bytes += (size_t)total * sizeof(TriggerOut);
     }
-    // the first part of the list, sized from the last pull (the rest is copied when needed)
-    const long long want = std::min<long long>(total, std::max<long long>({256, 2 * ctx->last_pull + 64, want_at_least}));
-    if (want > ps->cap) {
-        CK(cudaEventSynchronize(ps->ev));   // the slot's earlier copy is done with the buffer
-        const long long cap2 = std::max<long long>(want, 2 * ps->cap);
-        cudaFreeHost(ps->h);
-        ps->h = nullptr;
-        ps->cap = 0;
-        CK(cudaHostAlloc((void**)&ps->h, cap2 * sizeof(TriggerOut), cudaHostAllocDefault));
-        ps->cap = cap2;
-    }
-    CK(cudaStreamWaitEvent(ctx->stream, ctx->copied, 0));   // the last list has left d_trig
+    CK(cudaStreamWaitEvent(ctx->stream, ps->ev, 0));   // the slot's last copy has left its list
+    // the head copied now: sized from the last pull, at most what the pinned part holds
+    // (the rest is read from the device list when the pull is collected)
+    const long long want =
+        std::min<long long>({total, ps->cap, std::max<long long>(256, ctx->last_pull + ctx->last_pull / 2 + 1024)});
     {
         StageTimer tmg(ctx, 6);
         CK(launch_pdl(k_gather_count, dim3(chunks), dim3(1024), 0, ctx->stream, (const SlabEntry*)ctx->d_slab,
@@ -2298,24 +2295,23 @@ static lloid_status pull_enqueue(lloid_ctx* ctx, long long w0, long long n_windo
         CK(launch_pdl(k_gather_scatter, dim3(chunks), dim3(1024), 0, ctx->stream, (const SlabEntry*)ctx->d_slab,
                       (long long)ctx->M_cap, M_used, nd, (long long)w0, (int)n_windows, (int)kWindowRing,
                       (const int*)ctx->d_counts, chunks, (const int*)ctx->d_bank_of, (const int*)ctx->d_tmpl0_of,
-                      W, ctx->d_trig, ctx->trig_cap, ctx->d_total));
+                      W, ps->d, ps->d_cap, ps->d_total));
         ctx->launches += 2;
     }
     ps->want = want;
-    ps->seq = ++ctx->gather_seq;
     CK(cudaEventRecord(ctx->gathered, ctx->stream));
     CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->gathered, 0));
     CK(cudaMemcpyAsync(ps->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->copy_stream));
-    CK(cudaMemcpyAsync(ps->h_total, ctx->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->copy_stream));
-    CK(cudaMemcpyAsync(ps->h, ctx->d_trig, want * sizeof(TriggerOut), cudaMemcpyDeviceToHost, ctx->copy_stream));
+    CK(cudaMemcpyAsync(ps->h_total, ps->d_total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->copy_stream));
+    if (want > 0)
+        CK(cudaMemcpyAsync(ps->h, ps->d, want * sizeof(TriggerOut), cudaMemcpyDeviceToHost, ctx->copy_stream));
     CK(cudaEventRecord(ps->ev, ctx->copy_stream));
-    CK(cudaEventRecord(ctx->copied, ctx->copy_stream));
     return LLOID_OK;
 }
 
-// Waits for slot ps, then copies its list into out[cap].  A list longer than the slot's
-// first part takes the rest from d_trig when no later compaction has replaced it, or is
-// compacted again from the trigger slab (blocking) when one has.
+// Waits for slot ps, then copies its list into out[cap]: the head from pinned memory,
+// the rest (a list longer than the head) from the slot's device list.  A list longer
+// than the pinned part grows it, for the slot's next pulls, once the list is out.
 static lloid_status pull_finish(lloid_ctx* ctx, lloid_ctx::PullSlot* ps, lloid_trigger* out, int64_t cap,
                                 int64_t* n_out, int32_t timeout_ms) {
     lloid_status st;
@@ -2331,14 +2327,17 @@ static lloid_status pull_finish(lloid_ctx* ctx, lloid_ctx::PullSlot* ps, lloid_t
     const long long head = std::min(cnt, ps->want);
     if (head > 0) std::memcpy(out, ps->h, head * sizeof(lloid_trigger));
     if (cnt > head) {
-        if (ps->seq != ctx->gather_seq) {   // d_trig holds a later list: compact these windows again
-            lloid_ctx::PullSlot& s0 = ctx->pull[0];
-            if ((st = pull_enqueue(ctx, ps->w0, ps->n_windows, &s0, cnt))) return st;
-            return pull_finish(ctx, &s0, out, cap, n_out, timeout_ms);
-        }
-        CK(cudaMemcpyAsync(out + head, ctx->d_trig + head, (cnt - head) * sizeof(lloid_trigger),
-                           cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpyAsync(out + head, ps->d + head, (cnt - head) * sizeof(lloid_trigger), cudaMemcpyDeviceToHost,
+                           ctx->rest_stream));
+        CK(cudaStreamSynchronize(ctx->rest_stream));
+    }
+    if (cnt > ps->cap) {
+        cudaFreeHost(ps->h);
+        ps->h = nullptr;
+        ps->cap = 0;
+        const long long cap2 = std::min<long long>(ps->d_cap, std::max<long long>(2 * cnt, 4096));
+        CK(cudaHostAlloc((void**)&ps->h, cap2 * sizeof(TriggerOut), cudaHostAllocDefault));
+        ps->cap = cap2;
     }
     return LLOID_OK;
 }
@@ -2355,7 +2354,7 @@ lloid_status lloid_pull_triggers_range(lloid_ctx* ctx, int64_t w0, int64_t n_win
         return check_kernel_err(ctx);
     }
     lloid_ctx::PullSlot* ps = &ctx->pull[0];
-    if ((st = pull_enqueue(ctx, w0, n_windows, ps, 0))) return st;
+    if ((st = pull_enqueue(ctx, w0, n_windows, ps))) return st;
     return pull_finish(ctx, ps, out, cap, n_out, timeout_ms);
 }
 
@@ -2367,7 +2366,7 @@ lloid_status lloid_pull_submit(lloid_ctx* ctx, int64_t w0, int64_t n_windows, in
     while (k <= lloid_ctx::kPullSlots && ctx->pull[k].busy) ++k;
     if (k > lloid_ctx::kPullSlots) return fail(ctx, LLOID_EINVAL, "%d pulls already submitted", lloid_ctx::kPullSlots);
     lloid_status st;
-    if ((st = pull_enqueue(ctx, w0, n_windows, &ctx->pull[k], 0))) return st;
+    if ((st = pull_enqueue(ctx, w0, n_windows, &ctx->pull[k]))) return st;
     ctx->pull[k].busy = true;
     *ticket = k - 1;
     return LLOID_OK;

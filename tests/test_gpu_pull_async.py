@@ -2,10 +2,9 @@
 
 A pull submitted after a push and collected after the next push returns the
 same list, entry for entry, as a blocking pull taken right after the push:
-later pushes do not change it.  Lists longer than the part copied at submit
-time (the first pull of a context copies 256 entries) are completed either
-from the device buffer or, when a later pull has compacted since, by
-compacting the windows again.  The ticket limit and bad tickets are errors.
+later pushes and pulls do not change it.  Lists longer than the part copied at
+submit time (the first pull of a slot copies none) are completed from the
+slot's device list.  The ticket limit and bad tickets are errors.
 """
 import numpy as np
 import pytest
