@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--seconds", type=int, default=1024)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--whiten-seconds", type=int, default=64,
+    p.add_argument("--whiten-seconds", type=int, default=256,
                    help="seconds of 16384 Hz strain per detector for the whitening measurement (0: skip it)")
     p.add_argument("--xi2-half", type=int, default=None,
                    help="Eq. 10 autocorrelation half-length d for the xi2 measurement (0: skip it; "

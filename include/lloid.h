@@ -301,18 +301,20 @@ LLOID_API lloid_status lloid_get_background(lloid_ctx* ctx, int32_t bank, uint32
  * and overlap-added.  Output sample j corresponds to input sample
  * j rate_in / rate_out - z_pad, so the output lags the input by n_fft / 2
  * samples.  A block whose segment holds a non-finite sample (a gap) neither
- * updates the PSD nor adds output.  The forward and inverse transforms are
- * cuFFT calls; windowing, PSD, whitening and overlap-add are this library's
- * kernels.
+ * updates the PSD nor adds output.  Every step runs in this library's kernels,
+ * the transforms included: the forward one computes only the bins below the
+ * output Nyquist (n_fft rate_out / rate_in / 2 + 1 of them), the inverse one
+ * is a real transform of length n_fft rate_out / rate_in.
  * ------------------------------------------------------------------------- */
 typedef struct lloid_whitener lloid_whitener;
 
 typedef struct {
     int32_t rate_in;           /* input rate (Hz), power of two */
-    int32_t rate_out;          /* output rate, power of two <= rate_in */
-    int32_t n_fft;             /* N: input samples per block, power of two */
+    int32_t rate_out;          /* output rate, power of two <= rate_in, rate_in / rate_out <= 4096 */
+    int32_t n_fft;             /* N: input samples per block, power of two, <= 2^24,
+                                  with N rate_out / rate_in in 4 .. 16384 */
     int32_t z_pad;             /* Z: 0 <= Z < N/2, N/2 - Z a multiple of rate_in / rate_out */
-    int32_t n_med;             /* odd, 1 .. 31 */
+    int32_t n_med;             /* odd, 1 .. 15 */
     int32_t n_avg;             /* >= 1 */
     int32_t n_detectors;       /* 1 .. 64 */
     int32_t device;

@@ -1,11 +1,12 @@
 """PSD estimation and whitening (Section II.B.2) on the GPU against the FP64
 oracle, sample by sample, on coloured noise with an impulse and a gap.
 
-Tolerance: both sides transform the same blocks; the GPU in FP32 (cuFFT of
-length N and N_out, FP32 PSD bookkeeping).  A length-N FP32 FFT is accurate to
-about eps log2(N) times the block's norm, so a whitened sample (order 1) is off
-by ~1e-5; the bound asserted, 2e-3 absolute and 1e-3 relative on the PSD,
-leaves room for the log/exp of the running mean in FP32."""
+Tolerance: both sides transform the same blocks; the GPU in FP32 (the
+library's own FFTs: the low bins of the length-N transform from its polyphase
+components, and a length-N_out inverse; FP32 PSD bookkeeping).  An FP32 FFT is
+accurate to about eps log2(N) times the block's norm, so a whitened sample
+(order 1) is off by ~1e-5; the bound asserted, 2e-3 absolute and 1e-3 relative
+on the PSD, leaves room for the log/exp of the running mean in FP32."""
 import numpy as np
 import pytest
 
@@ -69,3 +70,30 @@ def test_whitened_noise_into_lloid(P):
         y = np.concatenate([wg.whiten(0, x[i:i + 4 * hop]) for i in range(0, x.size, 4 * hop)])
     y = y[20 * FO:35 * FO]
     assert abs(y.var() - 1.0) < 0.1
+
+
+@pytest.mark.parametrize("fi,fo,n_fft,z", [
+    (1024, 1024, 4096, 1024),        # R = 1: one polyphase component, no pair
+    (2048, 1024, 8192, 2048),        # R = 2: one pair
+    (16384, 2048, 65536, 16384),     # the default: R = 8, N_out = 8192 (64 KB of shared memory)
+])
+def test_whitening_rates_match_oracle(P, fi, fo, n_fft, z):
+    """The transforms at other decimation ratios and at the default size."""
+    from scipy.signal import lfilter
+    rng = np.random.default_rng(fi + fo)
+    x = (3.0 * lfilter([1.0, 0.7], [1.0, -0.6], rng.standard_normal(40 * fi))).astype(np.float32)
+    hop = n_fft // 2 - z
+    wo = O.Whitener(fi, fo, n_fft, z)
+    with P.Whitener(fi, fo, n_fft, z, max_push=4 * hop) as wg:
+        yo, yg = [], []
+        for i in range(0, x.size - 4 * hop + 1, 4 * hop):
+            yo.append(wo.push(x[i:i + 4 * hop].astype(np.float64)))
+            yg.append(wg.whiten(0, x[i:i + 4 * hop]))
+        psd_g = wg.psd(0)
+    yo, yg = np.concatenate(yo), np.concatenate(yg)
+    assert yo.size == yg.size > 20 * fo
+    err = np.max(np.abs(yo - yg))
+    rel = np.max(np.abs(psd_g - wo.psd()) / wo.psd())
+    print(f"R = {fi // fo}: max |dy| = {err:.2e}, PSD rel {rel:.2e}")
+    assert err < 2e-3
+    assert rel < 1e-3
