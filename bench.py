@@ -294,7 +294,10 @@ def yhat_flops(slices, f0=F0, n_up=8):
 # were taken with.
 TRAFFIC_SOURCES = ("kernels_f0.cuh", "kernels_tc.cuh", "kernels_tc2.cuh", "lloid_common.cuh")
 TRAFFIC_SHA = "3039a125aadd606d"
-TRAFFIC_PROFILE = "profiles/dram_banks500_bf16split.md (k_f0_top, one pass, all f0-possible banks in the f0 form)"
+TRAFFIC_PROFILE = ("profiles/dram_banks500_bf16split.md (one pass, all f0-possible banks in the f0 form); per launch of "
+                   "the stage's main kernel: k_f0_top for recon, k_yhat for upsample, k_fir_tc for fir (the few ladder "
+                   "levels in the same stages are not included)")
+TRAFFIC_KERNEL = {"recon": "k_f0_top", "upsample": "k_yhat", "fir": "k_fir_tc"}
 TRAFFIC = {("banks500", "bf16_split", 8, 3): {"recon": 3.379e9 + 0.201e9, "upsample": 8.333e9 + 3.261e9,
                                                "fir": 1.020e9 + 2.412e9}}
 
@@ -852,6 +855,9 @@ def run_lloid(args, rank, world, dist):
         per_stage[st_name] = {"kernel": kname, "bound": bound, "launch_ms": launch_ms, "launches_per_step": lps,
                               "achieved": achieved, "unit": unit, "peak": peak, "frac": achieved / peak,
                               "peak_source": note, "algorithmic_per_launch": work * det_s / lps}
+        t_meas = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, st_name)
+        if t_meas:
+            per_stage[st_name]["traffic"] = {"bytes_per_launch": t_meas, "kernel": TRAFFIC_KERNEL[st_name]}
         if st_name == "recon" and wk["f0_executed"] > 0:   # context: what the tensor pipe actually runs
             per_stage[st_name]["f0_kernel_executed_tflop_per_step"] = wk["f0_executed"] * det_s / 1e12
     dom = max(per_stage, key=lambda k: stages[k][0])
