@@ -311,8 +311,11 @@ def kernel_sources_sha():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload, precision, block_seconds, n_det, stage):
-    if not TRAFFIC_SHA or kernel_sources_sha() != TRAFFIC_SHA:
+def measured_traffic(workload, precision, block_seconds, n_det, stage, subset=False):
+    """The recorded bytes per launch of the stage's main kernel, or None: for the whole
+    workload only (subset: a --banks sample of it) and while the kernel sources are the
+    ones the figures were taken from."""
+    if subset or not TRAFFIC_SHA or kernel_sources_sha() != TRAFFIC_SHA:
         return None
     return TRAFFIC.get((workload, precision, block_seconds, n_det), {}).get(stage)
 
@@ -855,14 +858,16 @@ def run_lloid(args, rank, world, dist):
         per_stage[st_name] = {"kernel": kname, "bound": bound, "launch_ms": launch_ms, "launches_per_step": lps,
                               "achieved": achieved, "unit": unit, "peak": peak, "frac": achieved / peak,
                               "peak_source": note, "algorithmic_per_launch": work * det_s / lps}
-        t_meas = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, st_name)
+        t_meas = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, st_name,
+                                  subset=args.banks is not None)
         if t_meas:
             per_stage[st_name]["traffic"] = {"bytes_per_launch": t_meas, "kernel": TRAFFIC_KERNEL[st_name]}
         if st_name == "recon" and wk["f0_executed"] > 0:   # context: what the tensor pipe actually runs
             per_stage[st_name]["f0_kernel_executed_tflop_per_step"] = wk["f0_executed"] * det_s / 1e12
     dom = max(per_stage, key=lambda k: stages[k][0])
     d = per_stage[dom]
-    traffic = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, dom)
+    traffic = measured_traffic(args.workload, args.precision, args.block_seconds, n_det, dom,
+                               subset=args.banks is not None)
     roofline = {"kernel": d["kernel"], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
                 "unit": d["unit"], "frac": d["frac"], "traffic": traffic, "peak_source": d["peak_source"],
                 "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, {TRAFFIC_PROFILE}"
