@@ -105,6 +105,27 @@ def test_create_rejects_pushes_of_more_than_16_windows(lib):
     assert not h.value
 
 
+@pytest.mark.parametrize("rate_in,rate_out,n_fft,z_pad", [
+    (16384, 512, 1 << 20, 1 << 18),      # N_out = 32768: one transform no longer fits shared memory
+    (1 << 14, 1, 1 << 16, 1 << 14),      # R = 16384 > 4096 polyphase components
+    (16384, 2048, 65536, 32768),         # Z = N / 2: no hop
+    (16384, 2048, 65536 + 8, 16384),     # N not a power of two
+])
+def test_whitener_create_rejects_unsupported_sizes(lib, rate_in, rate_out, n_fft, z_pad):
+    """The whitener's size checks run before any device call: its own FFTs take
+    N_out = n_fft rate_out / rate_in of 4 .. 16384, at most 4096 polyphase
+    components and n_fft <= 2^24; the rest is refused with LLOID_EINVAL."""
+    from paper_2511_04730_b300 import _lib
+    cfg = _lib.LloidWhitenerConfig()
+    lib.lloid_whitener_config_default(ctypes.byref(cfg))
+    assert (cfg.rate_in, cfg.rate_out, cfg.n_fft, cfg.z_pad, cfg.n_med) == (16384, 2048, 65536, 16384, 7)
+    cfg.rate_in, cfg.rate_out, cfg.n_fft, cfg.z_pad = rate_in, rate_out, n_fft, z_pad
+    cfg.max_push = 4 * (n_fft // 2 - z_pad) if n_fft // 2 > z_pad else n_fft
+    h = ctypes.c_void_p()
+    assert lib.lloid_whitener_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    assert not h.value
+
+
 def test_product_path_has_no_oracle_import():
     """The product package never imports the oracle (test infrastructure)."""
     pkg = os.path.join(ROOT, "paper_2511_04730_b300")
