@@ -565,9 +565,10 @@ def run_lloid(args, rank, world, dist):
         """k_steps timed steps; returns (ms per step list, pos, launches, h2d, d2h).
         lag = 1: pull the windows that became ready (xi2 needs d samples of the
         next block), i.e. the previous block's last window and this block's others.
-        pipelined: each step's pull is submitted behind its push and collected after
-        the next push (the host reads a block's triggers while the GPU filters the
-        next); the K steps are timed as one region and every pull is collected in it."""
+        pipelined: each step's pull is submitted behind its push and collected two
+        pushes later (the host reads a block's triggers while the GPU filters the next
+        two, so a host stall shorter than a step does not idle the GPU); the K steps
+        are timed as one region and every pull is collected in it."""
         ext = torch.cuda.ExternalStream(ctx.stream_ptr, device=f"cuda:{dev}")
         ms, h2d, d2h = [], 0, 0
         l0 = ctx.launch_count()
@@ -588,7 +589,7 @@ def run_lloid(args, rank, world, dist):
                         ctx.push_all(pos, d_blocks[k])
                     w_lo = max(0, pos // F0 - lag)
                     tickets.append(ctx.pull_submit(w_lo, n_windows=(pos + B) // F0 - lag - w_lo))
-                    if len(tickets) > 1:
+                    if len(tickets) > 2:
                         d2h += 8 + ctx.pull_collect(tickets.pop(0)).nbytes
                     pos += B
                 for t in tickets:
@@ -891,7 +892,7 @@ def run_lloid(args, rank, world, dist):
             "config": {"workload": WORKLOADS[args.workload], "n_templates": M, "n_banks": len(banks_sb),
                        "n_detectors": n_det, "block_seconds": args.block_seconds, "precision": args.precision,
                        "l2": "flushed between steps (256 MB write on the stream, inside the timed region)",
-                       "pulls": "each step's triggers submitted behind its push, collected after the next push",
+                       "pulls": "each step's triggers submitted behind its push, collected two pushes later",
                        "bases_total": sum(s.n_basis for x in banks_sb for s in x), "bank_forms": forms,
                        "parallelism": (f"replicas x{world}" if len(all_banks) == 1 else f"bank shards x{world}")},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks,

@@ -2331,11 +2331,11 @@ static lloid_status pull_finish(lloid_ctx* ctx, lloid_ctx::PullSlot* ps, lloid_t
                            ctx->rest_stream));
         CK(cudaStreamSynchronize(ctx->rest_stream));
     }
-    if (cnt > ps->cap) {
+    if (cnt > ps->cap) {   // to twice this list, and at least a quarter of the device list
         cudaFreeHost(ps->h);
         ps->h = nullptr;
         ps->cap = 0;
-        const long long cap2 = std::min<long long>(ps->d_cap, std::max<long long>(2 * cnt, 4096));
+        const long long cap2 = std::min<long long>(ps->d_cap, std::max<long long>({2 * cnt, 4096, ps->d_cap / 4}));
         CK(cudaHostAlloc((void**)&ps->h, cap2 * sizeof(TriggerOut), cudaHostAllocDefault));
         ps->cap = cap2;
     }
