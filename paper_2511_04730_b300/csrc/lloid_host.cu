@@ -2336,8 +2336,14 @@ static lloid_status pull_finish(lloid_ctx* ctx, lloid_ctx::PullSlot* ps, lloid_t
         ps->h = nullptr;
         ps->cap = 0;
         const long long cap2 = std::min<long long>(ps->d_cap, std::max<long long>({2 * cnt, 4096, ps->d_cap / 4}));
-        CK(cudaHostAlloc((void**)&ps->h, cap2 * sizeof(TriggerOut), cudaHostAllocDefault));
-        ps->cap = cap2;
+        // best effort: the list is already out, and without a pinned head a later pull
+        // reads all of its list from the device
+        if (cudaHostAlloc((void**)&ps->h, cap2 * sizeof(TriggerOut), cudaHostAllocDefault) == cudaSuccess) {
+            ps->cap = cap2;
+        } else {
+            ps->h = nullptr;
+            (void)cudaGetLastError();
+        }
     }
     return LLOID_OK;
 }
